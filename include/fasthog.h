@@ -1,0 +1,224 @@
+/*
+ * fasthog.h -- C ABI of the GB300 (sm_103a) fast-HOG detection library.
+ *
+ * The library implements the detection path of "A Fast HOG Descriptor Using
+ * Lookup Table and Integral Image" (Huang & Huang): a 511 x 511 gradient
+ * lookup table, a per-pixel orientation-bin map, one integral image per bin,
+ * per-cell histograms from four integral-image corners, a linear score per
+ * window position, and a threshold that compacts the windows into a list.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every pointer argument is a DEVICE pointer, allocated and owned by the
+ *    caller, unless its comment says otherwise.  No call allocates device or
+ *    host memory, and no call synchronises the stream: work is enqueued on
+ *    `stream` (NULL = the legacy default stream) and the call returns.
+ *  - Images are W columns (x, to the right) by H rows (y, downwards).
+ *  - Every call returns a hog_status.  Arguments are checked on the host
+ *    before anything is enqueued; on any error nothing is enqueued and the
+ *    outputs are left untouched.  HOG_ERR_CUDA means a launch failed; the CUDA
+ *    error code is then available from hog_last_cuda_error().
+ *  - Sizes are limited to 1 <= W, H <= 65535 (W * H < 2^31) and 1 <= N_b <= 64.
+ *  - The library is thread-safe in the sense that calls on different streams
+ *    from different host threads do not share host state, apart from the
+ *    last-error slot, which is per thread.
+ */
+#ifndef FASTHOG_H
+#define FASTHOG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A cudaStream_t, spelled without the CUDA headers. */
+typedef struct CUstream_st* hog_stream_t;
+
+typedef enum {
+    HOG_OK = 0,
+    HOG_ERR_ARG = 1,          /* null pointer, size, pitch, dtype or N_b out of range,
+                                 or a workspace that is too small */
+    HOG_ERR_UNSUPPORTED = 2,  /* a valid combination this build does not implement */
+    HOG_ERR_CUDA = 3,         /* a CUDA call failed; see hog_last_cuda_error() */
+    HOG_ERR_TIMEOUT = 4       /* a bounded device-side wait gave up (see the call) */
+} hog_status;
+
+/* Element types named by the dtype arguments. */
+typedef enum {
+    HOG_U8 = 0,
+    HOG_I32 = 1,
+    HOG_BF16 = 2,
+    HOG_F32 = 3,
+    HOG_I8 = 4,
+    HOG_U16 = 5
+} hog_dtype;
+
+/* The value a bin map holds where a pixel has no orientation bin. */
+#define HOG_NO_BIN 0xFF
+/* Side of the gradient lookup table: dx and dy both range over [-255, 255]. */
+#define HOG_LUT_SIDE 511
+/* Row pitch of the table in memory: 511 entries and one pad byte, so that
+ * every row half starts on a 16-byte boundary. */
+#define HOG_LUT_PITCH 512
+/* Bytes of one table: 511 rows of HOG_LUT_PITCH. */
+#define HOG_LUT_BYTES (HOG_LUT_SIDE * HOG_LUT_PITCH)
+
+/* One detection: window origin (x, y) in pixels, its score, and the image
+ * index and pyramid level the caller tagged the call with. */
+typedef struct {
+    int32_t x;
+    int32_t y;
+    float score;
+    int32_t image;
+    int32_t level;
+} hog_det;
+
+/* Human-readable name of a status. */
+const char* hog_status_string(hog_status s);
+/* CUDA error code (cudaError_t as int) of the last HOG_ERR_CUDA on this thread. */
+int hog_last_cuda_error(void);
+/* Library version, major * 10000 + minor * 100 + patch. */
+int hog_version(void);
+
+/* Device-side status of the current device: bit 0 (HOG_STATUS_TIMEOUT) is set
+ * when a bounded wait inside a kernel gave up (the kernel then returned
+ * without finishing its work, so its outputs are undefined).  `flags` is a
+ * host pointer.  With clear != 0 the status is reset to 0.  This call
+ * synchronises with the device (it copies one word), unlike every other call. */
+#define HOG_STATUS_TIMEOUT 1u
+hog_status hog_device_status(uint32_t* flags, int clear);
+
+/*
+ * hog_build_lut -- the 511 x 511 gradient lookup table (paper Section 2).
+ *
+ * For every (dx, dy) in [-255, 255]^2 (the paper's "-225" is read as -255,
+ * since 511 = 2 * 255 + 1) the entry at lut[(dy + 255) * 512 + (dx + 255)]
+ * is the orientation bin of the gradient with unit magnitude: the angle phi
+ * of (dx, dy), measured from +x towards +y (image y axis pointing down) in
+ * [0, 2*pi), falls in the half-open sector [k * 2*pi/N_b, (k+1) * 2*pi/N_b)
+ * and the entry is k.  (0, 0) has no angle and gets HOG_NO_BIN.
+ * The bin of every entry is decided exactly (no floating-point atan2).
+ *
+ *   n_bins  N_b, 1..64
+ *   lut     out: HOG_LUT_BYTES bytes (uint8), 16-byte aligned; row dy + 255
+ *           holds the 511 entries of that dy, then one pad byte (written 0xFF)
+ * Built once per N_b and kept resident; hog_bin_map reads it.
+ */
+hog_status hog_build_lut(int n_bins, uint8_t* lut, hog_stream_t stream);
+
+/*
+ * hog_bin_map -- oriented-gradient map (paper Section 2, Eq. 1).
+ *
+ * For every pixel with 0 < x < W-1 and 0 < y < H-1:
+ *   dx = P[x+1][y] - P[x-1][y],  dy = P[x][y+1] - P[x][y-1]
+ * per channel; with 3 channels the channel with the largest dx^2 + dy^2 is
+ * used (ties: the lowest channel index).  The pixel's bin is the table entry
+ * of its (dx, dy).  Border pixels (where Eq. 1 would read outside the image)
+ * and pixels with dx = dy = 0 get HOG_NO_BIN.
+ *
+ *   img          in: H rows of pitch_bytes; gray pixel img[y*pitch + x],
+ *                RGB pixel img[y*pitch + 3*x + c] (interleaved, c = R, G, B)
+ *   channels     1 or 3
+ *   pitch_bytes  >= W * channels
+ *   lut          in: the table from hog_build_lut for this n_bins
+ *   bins         out: H * W bytes, row-major, pitch W
+ */
+hog_status hog_bin_map(const uint8_t* img, int W, int H, int channels, size_t pitch_bytes,
+                       const uint8_t* lut, int n_bins, uint8_t* bins, hog_stream_t stream);
+
+/*
+ * hog_integral -- one integral image per bin (paper Section 3.2, Eq. 4-5).
+ *
+ *   ii[n][y][x] = #{ (x', y') : x' <= x, y' <= y, bins[y'][x'] == n }
+ *
+ * i.e. the inclusive 2-D prefix sum (Eq. 2) of the one-hot image of bin n
+ * (Eq. 4).  HOG_NO_BIN pixels count in no plane.
+ *
+ *   ii_dtype   HOG_I32 (exact), or HOG_U16: every entry modulo 2^16.  Box sums
+ *              of the U16 planes taken modulo 2^16 are exact for any box of
+ *              fewer than 65536 pixels (the paper's 16-bit integral images,
+ *              Section 4), whatever the image size.
+ *   ii         out: n_bins planes of H * W entries, [n][y][x]
+ *   workspace  scratch of at least hog_integral_workspace_bytes(W, H, n_bins)
+ *              bytes; contents on entry are ignored, on exit undefined.
+ *              Calls that overlap on the device must not share a workspace.
+ */
+size_t hog_integral_workspace_bytes(int W, int H, int n_bins);
+hog_status hog_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
+                        void* workspace, size_t workspace_bytes, hog_stream_t stream);
+
+/*
+ * hog_cell_hist -- histogram of every cell from its four integral-image
+ * corners (paper Section 3.3, Eq. 6 applying Section 3.1, Eq. 3 per bin).
+ *
+ * Cells are cell x cell pixels with origins (s*i, s*j), s = stride, for
+ * i < ncx = (W - cell)/s + 1 and j < ncy = (H - cell)/s + 1.  With
+ * x0 = s*i, y0 = s*j, x1 = x0 + cell - 1, y1 = y0 + cell - 1:
+ *   cells[j][i][n] = ii_n(x1,y1) + ii_n(x0-1,y0-1) - ii_n(x1,y0-1) - ii_n(x0-1,y1)
+ * where an index of -1 reads 0.  These are the area histograms the paper
+ * caches so that overlapping windows reuse them.
+ *
+ *   ii, ii_dtype  the planes written by hog_integral (HOG_I32 or HOG_U16)
+ *   cell          cell side in pixels, 1..64 (cell * cell < 65536)
+ *   stride        1..cell
+ *   cell_dtype    HOG_I32 or HOG_BF16 (counts <= cell^2 <= 256 are exact in
+ *                 bf16 for cell <= 16)
+ *   cells         out: [ncy][ncx][n_bins], bin innermost
+ */
+hog_status hog_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype, int cell,
+                         int stride, int cell_dtype, void* cells, hog_stream_t stream);
+
+/*
+ * hog_window_score -- linear objectness score of every window position
+ * (paper Section 1: the cached histograms feed a score at every scan
+ * position; Section 4: that score is an inner product of the window feature
+ * with a weight vector).
+ *
+ * A window is cells_x x cells_y cells; its feature is the concatenation of its
+ * cell histograms with index (cy * cells_x + cx) * n_bins + b.  With
+ * r = cell / stride, the window at pixel (px*s, py*s) uses cell-map entry
+ * (px + cx*r, py + cy*r) for its cell (cx, cy), so
+ *   scores[py][px] = bias + sum_{cy, cx, b} w[(cy*cells_x + cx)*n_bins + b]
+ *                                        * cells[py + cy*r][px + cx*r][b]
+ * for px < nx = ncx - (cells_x - 1) r and py < ny = ncy - (cells_y - 1) r.
+ *
+ *   cells, cell_dtype  from hog_cell_hist (HOG_I32 or HOG_BF16)
+ *   cell, stride       as given to hog_cell_hist; stride must divide cell
+ *   w, w_dtype         cells_x * cells_y * n_bins weights:
+ *                      HOG_F32  -> FP32 arithmetic on CUDA cores, scores f32
+ *                      HOG_BF16 -> tensor cores (tcgen05, bf16 x bf16 -> f32),
+ *                                  scores f32; needs HOG_BF16 cells and
+ *                                  n_bins a multiple of 8
+ *                      HOG_I8   -> tensor cores, exact; scores int32 (the bias
+ *                                  is rounded to the nearest integer)
+ *   scores             out: [ny][nx], f32 (F32/BF16 weights) or int32 (I8)
+ */
+hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins,
+                            int cells_x, int cells_y, int cell, int stride, const void* w,
+                            int w_dtype, float bias, void* scores, hog_stream_t stream);
+
+/*
+ * hog_detect -- threshold and ordered compaction of the score map.
+ *
+ * Every window with score >= thr is written to out[] in row-major (py, px)
+ * order as { x = px*stride, y = py*stride, score, image, level }.  The total
+ * number of such windows is written to *d_count (device int32), even when it
+ * exceeds max_out; only the first max_out entries are written.
+ *
+ *   scores, score_dtype  [ny][nx] of HOG_F32 or HOG_I32
+ *   image, level         copied into every detection (caller's tags)
+ *   workspace            at least hog_detect_workspace_bytes(nx, ny) bytes of
+ *                        scratch; contents ignored on entry
+ */
+size_t hog_detect_workspace_bytes(int nx, int ny);
+hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
+                      int image, int level, hog_det* out, int max_out, int32_t* d_count,
+                      void* workspace, size_t workspace_bytes, hog_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTHOG_H */

@@ -1,0 +1,194 @@
+"""Python binding of libfasthog, the GB300 (sm_103a) fast-HOG detection library.
+
+The functions below carry the names of the C ABI in ``include/fasthog.h`` and
+do argument marshalling only: every step runs in the library's CUDA kernels.
+Tensors are PyTorch CUDA tensors (PyTorch provides device memory and streams);
+each call enqueues work on the given stream (default: the current stream) and
+returns.  A non-OK status raises :class:`HogError`.
+
+There is no CPU path: if the library has not been built, importing this
+package raises.  Build it with ``python -m paper_1703_06256_gb300.build``.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfasthog.so")
+
+HOG_OK, HOG_ERR_ARG, HOG_ERR_UNSUPPORTED, HOG_ERR_CUDA, HOG_ERR_TIMEOUT = range(5)
+HOG_U8, HOG_I32, HOG_BF16, HOG_F32, HOG_I8, HOG_U16 = range(6)
+HOG_NO_BIN = 0xFF
+HOG_LUT_SIDE = 511
+HOG_LUT_PITCH = 512
+HOG_LUT_BYTES = HOG_LUT_SIDE * HOG_LUT_PITCH
+HOG_STATUS_TIMEOUT = 1
+
+TORCH_DTYPE = {HOG_U8: torch.uint8, HOG_I32: torch.int32, HOG_BF16: torch.bfloat16, HOG_F32: torch.float32,
+               HOG_I8: torch.int8, HOG_U16: torch.uint16 if hasattr(torch, "uint16") else torch.int16}
+
+
+class HogDet(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32), ("score", ctypes.c_float),
+                ("image", ctypes.c_int32), ("level", ctypes.c_int32)]
+
+
+DET_BYTES = ctypes.sizeof(HogDet)  # 20
+
+
+class HogError(RuntimeError):
+    def __init__(self, fn: str, status: int, cuda_error: int = 0):
+        self.status = status
+        self.cuda_error = cuda_error
+        names = ["HOG_OK", "HOG_ERR_ARG", "HOG_ERR_UNSUPPORTED", "HOG_ERR_CUDA", "HOG_ERR_TIMEOUT"]
+        name = names[status] if 0 <= status < len(names) else str(status)
+        extra = f" (cudaError {cuda_error})" if status == HOG_ERR_CUDA else ""
+        super().__init__(f"{fn} failed: {name}{extra}")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfasthog is not built ({LIB_PATH} missing); run "
+                          "`python -m paper_1703_06256_gb300.build` (needs nvcc)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, Z, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
+    sig = {
+        "hog_status_string": (ctypes.c_char_p, [I]),
+        "hog_last_cuda_error": (I, []),
+        "hog_version": (I, []),
+        "hog_device_status": (I, [P, I]),
+        "hog_build_lut": (I, [I, P, P]),
+        "hog_bin_map": (I, [P, I, I, I, Z, P, I, P, P]),
+        "hog_integral_workspace_bytes": (Z, [I, I, I]),
+        "hog_integral": (I, [P, I, I, I, I, P, P, Z, P]),
+        "hog_cell_hist": (I, [P, I, I, I, I, I, I, I, P, P]),
+        "hog_window_score": (I, [P, I, I, I, I, I, I, I, I, P, I, F, P, P]),
+        "hog_detect_workspace_bytes": (Z, [I, I]),
+        "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = _load()
+EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
+            "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
+            "hog_detect_workspace_bytes", "hog_detect")
+
+
+def lib() -> ctypes.CDLL:
+    return _lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, torch.Tensor):
+        if x.device.type != "cuda":
+            raise ValueError("libfasthog takes CUDA tensors (device memory); got a CPU tensor")
+        return x.data_ptr()
+    return int(x)
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(fn: str, status: int) -> None:
+    if status != HOG_OK:
+        raise HogError(fn, status, _lib.hog_last_cuda_error() if status == HOG_ERR_CUDA else 0)
+
+
+# ---- entry points (same names and argument order as the C ABI) -------------
+
+def hog_version() -> int:
+    return _lib.hog_version()
+
+
+def hog_device_status(clear: bool = False) -> int:
+    v = ctypes.c_uint32(0)
+    _check("hog_device_status", _lib.hog_device_status(ctypes.addressof(v), int(clear)))
+    return v.value
+
+
+def hog_build_lut(n_bins: int, lut, stream=None) -> None:
+    _check("hog_build_lut", _lib.hog_build_lut(n_bins, _ptr(lut), _stream(stream)))
+
+
+def hog_bin_map(img, W: int, H: int, channels: int, pitch_bytes: int, lut, n_bins: int, bins,
+                stream=None) -> None:
+    _check("hog_bin_map", _lib.hog_bin_map(_ptr(img), W, H, channels, pitch_bytes, _ptr(lut), n_bins,
+                                           _ptr(bins), _stream(stream)))
+
+
+def hog_integral_workspace_bytes(W: int, H: int, n_bins: int) -> int:
+    return _lib.hog_integral_workspace_bytes(W, H, n_bins)
+
+
+def hog_integral(bins, W: int, H: int, n_bins: int, ii_dtype: int, ii, workspace, workspace_bytes: int,
+                 stream=None) -> None:
+    _check("hog_integral", _lib.hog_integral(_ptr(bins), W, H, n_bins, ii_dtype, _ptr(ii), _ptr(workspace),
+                                             workspace_bytes, _stream(stream)))
+
+
+def hog_cell_hist(ii, W: int, H: int, n_bins: int, ii_dtype: int, cell: int, stride: int, cell_dtype: int,
+                  cells, stream=None) -> None:
+    _check("hog_cell_hist", _lib.hog_cell_hist(_ptr(ii), W, H, n_bins, ii_dtype, cell, stride, cell_dtype,
+                                               _ptr(cells), _stream(stream)))
+
+
+def hog_window_score(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, cells_x: int, cells_y: int,
+                     cell: int, stride: int, w, w_dtype: int, bias: float, scores, stream=None) -> None:
+    _check("hog_window_score", _lib.hog_window_score(_ptr(cells), cell_dtype, ncx, ncy, n_bins, cells_x, cells_y,
+                                                     cell, stride, _ptr(w), w_dtype, float(bias), _ptr(scores),
+                                                     _stream(stream)))
+
+
+def hog_detect_workspace_bytes(nx: int, ny: int) -> int:
+    return _lib.hog_detect_workspace_bytes(nx, ny)
+
+
+def hog_detect(scores, score_dtype: int, nx: int, ny: int, stride: int, thr: float, image: int, level: int, out,
+               max_out: int, d_count, workspace, workspace_bytes: int, stream=None) -> None:
+    _check("hog_detect", _lib.hog_detect(_ptr(scores), score_dtype, nx, ny, stride, float(thr), image, level,
+                                         _ptr(out), max_out, _ptr(d_count), _ptr(workspace), workspace_bytes,
+                                         _stream(stream)))
+
+
+# ---- shapes (host arithmetic only) --------------------------------------------
+
+def n_positions(extent: int, box: int, stride: int) -> int:
+    return 0 if extent < box else (extent - box) // stride + 1
+
+
+def grid_shapes(W: int, H: int, cell: int = 8, stride: int = 8, cells_x: int = 8, cells_y: int = 16):
+    """(ncx, ncy, nx, ny): cell-map and window-grid sizes of a W x H image."""
+    ncx, ncy = n_positions(W, cell, stride), n_positions(H, cell, stride)
+    r = cell // stride
+    nx, ny = max(0, ncx - (cells_x - 1) * r), max(0, ncy - (cells_y - 1) * r)
+    return ncx, ncy, nx, ny
+
+
+def dets_to_numpy(raw: torch.Tensor, count: int):
+    """Unpack `count` hog_det records from a uint8 tensor (host or device)."""
+    import numpy as np
+
+    dt = np.dtype([("x", "<i4"), ("y", "<i4"), ("score", "<f4"), ("image", "<i4"), ("level", "<i4")])
+    a = raw[: count * DET_BYTES].cpu().numpy().view(dt)
+    return a
+
+
+from .pipeline import HogPipeline  # noqa: E402  (after the entry points it calls)
+
+__all__ = [n for n in EXPORTED] + ["HogPipeline", "HogError", "grid_shapes", "n_positions", "dets_to_numpy"]

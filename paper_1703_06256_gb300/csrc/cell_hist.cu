@@ -1,0 +1,75 @@
+// cell_hist.cu -- area histograms from four integral-image corners
+// (paper Section 3.3, Eq. 6; Section 3.1, Eq. 3 applied per bin).
+//
+// One thread per cell.  For each bin the thread reads the four corners
+//   ii(x1, y1), ii(x0-1, y0-1), ii(x1, y0-1), ii(x0-1, y1)
+// (an index of -1 reads 0) and writes the cell's histogram contiguously,
+// bin innermost, as int32 or bf16 (counts <= cell^2 are small integers).
+// Consecutive threads take consecutive cells of a row, so the corner loads
+// of a warp fall in a few 128-byte lines of the same two ii rows; corners
+// shared by neighbouring cells are served by L1.
+//
+// With uint16 integral images the four-term sum is taken modulo 2^16, which
+// is exact because a cell holds fewer than 65536 pixels.
+#include "internal.cuh"
+
+namespace fasthog {
+
+namespace {
+
+template <typename InT, typename OutT>
+__global__ void __launch_bounds__(128)
+    cell_hist_kernel(const InT* __restrict__ ii, int W, int H, int nb, int cell, int stride, int ncx, int ncy,
+                     OutT* __restrict__ cells) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i >= ncx || j >= ncy) return;
+    const int x0 = i * stride, y0 = j * stride;
+    const int x1 = x0 + cell - 1, y1 = y0 + cell - 1;
+    const bool hx = x0 > 0, hy = y0 > 0;
+    const size_t plane = (size_t)W * H;
+    const size_t o11 = (size_t)y1 * W + x1;
+    const size_t o01 = (size_t)y1 * W + (x0 - 1);
+    const size_t o10 = (size_t)(y0 - 1) * W + x1;
+    const size_t o00 = (size_t)(y0 - 1) * W + (x0 - 1);
+    OutT* out = cells + ((size_t)j * ncx + i) * nb;
+    for (int b = 0; b < nb; ++b) {
+        const InT* p = ii + (size_t)b * plane;
+        uint32_t v = (uint32_t)__ldg(p + o11);
+        if (hx) v -= (uint32_t)__ldg(p + o01);
+        if (hy) v -= (uint32_t)__ldg(p + o10);
+        if (hx && hy) v += (uint32_t)__ldg(p + o00);
+        if (sizeof(InT) == 2) v &= 0xFFFFu;
+        if (sizeof(OutT) == 4) {
+            out[b] = (OutT)v;
+        } else {
+            out[b] = f32_to_bf16_exact_int((float)v);
+        }
+    }
+}
+
+template <typename InT, typename OutT>
+hog_status launch_t(const void* ii, int W, int H, int nb, int cell, int stride, int ncx, int ncy, void* cells,
+                    cudaStream_t st) {
+    dim3 grid(ceil_div(ncx, 128), ncy);
+    cell_hist_kernel<InT, OutT><<<grid, 128, 0, st>>>(static_cast<const InT*>(ii), W, H, nb, cell, stride, ncx,
+                                                      ncy, static_cast<OutT*>(cells));
+    return check_launch();
+}
+
+}  // namespace
+
+hog_status launch_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype, int cell, int stride,
+                            int cell_dtype, void* cells, cudaStream_t st) {
+    const int ncx = W < cell ? 0 : (W - cell) / stride + 1;
+    const int ncy = H < cell ? 0 : (H - cell) / stride + 1;
+    if (ncx == 0 || ncy == 0) return HOG_OK;
+    if (ii_dtype == HOG_U16)
+        return cell_dtype == HOG_BF16
+                   ? launch_t<uint16_t, uint16_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st)
+                   : launch_t<uint16_t, int32_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+    return cell_dtype == HOG_BF16 ? launch_t<int32_t, uint16_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st)
+                                  : launch_t<int32_t, int32_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+}
+
+}  // namespace fasthog

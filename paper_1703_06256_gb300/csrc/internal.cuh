@@ -1,0 +1,73 @@
+// internal.cuh -- declarations shared by the translation units of libfasthog.
+// Not installed; the public interface is include/fasthog.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/fasthog.h"
+
+namespace fasthog {
+
+constexpr int kLutSide = HOG_LUT_SIDE;   // 511
+constexpr int kLutPitch = HOG_LUT_PITCH; // 512
+constexpr int kDMax = 255;
+constexpr int kMaxBins = 64;
+constexpr uint8_t kNoBin = HOG_NO_BIN;
+constexpr int kNumSMs = 152;             // GB300: 2 dies x 76 SMs (queried at run time too)
+
+// Record a CUDA failure for hog_last_cuda_error() and map it to a status.
+hog_status cuda_fail(cudaError_t e);
+// Check the launch that was just enqueued.
+hog_status check_launch();
+// Number of SMs of the current device (cached per device).
+int sm_count();
+
+// ---- launchers (one per kernel family), called by api.cu after argument checks
+struct LutParams {
+    int n_bins;
+    // Boundary directions theta_k = 2*pi*k/N_b, k = 1..N_b-1, as fixed-point
+    // cos/sin scaled by 2^40 (see lut.cu).
+    long long c[kMaxBins];
+    long long s[kMaxBins];
+};
+hog_status launch_build_lut(const LutParams& p, uint8_t* lut, cudaStream_t st);
+
+hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t pitch,
+                          const uint8_t* lut, int n_bins, uint8_t* bins, unsigned int* status,
+                          cudaStream_t st);
+
+size_t integral_workspace_bytes(int W, int H, int n_bins);
+hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
+                           void* ws, cudaStream_t st);
+
+hog_status launch_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype, int cell,
+                            int stride, int cell_dtype, void* cells, cudaStream_t st);
+
+hog_status launch_score_cuda_cores(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins,
+                                   int cells_x, int cells_y, int r, const void* w, int w_dtype,
+                                   float bias, void* scores, cudaStream_t st);
+bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx);
+hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x,
+                           int cells_y, int r, const void* w, int w_dtype, float bias,
+                           void* scores, cudaStream_t st);
+
+size_t detect_workspace_bytes(int nx, int ny);
+hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
+                         int image, int level, hog_det* out, int max_out, int32_t* d_count, void* ws,
+                         cudaStream_t st);
+
+// ---- small device helpers
+__device__ __forceinline__ uint16_t f32_to_bf16_exact_int(float v) {
+    // Only called on small integers (|v| < 2^8) and on values already
+    // representable in bf16, where dropping the low 16 bits is exact.
+    return static_cast<uint16_t>(__float_as_uint(v) >> 16);
+}
+__device__ __forceinline__ float bf16_to_f32(uint16_t h) {
+    return __uint_as_float(static_cast<uint32_t>(h) << 16);
+}
+
+inline int ceil_div(long a, long b) { return static_cast<int>((a + b - 1) / b); }
+
+}  // namespace fasthog

@@ -1,0 +1,135 @@
+"""HogPipeline: device buffers for one image size plus the five per-image
+calls of the C ABI, in the paper's order (bin map -> integral images -> cell
+histograms -> window scores -> detections).
+
+Buffers are allocated once with PyTorch (the C ABI never allocates); the
+gradient table is built once per N_b at construction (the paper builds it a
+single time and only reads it afterwards).  ``run`` enqueues the five calls
+on a stream; ``detect_host`` is the end-to-end path a caller with a host
+image uses: copy in, run, copy the detections out.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import (DET_BYTES, HOG_BF16, HOG_F32, HOG_I8, HOG_I32, HOG_LUT_BYTES, HOG_U16, TORCH_DTYPE,
+               dets_to_numpy, grid_shapes, hog_bin_map, hog_build_lut, hog_cell_hist, hog_detect,
+               hog_detect_workspace_bytes, hog_integral, hog_integral_workspace_bytes, hog_window_score)
+
+_W_DTYPE = {HOG_F32: torch.float32, HOG_BF16: torch.bfloat16, HOG_I8: torch.int8}
+
+
+class HogPipeline:
+    def __init__(self, W: int, H: int, channels: int = 3, n_bins: int = 8, stride: int = 8, cell: int = 8,
+                 cells_x: int = 8, cells_y: int = 16, ii_dtype: int = HOG_I32, cell_dtype: int = HOG_I32,
+                 w_dtype: int = HOG_F32, max_out: int | None = None, device: str | torch.device = "cuda"):
+        self.W, self.H, self.channels, self.n_bins = W, H, channels, n_bins
+        self.stride, self.cell, self.cells_x, self.cells_y = stride, cell, cells_x, cells_y
+        self.ii_dtype, self.cell_dtype, self.w_dtype = ii_dtype, cell_dtype, w_dtype
+        self.device = torch.device(device)
+        self.ncx, self.ncy, self.nx, self.ny = grid_shapes(W, H, cell, stride, cells_x, cells_y)
+        self.max_out = max(self.nx * self.ny, 1) if max_out is None else max_out
+        dev = self.device
+        self.lut = torch.empty(HOG_LUT_BYTES, dtype=torch.uint8, device=dev)
+        self.img = torch.empty(H * W * channels, dtype=torch.uint8, device=dev)
+        self.bins = torch.empty(H * W, dtype=torch.uint8, device=dev)
+        self.ii = torch.empty(n_bins * H * W, dtype=TORCH_DTYPE[ii_dtype], device=dev)
+        self.ws_ii_bytes = hog_integral_workspace_bytes(W, H, n_bins)
+        self.ws_ii = torch.empty(max(self.ws_ii_bytes, 256), dtype=torch.uint8, device=dev)
+        self.cells = torch.empty(max(self.ncx * self.ncy * n_bins, 1), dtype=TORCH_DTYPE[cell_dtype], device=dev)
+        self.score_dtype = HOG_I32 if w_dtype == HOG_I8 else HOG_F32
+        self.scores = torch.empty(max(self.nx * self.ny, 1), dtype=TORCH_DTYPE[self.score_dtype], device=dev)
+        self.det = torch.empty(self.max_out * DET_BYTES, dtype=torch.uint8, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.ws_det_bytes = hog_detect_workspace_bytes(self.nx, self.ny)
+        self.ws_det = torch.empty(max(self.ws_det_bytes, 256), dtype=torch.uint8, device=dev)
+        self.w = torch.zeros(cells_x * cells_y * n_bins, dtype=_W_DTYPE[w_dtype], device=dev)
+        self.bias = 0.0
+        self.thr = 0.0
+        with torch.cuda.device(dev):
+            hog_build_lut(n_bins, self.lut)
+        # pinned host staging for the end-to-end path
+        self.img_host = torch.empty(H * W * channels, dtype=torch.uint8, pin_memory=True)
+        self.count_host = torch.zeros(1, dtype=torch.int32, pin_memory=True)
+        self.det_host = torch.empty(self.max_out * DET_BYTES, dtype=torch.uint8, pin_memory=True)
+
+    def set_weights(self, w, bias: float = 0.0, thr: float = 0.0) -> None:
+        t = torch.as_tensor(np.asarray(w)).reshape(-1)
+        if t.numel() != self.w.numel():
+            raise ValueError(f"expected {self.w.numel()} weights, got {t.numel()}")
+        self.w.copy_(t.to(self.w.dtype))
+        self.bias, self.thr = float(bias), float(thr)
+
+    def set_image(self, img: np.ndarray) -> None:
+        a = np.ascontiguousarray(img, dtype=np.uint8).reshape(-1)
+        self.img.copy_(torch.from_numpy(a))
+
+    # -- the five per-image calls
+    def stage_bin_map(self, stream=None):
+        hog_bin_map(self.img, self.W, self.H, self.channels, self.W * self.channels, self.lut, self.n_bins,
+                    self.bins, stream)
+
+    def stage_integral(self, stream=None):
+        hog_integral(self.bins, self.W, self.H, self.n_bins, self.ii_dtype, self.ii, self.ws_ii, self.ws_ii_bytes,
+                     stream)
+
+    def stage_cell_hist(self, stream=None):
+        hog_cell_hist(self.ii, self.W, self.H, self.n_bins, self.ii_dtype, self.cell, self.stride, self.cell_dtype,
+                      self.cells, stream)
+
+    def stage_score(self, stream=None):
+        hog_window_score(self.cells, self.cell_dtype, self.ncx, self.ncy, self.n_bins, self.cells_x, self.cells_y,
+                         self.cell, self.stride, self.w, self.w_dtype, self.bias, self.scores, stream)
+
+    def stage_detect(self, stream=None):
+        hog_detect(self.scores, self.score_dtype, self.nx, self.ny, self.stride, self.thr, 0, 0, self.det,
+                   self.max_out, self.count, self.ws_det, self.ws_det_bytes, stream)
+
+    def run(self, stream=None) -> None:
+        """Enqueue the whole path for the image already in ``self.img``."""
+        self.stage_bin_map(stream)
+        self.stage_integral(stream)
+        self.stage_cell_hist(stream)
+        self.stage_score(stream)
+        self.stage_detect(stream)
+
+    def detect_host(self, img_host: torch.Tensor | None = None, stream=None):
+        """End to end from pinned host memory: H2D copy, the path, D2H of the
+        count and of the detections.  Returns the detections as a numpy
+        record array.  Synchronises the stream."""
+        s = torch.cuda.current_stream(self.device) if stream is None else stream
+        src = self.img_host if img_host is None else img_host
+        with torch.cuda.stream(s):
+            self.img.copy_(src, non_blocking=True)
+            self.run(s)
+            self.count_host.copy_(self.count, non_blocking=True)
+        s.synchronize()
+        n = min(int(self.count_host[0]), self.max_out)
+        if n:
+            with torch.cuda.stream(s):
+                self.det_host[: n * DET_BYTES].copy_(self.det[: n * DET_BYTES], non_blocking=True)
+            s.synchronize()
+        return dets_to_numpy(self.det_host, n), int(self.count_host[0])
+
+    def h2d_bytes(self) -> int:
+        return self.img.numel()
+
+    def results(self) -> dict:
+        """Copy every intermediate to host numpy arrays (for tests)."""
+        torch.cuda.synchronize(self.device)
+        ii = self.ii.view(torch.int16) if self.ii_dtype == HOG_U16 else self.ii
+        ii_np = ii.cpu().numpy()
+        if self.ii_dtype == HOG_U16:
+            ii_np = ii_np.view(np.uint16)
+        cells = self.cells.float() if self.cell_dtype == HOG_BF16 else self.cells
+        n = int(self.count.item())
+        return {
+            "bins": self.bins.cpu().numpy().reshape(self.H, self.W),
+            "ii": ii_np.reshape(self.n_bins, self.H, self.W),
+            "cells": cells.cpu().numpy().reshape(self.ncy, self.ncx, self.n_bins).astype(np.int64),
+            "scores": self.scores[: self.nx * self.ny].cpu().numpy().reshape(self.ny, self.nx),
+            "count": n,
+            "detections": dets_to_numpy(self.det.cpu(), min(n, self.max_out)),
+        }

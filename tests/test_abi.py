@@ -1,0 +1,80 @@
+"""The C-ABI library loads and exports every entry point include/fasthog.h
+declares; host-side argument checks reject bad calls before touching CUDA.
+No compute call is made here (this runs without a GPU)."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fasthog.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\*?\s+\*?(hog_[a-z_0-9]+)\s*\(", src, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def fh():
+    from paper_1703_06256_gb300 import build as b
+
+    b.build()
+    import paper_1703_06256_gb300 as m
+
+    return m
+
+
+def test_header_declares_the_six_stage_calls():
+    names = declared_functions()
+    for n in ["hog_build_lut", "hog_bin_map", "hog_integral", "hog_cell_hist", "hog_window_score", "hog_detect"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(fh):
+    lib = ctypes.CDLL(fh.LIB_PATH)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(fh.EXPORTED) == set(declared_functions())
+
+
+def test_version_and_strings(fh):
+    assert fh.hog_version() >= 100
+    assert fh.lib().hog_status_string(fh.HOG_ERR_ARG) == b"HOG_ERR_ARG"
+
+
+def test_workspace_sizes(fh):
+    assert fh.hog_integral_workspace_bytes(800, 600, 8) > 0
+    assert fh.hog_integral_workspace_bytes(0, 600, 8) == 0
+    assert fh.hog_integral_workspace_bytes(800, 600, 0) == 0
+    assert fh.hog_detect_workspace_bytes(185, 119) >= 4 * 11
+    assert fh.hog_detect_workspace_bytes(-1, 5) == 0
+
+
+def test_argument_errors_need_no_gpu(fh):
+    L = fh.lib()
+    ARG = fh.HOG_ERR_ARG
+    assert L.hog_build_lut(8, None, None) == ARG
+    assert L.hog_build_lut(0, 4096, None) == ARG
+    assert L.hog_build_lut(65, 4096, None) == ARG
+    assert L.hog_build_lut(8, 4097, None) == ARG  # table must be 16-byte aligned
+    assert L.hog_bin_map(None, 8, 8, 1, 8, 4096, 8, 4096, None) == ARG
+    assert L.hog_bin_map(4096, 8, 8, 2, 16, 4096, 8, 4096, None) == ARG      # channels
+    assert L.hog_bin_map(4096, 8, 8, 3, 23, 4096, 8, 4096, None) == ARG      # pitch < 3W
+    assert L.hog_bin_map(4096, 0, 8, 1, 8, 4096, 8, 4096, None) == ARG       # W
+    assert L.hog_integral(4096, 8, 8, 8, fh.HOG_F32, 4096, 4096, 1 << 20, None) == ARG  # dtype
+    assert L.hog_integral(4096, 8, 8, 8, fh.HOG_I32, 4096, 4096, 0, None) == ARG        # workspace
+    assert L.hog_integral(4096, 8, 8, 8, fh.HOG_I32, 4096, 4097, 1 << 20, None) == ARG  # alignment
+    assert L.hog_cell_hist(4096, 64, 64, 8, fh.HOG_I32, 8, 9, fh.HOG_I32, 4096, None) == ARG  # stride > cell
+    assert L.hog_cell_hist(4096, 64, 64, 8, fh.HOG_I32, 32, 8, fh.HOG_BF16, 4096, None) == ARG  # bf16, cell 32
+    assert L.hog_window_score(4096, fh.HOG_I32, 10, 10, 8, 8, 16, 8, 3, 4096, fh.HOG_F32, 0.0, 4096, None) == ARG
+    assert L.hog_window_score(4096, fh.HOG_I32, 10, 10, 8, 8, 16, 8, 4, 4096, fh.HOG_U8, 0.0, 4096, None) == ARG
+    assert L.hog_window_score(4096, fh.HOG_I32, 10, 10, 8, 8, 16, 8, 4, 4096, fh.HOG_F32, float("nan"), 4096,
+                              None) == ARG
+    assert L.hog_detect(4096, fh.HOG_F32, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 0, None) == ARG
+    assert L.hog_detect(4096, fh.HOG_BF16, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 256, None) == ARG
+    assert L.hog_detect(None, fh.HOG_F32, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 256, None) == ARG
+    assert L.hog_device_status(None, 0) == ARG

@@ -1,0 +1,275 @@
+"""GPU parity: every stage of the CUDA path against the oracle, called through
+the C ABI, on seeded inputs that span several tiles and ragged tails.
+
+Bar: bit-exact for the table, bin map, integral images, cell histograms,
+integer scores and detection lists; FP32 scores within
+1e-5 * (sum_k |w_k| h_k + |bias|) of the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import workloads as wl  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def fh():
+    import paper_1703_06256_gb300 as m
+
+    assert torch.cuda.is_available()
+    m.hog_device_status(clear=True)
+    yield m
+    assert m.hog_device_status() == 0, "a kernel reported a timed-out wait"
+
+
+@pytest.fixture(scope="module")
+def g(fh):
+    import _gpu
+
+    return _gpu
+
+
+def rand_img(H, W, ch, seed):
+    rng = np.random.default_rng(seed)
+    shape = (H, W) if ch == 1 else (H, W, 3)
+    return rng.integers(0, 256, size=shape, dtype=np.uint8)
+
+
+# ---------------------------------------------------------------- table
+@pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 17, 31, 32, 64])
+def test_lut_exhaustive(fh, g, nb):
+    lut = g.gpu_lut(nb).cpu().numpy().reshape(511, 512)
+    assert np.all(lut[:, 511] == 255)  # pad column
+    assert np.array_equal(lut[:, :511].reshape(-1), oracle.lut(nb))
+
+
+# ---------------------------------------------------------------- bin map
+SHAPES = [(1, 1), (2, 2), (3, 3), (1, 100), (100, 1), (17, 129), (35, 131), (7, 1000), (240, 320), (33, 257)]
+
+
+@pytest.mark.parametrize("nb", [8, 9, 16, 6])
+@pytest.mark.parametrize("ch", [1, 3])
+def test_bin_map_random(fh, g, nb, ch):
+    for i, (H, W) in enumerate(SHAPES):
+        img = rand_img(H, W, ch, 100 * nb + 10 * ch + i)
+        assert np.array_equal(g.gpu_bins(img, nb), oracle.bin_map(img, nb)), (H, W)
+
+
+@pytest.mark.parametrize("ch", [1, 3])
+def test_bin_map_pitch_and_alignment(fh, g, ch):
+    img = rand_img(45, 203, ch, 5)
+    ref = oracle.bin_map(img, 8)
+    for pad, off in [(0, 1), (1, 0), (5, 3), (16, 0), (13, 2)]:
+        assert np.array_equal(g.gpu_bins(img, 8, pitch_pad=pad, offset=off), ref), (pad, off)
+
+
+def test_bin_map_closed_form_ramps(fh, g):
+    yy, xx = np.mgrid[0:50, 0:85]
+    for img, b in [(3 * xx, 0), (5 * yy, 2), (250 - 5 * yy, 6), (250 - 2 * xx, 4), (2 * xx + 2 * yy, 1)]:
+        bins = g.gpu_bins(img.astype(np.uint8), 8)
+        assert np.all(bins[1:-1, 1:-1] == b)
+        assert np.all(bins[0] == 255) and np.all(bins[:, -1] == 255)
+
+
+def test_bin_map_workloads(fh, g):
+    for cfg in (wl.config0(), wl.config1()):
+        img = cfg["images"][0]
+        assert np.array_equal(g.gpu_bins(img, cfg["n_bins"]), oracle.bin_map(img, cfg["n_bins"]))
+
+
+# ---------------------------------------------------------------- integral images
+II_SHAPES = [(1, 1), (5, 5), (2, 3), (8, 513), (33, 1025), (37, 2000), (600, 800), (240, 320), (19, 511),
+             (3, 4097), (301, 6)]
+
+
+def oracle_bins(H, W, nb, seed, p_none=0.3):
+    rng = np.random.default_rng(seed)
+    b = rng.integers(0, nb, size=(H, W)).astype(np.uint8)
+    b[rng.random((H, W)) < p_none] = 255
+    return b
+
+
+@pytest.mark.parametrize("nb", [8, 3, 16, 20])
+def test_integral_int32(fh, g, nb):
+    for i, (H, W) in enumerate(II_SHAPES):
+        bins = oracle_bins(H, W, nb, 7 * nb + i)
+        assert np.array_equal(g.gpu_integral(bins, nb), oracle.integral(bins, nb)), (H, W)
+
+
+@pytest.mark.parametrize("nb", [8, 16])
+def test_integral_uint16_modular(fh, g, nb):
+    for i, (H, W) in enumerate([(600, 800), (37, 2000), (300, 700)]):
+        bins = oracle_bins(H, W, nb, 31 * nb + i, p_none=0.05)
+        ref = oracle.integral(bins, nb)
+        assert ref.max() > 65535 or (H, W) != (600, 800)
+        assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16), (ref & 0xFFFF).astype(np.uint16)), (H, W)
+
+
+def test_integral_workload_bins(fh, g):
+    img = wl.config1()["images"][0]
+    bins = oracle.bin_map(img, 8)
+    assert np.array_equal(g.gpu_integral(bins, 8), oracle.integral(bins, 8))
+
+
+# ---------------------------------------------------------------- cell histograms
+@pytest.mark.parametrize("stride", [1, 2, 4, 8])
+@pytest.mark.parametrize("cell_dtype", ["i32", "bf16"])
+def test_cell_hist(fh, g, stride, cell_dtype):
+    cd = fh.HOG_I32 if cell_dtype == "i32" else fh.HOG_BF16
+    for i, (H, W) in enumerate([(8, 8), (40, 77), (130, 259), (7, 30)]):
+        bins = oracle_bins(H, W, 8, 3 * stride + i)
+        ii = oracle.integral(bins, 8)
+        ref = oracle.cell_hist_ii(ii, 8, 8, stride)
+        assert np.array_equal(g.gpu_cells(ii, 8, 8, stride, cell_dtype=cd), ref), (H, W)
+
+
+def test_cell_hist_from_uint16(fh, g):
+    bins = oracle_bins(600, 800, 8, 99, p_none=0.02)
+    ii = oracle.integral(bins, 8)
+    ref = oracle.cell_hist_ii(ii, 8, 8, 4)
+    got = g.gpu_cells((ii & 0xFFFF).astype(np.uint16), 8, 8, 4, ii_dtype=fh.HOG_U16)
+    assert np.array_equal(got, ref)
+
+
+def test_cell_hist_other_cells(fh, g):
+    bins = oracle_bins(70, 90, 9, 4)
+    ii = oracle.integral(bins, 9)
+    for cell, stride in [(16, 4), (6, 3), (5, 5), (1, 1)]:
+        assert np.array_equal(g.gpu_cells(ii, 9, cell, stride), oracle.cell_hist_ii(ii, 9, cell, stride))
+
+
+# ---------------------------------------------------------------- window scores
+def cells_of(img, nb, stride):
+    return oracle.cell_hist_direct(oracle.bin_map(img, nb), nb, 8, stride)
+
+
+@pytest.mark.parametrize("stride", [8, 4, 2])
+def test_score_f32(fh, g, stride):
+    rng = np.random.default_rng(stride)
+    img = rand_img(300, 260, 3, stride)
+    cells = cells_of(img, 8, stride)
+    w = rng.normal(0, 0.01, 1024).astype(np.float32)
+    for bias in (0.0, 0.37):
+        ref = oracle.window_score(cells, w, bias, stride=stride)
+        got = g.gpu_scores(cells, w, fh.HOG_F32, bias, stride=stride)
+        tol = g.score_tolerance(cells, w, bias, stride=stride)
+        assert got.shape == ref.shape
+        assert np.all(np.abs(got - ref) <= tol)
+
+
+def test_score_i8_exact(fh, g):
+    rng = np.random.default_rng(8)
+    img = rand_img(280, 200, 3, 8)
+    cells = cells_of(img, 8, 4)
+    w = rng.integers(-127, 128, 1024).astype(np.int8)
+    ref = oracle.window_score(cells, w, 3.0, stride=4)
+    got = g.gpu_scores(cells, w, fh.HOG_I8, 3.0, stride=4)
+    assert got.dtype == np.int32 and np.array_equal(got, ref.astype(np.int64))
+
+
+def test_score_bf16_weights_and_cells(fh, g):
+    rng = np.random.default_rng(9)
+    img = rand_img(290, 230, 3, 9)
+    cells = cells_of(img, 8, 4)
+    w = rng.normal(0, 0.01, 1024).astype(np.float32)
+    w_bf = torch.from_numpy(w).to(torch.bfloat16).float().numpy()  # the weights the kernel sees
+    ref = oracle.window_score(cells, w_bf, 0.0, stride=4)
+    for cd in (fh.HOG_I32, fh.HOG_BF16):
+        got = g.gpu_scores(cells, w, fh.HOG_BF16, 0.0, stride=4, cell_dtype=cd)
+        assert np.all(np.abs(got - ref) <= g.score_tolerance(cells, w_bf, 0.0, stride=4))
+
+
+def test_score_shapes(fh, g):
+    rng = np.random.default_rng(10)
+    for (H, W, nb, cx, cy, stride) in [(128, 64, 8, 8, 16, 8), (127, 64, 8, 8, 16, 8), (140, 80, 9, 8, 16, 4),
+                                       (96, 96, 4, 4, 4, 2), (64, 64, 16, 3, 5, 1)]:
+        img = rand_img(H, W, 1, H + W)
+        cells = oracle.cell_hist_direct(oracle.bin_map(img, nb), nb, 8, stride)
+        w = rng.normal(0, 0.1, cx * cy * nb).astype(np.float32)
+        ref = oracle.window_score(cells, w, 0.0, cx, cy, 8, stride)
+        got = g.gpu_scores(cells, w, fh.HOG_F32, 0.0, stride=stride, cells_x=cx, cells_y=cy)
+        assert got.shape == ref.shape
+        if ref.size:
+            assert np.all(np.abs(got - ref) <= g.score_tolerance(cells, w, 0.0, 8, stride, cx, cy))
+
+
+# ---------------------------------------------------------------- detection list
+def test_detect_int_exact(fh, g):
+    rng = np.random.default_rng(11)
+    for ny, nx in [(1, 1), (7, 9), (119, 185), (300, 401), (0, 5)]:
+        S = rng.integers(-50, 50, size=(ny, nx)).astype(np.int32)
+        xs, ys, sc = oracle.detect(S.astype(np.float64), 4, 10.0)
+        det, n = g.gpu_detect(S, 4, 10.0, image=3, level=2)
+        assert n == len(xs)
+        assert np.array_equal(det["x"], xs) and np.array_equal(det["y"], ys)
+        assert np.array_equal(det["score"], sc.astype(np.float32))
+        assert np.all(det["image"] == 3) and np.all(det["level"] == 2)
+
+
+def test_detect_float_and_overflow(fh, g):
+    rng = np.random.default_rng(12)
+    S = rng.normal(0, 1, size=(211, 333)).astype(np.float32)
+    S[5, 7] = 0.5  # exactly on the threshold: kept
+    xs, ys, sc = oracle.detect(S.astype(np.float64), 4, 0.5)
+    det, n = g.gpu_detect(S, 4, 0.5)
+    assert n == len(xs) and np.array_equal(det["x"], xs) and np.array_equal(det["y"], ys)
+    det, n2 = g.gpu_detect(S, 4, 0.5, max_out=100)
+    assert n2 == len(xs) and len(det) == 100 and np.array_equal(det["x"], xs[:100])
+
+
+# ---------------------------------------------------------------- whole path
+def compare_pipeline(fh, g, img, nb, stride, w, bias, thr, ii_dtype, cell_dtype):
+    H, W = img.shape[:2]
+    ch = 1 if img.ndim == 2 else 3
+    pipe = fh.HogPipeline(W, H, ch, nb, stride, ii_dtype=ii_dtype, cell_dtype=cell_dtype)
+    pipe.set_weights(w, bias, thr if thr is not None else -1e30)
+    pipe.set_image(img)
+    pipe.run()
+    got = pipe.results()
+    ref = oracle.pipeline(img, nb, w, bias, stride, thr if thr is not None else -1e30)
+    assert np.array_equal(got["bins"], ref["bins"])
+    if ii_dtype == fh.HOG_I32:
+        assert np.array_equal(got["ii"], ref["ii"])
+    else:
+        assert np.array_equal(got["ii"], (ref["ii"] & 0xFFFF).astype(np.uint16))
+    assert np.array_equal(got["cells"], ref["cells"])
+    tol = g.score_tolerance(ref["cells"], w, bias, stride=stride)
+    assert np.all(np.abs(got["scores"] - ref["scores"]) <= tol)
+    xs, ys, sc = ref["detections"]
+    # windows whose FP64 score is within the tolerance of the threshold may go
+    # either way; there should be none, and every other window must agree
+    S64 = ref["scores"]
+    t = thr if thr is not None else -1e30
+    near = np.abs(S64 - t) <= tol
+    assert not near.any()
+    assert got["count"] == len(xs)
+    assert np.array_equal(got["detections"]["x"], xs) and np.array_equal(got["detections"]["y"], ys)
+    return got
+
+
+def test_pipeline_config0(fh, g):
+    c = wl.config0()
+    compare_pipeline(fh, g, c["images"][0], 8, 8, c["w"], 0.0, 0.0, fh.HOG_I32, fh.HOG_I32)
+
+
+@pytest.mark.parametrize("ii_dtype", ["i32", "u16"])
+def test_pipeline_config1(fh, g, ii_dtype):
+    c = wl.config1()
+    it = fh.HOG_I32 if ii_dtype == "i32" else fh.HOG_U16
+    got = compare_pipeline(fh, g, c["images"][0], 8, 4, c["w"], 0.0, c["thr"], it, fh.HOG_I32)
+    assert got["count"] > 0
+
+
+def test_pipeline_end_to_end_host(fh, g):
+    c = wl.config1()
+    img = c["images"][0]
+    pipe = fh.HogPipeline(800, 600, 3, 8, 4)
+    pipe.set_weights(c["w"], 0.0, c["thr"])
+    pipe.img_host.copy_(torch.from_numpy(img.reshape(-1)))
+    det, n = pipe.detect_host()
+    xs, ys, _ = oracle.detect(oracle.pipeline(img, 8, c["w"], 0.0, 4)["scores"], 4, c["thr"])
+    assert n == len(xs) and np.array_equal(det["x"], xs) and np.array_equal(det["y"], ys)

@@ -68,9 +68,9 @@ def test_matches_arctan2_off_boundary(oracle_mod, nb):
 def test_margin_certificate(oracle_mod):
     """The FP64 sign tests against irrational boundaries keep a margin far above
     any fixed-point evaluation error (2^-40 scale): the smallest |cross| over
-    all lattice points and all N_b <= 32 stays above 1e-6."""
+    all lattice points and all N_b <= 64 stays above 1e-6."""
     oracle_mod.reset_margin()
-    for nb in range(1, 33):
+    for nb in range(1, 65):
         oracle_mod.lut(nb)
     assert not oracle_mod.margin_violation()
     assert oracle_mod.min_margin() > 1e-6
