@@ -163,8 +163,8 @@ hog_status hog_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dt
  *   ii, ii_dtype  the planes written by hog_integral (HOG_I32 or HOG_U16)
  *   cell          cell side in pixels, 1..64 (cell * cell < 65536)
  *   stride        1..cell
- *   cell_dtype    HOG_I32 or HOG_BF16 (counts <= cell^2 <= 256 are exact in
- *                 bf16 for cell <= 16)
+ *   cell_dtype    HOG_I32, HOG_F32 (counts are exact in either), or HOG_BF16
+ *                 (counts <= cell^2 <= 256 are exact in bf16 for cell <= 16)
  *   cells         out: [ncy][ncx][n_bins], bin innermost
  */
 hog_status hog_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype, int cell,
@@ -184,7 +184,8 @@ hog_status hog_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype,
  *                                        * cells[py + cy*r][px + cx*r][b]
  * for px < nx = ncx - (cells_x - 1) r and py < ny = ncy - (cells_y - 1) r.
  *
- *   cells, cell_dtype  from hog_cell_hist (HOG_I32 or HOG_BF16)
+ *   cells, cell_dtype  from hog_cell_hist (HOG_I32, HOG_F32 or HOG_BF16;
+ *                      16-byte aligned for the fast kernels)
  *   cell, stride       as given to hog_cell_hist; stride must divide cell
  *   w, w_dtype         cells_x * cells_y * n_bins weights:
  *                      HOG_F32  -> FP32 arithmetic on CUDA cores, scores f32

@@ -7,7 +7,7 @@ each call enqueues work on the given stream (default: the current stream) and
 returns.  A non-OK status raises :class:`HogError`.
 
 There is no CPU path: if the library has not been built, importing this
-package raises.  Build it with ``python -m paper_1703_06256_gb300.build``.
+package raises.  Build it with ``python paper_1703_06256_gb300/build.py``.
 """
 
 from __future__ import annotations
@@ -53,7 +53,7 @@ class HogError(RuntimeError):
 def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libfasthog is not built ({LIB_PATH} missing); run "
-                          "`python -m paper_1703_06256_gb300.build` (needs nvcc)")
+                          "`python paper_1703_06256_gb300/build.py` (needs nvcc)")
     lib = ctypes.CDLL(LIB_PATH)
     P, I, Z, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t, ctypes.c_float
     sig = {

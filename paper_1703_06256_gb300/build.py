@@ -2,7 +2,7 @@
 
 Every translation unit under csrc/ is compiled by nvcc in parallel, then
 linked into one shared library inside this package (in-tree, so the library a
-process loads is the one built here).  `python -m paper_1703_06256_gb300.build`
+process loads is the one built here).  `python paper_1703_06256_gb300/build.py`
 runs it; ``__graft_entry__.build()`` calls :func:`build`.
 """
 

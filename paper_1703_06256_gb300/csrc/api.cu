@@ -159,7 +159,7 @@ hog_status hog_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype,
     if (!size_ok(W, H) || n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
     if (ii_dtype != HOG_I32 && ii_dtype != HOG_U16) return HOG_ERR_ARG;
     if (cell < 1 || cell > 64 || stride < 1 || stride > cell) return HOG_ERR_ARG;
-    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16) return HOG_ERR_ARG;
+    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
     if (cell_dtype == HOG_BF16 && cell > 16) return HOG_ERR_ARG;  // counts above 256 are not exact in bf16
     return launch_cell_hist(ii, W, H, n_bins, ii_dtype, cell, stride, cell_dtype, cells,
                             reinterpret_cast<cudaStream_t>(stream));
@@ -172,7 +172,7 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
     if (ncx < 0 || ncy < 0 || n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
     if (cells_x < 1 || cells_y < 1 || cells_x > 64 || cells_y > 64) return HOG_ERR_ARG;
     if (cell < 1 || stride < 1 || cell % stride != 0) return HOG_ERR_ARG;
-    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16) return HOG_ERR_ARG;
+    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
     if (w_dtype != HOG_F32 && w_dtype != HOG_BF16 && w_dtype != HOG_I8) return HOG_ERR_ARG;
     if (!std::isfinite(bias)) return HOG_ERR_ARG;
     const int r = cell / stride;
@@ -181,6 +181,8 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
     if (w_dtype != HOG_F32 && score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx))
         return launch_score_tc(static_cast<const uint16_t*>(cells), ncx, ncy, n_bins, cells_x, cells_y, r, w,
                                w_dtype, b, scores, st);
+    if (score_slide_supported(cells, n_bins, cells_x, cells_y))
+        return launch_score_slide(cells, cell_dtype, ncx, ncy, r, w, w_dtype, b, scores, st);
     return launch_score_cuda_cores(cells, cell_dtype, ncx, ncy, n_bins, cells_x, cells_y, r, w, w_dtype, b, scores,
                                    st);
 }

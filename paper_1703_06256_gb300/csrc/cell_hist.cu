@@ -11,6 +11,8 @@
 //
 // With uint16 integral images the four-term sum is taken modulo 2^16, which
 // is exact because a cell holds fewer than 65536 pixels.
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace fasthog {
@@ -40,10 +42,10 @@ __global__ void __launch_bounds__(128)
         if (hy) v -= (uint32_t)__ldg(p + o10);
         if (hx && hy) v += (uint32_t)__ldg(p + o00);
         if (sizeof(InT) == 2) v &= 0xFFFFu;
-        if (sizeof(OutT) == 4) {
-            out[b] = (OutT)v;
-        } else {
+        if constexpr (std::is_same<OutT, uint16_t>::value) {
             out[b] = f32_to_bf16_exact_int((float)v);
+        } else {
+            out[b] = (OutT)v;  // int32, or float (counts are exact)
         }
     }
 }
@@ -64,12 +66,14 @@ hog_status launch_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dty
     const int ncx = W < cell ? 0 : (W - cell) / stride + 1;
     const int ncy = H < cell ? 0 : (H - cell) / stride + 1;
     if (ncx == 0 || ncy == 0) return HOG_OK;
-    if (ii_dtype == HOG_U16)
-        return cell_dtype == HOG_BF16
-                   ? launch_t<uint16_t, uint16_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st)
-                   : launch_t<uint16_t, int32_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
-    return cell_dtype == HOG_BF16 ? launch_t<int32_t, uint16_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st)
-                                  : launch_t<int32_t, int32_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+    if (ii_dtype == HOG_U16) {
+        if (cell_dtype == HOG_BF16) return launch_t<uint16_t, uint16_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+        if (cell_dtype == HOG_F32) return launch_t<uint16_t, float>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+        return launch_t<uint16_t, int32_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+    }
+    if (cell_dtype == HOG_BF16) return launch_t<int32_t, uint16_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+    if (cell_dtype == HOG_F32) return launch_t<int32_t, float>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
+    return launch_t<int32_t, int32_t>(ii, W, H, n_bins, cell, stride, ncx, ncy, cells, st);
 }
 
 }  // namespace fasthog

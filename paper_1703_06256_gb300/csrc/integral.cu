@@ -43,7 +43,7 @@ constexpr int kQ = 4;             // columns per thread
 constexpr int kThreads = 128;     // threads per tile CTA
 constexpr int kGroup = kQ * kThreads;  // 512 columns per group
 constexpr int kWarps = kThreads / 32;
-constexpr int kSegments = 8;      // phase B(a): band segments per column
+constexpr int kSegments = 32;     // phase B(a): band segments per column
 constexpr int kMaxBand = 32;
 
 struct Plan {
@@ -58,8 +58,8 @@ Plan make_plan(int W, int H, int n_bins) {
     p.W = W;
     p.H = H;
     p.n_groups = ceil_div(W, kGroup);
-    // The tallest band that still gives every SM at least one tile.
-    const int target = sm_count();
+    // The tallest band that still gives every SM four tiles (16 warps).
+    const int target = 4 * sm_count();
     p.h = 4;
     for (int h : {32, 16, 8})
         if ((long)ceil_div(H, h) * p.n_groups >= target) {
@@ -114,6 +114,28 @@ __device__ __forceinline__ void load_bins4(const uint8_t* __restrict__ bins, int
     }
 }
 
+// Issue the loads of this thread's kQ bins for every row of the band up
+// front, so their latency is paid once per tile rather than once per row,
+// and park them in shared memory (each thread reads back only its own slot).
+__device__ __forceinline__ void stage_band(const uint8_t* __restrict__ bins, int W, int y0, int y1, int x0, int ncol,
+                                           bool vec, uint32_t (*slot)[kThreads]) {
+    for (int y = y0; y < y1; y += 8) {
+        uint32_t w[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            w[k] = 0xFFFFFFFFu;
+            if (y + k < y1) {
+                uint32_t v[kQ];
+                load_bins4(bins, W, y + k, x0, ncol, vec, v);
+                w[k] = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (y + k < y1) slot[y + k - y0][threadIdx.x] = w[k];
+    }
+}
+
 // ---------------------------------------------------------------- phase A
 template <int WIN>
 __global__ void __launch_bounds__(kThreads)
@@ -122,12 +144,14 @@ __global__ void __launch_bounds__(kThreads)
     constexpr int NWD = WIN / 4;  // 8-bit packed words per column
     constexpr int NW = WIN / 2;   // 16-bit packed words per row
     __shared__ uint32_t row_acc[kMaxBand][NW];
+    __shared__ uint32_t band_bins[kMaxBand][kThreads];
     const int band = blockIdx.x, g = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31;
     const int x0 = g * kGroup + tid * kQ;
     const int ncol = max(0, min(kQ, W - x0));
     const int y0 = band * h, y1 = min(H, y0 + h);
 
+    stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
     for (int i = tid; i < kMaxBand * NW; i += kThreads) (&row_acc[0][0])[i] = 0;
     __syncthreads();
 
@@ -139,7 +163,11 @@ __global__ void __launch_bounds__(kThreads)
 
     for (int y = y0; y < y1; ++y) {
         uint32_t v[kQ];
-        load_bins4(bins, W, y, x0, ncol, vec, v);
+        {
+            const uint32_t w = band_bins[y - y0][tid];
+#pragma unroll
+            for (int c = 0; c < kQ; ++c) v[c] = (w >> (8 * c)) & 0xFFu;
+        }
         uint32_t rowp[NW];
 #pragma unroll
         for (int k = 0; k < NW; ++k) rowp[k] = 0;
@@ -221,13 +249,18 @@ __global__ void __launch_bounds__(32 * kSegments)
     const int x = (blockIdx.x - kw * words_x) * 32 + lane;
     const int per = (n_bands + kSegments - 1) / kSegments;
     const int b0 = seg * per, b1 = min(n_bands, b0 + per);
+    constexpr int kPF = 8;  // loads in flight per thread
     uint32_t s[4] = {0, 0, 0, 0};
-    if (x < W)
-        for (int b = b0; b < b1; ++b) {
-            const uint32_t w = __ldg(ws.colcnt + ((size_t)b * NWD + kw) * W + x);
+    for (int b = b0; b < b1; b += kPF) {
+        uint32_t wv[kPF];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) s[e] += (w >> (8 * e)) & 0xFFu;
-        }
+        for (int k = 0; k < kPF; ++k)
+            wv[k] = (x < W && b + k < b1) ? __ldg(ws.colcnt + ((size_t)(b + k) * NWD + kw) * W + x) : 0u;
+#pragma unroll
+        for (int k = 0; k < kPF; ++k)
+#pragma unroll
+            for (int e = 0; e < 4; ++e) s[e] += (wv[k] >> (8 * e)) & 0xFFu;
+    }
 #pragma unroll
     for (int e = 0; e < 4; ++e) seg_sum[seg][lane][e] = s[e];
     __syncthreads();
@@ -236,12 +269,20 @@ __global__ void __launch_bounds__(32 * kSegments)
 #pragma unroll
         for (int e = 0; e < 4; ++e) run[e] += seg_sum[t][lane][e];
     if (x >= W) return;
-    for (int b = b0; b < b1; ++b) {
-        const uint32_t w = __ldg(ws.colcnt + ((size_t)b * NWD + kw) * W + x);
+    for (int b = b0; b < b1; b += kPF) {
+        uint32_t wv[kPF];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            ws.carry[((size_t)b * WIN + 4 * kw + e) * W + x] = (uint16_t)run[e];
-            run[e] += (w >> (8 * e)) & 0xFFu;
+        for (int k = 0; k < kPF; ++k)
+            wv[k] = b + k < b1 ? __ldg(ws.colcnt + ((size_t)(b + k) * NWD + kw) * W + x) : 0u;
+#pragma unroll
+        for (int k = 0; k < kPF; ++k) {
+            if (b + k < b1) {
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    ws.carry[((size_t)(b + k) * WIN + 4 * kw + e) * W + x] = (uint16_t)run[e];
+                    run[e] += (wv[k] >> (8 * e)) & 0xFFu;
+                }
+            }
         }
     }
 }
@@ -284,6 +325,8 @@ __global__ void __launch_bounds__(kThreads)
     const int ncol = max(0, min(kQ, W - x0));
     const int y0 = band * h, y1 = min(H, y0 + h);
     const int wins = min(WIN, n_bins - bin_base);
+    __shared__ uint32_t band_bins[kMaxBand][kThreads];
+    stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
 
     // corner = ii(group_left - 1, y0 - 1); RL(y) for the band's rows
     if (tid < WIN) {
@@ -307,11 +350,22 @@ __global__ void __launch_bounds__(kThreads)
     int tot[WIN];
 #pragma unroll
     for (int b = 0; b < WIN; ++b) {
+        const uint16_t* cp = ws.carry + ((size_t)band * WIN + b) * W + x0;
+        int cv[kQ];
+        if (vec && ncol == kQ) {
+            const uint2 u = __ldg(reinterpret_cast<const uint2*>(cp));
+            cv[0] = (int)(u.x & 0xFFFFu);
+            cv[1] = (int)(u.x >> 16);
+            cv[2] = (int)(u.y & 0xFFFFu);
+            cv[3] = (int)(u.y >> 16);
+        } else {
+#pragma unroll
+            for (int c = 0; c < kQ; ++c) cv[c] = c < ncol ? (int)__ldg(cp + c) : 0;
+        }
         int run = 0;
 #pragma unroll
         for (int c = 0; c < kQ; ++c) {
-            const int v = c < ncol ? (int)__ldg(ws.carry + ((size_t)band * WIN + b) * W + x0 + c) : 0;
-            run += v;
+            run += cv[c];
             acc[c][b] = run;
         }
         tot[b] = run;
@@ -340,7 +394,11 @@ __global__ void __launch_bounds__(kThreads)
     int buf = 0;
     for (int y = y0; y < y1; ++y) {
         uint32_t v[kQ];
-        load_bins4(bins, W, y, x0, ncol, vec, v);
+        {
+            const uint32_t w = band_bins[y - y0][tid];
+#pragma unroll
+            for (int c = 0; c < kQ; ++c) v[c] = (w >> (8 * c)) & 0xFFu;
+        }
         uint32_t run[NW], pre[kQ][NW];
 #pragma unroll
         for (int k = 0; k < NW; ++k) run[k] = 0;

@@ -48,6 +48,9 @@ hog_status launch_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dty
 hog_status launch_score_cuda_cores(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins,
                                    int cells_x, int cells_y, int r, const void* w, int w_dtype,
                                    float bias, void* scores, cudaStream_t st);
+bool score_slide_supported(const void* cells, int n_bins, int cells_x, int cells_y);
+hog_status launch_score_slide(const void* cells, int cell_dtype, int ncx, int ncy, int r, const void* w,
+                              int w_dtype, float bias, void* scores, cudaStream_t st);
 bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx);
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x,
                            int cells_y, int r, const void* w, int w_dtype, float bias,

@@ -49,6 +49,10 @@ __device__ __forceinline__ float cell_val<int32_t>(const int32_t* c, size_t idx)
     return (float)__ldg(c + idx);
 }
 template <>
+__device__ __forceinline__ float cell_val<float>(const float* c, size_t idx) {
+    return __ldg(c + idx);
+}
+template <>
 __device__ __forceinline__ float cell_val<uint16_t>(const uint16_t* c, size_t idx) {
     return bf16_to_f32(__ldg(c + idx));
 }
@@ -192,6 +196,8 @@ hog_status launch_score_cuda_cores(const void* cells, int cell_dtype, int ncx, i
                                    cudaStream_t st) {
     if (cell_dtype == HOG_BF16)
         return by_weight<uint16_t>(cells, ncx, ncy, n_bins, cells_x, cells_y, r, w, w_dtype, bias, scores, st);
+    if (cell_dtype == HOG_F32)
+        return by_weight<float>(cells, ncx, ncy, n_bins, cells_x, cells_y, r, w, w_dtype, bias, scores, st);
     return by_weight<int32_t>(cells, ncx, ncy, n_bins, cells_x, cells_y, r, w, w_dtype, bias, scores, st);
 }
 

@@ -23,7 +23,7 @@ _W_DTYPE = {HOG_F32: torch.float32, HOG_BF16: torch.bfloat16, HOG_I8: torch.int8
 
 class HogPipeline:
     def __init__(self, W: int, H: int, channels: int = 3, n_bins: int = 8, stride: int = 8, cell: int = 8,
-                 cells_x: int = 8, cells_y: int = 16, ii_dtype: int = HOG_I32, cell_dtype: int = HOG_I32,
+                 cells_x: int = 8, cells_y: int = 16, ii_dtype: int = HOG_I32, cell_dtype: int = HOG_F32,
                  w_dtype: int = HOG_F32, max_out: int | None = None, device: str | torch.device = "cuda"):
         self.W, self.H, self.channels, self.n_bins = W, H, channels, n_bins
         self.stride, self.cell, self.cells_x, self.cells_y = stride, cell, cells_x, cells_y
@@ -61,6 +61,7 @@ class HogPipeline:
             raise ValueError(f"expected {self.w.numel()} weights, got {t.numel()}")
         self.w.copy_(t.to(self.w.dtype))
         self.bias, self.thr = float(bias), float(thr)
+        self.graph = None  # bias and threshold are launch arguments: recapture
 
     def set_image(self, img: np.ndarray) -> None:
         a = np.ascontiguousarray(img, dtype=np.uint8).reshape(-1)
@@ -87,13 +88,42 @@ class HogPipeline:
         hog_detect(self.scores, self.score_dtype, self.nx, self.ny, self.stride, self.thr, 0, 0, self.det,
                    self.max_out, self.count, self.ws_det, self.ws_det_bytes, stream)
 
-    def run(self, stream=None) -> None:
-        """Enqueue the whole path for the image already in ``self.img``."""
+    def run_eager(self, stream=None) -> None:
+        """Enqueue the five calls for the image already in ``self.img``."""
         self.stage_bin_map(stream)
         self.stage_integral(stream)
         self.stage_cell_hist(stream)
         self.stage_score(stream)
         self.stage_detect(stream)
+
+    def capture(self) -> None:
+        """Record the five calls once as a CUDA graph; ``run`` then replays it
+        (one launch instead of eight, no host work between the kernels).  The
+        calls allocate nothing and never synchronise, so they capture as is.
+        Weights, bias and threshold must be set before capturing."""
+        with torch.cuda.device(self.device):
+            s = torch.cuda.Stream(self.device)
+            s.wait_stream(torch.cuda.current_stream(self.device))
+            with torch.cuda.stream(s):
+                self.run_eager(s)  # first launches load the kernels outside the capture
+            torch.cuda.current_stream(self.device).wait_stream(s)
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self.run_eager()
+            self.graph = g
+
+    graph = None
+
+    def run(self, stream=None) -> None:
+        """Enqueue the whole path: the captured graph if there is one."""
+        if self.graph is not None:
+            if stream is None:
+                self.graph.replay()
+            else:
+                with torch.cuda.stream(stream):
+                    self.graph.replay()
+        else:
+            self.run_eager(stream)
 
     def detect_host(self, img_host: torch.Tensor | None = None, stream=None):
         """End to end from pinned host memory: H2D copy, the path, D2H of the

@@ -56,7 +56,7 @@ def gpu_cells(ii: np.ndarray, nb: int, cell: int, stride: int, ii_dtype=fh.HOG_I
     src = ii.astype(np.int32) if ii_dtype == fh.HOG_I32 else ii.astype(np.uint16).view(np.int16)
     d = dev(src.reshape(-1))
     n = max(ncx * ncy * nb, 1)
-    out = torch.zeros(n, dtype=torch.int32 if cell_dtype == fh.HOG_I32 else torch.bfloat16, device="cuda")
+    out = torch.zeros(n, dtype=fh.TORCH_DTYPE[cell_dtype], device="cuda")
     fh.hog_cell_hist(d, W, H, nb, ii_dtype, cell, stride, cell_dtype, out)
     return out.float().cpu().numpy()[: ncx * ncy * nb].reshape(ncy, ncx, nb)
 
@@ -68,6 +68,8 @@ def gpu_scores(cells: np.ndarray, w: np.ndarray, w_dtype: int, bias: float, cell
     nx, ny = ncx - (cells_x - 1) * r, ncy - (cells_y - 1) * r
     if cell_dtype == fh.HOG_I32:
         c = dev(cells.astype(np.int32).reshape(-1))
+    elif cell_dtype == fh.HOG_F32:
+        c = dev(cells.astype(np.float32).reshape(-1))
     else:
         c = torch.from_numpy(cells.astype(np.float32).reshape(-1)).to(torch.bfloat16).cuda()
     if w_dtype == fh.HOG_F32:
@@ -103,3 +105,17 @@ def score_tolerance(cells: np.ndarray, w: np.ndarray, bias: float, cell=8, strid
 
     return 1e-5 * (oracle.window_score(np.abs(cells), np.abs(np.asarray(w, np.float64)), abs(bias), cells_x,
                                        cells_y, cell, stride))
+
+
+def check_detections(det, n, S_gpu, S64, tol, thr, stride):
+    """The list must be exactly the row-major compaction of the GPU's own
+    scores (same precision decides), and may differ from the FP64 decision
+    only for windows whose FP64 score lies within `tol` of the threshold.
+    Returns the number of such near-threshold windows."""
+    ys, xs = np.nonzero(S_gpu >= np.float32(thr))
+    assert n == len(xs)
+    assert np.array_equal(det["x"], xs * stride) and np.array_equal(det["y"], ys * stride)
+    assert np.array_equal(det["score"], S_gpu[ys, xs])
+    near = np.abs(S64 - thr) <= tol
+    assert np.array_equal((S_gpu >= np.float32(thr))[~near], (S64 >= thr)[~near])
+    return int(near.sum())

@@ -20,8 +20,12 @@ def declared_functions():
 
 @pytest.fixture(scope="module")
 def fh():
-    from paper_1703_06256_gb300 import build as b
+    import importlib.util
 
+    spec = importlib.util.spec_from_file_location("_fasthog_build", os.path.join(ROOT, "paper_1703_06256_gb300",
+                                                                                  "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
     b.build()
     import paper_1703_06256_gb300 as m
 
