@@ -62,8 +62,13 @@ typedef enum {
 /* Row pitch of the table in memory: 511 entries and one pad byte, so that
  * every row half starts on a 16-byte boundary. */
 #define HOG_LUT_PITCH 512
-/* Bytes of one table: 511 rows of HOG_LUT_PITCH. */
-#define HOG_LUT_BYTES (HOG_LUT_SIDE * HOG_LUT_PITCH)
+/* Offset of the quadrant copy that follows the table: 256 rows of 256 bytes,
+ * row dy (0..255), column dx - 1 (dx = 1..256), entry = the table's entry for
+ * (dx, dy) (0xFF for dx = 256).  It is a contiguous duplicate of part of the
+ * table that the bin-map kernel stages into shared memory in one copy. */
+#define HOG_LUT_QUAD_OFFSET (HOG_LUT_SIDE * HOG_LUT_PITCH)
+/* Bytes of one table buffer: 511 rows of HOG_LUT_PITCH, then the quadrant. */
+#define HOG_LUT_BYTES (HOG_LUT_QUAD_OFFSET + 256 * 256)
 
 /* One detection: window origin (x, y) in pixels, its score, and the image
  * index and pyramid level the caller tagged the call with. */
@@ -103,7 +108,8 @@ hog_status hog_device_status(uint32_t* flags, int clear);
  *
  *   n_bins  N_b, 1..64
  *   lut     out: HOG_LUT_BYTES bytes (uint8), 16-byte aligned; row dy + 255
- *           holds the 511 entries of that dy, then one pad byte (written 0xFF)
+ *           holds the 511 entries of that dy, then one pad byte (written
+ *           0xFF); the quadrant copy follows at HOG_LUT_QUAD_OFFSET
  * Built once per N_b and kept resident; hog_bin_map reads it.
  */
 hog_status hog_build_lut(int n_bins, uint8_t* lut, hog_stream_t stream);

@@ -25,7 +25,8 @@ HOG_U8, HOG_I32, HOG_BF16, HOG_F32, HOG_I8, HOG_U16 = range(6)
 HOG_NO_BIN = 0xFF
 HOG_LUT_SIDE = 511
 HOG_LUT_PITCH = 512
-HOG_LUT_BYTES = HOG_LUT_SIDE * HOG_LUT_PITCH
+HOG_LUT_QUAD_OFFSET = HOG_LUT_SIDE * HOG_LUT_PITCH
+HOG_LUT_BYTES = HOG_LUT_QUAD_OFFSET + 256 * 256
 HOG_STATUS_TIMEOUT = 1
 
 TORCH_DTYPE = {HOG_U8: torch.uint8, HOG_I32: torch.int32, HOG_BF16: torch.bfloat16, HOG_F32: torch.float32,

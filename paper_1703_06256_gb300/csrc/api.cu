@@ -181,7 +181,7 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
     if (w_dtype != HOG_F32 && score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx))
         return launch_score_tc(static_cast<const uint16_t*>(cells), ncx, ncy, n_bins, cells_x, cells_y, r, w,
                                w_dtype, b, scores, st);
-    if (score_slide_supported(cells, n_bins, cells_x, cells_y))
+    if (score_slide_supported(cells, n_bins, cells_x, cells_y, r))
         return launch_score_slide(cells, cell_dtype, ncx, ncy, r, w, w_dtype, b, scores, st);
     return launch_score_cuda_cores(cells, cell_dtype, ncx, ncy, n_bins, cells_x, cells_y, r, w, w_dtype, b, scores,
                                    st);

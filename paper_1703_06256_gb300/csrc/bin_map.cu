@@ -4,10 +4,17 @@
 // 32-bit word.  A thread loads the 32-bit words that hold its quad and the
 // one-pixel halo straight from global memory (through L1: neighbouring
 // quads share their edge words): for RGB, 5 words of the centre row and 3
-// of the rows above and below; for gray, 3 + 1 + 1.  Every byte position
-// inside those words is a compile-time constant, so Eq. 1 for the 4 x C
-// channel values needs only register shifts, no shared-memory traffic.
-// Rows start at arbitrary addresses; unaligned images take a byte path.
+// of the rows above and below; for gray, 3 + 1 + 1.  Interior quads of
+// 4-byte aligned images load without bounds tests; edge quads and unaligned
+// images take a guarded byte path.
+//
+// Eq. 1 runs four channel values per instruction: the right and left
+// neighbours of the quad's 4 x C channel values are realigned into words by
+// funnel shifts, then one vabsdiff4 gives |dx| and one vcmpgtu4 the sign of
+// dx for four values at once (likewise dy from the rows below and above).
+// Each channel value becomes a key (|dx|, |dy|, dx > 0, dy > 0) in one word;
+// dp4a of the key with its low half gives dx^2 + dy^2 for the channel
+// choice (strongest channel, ties to the lowest index).
 //
 // The table lives in shared memory.  The full 511 x 511 table (255.5 KiB)
 // does not fit, so when 4 divides N_b the CTA holds one quadrant only:
@@ -15,11 +22,12 @@
 // quarter turn (dx, dy) -> (-dy, dx) adds pi/2 to the angle and, because
 // the sectors are half-open and N_b/4 of them span pi/2, adds exactly N_b/4
 // to the bin.  So any gradient is turned into that quadrant by q quarter
-// turns and its bin is (quadrant entry + q * N_b/4) mod N_b.  The quadrant
-// (rows 255..510, columns 256..511 of the table, each row 16-byte aligned
-// thanks to the 512-byte pitch) arrives by 256 bulk async copies that
-// complete on one mbarrier, while the first quads' pixels are loaded.
-// For other N_b the kernel reads the table through the read-only cache.
+// turns -- which lands on (|dx|, |dy|) for even q and on (|dy|, |dx|) for odd
+// q -- and its bin is (quadrant entry + q * N_b/4) mod N_b.  The quadrant
+// (stored contiguously after the table by hog_build_lut) arrives by one
+// 64 KiB bulk async copy that completes on an mbarrier, while the first
+// quads' pixels are loaded.  For other N_b the kernel reads the table
+// through the read-only cache.
 //
 // The grid is persistent (a few CTAs per SM, grid-stride over quads) so
 // that each CTA stages the table once.
@@ -33,8 +41,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kQuadBytes = 256 * 256;  // 256 rows (dy 0..255) x 256 columns (dx 1..256)
 
-// Load the 32-bit word at byte offset `off` of a row of `row_bytes` bytes;
-// bytes outside the row read as 0.
+// The 32-bit word at byte offset `off` of a row of `row_bytes` bytes; bytes
+// outside the row read as 0.
 __device__ __forceinline__ uint32_t row_word(const uint8_t* __restrict__ row, long off, long row_bytes, bool aligned) {
     if (aligned && off >= 0 && off + 4 <= row_bytes) return __ldg(reinterpret_cast<const uint32_t*>(row + off));
     uint32_t w = 0;
@@ -44,9 +52,20 @@ __device__ __forceinline__ uint32_t row_word(const uint8_t* __restrict__ row, lo
     return w;
 }
 
+// Byte i of a little-endian word array, i a compile-time constant.
 template <int N>
-__device__ __forceinline__ int byte_at(const uint32_t (&w)[N], int i) {
-    return (int)((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[N], int i) {
+    return (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+}
+
+// Key of channel value i: bytes (|dx|, |dy|, dx > 0 ? 0xFF : 0, dy > 0 ? 0xFF : 0).
+template <int N>
+__device__ __forceinline__ uint32_t key_of(const uint32_t (&ax)[N], const uint32_t (&ay)[N], const uint32_t (&gx)[N],
+                                           const uint32_t (&gy)[N], int i) {
+    const int k = i >> 2, b = i & 3;
+    const uint32_t mag = __byte_perm(ax[k], ay[k], (uint32_t)(b | ((b + 4) << 4)));
+    const uint32_t sgn = __byte_perm(gx[k], gy[k], (uint32_t)(b | ((b + 4) << 4)));
+    return __byte_perm(mag, sgn, 0x5410);
 }
 
 template <int CH, bool QUAD>
@@ -54,8 +73,7 @@ __global__ void __launch_bounds__(kThreads)
     bin_map_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                    const uint8_t* __restrict__ lut, int nb, uint8_t* __restrict__ bins, bool word_stores,
                    unsigned int* status) {
-    // centre-row words: bytes [4*CH*k - 4, ...) hold pixels x-1 .. x+4
-    constexpr int NC = CH == 3 ? 5 : 3;
+    constexpr int NC = CH == 3 ? 5 : 3;  // centre-row words, from byte 4*CH*quad - 4
     constexpr int NV = CH == 3 ? 3 : 1;  // rows above / below: the quad's own bytes
     extern __shared__ __align__(128) uint8_t lutq[];
     __shared__ __align__(8) uint64_t lut_bar;
@@ -68,12 +86,10 @@ __global__ void __launch_bounds__(kThreads)
             ptx::fence_mbar_init();
         }
         __syncthreads();
-        if (tid < 32) {
-            if (tid == 0) ptx::mbar_arrive_expect_tx(&lut_bar, kQuadBytes);
-            __syncwarp();
-            // table row dy + 255, columns 256..511 -> quadrant row dy
-            for (int row = tid; row < 256; row += 32)
-                ptx::bulk_g2s(lutq + row * 256, lut + (size_t)(row + kDMax) * kLutPitch + 256, 256, &lut_bar);
+        if (tid == 0) {
+            // the contiguous quadrant copy that follows the table: one bulk copy
+            ptx::mbar_arrive_expect_tx(&lut_bar, kQuadBytes);
+            ptx::bulk_g2s(lutq, lut + kLutQuadOffset, kQuadBytes, &lut_bar);
         }
     }
     bool lut_ready = !QUAD;
@@ -91,12 +107,37 @@ __global__ void __launch_bounds__(kThreads)
             const uint8_t* dn = mid + pitch;
             const long o = (long)x * CH;
             uint32_t wc[NC], wu[NV], wd[NV];
+            if (aligned && x >= 4 && o + 4 * NC - 4 <= row_bytes) {
+                const uint32_t* m4 = reinterpret_cast<const uint32_t*>(mid + o - 4);
+                const uint32_t* u4 = reinterpret_cast<const uint32_t*>(up + o);
+                const uint32_t* d4 = reinterpret_cast<const uint32_t*>(dn + o);
 #pragma unroll
-            for (int k = 0; k < NC; ++k) wc[k] = row_word(mid, o - 4 + 4 * k, row_bytes, aligned);
+                for (int k = 0; k < NC; ++k) wc[k] = __ldg(m4 + k);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    wu[k] = __ldg(u4 + k);
+                    wd[k] = __ldg(d4 + k);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < NC; ++k) wc[k] = row_word(mid, o - 4 + 4 * k, row_bytes, aligned);
+#pragma unroll
+                for (int k = 0; k < NV; ++k) {
+                    wu[k] = row_word(up, o + 4 * k, row_bytes, aligned);
+                    wd[k] = row_word(dn, o + 4 * k, row_bytes, aligned);
+                }
+            }
+            // channel value i = CH * p + c of pixel x + p: right neighbour at
+            // byte i + CH + 4 of wc, left neighbour at byte i - CH + 4
+            uint32_t ax[NV], ay[NV], gx[NV], gy[NV];
 #pragma unroll
             for (int k = 0; k < NV; ++k) {
-                wu[k] = row_word(up, o + 4 * k, row_bytes, aligned);
-                wd[k] = row_word(dn, o + 4 * k, row_bytes, aligned);
+                const uint32_t rgt = __funnelshift_r(wc[k + (CH + 4) / 4], wc[k + (CH + 4) / 4 + 1], 8 * ((CH + 4) % 4));
+                const uint32_t lft = __funnelshift_r(wc[k], wc[k + 1], 8 * (4 - CH));
+                ax[k] = __vabsdiff4(rgt, lft);
+                gx[k] = __vcmpgtu4(rgt, lft);
+                ay[k] = __vabsdiff4(wd[k], wu[k]);
+                gy[k] = __vcmpgtu4(wd[k], wu[k]);
             }
             if (!lut_ready) {
                 if (!ptx::mbar_wait_bounded(&lut_bar, 0, kWaitLimitNs)) {
@@ -107,42 +148,43 @@ __global__ void __launch_bounds__(kThreads)
             }
             packed = 0;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
+            for (int p = 0; p < 4; ++p) {
                 uint32_t bin = kNoBin;
-                const int xe = x + e;
-                if (xe > 0 && xe < W - 1) {
-                    // byte of pixel xe+d, channel c in wc: 4 + (e + d) * CH + c
-                    int dx = byte_at(wc, 4 + (e + 1) * CH) - byte_at(wc, 4 + (e - 1) * CH);
-                    int dy = byte_at(wd, e * CH) - byte_at(wu, e * CH);
+                const int xp = x + p;
+                if (xp > 0 && xp < W - 1) {
+                    uint32_t key = key_of(ax, ay, gx, gy, CH * p);
                     if (CH == 3) {
-                        int best = dx * dx + dy * dy;
+                        uint32_t best = __dp4a(key, key & 0xFFFFu, 0u);
 #pragma unroll
                         for (int c = 1; c < 3; ++c) {
-                            const int ddx = byte_at(wc, 4 + (e + 1) * CH + c) - byte_at(wc, 4 + (e - 1) * CH + c);
-                            const int ddy = byte_at(wd, e * CH + c) - byte_at(wu, e * CH + c);
-                            const int m = ddx * ddx + ddy * ddy;
+                            const uint32_t kc = key_of(ax, ay, gx, gy, CH * p + c);
+                            const uint32_t m = __dp4a(kc, kc & 0xFFFFu, 0u);
                             if (m > best) {  // strict: ties keep the lower channel
                                 best = m;
-                                dx = ddx;
-                                dy = ddy;
+                                key = kc;
                             }
                         }
                     }
-                    if (dx != 0 || dy != 0) {
+                    const int adx = key & 0xFF, ady = (key >> 8) & 0xFF;
+                    if (adx | ady) {
+                        const int dx = (key & 0x00FF0000u) ? adx : -adx;
+                        const int dy = (key & 0xFF000000u) ? ady : -ady;
                         if (QUAD) {
-                            int qd, ax, ay;
-                            if (dx > 0 && dy >= 0) { qd = 0; ax = dx; ay = dy; }
-                            else if (dx <= 0 && dy > 0) { qd = 1; ax = dy; ay = -dx; }
-                            else if (dx < 0 && dy <= 0) { qd = 2; ax = -dx; ay = -dy; }
-                            else { qd = 3; ax = -dy; ay = dx; }
-                            const int v = lutq[ay * 256 + ax - 1] + qd * nb4;
-                            bin = v >= nb ? v - nb : v;
+                            int qd;
+                            if (dx > 0 && dy >= 0) qd = 0;
+                            else if (dx <= 0 && dy > 0) qd = 1;
+                            else if (dx < 0 && dy <= 0) qd = 2;
+                            else qd = 3;
+                            const int u = (qd & 1) ? ady : adx;  // quadrant-0 coordinates
+                            const int v = (qd & 1) ? adx : ady;
+                            const int t = lutq[v * 256 + u - 1] + qd * nb4;
+                            bin = t >= nb ? t - nb : t;
                         } else {
                             bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
                         }
                     }
                 }
-                packed = (packed & ~(0xFFu << (8 * e))) | (bin << (8 * e));
+                packed |= bin << (8 * p);
             }
         }
         uint8_t* out = bins + (size_t)y * W + x;
@@ -155,8 +197,8 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
     if (QUAD && !lut_ready) {
-        // This thread never needed the table: still let the copies land
-        // before the CTA exits.
+        // This thread never needed the table: still let the copy land before
+        // the CTA exits.
         if (!ptx::mbar_wait_bounded(&lut_bar, 0, kWaitLimitNs)) atomicOr(status, kStatusTimeout);
     }
 }
@@ -171,7 +213,8 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
         if (e != cudaSuccess) return cuda_fail(e);
     }
     const long n_quads = (long)((W + 3) / 4) * H;
-    const long need = (n_quads + kThreads - 1) / kThreads;
+    // at least 4 quads per thread, so each staged table copy serves a fair share of pixels
+    const long need = (n_quads + 4 * kThreads - 1) / (4 * kThreads);
     const long cap = (long)sm_count() * (QUAD ? 3 : 8);
     const int grid = (int)(need < cap ? need : cap);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);

@@ -19,33 +19,56 @@ namespace fasthog {
 
 namespace {
 
-template <typename InT, typename OutT>
+template <typename OutT>
+__device__ __forceinline__ OutT count_as(uint32_t v) {
+    if constexpr (std::is_same<OutT, uint16_t>::value) {
+        return f32_to_bf16_exact_int((float)v);
+    } else {
+        return (OutT)v;  // int32, or float (counts are exact)
+    }
+}
+
+// NB > 0: the bin count is a compile-time constant, so all 4 * NB corner
+// loads of a cell are issued before any of them is used.  NB == 0: any N_b.
+template <typename InT, typename OutT, int NB>
 __global__ void __launch_bounds__(128)
-    cell_hist_kernel(const InT* __restrict__ ii, int W, int H, int nb, int cell, int stride, int ncx, int ncy,
+    cell_hist_kernel(const InT* __restrict__ ii, int W, int H, int nb_rt, int cell, int stride, int ncx, int ncy,
                      OutT* __restrict__ cells) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= ncx || j >= ncy) return;
+    const int nb = NB > 0 ? NB : nb_rt;
     const int x0 = i * stride, y0 = j * stride;
     const int x1 = x0 + cell - 1, y1 = y0 + cell - 1;
     const bool hx = x0 > 0, hy = y0 > 0;
     const size_t plane = (size_t)W * H;
-    const size_t o11 = (size_t)y1 * W + x1;
-    const size_t o01 = (size_t)y1 * W + (x0 - 1);
-    const size_t o10 = (size_t)(y0 - 1) * W + x1;
-    const size_t o00 = (size_t)(y0 - 1) * W + (x0 - 1);
+    const InT* p11 = ii + (size_t)y1 * W + x1;
+    const InT* p01 = ii + (size_t)y1 * W + (x0 - 1);
+    const InT* p10 = ii + (size_t)(y0 - 1) * W + x1;
+    const InT* p00 = ii + (size_t)(y0 - 1) * W + (x0 - 1);
     OutT* out = cells + ((size_t)j * ncx + i) * nb;
-    for (int b = 0; b < nb; ++b) {
-        const InT* p = ii + (size_t)b * plane;
-        uint32_t v = (uint32_t)__ldg(p + o11);
-        if (hx) v -= (uint32_t)__ldg(p + o01);
-        if (hy) v -= (uint32_t)__ldg(p + o10);
-        if (hx && hy) v += (uint32_t)__ldg(p + o00);
-        if (sizeof(InT) == 2) v &= 0xFFFFu;
-        if constexpr (std::is_same<OutT, uint16_t>::value) {
-            out[b] = f32_to_bf16_exact_int((float)v);
-        } else {
-            out[b] = (OutT)v;  // int32, or float (counts are exact)
+    if constexpr (NB > 0) {
+        uint32_t v[NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            v[b] = (uint32_t)__ldg(p11 + b * plane);
+            if (hx) v[b] -= (uint32_t)__ldg(p01 + b * plane);
+            if (hy) v[b] -= (uint32_t)__ldg(p10 + b * plane);
+            if (hx && hy) v[b] += (uint32_t)__ldg(p00 + b * plane);
+        }
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+            if (sizeof(InT) == 2) v[b] &= 0xFFFFu;
+            out[b] = count_as<OutT>(v[b]);
+        }
+    } else {
+        for (int b = 0; b < nb; ++b) {
+            uint32_t v = (uint32_t)__ldg(p11 + b * plane);
+            if (hx) v -= (uint32_t)__ldg(p01 + b * plane);
+            if (hy) v -= (uint32_t)__ldg(p10 + b * plane);
+            if (hx && hy) v += (uint32_t)__ldg(p00 + b * plane);
+            if (sizeof(InT) == 2) v &= 0xFFFFu;
+            out[b] = count_as<OutT>(v);
         }
     }
 }
@@ -54,8 +77,14 @@ template <typename InT, typename OutT>
 hog_status launch_t(const void* ii, int W, int H, int nb, int cell, int stride, int ncx, int ncy, void* cells,
                     cudaStream_t st) {
     dim3 grid(ceil_div(ncx, 128), ncy);
-    cell_hist_kernel<InT, OutT><<<grid, 128, 0, st>>>(static_cast<const InT*>(ii), W, H, nb, cell, stride, ncx,
-                                                      ncy, static_cast<OutT*>(cells));
+    const InT* src = static_cast<const InT*>(ii);
+    OutT* dst = static_cast<OutT*>(cells);
+    if (nb == 8)
+        cell_hist_kernel<InT, OutT, 8><<<grid, 128, 0, st>>>(src, W, H, nb, cell, stride, ncx, ncy, dst);
+    else if (nb == 16)
+        cell_hist_kernel<InT, OutT, 16><<<grid, 128, 0, st>>>(src, W, H, nb, cell, stride, ncx, ncy, dst);
+    else
+        cell_hist_kernel<InT, OutT, 0><<<grid, 128, 0, st>>>(src, W, H, nb, cell, stride, ncx, ncy, dst);
     return check_launch();
 }
 

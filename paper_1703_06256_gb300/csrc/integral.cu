@@ -136,14 +136,27 @@ __device__ __forceinline__ void stage_band(const uint8_t* __restrict__ bins, int
     }
 }
 
+// SIMD-within-a-register helpers.  A thread's 4 bins sit in one 32-bit word,
+// one byte per column.
+//
+// One-hot of bin value v (bv4 = v in all four bytes): 0x01 in every byte
+// whose column holds bin v.
+__device__ __forceinline__ uint32_t onehot4(uint32_t w, uint32_t bv4) { return __vcmpeq4(w, bv4) & 0x01010101u; }
+// Counts of 4 bins in 8-bit fields (word m: bins 4m..4m+3) widen to 16-bit
+// fields two bins per word, paired as E[2m] = (4m, 4m+2), E[2m+1] = (4m+1, 4m+3).
+__device__ __forceinline__ uint32_t even16(uint32_t t) { return t & 0x00FF00FFu; }
+__device__ __forceinline__ uint32_t odd16(uint32_t t) { return (t >> 8) & 0x00FF00FFu; }
+__host__ __device__ constexpr int e_word(int b) { return 2 * (b >> 2) + (b & 1); }
+__host__ __device__ constexpr int e_half(int b) { return (b >> 1) & 1; }
+
 // ---------------------------------------------------------------- phase A
 template <int WIN>
 __global__ void __launch_bounds__(kThreads)
     ii_tile_reduce_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_bands, int n_groups,
                           int bin_base, bool vec, Ws ws) {
-    constexpr int NWD = WIN / 4;  // 8-bit packed words per column
-    constexpr int NW = WIN / 2;   // 16-bit packed words per row
-    __shared__ uint32_t row_acc[kMaxBand][NW];
+    constexpr int NM = WIN / 4;  // 8-bit-field words (4 bins each)
+    constexpr int NE = WIN / 2;  // 16-bit-field words (2 bins each)
+    __shared__ uint32_t row_acc[kMaxBand][NE];
     __shared__ uint32_t band_bins[kMaxBand][kThreads];
     const int band = blockIdx.x, g = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31;
@@ -152,43 +165,46 @@ __global__ void __launch_bounds__(kThreads)
     const int y0 = band * h, y1 = min(H, y0 + h);
 
     stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
-    for (int i = tid; i < kMaxBand * NW; i += kThreads) (&row_acc[0][0])[i] = 0;
+    for (int i = tid; i < kMaxBand * NE; i += kThreads) (&row_acc[0][0])[i] = 0;
     __syncthreads();
 
-    uint32_t col[kQ][NWD];
+    uint32_t bv4[WIN];
+#pragma unroll
+    for (int b = 0; b < WIN; ++b) bv4[b] = (uint32_t)(bin_base + b) * 0x01010101u;
+    // col[c][m]: counts over the band's rows of bins 4m..4m+3 in column c (8-bit fields)
+    uint32_t col[kQ][NM];
 #pragma unroll
     for (int c = 0; c < kQ; ++c)
 #pragma unroll
-        for (int k = 0; k < NWD; ++k) col[c][k] = 0;
+        for (int m = 0; m < NM; ++m) col[c][m] = 0;
 
     for (int y = y0; y < y1; ++y) {
-        uint32_t v[kQ];
-        {
-            const uint32_t w = band_bins[y - y0][tid];
+        const uint32_t w = band_bins[y - y0][tid];
+        uint32_t rowt[NM];
 #pragma unroll
-            for (int c = 0; c < kQ; ++c) v[c] = (w >> (8 * c)) & 0xFFu;
-        }
-        uint32_t rowp[NW];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) rowp[k] = 0;
-#pragma unroll
-        for (int c = 0; c < kQ; ++c) {
-            const uint32_t u = v[c] - (uint32_t)bin_base;
-            if (u < WIN) {
-                const uint32_t inc8 = 1u << ((u & 3) << 3);
-                const uint32_t inc16 = 1u << ((u & 1) << 4);
-#pragma unroll
-                for (int k = 0; k < NWD; ++k) col[c][k] += ((u >> 2) == (uint32_t)k) ? inc8 : 0u;
-#pragma unroll
-                for (int k = 0; k < NW; ++k) rowp[k] += ((u >> 1) == (uint32_t)k) ? inc16 : 0u;
-            }
+        for (int m = 0; m < NM; ++m) {
+            const uint32_t e0 = onehot4(w, bv4[4 * m]), e1 = onehot4(w, bv4[4 * m + 1]);
+            const uint32_t e2 = onehot4(w, bv4[4 * m + 2]), e3 = onehot4(w, bv4[4 * m + 3]);
+            // 4x4 byte transpose: per bin (bytes = columns) -> per column (bytes = bins)
+            const uint32_t lo01 = __byte_perm(e0, e1, 0x5140), lo23 = __byte_perm(e2, e3, 0x5140);
+            const uint32_t hi01 = __byte_perm(e0, e1, 0x7362), hi23 = __byte_perm(e2, e3, 0x7362);
+            const uint32_t t0 = __byte_perm(lo01, lo23, 0x5410), t1 = __byte_perm(lo01, lo23, 0x7632);
+            const uint32_t t2 = __byte_perm(hi01, hi23, 0x5410), t3 = __byte_perm(hi01, hi23, 0x7632);
+            col[0][m] += t0;
+            col[1][m] += t1;
+            col[2][m] += t2;
+            col[3][m] += t3;
+            rowt[m] = (t0 + t1) + (t2 + t3);
         }
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            uint32_t s = rowp[k];
+        for (int m = 0; m < NM; ++m) {
+            uint32_t s = rowt[m];  // 8-bit fields: a warp's row count is at most 128
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-            if (lane == 0 && s) atomicAdd(&row_acc[y - y0][k], s);
+            if (lane == 0 && s) {
+                atomicAdd(&row_acc[y - y0][2 * m], even16(s));
+                atomicAdd(&row_acc[y - y0][2 * m + 1], odd16(s));
+            }
         }
     }
     // per-column counts of the band
@@ -197,18 +213,18 @@ __global__ void __launch_bounds__(kThreads)
         for (int c = 0; c < kQ; ++c)
             if (c < ncol)
 #pragma unroll
-                for (int k = 0; k < NWD; ++k) ws.colcnt[((size_t)band * NWD + k) * W + x0 + c] = col[c][k];
+                for (int m = 0; m < NM; ++m) ws.colcnt[((size_t)band * NM + m) * W + x0 + c] = col[c][m];
     }
     __syncthreads();
     // per-row counts of the group, and the tile total
     for (int i = tid; i < (y1 - y0) * WIN; i += kThreads) {
         const int r = i / WIN, b = i - r * WIN;
-        const uint32_t w = row_acc[r][b >> 1];
-        ws.rowcnt[((size_t)(y0 + r) * n_groups + g) * WIN + b] = (uint16_t)((w >> ((b & 1) << 4)) & 0xFFFFu);
+        const uint32_t v = (row_acc[r][e_word(b)] >> (16 * e_half(b))) & 0xFFFFu;
+        ws.rowcnt[((size_t)(y0 + r) * n_groups + g) * WIN + b] = (uint16_t)v;
     }
     if (tid < WIN) {
         uint32_t t = 0;
-        for (int r = 0; r < y1 - y0; ++r) t += (row_acc[r][tid >> 1] >> ((tid & 1) << 4)) & 0xFFFFu;
+        for (int r = 0; r < y1 - y0; ++r) t += (row_acc[r][e_word(tid)] >> (16 * e_half(tid))) & 0xFFFFu;
         ws.bt[((size_t)g * WIN + tid) * n_bands + band] = t;
     }
 }
@@ -313,11 +329,12 @@ template <int WIN, typename OutT>
 __global__ void __launch_bounds__(kThreads)
     ii_tile_scan_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_groups, int bin_base,
                         int n_bins, bool vec, Ws ws, OutT* __restrict__ ii) {
-    constexpr int NW = WIN / 2;
+    constexpr int NM = WIN / 4;  // 8-bit-field words (4 bins each)
+    constexpr int NE = WIN / 2;  // 16-bit-field words (2 bins each, e_word/e_half pairing)
     __shared__ int corner_s[WIN];
-    __shared__ uint32_t rl_s[kMaxBand][NW];
+    __shared__ uint32_t rl_s[kMaxBand][NE];
     __shared__ int wtot_init[kWarps][WIN];
-    __shared__ uint32_t wtot[2][kWarps][NW];
+    __shared__ uint32_t wtot[2][kWarps][NM];
 
     const int band = blockIdx.x, g = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -334,13 +351,14 @@ __global__ void __launch_bounds__(kThreads)
         for (int gg = 0; gg < g; ++gg) s += __ldg(ws.gv + ((size_t)band * n_groups + gg) * WIN + tid);
         corner_s[tid] = (int)s;
     }
-    for (int i = tid; i < (y1 - y0) * NW; i += kThreads) {
-        const int r = i / NW, k = i - r * NW;
+    for (int i = tid; i < (y1 - y0) * NE; i += kThreads) {
+        const int r = i / NE, k = i - r * NE;
+        const int blo = 4 * (k >> 1) + (k & 1), bhi = blo + 2;  // the bins of E[k]
         uint32_t lo = 0, hi = 0;
-        const uint16_t* rc = ws.rowcnt + (size_t)(y0 + r) * n_groups * WIN + 2 * k;
+        const uint16_t* rc = ws.rowcnt + (size_t)(y0 + r) * n_groups * WIN;
         for (int gg = 0; gg < g; ++gg) {
-            lo += __ldg(rc + gg * WIN);
-            hi += __ldg(rc + gg * WIN + 1);
+            lo += __ldg(rc + gg * WIN + blo);
+            hi += __ldg(rc + gg * WIN + bhi);
         }
         rl_s[r][k] = lo | (hi << 16);
     }
@@ -390,61 +408,64 @@ __global__ void __launch_bounds__(kThreads)
         for (int c = 0; c < kQ; ++c) acc[c][b] += off;
     }
 
-    // rows of the band
+    // rows of the band: ii(x, y) = ii(x, y-1) + R(x, y), R = row prefix of
+    // the one-hot row = RL(y) + (count left of this thread in the group)
+    //                        + (count in this thread's columns up to x)
+    uint32_t bv4[WIN];
+#pragma unroll
+    for (int b = 0; b < WIN; ++b) bv4[b] = (uint32_t)(bin_base + b) * 0x01010101u;
+    const size_t plane = (size_t)H * W;
+    OutT* out_row = ii + (size_t)bin_base * plane + (size_t)y0 * W + x0;
     int buf = 0;
-    for (int y = y0; y < y1; ++y) {
-        uint32_t v[kQ];
-        {
-            const uint32_t w = band_bins[y - y0][tid];
+    for (int y = y0; y < y1; ++y, out_row += W) {
+        const uint32_t w = band_bins[y - y0][tid];
+        // pre4[b] byte c = count of bin b in this thread's columns 0..c
+        uint32_t pre4[WIN];
 #pragma unroll
-            for (int c = 0; c < kQ; ++c) v[c] = (w >> (8 * c)) & 0xFFu;
+        for (int b = 0; b < WIN; ++b) pre4[b] = onehot4(w, bv4[b]) * 0x01010101u;
+        // thread totals (8-bit fields) and their inclusive warp scan
+        uint32_t T[NM], S[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            T[m] = __byte_perm(__byte_perm(pre4[4 * m], pre4[4 * m + 1], 0x0073),
+                               __byte_perm(pre4[4 * m + 2], pre4[4 * m + 3], 0x0073), 0x5410);
+            S[m] = T[m];
         }
-        uint32_t run[NW], pre[kQ][NW];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) run[k] = 0;
-#pragma unroll
-        for (int c = 0; c < kQ; ++c) {
-            const uint32_t u = v[c] - (uint32_t)bin_base;
-            const uint32_t inc = (u < WIN) ? (1u << ((u & 1) << 4)) : 0u;
-            const uint32_t kw = u >> 1;
-#pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                run[k] += (kw == (uint32_t)k) ? inc : 0u;
-                pre[c][k] = run[k];
-            }
-        }
-        uint32_t sc[NW];
-#pragma unroll
-        for (int k = 0; k < NW; ++k) sc[k] = run[k];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, sc[k], d);
-                if (lane >= d) sc[k] += t;
+            for (int m = 0; m < NM; ++m) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, S[m], d);
+                if (lane >= d) S[m] += t;  // a warp's row count per bin is at most 128
             }
         }
         if (lane == 31) {
 #pragma unroll
-            for (int k = 0; k < NW; ++k) wtot[buf][warp][k] = sc[k];
+            for (int m = 0; m < NM; ++m) wtot[buf][warp][m] = S[m];
         }
         __syncthreads();
-        uint32_t base[NW];
+        // exclusive offset of this thread's first column, 16-bit fields
+        uint32_t E[NE];
 #pragma unroll
-        for (int k = 0; k < NW; ++k) {
-            uint32_t off = rl_s[y - y0][k] + sc[k] - run[k];
-            for (int w = 0; w < warp; ++w) off += wtot[buf][w][k];
-            base[k] = off;
+        for (int m = 0; m < NM; ++m) {
+            const uint32_t x = S[m] - T[m];
+            E[2 * m] = rl_s[y - y0][2 * m] + even16(x);
+            E[2 * m + 1] = rl_s[y - y0][2 * m + 1] + odd16(x);
+        }
+        for (int w2 = 0; w2 < warp; ++w2) {
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const uint32_t t = wtot[buf][w2][m];
+                E[2 * m] += even16(t);
+                E[2 * m + 1] += odd16(t);
+            }
         }
         buf ^= 1;
 #pragma unroll
-        for (int c = 0; c < kQ; ++c) {
+        for (int b = 0; b < WIN; ++b) {
+            const uint32_t base = (E[e_word(b)] >> (16 * e_half(b))) & 0xFFFFu;
 #pragma unroll
-            for (int k = 0; k < NW; ++k) {
-                const uint32_t r = base[k] + pre[c][k];
-                acc[c][2 * k] += (int)(r & 0xFFFFu);
-                acc[c][2 * k + 1] += (int)(r >> 16);
-            }
+            for (int c = 0; c < kQ; ++c) acc[c][b] += (int)(base + ((pre4[b] >> (8 * c)) & 0xFFu));
         }
         if (ncol > 0) {
 #pragma unroll
@@ -453,7 +474,7 @@ __global__ void __launch_bounds__(kThreads)
                     int vals[kQ];
 #pragma unroll
                     for (int c = 0; c < kQ; ++c) vals[c] = acc[c][b];
-                    store4<OutT>(ii + (((size_t)(bin_base + b)) * H + y) * W + x0, vals, ncol, vec);
+                    store4<OutT>(out_row + (size_t)b * plane, vals, ncol, vec);
                 }
             }
         }

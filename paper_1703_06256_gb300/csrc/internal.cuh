@@ -12,6 +12,8 @@ namespace fasthog {
 
 constexpr int kLutSide = HOG_LUT_SIDE;   // 511
 constexpr int kLutPitch = HOG_LUT_PITCH; // 512
+constexpr int kLutQuadOffset = HOG_LUT_QUAD_OFFSET;
+constexpr int kLutTotal = HOG_LUT_BYTES;
 constexpr int kDMax = 255;
 constexpr int kMaxBins = 64;
 constexpr uint8_t kNoBin = HOG_NO_BIN;
@@ -48,7 +50,7 @@ hog_status launch_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dty
 hog_status launch_score_cuda_cores(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins,
                                    int cells_x, int cells_y, int r, const void* w, int w_dtype,
                                    float bias, void* scores, cudaStream_t st);
-bool score_slide_supported(const void* cells, int n_bins, int cells_x, int cells_y);
+bool score_slide_supported(const void* cells, int n_bins, int cells_x, int cells_y, int r);
 hog_status launch_score_slide(const void* cells, int cell_dtype, int ncx, int ncy, int r, const void* w,
                               int w_dtype, float bias, void* scores, cudaStream_t st);
 bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx);

@@ -21,22 +21,20 @@
 // (|dx| + |dy|) * 0.5 * 2^-40 < 2.4e-10, far below the smallest true
 // |cross product| of any lattice point against such a boundary (about
 // 9.2e-6 over all N_b <= 64).
+//
+// The buffer also carries a contiguous copy of one quadrant of the table
+// (dx in 1..255, dy in 0..255, rows of 256 bytes), which the bin-map kernel
+// pulls into shared memory with a single bulk copy.
 #include <cmath>
 
 #include "internal.cuh"
 
 namespace fasthog {
 
-__global__ void __launch_bounds__(256) build_lut_kernel(LutParams p, uint8_t* __restrict__ lut) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= kLutSide * kLutPitch) return;
-    const int dy = idx / kLutPitch - kDMax;
-    const int col = idx % kLutPitch;
-    const int dx = col - kDMax;
-    if (col == kLutSide || (dx == 0 && dy == 0)) {  // pad byte, or no angle
-        lut[idx] = kNoBin;
-        return;
-    }
+namespace {
+
+// Bin of the gradient (dx, dy) != (0, 0), decided exactly as described above.
+__device__ __forceinline__ int exact_bin(const LutParams& p, int dx, int dy) {
     int q;
     if (dx > 0 && dy >= 0) q = 0;
     else if (dx <= 0 && dy > 0) q = 1;
@@ -55,12 +53,35 @@ __global__ void __launch_bounds__(256) build_lut_kernel(LutParams p, uint8_t* __
             break;
         }
     }
-    lut[idx] = static_cast<uint8_t>(bin);
+    return bin;
 }
 
+// Entries [0, 511*512): the table, row dy + 255, column dx + 255, pad column 511.
+// Entries [511*512, +65536): the quadrant copy, row dy (0..255), column dx - 1
+// (dx = 1..256; dx = 256 is outside the table and holds 0xFF).
+__global__ void __launch_bounds__(256) build_lut_kernel(LutParams p, uint8_t* __restrict__ lut) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= kLutTotal) return;
+    int dx, dy;
+    bool pad;
+    if (idx < kLutSide * kLutPitch) {
+        dy = idx / kLutPitch - kDMax;
+        const int col = idx % kLutPitch;
+        dx = col - kDMax;
+        pad = col == kLutSide;
+    } else {
+        const int q = idx - kLutSide * kLutPitch;
+        dy = q >> 8;
+        dx = (q & 255) + 1;
+        pad = dx > kDMax;
+    }
+    lut[idx] = (pad || (dx == 0 && dy == 0)) ? kNoBin : static_cast<uint8_t>(exact_bin(p, dx, dy));
+}
+
+}  // namespace
+
 hog_status launch_build_lut(const LutParams& p, uint8_t* lut, cudaStream_t st) {
-    const int n = kLutSide * kLutPitch;
-    build_lut_kernel<<<ceil_div(n, 256), 256, 0, st>>>(p, lut);
+    build_lut_kernel<<<ceil_div(kLutTotal, 256), 256, 0, st>>>(p, lut);
     return check_launch();
 }
 

@@ -75,57 +75,89 @@ __device__ __forceinline__ float wval<uint16_t>(const uint16_t* w, int k) { retu
 template <>
 __device__ __forceinline__ float wval<int8_t>(const int8_t* w, int k) { return (float)__ldg(w + k); }
 
+// Shared-memory block of cells for one work item: cell rows py0 .. py0 + RB - 1 + 15 r
+// (RB = 8 / r output rows) and the cell columns of one segment of T windows
+// for all r residues.  Rows are stored grouped by residue class (row % r), so
+// the 16 rows a half-warp reads (py + j r, j < 16) are consecutive; the row
+// stride is an odd number of 16-byte slots, so 8 consecutive rows fall in 8
+// different bank groups.
+struct SlideGeom {
+    int r, rb, T, rows, cols, rpc, stride4;  // stride4: float4 slots per smem row
+    __host__ __device__ SlideGeom(int r_, int T_) : r(r_), rb(8 / r_), T(T_) {
+        rows = rb + (kCY - 1) * r;
+        cols = r * (T + kCX - 1);
+        rpc = (rows + r - 1) / r;
+        stride4 = 2 * cols + 1;
+    }
+    __host__ __device__ size_t smem_bytes() const { return (size_t)r * rpc * stride4 * 16; }
+    __host__ __device__ int ridx(int row) const { return (row % r) * rpc + row / r; }
+};
+
 template <typename CellT, typename WT, typename OutT>
 __global__ void __launch_bounds__(kThreads, 3)
-    score_slide_kernel(const CellT* __restrict__ cells, int ncx, int r, const WT* __restrict__ w, float bias, int nx,
-                       int ny, int T, int S, long Q, OutT* __restrict__ scores) {
-    const int lane = threadIdx.x & 31;
-    const int j = lane & 15, half = lane >> 4;
+    score_slide_kernel(const CellT* __restrict__ cells, int ncx, int ncy, int r, int T, const WT* __restrict__ w,
+                       float bias, int nx, int ny, int S, int n_items, OutT* __restrict__ scores) {
+    extern __shared__ __align__(16) float4 blk[];
+    const SlideGeom G(r, T);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = lane & 15;
+    const int seq = warp * 2 + (lane >> 4);  // 0..7: (output row offset, residue)
+    const int dpy = seq / r, rho = seq % r;
     float wr[kCX][kNB];
 #pragma unroll
     for (int i = 0; i < kCX; ++i)
 #pragma unroll
         for (int b = 0; b < kNB; ++b) wr[i][b] = wval<WT>(w, (j * kCX + i) * kNB + b);
 
-    const long warps_total = (long)gridDim.x * (kThreads / 32);
-    const long warp0 = (long)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
-    for (long pair = warp0; 2 * pair < Q; pair += warps_total) {
-        const long q = 2 * pair + half;
-        const bool seq_ok = q < Q;
-        // q = (py * S + s) * r + rho
-        const long qq = seq_ok ? q : 0;
-        const int rho = (int)(qq % r);
-        const long t2 = qq / r;
-        const int s = (int)(t2 % S);
-        const int py = (int)(t2 / S);
-        const int row = py + j * r;
-        const CellT* rowp = cells + (size_t)row * ncx * kNB;
-        const int u0 = s * T;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const int s = item % S, rblk = item / S;
+        const int py0 = rblk * G.rb, u0 = s * T;
+        const int cx0 = r * u0;  // first cell column of the block
+        __syncthreads();          // the previous item's reads are done
+        for (int idx = threadIdx.x; idx < G.rows * G.cols; idx += kThreads) {
+            const int row = idx / G.cols, col = idx - row * G.cols;
+            const int gy = py0 + row, gx = cx0 + col;
+            float c[kNB];
+            load_cell<CellT>(cells + ((size_t)gy * ncx + gx) * kNB, gy < ncy && gx < ncx, c);
+            float4* d = blk + (size_t)G.ridx(row) * G.stride4 + 2 * col;
+            d[0] = make_float4(c[0], c[1], c[2], c[3]);
+            d[1] = make_float4(c[4], c[5], c[6], c[7]);
+        }
+        __syncthreads();
+        const int py = py0 + dpy;
+        const bool seq_ok = py < ny;
+        // smem row of filter row j for this sequence, and the first cell column
+        const float4* rowp = blk + (size_t)G.ridx(dpy + j * r) * G.stride4 + 2 * rho;
         float ring[kCX][kNB];
 #pragma unroll
         for (int i = 0; i < kCX - 1; ++i) {
-            const int pos = rho + r * (u0 + i);
-            load_cell<CellT>(rowp + (size_t)pos * kNB, seq_ok && pos < ncx, ring[i]);
+            const float4 a = rowp[2 * r * i], b2 = rowp[2 * r * i + 1];
+            ring[i][0] = a.x; ring[i][1] = a.y; ring[i][2] = a.z; ring[i][3] = a.w;
+            ring[i][4] = b2.x; ring[i][5] = b2.y; ring[i][6] = b2.z; ring[i][7] = b2.w;
         }
-        for (int blk = 0; blk < T; blk += kCX) {
+        for (int blk8 = 0; blk8 < T; blk8 += kCX) {
 #pragma unroll
             for (int t = 0; t < kCX; ++t) {
-                const int u = u0 + blk + t;
-                const int pos_new = rho + r * (u + kCX - 1);
-                load_cell<CellT>(rowp + (size_t)pos_new * kNB, seq_ok && pos_new < ncx, ring[(t + kCX - 1) % kCX]);
+                const int tt = blk8 + t;
+                {
+                    const int slot = (t + kCX - 1) % kCX;
+                    const float4 a = rowp[2 * r * (tt + kCX - 1)], b2 = rowp[2 * r * (tt + kCX - 1) + 1];
+                    ring[slot][0] = a.x; ring[slot][1] = a.y; ring[slot][2] = a.z; ring[slot][3] = a.w;
+                    ring[slot][4] = b2.x; ring[slot][5] = b2.y; ring[slot][6] = b2.z; ring[slot][7] = b2.w;
+                }
                 float part[kCX];
 #pragma unroll
                 for (int i = 0; i < kCX; ++i) {
                     const float* c = ring[(t + i) % kCX];
-                    float a = wr[i][0] * c[0];
+                    float acc = wr[i][0] * c[0];
 #pragma unroll
-                    for (int b = 1; b < kNB; ++b) a = fmaf(wr[i][b], c[b], a);
-                    part[i] = a;
+                    for (int b = 1; b < kNB; ++b) acc = fmaf(wr[i][b], c[b], acc);
+                    part[i] = acc;
                 }
                 float p = ((part[0] + part[1]) + (part[2] + part[3])) + ((part[4] + part[5]) + (part[6] + part[7]));
 #pragma unroll
                 for (int off = 8; off > 0; off >>= 1) p += __shfl_xor_sync(0xffffffffu, p, off);
-                const int px = rho + r * u;
+                const int px = rho + r * (u0 + tt);
                 if (j == 0 && seq_ok && px < nx) {
                     const float sc = p + bias;
                     if constexpr (std::is_same<OutT, int32_t>::value) {
@@ -144,20 +176,20 @@ hog_status launch_t(const void* cells, int ncx, int ncy, int r, const void* w, f
                     cudaStream_t st) {
     const int nx = ncx - (kCX - 1) * r, ny = ncy - (kCY - 1) * r;
     if (nx <= 0 || ny <= 0) return HOG_OK;
+    const int T = r <= 2 ? 16 : 8;
+    const SlideGeom G(r, T);
     const int per_class = (nx + r - 1) / r;
-    // segments of 16 windows when that still gives every SM several warps
-    int T = 16;
-    long Q = (long)ny * r * ((per_class + T - 1) / T);
-    if (Q / 2 < 4L * sm_count() * 4) T = 8;
     const int S = (per_class + T - 1) / T;
-    Q = (long)ny * r * S;
-    const long warps = (Q + 1) / 2;
-    const long blocks_needed = (warps + kThreads / 32 - 1) / (kThreads / 32);
-    const long cap = 3L * sm_count() * 4;
-    const int grid = (int)(blocks_needed < cap ? blocks_needed : cap);
-    score_slide_kernel<CellT, WT, OutT><<<grid, kThreads, 0, st>>>(static_cast<const CellT*>(cells), ncx, r,
-                                                                    static_cast<const WT*>(w), bias, nx, ny, T, S, Q,
-                                                                    static_cast<OutT*>(scores));
+    const int n_items = ((ny + G.rb - 1) / G.rb) * S;
+    const size_t smem = G.smem_bytes();
+    auto kern = score_slide_kernel<CellT, WT, OutT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int per_sm = smem <= 70 * 1024 ? 3 : (smem <= 110 * 1024 ? 2 : 1);
+    const int cap = per_sm * sm_count();
+    const int grid = n_items < cap ? n_items : cap;
+    kern<<<grid, kThreads, smem, st>>>(static_cast<const CellT*>(cells), ncx, ncy, r, T, static_cast<const WT*>(w),
+                                       bias, nx, ny, S, n_items, static_cast<OutT*>(scores));
     return check_launch();
 }
 
@@ -174,8 +206,9 @@ hog_status by_weight(const void* cells, int ncx, int ncy, int r, const void* w, 
 
 }  // namespace
 
-bool score_slide_supported(const void* cells, int n_bins, int cells_x, int cells_y) {
-    return n_bins == kNB && cells_x == kCX && cells_y == kCY && reinterpret_cast<uintptr_t>(cells) % 16 == 0;
+bool score_slide_supported(const void* cells, int n_bins, int cells_x, int cells_y, int r) {
+    return n_bins == kNB && cells_x == kCX && cells_y == kCY && reinterpret_cast<uintptr_t>(cells) % 16 == 0 &&
+           (r == 1 || r == 2 || r == 4);
 }
 
 hog_status launch_score_slide(const void* cells, int cell_dtype, int ncx, int ncy, int r, const void* w, int w_dtype,

@@ -42,9 +42,12 @@ def rand_img(H, W, ch, seed):
 # ---------------------------------------------------------------- table
 @pytest.mark.parametrize("nb", [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 16, 17, 31, 32, 64])
 def test_lut_exhaustive(fh, g, nb):
-    lut = g.gpu_lut(nb).cpu().numpy().reshape(511, 512)
+    buf = g.gpu_lut(nb).cpu().numpy()
+    lut = buf[: fh.HOG_LUT_QUAD_OFFSET].reshape(511, 512)
     assert np.all(lut[:, 511] == 255)  # pad column
     assert np.array_equal(lut[:, :511].reshape(-1), oracle.lut(nb))
+    quad = buf[fh.HOG_LUT_QUAD_OFFSET:].reshape(256, 256)  # row dy, column dx - 1
+    assert np.array_equal(quad[:, :255], lut[255:, 256:511]) and np.all(quad[:, 255] == 255)
 
 
 # ---------------------------------------------------------------- bin map
