@@ -10,7 +10,7 @@
 //
 // Eq. 1 runs four channel values per instruction: the right and left
 // neighbours of the quad's 4 x C channel values are realigned into words by
-// funnel shifts, then one vabsdiff4 gives |dx| and one vcmpgtu4 the sign of
+// funnel shifts, then one vabsdiffu4 gives |dx| and one vcmpgtu4 the sign of
 // dx for four values at once (likewise dy from the rows below and above).
 // Each channel value becomes a key (|dx|, |dy|, dx > 0, dy > 0) in one word;
 // dp4a of the key with its low half gives dx^2 + dy^2 for the channel
@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(kThreads)
             for (int k = 0; k < NV; ++k) {
                 const uint32_t rgt = __funnelshift_r(wc[k + (CH + 4) / 4], wc[k + (CH + 4) / 4 + 1], 8 * ((CH + 4) % 4));
                 const uint32_t lft = __funnelshift_r(wc[k], wc[k + 1], 8 * (4 - CH));
-                ax[k] = __vabsdiff4(rgt, lft);
+                ax[k] = __vabsdiffu4(rgt, lft);
                 gx[k] = __vcmpgtu4(rgt, lft);
-                ay[k] = __vabsdiff4(wd[k], wu[k]);
+                ay[k] = __vabsdiffu4(wd[k], wu[k]);
                 gy[k] = __vcmpgtu4(wd[k], wu[k]);
             }
             if (!lut_ready) {
