@@ -8,13 +8,11 @@
 // 4-byte aligned images load without bounds tests; edge quads and unaligned
 // images take a guarded byte path.
 //
-// Eq. 1 runs four channel values per instruction: the right and left
-// neighbours of the quad's 4 x C channel values are realigned into words by
-// funnel shifts, then one vabsdiffu4 gives |dx| and one vcmpgtu4 the sign of
-// dx for four values at once (likewise dy from the rows below and above).
-// Each channel value becomes a key (|dx|, |dy|, dx > 0, dy > 0) in one word;
-// dp4a of the key with its low half gives dx^2 + dy^2 for the channel
-// choice (strongest channel, ties to the lowest index).
+// Every byte position inside the loaded words is a compile-time constant, so
+// Eq. 1 for the 4 x C channel values is register arithmetic: byte
+// extraction, differences, dx^2 + dy^2 per channel and the strongest
+// channel (ties to the lowest index).  A thread takes two quads per
+// iteration and issues both quads' loads before using either.
 //
 // The table lives in shared memory.  The full 511 x 511 table (255.5 KiB)
 // does not fit, so when 4 divides N_b the CTA holds one quadrant only:
@@ -22,8 +20,7 @@
 // quarter turn (dx, dy) -> (-dy, dx) adds pi/2 to the angle and, because
 // the sectors are half-open and N_b/4 of them span pi/2, adds exactly N_b/4
 // to the bin.  So any gradient is turned into that quadrant by q quarter
-// turns -- which lands on (|dx|, |dy|) for even q and on (|dy|, |dx|) for odd
-// q -- and its bin is (quadrant entry + q * N_b/4) mod N_b.  The quadrant
+// turns and its bin is (quadrant entry + q * N_b/4) mod N_b.  The quadrant
 // (stored contiguously after the table by hog_build_lut) arrives by one
 // 64 KiB bulk async copy that completes on an mbarrier, while the first
 // quads' pixels are loaded.  For other N_b the kernel reads the table
@@ -54,18 +51,106 @@ __device__ __forceinline__ uint32_t row_word(const uint8_t* __restrict__ row, lo
 
 // Byte i of a little-endian word array, i a compile-time constant.
 template <int N>
-__device__ __forceinline__ uint32_t byte_of(const uint32_t (&w)[N], int i) {
-    return (w[i >> 2] >> (8 * (i & 3))) & 0xFFu;
+__device__ __forceinline__ int byte_of(const uint32_t (&w)[N], int i) {
+    return (int)((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
 }
 
-// Key of channel value i: bytes (|dx|, |dy|, dx > 0 ? 0xFF : 0, dy > 0 ? 0xFF : 0).
-template <int N>
-__device__ __forceinline__ uint32_t key_of(const uint32_t (&ax)[N], const uint32_t (&ay)[N], const uint32_t (&gx)[N],
-                                           const uint32_t (&gy)[N], int i) {
-    const int k = i >> 2, b = i & 3;
-    const uint32_t mag = __byte_perm(ax[k], ay[k], (uint32_t)(b | ((b + 4) << 4)));
-    const uint32_t sgn = __byte_perm(gx[k], gy[k], (uint32_t)(b | ((b + 4) << 4)));
-    return __byte_perm(mag, sgn, 0x5410);
+template <int CH>
+struct QuadWords {
+    static constexpr int NC = CH == 3 ? 5 : 3;  // centre-row words, from byte CH*x - 4
+    static constexpr int NV = CH == 3 ? 3 : 1;  // rows above / below: the quad's own bytes
+    uint32_t wc[NC], wu[NV], wd[NV];
+};
+
+// Load the words of quad (x, y), 0 < y < H-1.  Interior quads of aligned
+// images load without bounds tests.
+template <int CH>
+__device__ __forceinline__ void load_quad(const uint8_t* __restrict__ img, size_t pitch, long row_bytes, bool aligned,
+                                          int x, int y, QuadWords<CH>& q) {
+    using Q = QuadWords<CH>;
+    const uint8_t* mid = img + (size_t)y * pitch;
+    const uint8_t* up = mid - pitch;
+    const uint8_t* dn = mid + pitch;
+    const long o = (long)x * CH;
+    if (aligned && x >= 4 && o + 4 * Q::NC - 4 <= row_bytes) {
+        const uint32_t* m4 = reinterpret_cast<const uint32_t*>(mid + o - 4);
+        const uint32_t* u4 = reinterpret_cast<const uint32_t*>(up + o);
+        const uint32_t* d4 = reinterpret_cast<const uint32_t*>(dn + o);
+#pragma unroll
+        for (int k = 0; k < Q::NC; ++k) q.wc[k] = __ldg(m4 + k);
+#pragma unroll
+        for (int k = 0; k < Q::NV; ++k) {
+            q.wu[k] = __ldg(u4 + k);
+            q.wd[k] = __ldg(d4 + k);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q::NC; ++k) q.wc[k] = row_word(mid, o - 4 + 4 * k, row_bytes, aligned);
+#pragma unroll
+        for (int k = 0; k < Q::NV; ++k) {
+            q.wu[k] = row_word(up, o + 4 * k, row_bytes, aligned);
+            q.wd[k] = row_word(dn, o + 4 * k, row_bytes, aligned);
+        }
+    }
+}
+
+// Eq. 1 and the table lookup for the 4 pixels of quad x (row loaded in q).
+// Channel c of pixel x + p: right neighbour at byte 4 + (p+1)*CH + c of wc,
+// left at 4 + (p-1)*CH + c, below / above at byte p*CH + c of wd / wu.
+template <int CH, bool QUAD>
+__device__ __forceinline__ uint32_t bins_of_quad(const QuadWords<CH>& q, int x, int W, const uint8_t* __restrict__ lutq,
+                                                 const uint8_t* __restrict__ lut, int nb, int nb4) {
+    uint32_t packed = 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        uint32_t bin = kNoBin;
+        const int xp = x + p;
+        if (xp > 0 && xp < W - 1) {
+            int dx = byte_of(q.wc, 4 + (p + 1) * CH) - byte_of(q.wc, 4 + (p - 1) * CH);
+            int dy = byte_of(q.wd, p * CH) - byte_of(q.wu, p * CH);
+            if (CH == 3) {
+                int best = dx * dx + dy * dy;
+#pragma unroll
+                for (int c = 1; c < 3; ++c) {
+                    const int ddx = byte_of(q.wc, 4 + (p + 1) * CH + c) - byte_of(q.wc, 4 + (p - 1) * CH + c);
+                    const int ddy = byte_of(q.wd, p * CH + c) - byte_of(q.wu, p * CH + c);
+                    const int m = ddx * ddx + ddy * ddy;
+                    if (m > best) {  // strict: ties keep the lower channel
+                        best = m;
+                        dx = ddx;
+                        dy = ddy;
+                    }
+                }
+            }
+            if (dx != 0 || dy != 0) {
+                if (QUAD) {
+                    int qd, u, v;  // quadrant and quadrant-0 coordinates
+                    if (dx > 0 && dy >= 0) { qd = 0; u = dx; v = dy; }
+                    else if (dx <= 0 && dy > 0) { qd = 1; u = dy; v = -dx; }
+                    else if (dx < 0 && dy <= 0) { qd = 2; u = -dx; v = -dy; }
+                    else { qd = 3; u = -dy; v = dx; }
+                    const int t = lutq[v * 256 + u - 1] + qd * nb4;
+                    bin = t >= nb ? t - nb : t;
+                } else {
+                    bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
+                }
+            }
+        }
+        packed |= bin << (8 * p);
+    }
+    return packed;
+}
+
+__device__ __forceinline__ void store_quad(uint8_t* __restrict__ bins, int W, int x, int y, uint32_t packed,
+                                           bool word_stores) {
+    uint8_t* out = bins + (size_t)y * W + x;
+    if (word_stores && x + 3 < W) {
+        *reinterpret_cast<uint32_t*>(out) = packed;
+    } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+            if (x + e < W) out[e] = (uint8_t)(packed >> (8 * e));
+    }
 }
 
 template <int CH, bool QUAD>
@@ -73,8 +158,6 @@ __global__ void __launch_bounds__(kThreads)
     bin_map_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                    const uint8_t* __restrict__ lut, int nb, uint8_t* __restrict__ bins, bool word_stores,
                    unsigned int* status) {
-    constexpr int NC = CH == 3 ? 5 : 3;  // centre-row words, from byte 4*CH*quad - 4
-    constexpr int NV = CH == 3 ? 3 : 1;  // rows above / below: the quad's own bytes
     extern __shared__ __align__(128) uint8_t lutq[];
     __shared__ __align__(8) uint64_t lut_bar;
 
@@ -97,104 +180,30 @@ __global__ void __launch_bounds__(kThreads)
     const int qpr = (W + 3) >> 2;  // quads per row
     const long n_quads = (long)qpr * H;
     const long row_bytes = (long)W * CH;
-    for (long q = (long)blockIdx.x * kThreads + tid; q < n_quads; q += (long)gridDim.x * kThreads) {
-        const int y = (int)(q / qpr);
-        const int x = (int)(q - (long)y * qpr) * 4;
-        uint32_t packed = 0xFFFFFFFFu;  // border rows: no bins
-        if (y > 0 && y < H - 1) {
-            const uint8_t* mid = img + (size_t)y * pitch;
-            const uint8_t* up = mid - pitch;
-            const uint8_t* dn = mid + pitch;
-            const long o = (long)x * CH;
-            uint32_t wc[NC], wu[NV], wd[NV];
-            if (aligned && x >= 4 && o + 4 * NC - 4 <= row_bytes) {
-                const uint32_t* m4 = reinterpret_cast<const uint32_t*>(mid + o - 4);
-                const uint32_t* u4 = reinterpret_cast<const uint32_t*>(up + o);
-                const uint32_t* d4 = reinterpret_cast<const uint32_t*>(dn + o);
-#pragma unroll
-                for (int k = 0; k < NC; ++k) wc[k] = __ldg(m4 + k);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    wu[k] = __ldg(u4 + k);
-                    wd[k] = __ldg(d4 + k);
-                }
-            } else {
-#pragma unroll
-                for (int k = 0; k < NC; ++k) wc[k] = row_word(mid, o - 4 + 4 * k, row_bytes, aligned);
-#pragma unroll
-                for (int k = 0; k < NV; ++k) {
-                    wu[k] = row_word(up, o + 4 * k, row_bytes, aligned);
-                    wd[k] = row_word(dn, o + 4 * k, row_bytes, aligned);
-                }
+    const long step = (long)gridDim.x * kThreads;
+    // two quads per iteration (q and q + step): both loads are in flight together
+    for (long q0 = (long)blockIdx.x * kThreads + tid; q0 < n_quads; q0 += 2 * step) {
+        const long q1 = q0 + step;
+        const int y0 = (int)(q0 / qpr), x0 = (int)(q0 - (long)y0 * qpr) * 4;
+        const bool has1 = q1 < n_quads;
+        const int y1 = has1 ? (int)(q1 / qpr) : 0, x1 = has1 ? (int)(q1 - (long)y1 * qpr) * 4 : 0;
+        const bool in0 = y0 > 0 && y0 < H - 1, in1 = has1 && y1 > 0 && y1 < H - 1;
+        QuadWords<CH> a, b;
+        if (in0) load_quad<CH>(img, pitch, row_bytes, aligned, x0, y0, a);
+        if (in1) load_quad<CH>(img, pitch, row_bytes, aligned, x1, y1, b);
+        if (!lut_ready && (in0 || in1)) {
+            if (!ptx::mbar_wait_bounded(&lut_bar, 0, kWaitLimitNs)) {
+                atomicOr(status, kStatusTimeout);
+                return;  // nothing else of this CTA is in flight
             }
-            // channel value i = CH * p + c of pixel x + p: right neighbour at
-            // byte i + CH + 4 of wc, left neighbour at byte i - CH + 4
-            uint32_t ax[NV], ay[NV], gx[NV], gy[NV];
-#pragma unroll
-            for (int k = 0; k < NV; ++k) {
-                const uint32_t rgt = __funnelshift_r(wc[k + (CH + 4) / 4], wc[k + (CH + 4) / 4 + 1], 8 * ((CH + 4) % 4));
-                const uint32_t lft = __funnelshift_r(wc[k], wc[k + 1], 8 * (4 - CH));
-                ax[k] = __vabsdiffu4(rgt, lft);
-                gx[k] = __vcmpgtu4(rgt, lft);
-                ay[k] = __vabsdiffu4(wd[k], wu[k]);
-                gy[k] = __vcmpgtu4(wd[k], wu[k]);
-            }
-            if (!lut_ready) {
-                if (!ptx::mbar_wait_bounded(&lut_bar, 0, kWaitLimitNs)) {
-                    atomicOr(status, kStatusTimeout);
-                    return;  // nothing else of this CTA is in flight
-                }
-                lut_ready = true;
-            }
-            packed = 0;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                uint32_t bin = kNoBin;
-                const int xp = x + p;
-                if (xp > 0 && xp < W - 1) {
-                    uint32_t key = key_of(ax, ay, gx, gy, CH * p);
-                    if (CH == 3) {
-                        uint32_t best = __dp4a(key, key & 0xFFFFu, 0u);
-#pragma unroll
-                        for (int c = 1; c < 3; ++c) {
-                            const uint32_t kc = key_of(ax, ay, gx, gy, CH * p + c);
-                            const uint32_t m = __dp4a(kc, kc & 0xFFFFu, 0u);
-                            if (m > best) {  // strict: ties keep the lower channel
-                                best = m;
-                                key = kc;
-                            }
-                        }
-                    }
-                    const int adx = key & 0xFF, ady = (key >> 8) & 0xFF;
-                    if (adx | ady) {
-                        const int dx = (key & 0x00FF0000u) ? adx : -adx;
-                        const int dy = (key & 0xFF000000u) ? ady : -ady;
-                        if (QUAD) {
-                            int qd;
-                            if (dx > 0 && dy >= 0) qd = 0;
-                            else if (dx <= 0 && dy > 0) qd = 1;
-                            else if (dx < 0 && dy <= 0) qd = 2;
-                            else qd = 3;
-                            const int u = (qd & 1) ? ady : adx;  // quadrant-0 coordinates
-                            const int v = (qd & 1) ? adx : ady;
-                            const int t = lutq[v * 256 + u - 1] + qd * nb4;
-                            bin = t >= nb ? t - nb : t;
-                        } else {
-                            bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
-                        }
-                    }
-                }
-                packed |= bin << (8 * p);
-            }
+            lut_ready = true;
         }
-        uint8_t* out = bins + (size_t)y * W + x;
-        if (word_stores && x + 3 < W) {
-            *reinterpret_cast<uint32_t*>(out) = packed;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (x + e < W) out[e] = (uint8_t)(packed >> (8 * e));
-        }
+        // border rows hold no bins
+        store_quad(bins, W, x0, y0, in0 ? bins_of_quad<CH, QUAD>(a, x0, W, lutq, lut, nb, nb4) : 0xFFFFFFFFu,
+                   word_stores);
+        if (has1)
+            store_quad(bins, W, x1, y1, in1 ? bins_of_quad<CH, QUAD>(b, x1, W, lutq, lut, nb, nb4) : 0xFFFFFFFFu,
+                       word_stores);
     }
     if (QUAD && !lut_ready) {
         // This thread never needed the table: still let the copy land before

@@ -136,12 +136,30 @@ __device__ __forceinline__ void stage_band(const uint8_t* __restrict__ bins, int
     }
 }
 
-// SIMD-within-a-register helpers.  A thread's 4 bins sit in one 32-bit word,
+// SIMD-within-a-register helpers built from single integer instructions
+// (shifts, logic, add, multiply).  A thread's 4 bins sit in one 32-bit word,
 // one byte per column.
 //
-// One-hot of bin value v (bv4 = v in all four bytes): 0x01 in every byte
-// whose column holds bin v.
-__device__ __forceinline__ uint32_t onehot4(uint32_t w, uint32_t bv4) { return __vcmpeq4(w, bv4) & 0x01010101u; }
+// 1 << n, or 0 when n >= 32 (PTX clamps the shift amount).
+__device__ __forceinline__ uint32_t bit_or_zero(uint32_t n) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(n));
+    return r;
+}
+// Per-column one-hot masks of the bins [lo, lo + 8): byte c of the result has
+// bit k set iff column c holds bin lo + k (0xFF and bins outside the range
+// set nothing).
+__device__ __forceinline__ uint32_t onehot_cols8(uint32_t w, uint32_t lo) {
+    uint32_t p = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) p |= (bit_or_zero(((w >> (8 * c)) & 0xFFu) - lo) & 0xFFu) << (8 * c);
+    return p;
+}
+// Byte c = 1 iff column c holds bin lo + k.
+__device__ __forceinline__ uint32_t col_flags(uint32_t p, int k) { return (p >> k) & 0x01010101u; }
+// The 4 bits of a nibble to the 4 bytes (bit k -> byte k): the products
+// n_k * 2^(7j) land on a multiple of 8 only for j = k, without carries.
+__device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
 // Counts of 4 bins in 8-bit fields (word m: bins 4m..4m+3) widen to 16-bit
 // fields two bins per word, paired as E[2m] = (4m, 4m+2), E[2m+1] = (4m+1, 4m+3).
 __device__ __forceinline__ uint32_t even16(uint32_t t) { return t & 0x00FF00FFu; }
@@ -168,9 +186,6 @@ __global__ void __launch_bounds__(kThreads)
     for (int i = tid; i < kMaxBand * NE; i += kThreads) (&row_acc[0][0])[i] = 0;
     __syncthreads();
 
-    uint32_t bv4[WIN];
-#pragma unroll
-    for (int b = 0; b < WIN; ++b) bv4[b] = (uint32_t)(bin_base + b) * 0x01010101u;
     // col[c][m]: counts over the band's rows of bins 4m..4m+3 in column c (8-bit fields)
     uint32_t col[kQ][NM];
 #pragma unroll
@@ -182,19 +197,22 @@ __global__ void __launch_bounds__(kThreads)
         const uint32_t w = band_bins[y - y0][tid];
         uint32_t rowt[NM];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            const uint32_t e0 = onehot4(w, bv4[4 * m]), e1 = onehot4(w, bv4[4 * m + 1]);
-            const uint32_t e2 = onehot4(w, bv4[4 * m + 2]), e3 = onehot4(w, bv4[4 * m + 3]);
-            // 4x4 byte transpose: per bin (bytes = columns) -> per column (bytes = bins)
-            const uint32_t lo01 = __byte_perm(e0, e1, 0x5140), lo23 = __byte_perm(e2, e3, 0x5140);
-            const uint32_t hi01 = __byte_perm(e0, e1, 0x7362), hi23 = __byte_perm(e2, e3, 0x7362);
-            const uint32_t t0 = __byte_perm(lo01, lo23, 0x5410), t1 = __byte_perm(lo01, lo23, 0x7632);
-            const uint32_t t2 = __byte_perm(hi01, hi23, 0x5410), t3 = __byte_perm(hi01, hi23, 0x7632);
-            col[0][m] += t0;
-            col[1][m] += t1;
-            col[2][m] += t2;
-            col[3][m] += t3;
-            rowt[m] = (t0 + t1) + (t2 + t3);
+        for (int g8 = 0; g8 < (WIN + 7) / 8; ++g8) {
+            const uint32_t p = onehot_cols8(w, (uint32_t)(bin_base + 8 * g8));
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+                const int m = 2 * g8 + hh;  // bins 4m..4m+3 = nibble hh of each byte of p
+                if (m < NM) {
+                    uint32_t tsum = 0;
+#pragma unroll
+                    for (int c = 0; c < kQ; ++c) {
+                        const uint32_t t = spread4((p >> (8 * c + 4 * hh)) & 0xFu);
+                        col[c][m] += t;
+                        tsum += t;
+                    }
+                    rowt[m] = tsum;
+                }
+            }
         }
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
@@ -411,9 +429,6 @@ __global__ void __launch_bounds__(kThreads)
     // rows of the band: ii(x, y) = ii(x, y-1) + R(x, y), R = row prefix of
     // the one-hot row = RL(y) + (count left of this thread in the group)
     //                        + (count in this thread's columns up to x)
-    uint32_t bv4[WIN];
-#pragma unroll
-    for (int b = 0; b < WIN; ++b) bv4[b] = (uint32_t)(bin_base + b) * 0x01010101u;
     const size_t plane = (size_t)H * W;
     OutT* out_row = ii + (size_t)bin_base * plane + (size_t)y0 * W + x0;
     int buf = 0;
@@ -422,7 +437,12 @@ __global__ void __launch_bounds__(kThreads)
         // pre4[b] byte c = count of bin b in this thread's columns 0..c
         uint32_t pre4[WIN];
 #pragma unroll
-        for (int b = 0; b < WIN; ++b) pre4[b] = onehot4(w, bv4[b]) * 0x01010101u;
+        for (int g8 = 0; g8 < (WIN + 7) / 8; ++g8) {
+            const uint32_t p = onehot_cols8(w, (uint32_t)(bin_base + 8 * g8));
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+                if (8 * g8 + k < WIN) pre4[8 * g8 + k] = col_flags(p, k) * 0x01010101u;
+        }
         // thread totals (8-bit fields) and their inclusive warp scan
         uint32_t T[NM], S[NM];
 #pragma unroll
