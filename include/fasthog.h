@@ -224,6 +224,33 @@ hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int s
                       int image, int level, hog_det* out, int max_out, int32_t* d_count,
                       void* workspace, size_t workspace_bytes, hog_stream_t stream);
 
+/*
+ * hog_detect_noalloc -- hog_detect without a caller-provided workspace.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory for scratch -- for example a plugin that is
+ * handed only its input and output buffers by a host application that owns
+ * all device memory, or a latency-critical loop that must not call
+ * cudaMalloc.  It computes exactly what hog_detect computes (same arguments
+ * minus the workspace) and allocates nothing.
+ *
+ * Its scratch is a fixed 64 KiB array inside the library's device memory,
+ * which every GPU that loads the library holds until the process exits.
+ * Limits and rules:
+ *  - nx * ny <= HOG_DETECT_NOALLOC_MAX_SCORES, otherwise HOG_ERR_ARG and
+ *    nothing is enqueued;
+ *  - the first call on a device looks up the array's device address (a
+ *    host-side step, done once per device with that device current); make
+ *    that first call before capturing a stream into a graph;
+ *  - all calls share the array: calls whose work overlaps on the GPU (on
+ *    different streams, or from different host threads without ordering)
+ *    race and may return wrong lists.  Serialise them on one stream.
+ */
+#define HOG_DETECT_NOALLOC_MAX_SCORES (16384 * 2048)
+hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
+                              int image, int level, hog_det* out, int max_out, int32_t* d_count,
+                              hog_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -70,6 +70,7 @@ def _load() -> ctypes.CDLL:
         "hog_window_score": (I, [P, I, I, I, I, I, I, I, I, P, I, F, P, P]),
         "hog_detect_workspace_bytes": (Z, [I, I]),
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
+        "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -81,7 +82,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
-            "hog_detect_workspace_bytes", "hog_detect")
+            "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc")
 
 
 def lib() -> ctypes.CDLL:
@@ -165,6 +166,18 @@ def hog_detect(scores, score_dtype: int, nx: int, ny: int, stride: int, thr: flo
     _check("hog_detect", _lib.hog_detect(_ptr(scores), score_dtype, nx, ny, stride, float(thr), image, level,
                                          _ptr(out), max_out, _ptr(d_count), _ptr(workspace), workspace_bytes,
                                          _stream(stream)))
+
+
+def hog_detect_noalloc(scores, score_dtype: int, nx: int, ny: int, stride: int, thr: float, image: int, level: int,
+                       out, max_out: int, d_count, stream=None) -> None:
+    """hog_detect for callers that cannot allocate scratch: the library uses
+    a fixed array of its own (see include/fasthog.h for the limits)."""
+    _check("hog_detect_noalloc", _lib.hog_detect_noalloc(_ptr(scores), score_dtype, nx, ny, stride, float(thr),
+                                                         image, level, _ptr(out), max_out, _ptr(d_count),
+                                                         _stream(stream)))
+
+
+HOG_DETECT_NOALLOC_MAX_SCORES = 16384 * 2048
 
 
 # ---- shapes (host arithmetic only) --------------------------------------------
