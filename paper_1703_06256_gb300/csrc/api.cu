@@ -43,7 +43,7 @@ int sm_count() {
 
 // Device address of g_device_status on the current device (looked up once
 // per device, with that device current).
-static hog_status status_word(unsigned int** out) {
+hog_status device_status_word(unsigned int** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e);
@@ -86,7 +86,7 @@ int hog_version(void) { return 100; }
 hog_status hog_device_status(uint32_t* flags, int clear) {
     if (flags == nullptr) return HOG_ERR_ARG;
     unsigned int* p = nullptr;
-    hog_status s = status_word(&p);
+    hog_status s = device_status_word(&p);
     if (s != HOG_OK) return s;
     unsigned int v = 0;
     cudaError_t e = cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost);
@@ -132,7 +132,7 @@ hog_status hog_bin_map(const uint8_t* img, int W, int H, int channels, size_t pi
     if (pitch_bytes < (size_t)W * channels || n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(lut) % 16 != 0) return HOG_ERR_ARG;
     unsigned int* status = nullptr;
-    hog_status s = status_word(&status);
+    hog_status s = device_status_word(&status);
     if (s != HOG_OK) return s;
     return launch_bin_map(img, W, H, channels, pitch_bytes, lut, n_bins, bins, status,
                           reinterpret_cast<cudaStream_t>(stream));

@@ -25,6 +25,8 @@ hog_status cuda_fail(cudaError_t e);
 hog_status check_launch();
 // Number of SMs of the current device (cached per device).
 int sm_count();
+// Device address of the library's status word on the current device.
+hog_status device_status_word(unsigned int** out);
 
 // ---- launchers (one per kernel family), called by api.cu after argument checks
 struct LutParams {

@@ -1,14 +1,330 @@
-// score_tc.cu -- window score on the tensor cores (tcgen05 implicit GEMM).
-// Placeholder until the tensor-core kernel lands: reports no support, so
-// hog_window_score uses the CUDA-core kernel for every weight type.
+// score_tc.cu -- window score on the tensor cores (tcgen05), as an implicit
+// GEMM (the paper's linear score, Sections 1 and 4: the inner product of the
+// window feature with a weight vector at every scan position).
+//
+//   S[py][px] = bias + sum_{j<16} sum_{i<8} sum_{b<8} w[j][i][b] * C[py + j r][px + i r][b]
+//
+// Output rows split into r residue classes: class phi holds the rows
+// py = py_lo + phi + r t (t < Tc), and they read only the cell rows
+// rho = py_lo + phi + r rho' of the same class (rho' < Tc + 15), with
+// py + j r = rho  <=>  j = rho' - t.  So for one cell row rho',
+//
+//   S[t][px] += sum_{i, b} C_rho'[px + i r][b] * Wband_rho'[t][(i, b)],
+//   Wband_rho'[t][(i, b)] = w[rho' - t][i][b]  (0 unless 0 <= rho' - t < 16)
+//
+// is a GEMM with M = 128 windows px, N = Tc output rows, K = 8 cells x 8
+// bins = 64, accumulated over the Tc + 15 cell rows of the class into one
+// fixed block of Tc TMEM columns.
+//
+// Neither operand is materialised per row.  A: in shared memory a cell row is
+// kept as in HBM, [px][8 bins] bf16 = 16 bytes per cell, so the 8 x 16-byte
+// core matrix (windows px0 + 8g .. +7, cell i) starts at byte (8g + i r) * 16:
+// the descriptor of an MMA over cells i, i+1 points at cell i r with a
+// K-direction core-matrix stride (LBO) of r * 16 bytes and an M-direction
+// stride (SBO) of 128 bytes -- an im2col done by the descriptor.  B: for each
+// cell i the 16 filter rows sit in a zero-padded, reversed plane
+// plane_i[v] = w[Tc + 14 - v][i] (16 bytes each); rows t = 0..Tc-1 of
+// Wband_rho' are the consecutive plane rows v = Tc + 14 - rho' + t, so the
+// band of cell row rho' is the same planes with the descriptor start moved
+// back 16 bytes per row (LBO = plane size, SBO = 128 bytes).
+//
+// One CTA: 128 windows (one TMEM lane each) by Tc * r output rows; 4 warps.
+// Warp 0 lane 0 streams cell rows into a ring of shared-memory stages with
+// bulk async copies (mbarrier full/empty pipeline), warp 1 lane 0 issues
+// the MMAs (the first of each class overwrites its columns, the rest
+// accumulate), then all four warps read their 32 TMEM lanes back
+// (tcgen05.ld), add the bias and store.  Every wait is bounded: on a timeout
+// the kernel flags the device status, lets its copies and MMAs drain (again
+// bounded), frees its TMEM and returns.
+//
+// Exactness: bin counts (<= 64) are exact in bf16, products of bf16 values
+// are exact in fp32.  With int8 weights (exact in bf16) every partial sum is
+// an integer of magnitude <= 127 * 8192 < 2^24, so the fp32 accumulation is
+// exact in any order and the int32 scores are bit-exact.
+#include <type_traits>
+
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace fasthog {
 
-bool score_tc_supported(int, int, int, int, int, int) { return false; }
+namespace {
 
-hog_status launch_score_tc(const uint16_t*, int, int, int, int, int, int, const void*, int, float, void*,
-                           cudaStream_t) {
+constexpr int kNB = 8, kCX = 8, kCY = 16;
+constexpr int kM = 128;                   // windows per CTA (TMEM lanes)
+constexpr int kThreads = 128;
+constexpr int kStages = 4;
+constexpr int kRowsPerStage = 4;
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    // tcgen05 shared-memory descriptor, no swizzle: start >> 4 in bits 0-13,
+    // leading-dimension byte offset >> 4 in bits 16-29, stride-dimension byte
+    // offset >> 4 in bits 32-45, fixed 0b001 in bits 46-48.
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D = f32, A = B = bf16, both K-major, N, M.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     ptx::smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <typename WT>
+__device__ __forceinline__ uint16_t weight_bf16(const WT* w, int k);
+template <>
+__device__ __forceinline__ uint16_t weight_bf16<uint16_t>(const uint16_t* w, int k) {
+    return __ldg(w + k);
+}
+template <>
+__device__ __forceinline__ uint16_t weight_bf16<int8_t>(const int8_t* w, int k) {
+    return f32_to_bf16_exact_int((float)__ldg(w + k));  // |w| <= 127: exact in bf16
+}
+
+struct TcGeom {
+    int r, Tc, rows;      // residue count, outputs per class per CTA, cell rows per CTA
+    int row_cells;        // cells staged per cell row: kM + (kCX - 1) r
+    int row_bytes;        // row_cells * 16
+    int stage_bytes;      // kRowsPerStage rows
+    int plane_rows;       // rows of one band plane: 2 Tc + 16
+    int plane_bytes;      // plane_rows * 16
+    int band_bytes;       // kCX planes
+    int cols;             // TMEM columns allocated (power of two >= 32)
+    __host__ __device__ TcGeom(int r_, int Tc_) : r(r_), Tc(Tc_) {
+        rows = (Tc + kCY - 1) * r;
+        row_cells = kM + (kCX - 1) * r;
+        row_bytes = row_cells * 16;
+        stage_bytes = kRowsPerStage * row_bytes;
+        plane_rows = 2 * Tc + 16;
+        plane_bytes = plane_rows * 16;
+        band_bytes = kCX * plane_bytes;
+        cols = 32;
+        while (cols < r * Tc) cols *= 2;
+    }
+    __host__ __device__ size_t smem_bytes() const {
+        return 1024 + (size_t)band_bytes + (size_t)kStages * stage_bytes + 256;
+    }
+};
+
+template <typename WT, typename OutT>
+__global__ void __launch_bounds__(kThreads, 1)
+    score_tc_kernel(const uint16_t* __restrict__ cells, int ncx, int ncy, int r, int Tc, const WT* __restrict__ w,
+                    float bias, int nx, int ny, OutT* __restrict__ scores, unsigned int* status) {
+    extern __shared__ uint8_t smem_raw[];
+    const TcGeom G(r, Tc);
+    // 1024-byte aligned working area: band planes, A stages, barriers
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* band = base;
+    uint8_t* stages = base + G.band_bytes;
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)kStages * G.stage_bytes);
+    uint64_t* full = bars;                                // [kStages]
+    uint64_t* empty = bars + kStages;                     // [kStages]
+    uint64_t* done = bars + 2 * kStages;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 1);
+    __shared__ int aborted;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int px0 = blockIdx.x * kM;
+    const int py_lo = blockIdx.y * Tc * r;
+
+    // band planes: plane_i[v][b] = w[Tc + 14 - v][i][b] for filter rows 0..15, zero elsewhere
+    for (int e = tid; e < kCX * G.plane_rows * kNB; e += kThreads) {
+        const int b = e % kNB, v = (e / kNB) % G.plane_rows, i = e / (kNB * G.plane_rows);
+        const int j = Tc + 14 - v;
+        reinterpret_cast<uint16_t*>(band)[e] =
+            (j >= 0 && j < kCY) ? weight_bf16<WT>(w, (j * kCX + i) * kNB + b) : (uint16_t)0;
+    }
+    if (tid == 0) {
+        aborted = 0;
+        for (int s = 0; s < kStages; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        ptx::mbar_init(done, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         ptx::smem_addr(tmem_slot)),
+                     "r"(G.cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the band was written by ordinary stores; the MMAs read it through the async proxy
+    ptx::fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int n_stage_loads = (G.rows + kRowsPerStage - 1) / kRowsPerStage;
+    const int valid_cells = min(G.row_cells, ncx - px0);  // > 0: px0 < nx <= ncx
+    if (warp == 0 && lane == 0) {
+        // producer: cell rows py_lo .. py_lo + rows - 1 into the stage ring
+        int armed = 0;  // stages whose copies were issued
+        for (int k = 0; k < n_stage_loads; ++k) {
+            const int s = k % kStages;
+            if (!ptx::mbar_wait_bounded(&empty[s], ((k / kStages) & 1) ^ 1, kWaitLimitNs)) {
+                atomicOr(status, kStatusTimeout);
+                atomicExch(&aborted, 1);
+                break;
+            }
+            uint32_t bytes = 0;
+            for (int q = 0; q < kRowsPerStage; ++q) {
+                const int row = py_lo + k * kRowsPerStage + q;
+                if (k * kRowsPerStage + q < G.rows && row < ncy) bytes += (uint32_t)valid_cells * 16;
+            }
+            ptx::mbar_arrive_expect_tx(&full[s], bytes);
+            for (int q = 0; q < kRowsPerStage; ++q) {
+                const int row = py_lo + k * kRowsPerStage + q;
+                if (k * kRowsPerStage + q < G.rows && row < ncy)
+                    ptx::bulk_g2s(stages + (size_t)s * G.stage_bytes + (size_t)q * G.row_bytes,
+                                  cells + ((size_t)row * ncx + px0) * kNB, (uint32_t)valid_cells * 16, &full[s]);
+            }
+            armed = k + 1;
+        }
+        if (*reinterpret_cast<volatile int*>(&aborted)) {
+            // let the copies already issued land before the CTA can exit (bounded)
+            for (int k = armed > kStages ? armed - kStages : 0; k < armed; ++k)
+                ptx::mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1, kWaitLimitNs);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        const uint32_t idesc = instr_desc(kM, Tc);
+        const uint32_t band_addr = ptx::smem_addr(band);
+        for (int k = 0; k < n_stage_loads; ++k) {
+            const int s = k % kStages;
+            if (!ptx::mbar_wait_bounded(&full[s], (k / kStages) & 1, kWaitLimitNs) ||
+                *reinterpret_cast<volatile int*>(&aborted)) {
+                atomicOr(status, kStatusTimeout);
+                atomicExch(&aborted, 1);
+                break;
+            }
+            tc_fence_after();
+            for (int q = 0; q < kRowsPerStage; ++q) {
+                const int rr = k * kRowsPerStage + q;  // cell row within the CTA
+                if (rr >= G.rows) break;
+                const int phi = rr % r, rho = rr / r;
+                const uint32_t dcol = (uint32_t)(phi * Tc);
+                const uint32_t a_addr = ptx::smem_addr(stages + (size_t)s * G.stage_bytes + (size_t)q * G.row_bytes);
+                const uint32_t b_row = band_addr + (uint32_t)((Tc + 14 - rho) * 16);
+#pragma unroll
+                for (int ks = 0; ks < kCX / 2; ++ks) {
+                    // cells 2ks, 2ks+1: A at cell 2ks*r, B at plane 2ks
+                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * r * 16), (uint32_t)(r * 16), 128);
+                    const uint64_t bd =
+                        smem_desc(b_row + (uint32_t)(2 * ks * G.plane_bytes), (uint32_t)G.plane_bytes, 128);
+                    mma_bf16(tmem + dcol, ad, bd, idesc, (rho == 0 && ks == 0) ? 0u : 1u);
+                }
+            }
+            mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+        }
+        mma_commit(done);
+    }
+    __syncwarp();
+
+    // epilogue: all warps, after the last MMA
+    const bool ok = ptx::mbar_wait_bounded(done, 0, kWaitLimitNs);
+    if (!ok) atomicOr(status, kStatusTimeout);
+    tc_fence_after();
+    __syncthreads();
+    const int px = px0 + warp * 32 + lane;
+    if (ok && !*reinterpret_cast<volatile int*>(&aborted)) {
+        for (int phi = 0; phi < r; ++phi) {
+            for (int c0 = 0; c0 < Tc; c0 += 16) {
+                uint32_t v[16];
+                tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(phi * Tc + c0), v);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const int py = py_lo + phi + r * (c0 + c);
+                    if (px < nx && py < ny) {
+                        const float sc = __uint_as_float(v[c]) + bias;
+                        if constexpr (std::is_same<OutT, int32_t>::value) {
+                            scores[(size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
+                        } else {
+                            scores[(size_t)py * nx + px] = sc;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.cols) : "memory");
+    }
+}
+
+int choose_tc(int nx, int ny, int r) {
+    // 32 output rows per class per CTA when that still gives every SM a CTA, else 16
+    const long tiles_x = (nx + kM - 1) / kM;
+    const long ctas32 = tiles_x * ((ny + 32 * r - 1) / (32 * r));
+    return ctas32 >= sm_count() ? 32 : 16;
+}
+
+template <typename WT, typename OutT>
+hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* w, float bias, void* scores,
+                    cudaStream_t st) {
+    const int nx = ncx - (kCX - 1) * r, ny = ncy - (kCY - 1) * r;
+    if (nx <= 0 || ny <= 0) return HOG_OK;
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    const int Tc = choose_tc(nx, ny, r);
+    const TcGeom G(r, Tc);
+    if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
+    const size_t smem = G.smem_bytes();
+    auto kern = score_tc_kernel<WT, OutT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    dim3 grid((nx + kM - 1) / kM, (ny + Tc * r - 1) / (Tc * r));
+    kern<<<grid, kThreads, smem, st>>>(cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias, nx, ny,
+                                      static_cast<OutT*>(scores), status);
+    return check_launch();
+}
+
+}  // namespace
+
+bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx) {
+    (void)ncx;
+    return cell_dtype == HOG_BF16 && n_bins == kNB && cells_x == kCX && cells_y == kCY && (r == 1 || r == 2 || r == 4);
+}
+
+hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x, int cells_y, int r,
+                           const void* w, int w_dtype, float bias, void* scores, cudaStream_t st) {
+    (void)n_bins;
+    (void)cells_x;
+    (void)cells_y;
+    if (reinterpret_cast<uintptr_t>(cells_bf16) % 16 != 0) return HOG_ERR_UNSUPPORTED;
+    if (w_dtype == HOG_BF16) return launch_t<uint16_t, float>(cells_bf16, ncx, ncy, r, w, bias, scores, st);
+    if (w_dtype == HOG_I8) return launch_t<int8_t, int32_t>(cells_bf16, ncx, ncy, r, w, bias, scores, st);
     return HOG_ERR_UNSUPPORTED;
 }
 

@@ -274,3 +274,42 @@ def test_pipeline_end_to_end_host(fh, g):
     S_gpu = pipe.scores[: pipe.nx * pipe.ny].cpu().numpy().reshape(pipe.ny, pipe.nx)
     tol = g.score_tolerance(ref["cells"], c["w"], 0.0, stride=4)
     g.check_detections(det, n, S_gpu, ref["scores"], tol, c["thr"], 4)
+
+
+# ---------------------------------------------------------------- tensor-core scores
+@pytest.mark.parametrize("stride", [8, 4, 2])
+def test_score_tensor_cores(fh, g, stride):
+    """bf16 cell map -> the tcgen05 implicit-GEMM kernel.  bf16 weights: within
+    the FP32-path bound of the oracle run on the same bf16-rounded weights;
+    int8 weights: bit-exact.  The image spans several 128-window tiles and
+    row bands, with ragged ends in both directions."""
+    rng = np.random.default_rng(20 + stride)
+    img = rand_img(520, 700, 3, 40 + stride)
+    cells = cells_of(img, 8, stride)
+    w = rng.normal(0, 0.01, 1024).astype(np.float32)
+    w_bf = torch.from_numpy(w).to(torch.bfloat16).float().numpy()
+    ref = oracle.window_score(cells, w_bf, 0.25, stride=stride)
+    got = g.gpu_scores(cells, w, fh.HOG_BF16, 0.25, stride=stride, cell_dtype=fh.HOG_BF16)
+    assert got.shape == ref.shape
+    assert np.all(np.abs(got - ref) <= g.score_tolerance(cells, w_bf, 0.25, stride=stride))
+    wi = rng.integers(-127, 128, 1024).astype(np.int8)
+    ref_i = oracle.window_score(cells, wi, 3.0, stride=stride)
+    got_i = g.gpu_scores(cells, wi, fh.HOG_I8, 3.0, stride=stride, cell_dtype=fh.HOG_BF16)
+    assert got_i.dtype == np.int32 and np.array_equal(got_i, ref_i.astype(np.int64))
+
+
+def test_score_bf16_error_against_f32_weights(fh, g):
+    """The bf16 path against the FP64 oracle with the original f32 weights:
+    the error is the weight rounding (bf16 keeps 8 significant bits, so at
+    most 2^-8 sum |w| h) plus the FP32 accumulation; the measured maximum is
+    printed."""
+    rng = np.random.default_rng(77)
+    img = wl.config1()["images"][0]
+    cells = cells_of(img, 8, 4)
+    w = rng.normal(0, 0.01, 1024).astype(np.float32)
+    ref = oracle.window_score(cells, w, 0.0, stride=4)
+    got = g.gpu_scores(cells, w, fh.HOG_BF16, 0.0, stride=4, cell_dtype=fh.HOG_BF16)
+    mass = oracle.window_score(cells, np.abs(w.astype(np.float64)), 0.0, stride=4)
+    err = np.abs(got - ref)
+    assert np.all(err <= (2.0 ** -8 + 1e-5) * mass)
+    print(f"bf16 scores: max abs error {err.max():.3g}, max relative to sum|w|h {(err / mass).max():.3g}")
