@@ -217,6 +217,7 @@ def main():
 
     import paper_1703_06256_gb300 as fh
     import workloads as wl
+    from paper_1703_06256_gb300 import replicas
 
     torch.cuda.set_device(local)
     dist = None
@@ -276,13 +277,10 @@ def main():
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
-    ms_per_step = total_ms / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_per_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    # the slowest replica sets the time; the rate counts every rank's pixels
+    ms_per_step = replicas.max_over_ranks(total_ms / args.steps, device="cuda")
     px = W * H
-    value = world * px / (ms_per_step * 1e-3) / 1e6
+    value = replicas.aggregate_rate(px, ms_per_step * 1e-3, world) / 1e6
     windows = pipe.nx * pipe.ny
 
     # end to end through the public API, from pinned host memory (graph replay)
@@ -294,11 +292,7 @@ def main():
     for _ in range(args.steps):
         _, n = pipe.detect_host()
         d2h.append(4 + min(n, pipe.max_out) * fh.DET_BYTES)
-    e2e_s = (time.perf_counter() - t0) / args.steps
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
 
     # roofline of the dominant stage
     stage_avg = {k: v / args.steps for k, v in stage_ms.items()}
@@ -328,7 +322,7 @@ def main():
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                      "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
                      "algorithmic_bytes_per_launch": alg_bytes[dom]},
-        "e2e": {"value": round(world * px / e2e_s / 1e6, 2), "unit": "Mpixel/s",
+        "e2e": {"value": round(replicas.aggregate_rate(px, e2e_s, world) / 1e6, 2), "unit": "Mpixel/s",
                 "h2d_bytes_per_step": pipe.h2d_bytes(), "d2h_bytes_per_step": int(statistics.mean(d2h))},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
