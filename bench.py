@@ -167,25 +167,31 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def graph_step(torch, fns):
-    """Record the five stages as CUDA graph(s) with timing events between them.
-    With events that can be recorded inside a graph, one graph holds the whole
-    step and its six timestamps; otherwise each stage is its own graph and
-    the events are recorded between replays."""
+def graph_step(torch, fns, between: bool):
+    """Record the five stages as one CUDA graph with timing events recorded
+    inside it: at the two ends only (between=False; the kernels keep their
+    programmatic dependent launches across stage boundaries), or also between
+    the stages (between=True; each event is a graph node, so the stages
+    serialise).  Falls back to one graph per stage with events between the
+    replays where events cannot be recorded inside a graph."""
+    n = len(fns)
     try:
-        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(len(fns) + 1)]
+        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(n + 1 if between else 2)]
         g = torch.cuda.CUDAGraph()
         with torch.cuda.graph(g):
+            evs[0].record()
             for i, fn in enumerate(fns):
-                evs[i].record()
                 fn()
-            evs[-1].record()
+                if between:
+                    evs[i + 1].record()
+            if not between:
+                evs[1].record()
 
         def step():
             g.replay()
         mode = "one CUDA graph per step, events recorded inside it"
     except TypeError:
-        evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)]
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1 if between else 2)]
         graphs = []
         for fn in fns:
             gi = torch.cuda.CUDAGraph()
@@ -194,15 +200,19 @@ def graph_step(torch, fns):
             graphs.append(gi)
 
         def step():
+            evs[0].record()
             for i, gi in enumerate(graphs):
-                evs[i].record()
                 gi.replay()
-            evs[-1].record()
+                if between:
+                    evs[i + 1].record()
+            if not between:
+                evs[1].record()
         mode = "one CUDA graph per stage, events between replays"
 
     def read_times():
-        st = [evs[i].elapsed_time(evs[i + 1]) for i in range(len(fns))]
-        return st, evs[0].elapsed_time(evs[-1])
+        if between:
+            return [evs[i].elapsed_time(evs[i + 1]) for i in range(n)], evs[0].elapsed_time(evs[-1])
+        return None, evs[0].elapsed_time(evs[1])
 
     return step, read_times, mode
 
@@ -244,10 +254,12 @@ def main():
         flush.fill_(1)
         pipe.run_eager()
     torch.cuda.synchronize()
-    step, read_times, timing_mode = graph_step(torch, fns)
+    step, read_total, timing_mode = graph_step(torch, fns, between=False)
+    step_st, read_stages, _ = graph_step(torch, fns, between=True)
     for _ in range(max(args.warmup, 3)):
-        flush.fill_(1)
-        step()
+        for fn in (step, step_st):
+            flush.fill_(1)
+            fn()
     torch.cuda.synchronize()
 
     sampler = ClockSampler(local)
@@ -259,8 +271,7 @@ def main():
         torch.cuda.synchronize()
 
     # timed region: each step is replayed from its graph after an L2 flush;
-    # the events are recorded by the GPU around the step (outside the flush)
-    stage_ms = {n: 0.0 for n in names}
+    # the events are recorded by the GPU at the two ends of the step
     total_ms = 0.0
     if dist is not None:
         dist.barrier()
@@ -269,16 +280,23 @@ def main():
         flush.fill_(k)
         step()
         torch.cuda.synchronize()
-        st, tot = read_times()
-        for n, v in zip(names, st):
-            stage_ms[n] += v
-        total_ms += tot
+        total_ms += read_total()[1]
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
     clocks = sampler.stop()
     # the slowest replica sets the time; the rate counts every rank's pixels
     ms_per_step = replicas.max_over_ranks(total_ms / args.steps, device="cuda")
+
+    # per-stage breakdown (same steps, events between the stages)
+    stage_ms = {n: 0.0 for n in names}
+    for k in range(args.steps):
+        flush.fill_(k)
+        step_st()
+        torch.cuda.synchronize()
+        st, _ = read_stages()
+        for n, v in zip(names, st):
+            stage_ms[n] += v
     px = W * H
     value = replicas.aggregate_rate(px, ms_per_step * 1e-3, world) / 1e6
     windows = pipe.nx * pipe.ny

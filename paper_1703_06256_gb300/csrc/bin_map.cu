@@ -176,6 +176,8 @@ __global__ void __launch_bounds__(kThreads)
         }
     }
     bool lut_ready = !QUAD;
+    pdl_trigger();
+    pdl_wait();  // the table copy above reads only the table, built before the path runs
 
     const int qpr = (W + 3) >> 2;  // quads per row
     const long n_quads = (long)qpr * H;
@@ -228,8 +230,8 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     const int grid = (int)(need < cap ? need : cap);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
     const bool word_stores = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (W % 4 == 0);
-    kern<<<grid, kThreads, smem, st>>>(img, W, H, pitch, aligned, lut, nb, bins, word_stores, status);
-    return check_launch();
+    return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, img, W, H, pitch, aligned, lut, nb, bins, word_stores,
+                      status);
 }
 
 }  // namespace

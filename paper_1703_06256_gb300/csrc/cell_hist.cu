@@ -34,6 +34,8 @@ template <typename InT, typename OutT, int NB>
 __global__ void __launch_bounds__(128)
     cell_hist_kernel(const InT* __restrict__ ii, int W, int H, int nb_rt, int cell, int stride, int ncx, int ncy,
                      OutT* __restrict__ cells) {
+    pdl_trigger();
+    pdl_wait();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= ncx || j >= ncy) return;
@@ -80,12 +82,13 @@ hog_status launch_t(const void* ii, int W, int H, int nb, int cell, int stride, 
     const InT* src = static_cast<const InT*>(ii);
     OutT* dst = static_cast<OutT*>(cells);
     if (nb == 8)
-        cell_hist_kernel<InT, OutT, 8><<<grid, 128, 0, st>>>(src, W, H, nb, cell, stride, ncx, ncy, dst);
-    else if (nb == 16)
-        cell_hist_kernel<InT, OutT, 16><<<grid, 128, 0, st>>>(src, W, H, nb, cell, stride, ncx, ncy, dst);
-    else
-        cell_hist_kernel<InT, OutT, 0><<<grid, 128, 0, st>>>(src, W, H, nb, cell, stride, ncx, ncy, dst);
-    return check_launch();
+        return launch_pdl(cell_hist_kernel<InT, OutT, 8>, grid, dim3(128), 0, st, src, W, H, nb, cell, stride, ncx,
+                          ncy, dst);
+    if (nb == 16)
+        return launch_pdl(cell_hist_kernel<InT, OutT, 16>, grid, dim3(128), 0, st, src, W, H, nb, cell, stride, ncx,
+                          ncy, dst);
+    return launch_pdl(cell_hist_kernel<InT, OutT, 0>, grid, dim3(128), 0, st, src, W, H, nb, cell, stride, ncx, ncy,
+                      dst);
 }
 
 }  // namespace

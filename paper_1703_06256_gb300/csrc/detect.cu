@@ -52,6 +52,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     detect_count_kernel(const T* __restrict__ scores, long n, float thr_f, int thr_i, int* __restrict__ tile_count) {
     __shared__ int red[kThreads / 32];
+    pdl_trigger();
+    pdl_wait();
     const long base = (long)blockIdx.x * kTile + (long)threadIdx.x * kPer;
     int c = 0;
 #pragma unroll
@@ -71,6 +73,8 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ int red[kThreads / 32];
     __shared__ int wsum[kThreads / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    pdl_trigger();
+    pdl_wait();
     // detections in the tiles before this one
     int before = 0;
     if (tile_count != nullptr)
@@ -135,13 +139,13 @@ hog_status launch_t(const void* scores, int nx, int ny, int stride, float thr, i
     int* tile_count = nullptr;
     if (tiles > 1) {
         tile_count = static_cast<int*>(ws);
-        detect_count_kernel<T><<<tiles, kThreads, 0, st>>>(static_cast<const T*>(scores), n, thr, thr_i, tile_count);
-        hog_status s = check_launch();
+        hog_status s = launch_pdl(detect_count_kernel<T>, dim3(tiles), dim3(kThreads), 0, st,
+                                  static_cast<const T*>(scores), n, thr, thr_i, tile_count);
         if (s != HOG_OK) return s;
     }
-    detect_scatter_kernel<T><<<tiles, kThreads, 0, st>>>(static_cast<const T*>(scores), nx > 0 ? nx : 1, n, stride,
-                                                         thr, thr_i, image, level, tile_count, out, max_out, d_count);
-    return check_launch();
+    return launch_pdl(detect_scatter_kernel<T>, dim3(tiles), dim3(kThreads), 0, st, static_cast<const T*>(scores),
+                      nx > 0 ? nx : 1, n, stride, thr, thr_i, image, level, (const int*)tile_count, out, max_out,
+                      d_count);
 }
 
 }  // namespace

@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(kThreads)
     const int ncol = max(0, min(kQ, W - x0));
     const int y0 = band * h, y1 = min(H, y0 + h);
 
+    pdl_trigger();
+    pdl_wait();
     stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
     for (int i = tid; i < kMaxBand * NE; i += kThreads) (&row_acc[0][0])[i] = 0;
     __syncthreads();
@@ -257,6 +259,8 @@ __global__ void __launch_bounds__(32 * kSegments)
     ii_carry_kernel(int W, int n_bands, int n_groups, int nb_a, Ws ws) {
     constexpr int NWD = WIN / 4;
     const int lane = threadIdx.x, seg = threadIdx.y;
+    pdl_trigger();
+    pdl_wait();
     if ((int)blockIdx.x >= nb_a) {
         const int pair = (blockIdx.x - nb_a) * kSegments + seg;
         if (pair >= n_groups * WIN) return;
@@ -361,6 +365,8 @@ __global__ void __launch_bounds__(kThreads)
     const int y0 = band * h, y1 = min(H, y0 + h);
     const int wins = min(WIN, n_bins - bin_base);
     __shared__ uint32_t band_bins[kMaxBand][kThreads];
+    pdl_trigger();
+    pdl_wait();
     stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
 
     // corner = ii(group_left - 1, y0 - 1); RL(y) for the band's rows
@@ -505,18 +511,16 @@ template <int WIN, typename OutT>
 hog_status run_window(const Plan& p, const uint8_t* bins, int n_bins, int bin_base, OutT* ii, const Ws& ws,
                       bool vec, cudaStream_t st) {
     dim3 grid_tiles(p.n_bands, p.n_groups);
-    ii_tile_reduce_kernel<WIN><<<grid_tiles, kThreads, 0, st>>>(bins, p.W, p.H, p.h, p.n_bands, p.n_groups,
-                                                                 bin_base, vec, ws);
-    hog_status s = check_launch();
+    hog_status s = launch_pdl(ii_tile_reduce_kernel<WIN>, grid_tiles, dim3(kThreads), 0, st, bins, p.W, p.H, p.h,
+                              p.n_bands, p.n_groups, bin_base, vec, ws);
     if (s != HOG_OK) return s;
     const int nb_a = ceil_div(p.W, 32) * (WIN / 4);
     const int nb_b = ceil_div(p.n_groups * WIN, kSegments);
-    ii_carry_kernel<WIN><<<nb_a + nb_b, dim3(32, kSegments), 0, st>>>(p.W, p.n_bands, p.n_groups, nb_a, ws);
-    s = check_launch();
+    s = launch_pdl(ii_carry_kernel<WIN>, dim3(nb_a + nb_b), dim3(32, kSegments), 0, st, p.W, p.n_bands, p.n_groups,
+                   nb_a, ws);
     if (s != HOG_OK) return s;
-    ii_tile_scan_kernel<WIN, OutT><<<grid_tiles, kThreads, 0, st>>>(bins, p.W, p.H, p.h, p.n_groups, bin_base,
-                                                                     n_bins, vec, ws, ii);
-    return check_launch();
+    return launch_pdl(ii_tile_scan_kernel<WIN, OutT>, grid_tiles, dim3(kThreads), 0, st, bins, p.W, p.H, p.h,
+                      p.n_groups, bin_base, n_bins, vec, ws, ii);
 }
 
 template <typename OutT>

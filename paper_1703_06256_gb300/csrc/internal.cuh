@@ -65,6 +65,34 @@ hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, in
                          int image, int level, hog_det* out, int max_out, int32_t* d_count, void* ws,
                          cudaStream_t st);
 
+// ---- programmatic dependent launch
+// Kernels of the detection path launch with programmatic stream
+// serialisation: a kernel may start while its stream predecessor is still
+// finishing.  Every such kernel calls pdl_trigger() first (its own
+// successor may then be scheduled once all of its CTAs are running) and
+// pdl_wait() before it reads its predecessor's results or writes memory an
+// earlier kernel reads; only independent set-up (tables, weights, barriers)
+// runs before the wait.  Under stream capture the dependency becomes a
+// programmatic graph edge.
+template <typename... KArgs, typename... Args>
+hog_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                      Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+    return e == cudaSuccess ? HOG_OK : cuda_fail(e);
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- small device helpers
 __device__ __forceinline__ uint16_t f32_to_bf16_exact_int(float v) {
     // Only called on small integers (|v| < 2^8) and on values already

@@ -85,6 +85,8 @@ __global__ void __launch_bounds__(kTX* kTY)
     float4* c_s = smem4 + K4;     // [rh][nb4][rw]
     const int tid = threadIdx.y * kTX + threadIdx.x;
     const int px0 = blockIdx.x * kTX, py0 = blockIdx.y * kTY;
+    pdl_trigger();
+    pdl_wait();
 
     // weights, padded per cell to nb4 float4s
     for (int i = tid; i < K4 * 4; i += kTX * kTY) {
@@ -162,16 +164,15 @@ hog_status launch_t(const void* cells, int ncx, int ncy, int nb, int cells_x, in
         auto k = score_kernel<CellT, WT, OutT, true>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e);
-        k<<<grid, block, smem, st>>>(static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y, r,
-                                    static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
+        return launch_pdl(k, grid, block, smem, st, static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y,
+                          r, static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
     } else {
         auto k = score_kernel<CellT, WT, OutT, false>;
         e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_fail(e);
-        k<<<grid, block, smem, st>>>(static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y, r,
-                                    static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
+        return launch_pdl(k, grid, block, smem, st, static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y,
+                          r, static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
     }
-    return check_launch();
 }
 
 template <typename CellT>

@@ -108,6 +108,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int i = 0; i < kCX; ++i)
 #pragma unroll
         for (int b = 0; b < kNB; ++b) wr[i][b] = wval<WT>(w, (j * kCX + i) * kNB + b);
+    pdl_trigger();
+    pdl_wait();  // the weights above are inputs of the call, not of a predecessor
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int s = item % S, rblk = item / S;
@@ -188,9 +190,8 @@ hog_status launch_t(const void* cells, int ncx, int ncy, int r, const void* w, f
     const int per_sm = smem <= 70 * 1024 ? 3 : (smem <= 110 * 1024 ? 2 : 1);
     const int cap = per_sm * sm_count();
     const int grid = n_items < cap ? n_items : cap;
-    kern<<<grid, kThreads, smem, st>>>(static_cast<const CellT*>(cells), ncx, ncy, r, T, static_cast<const WT*>(w),
-                                       bias, nx, ny, S, n_items, static_cast<OutT*>(scores));
-    return check_launch();
+    return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, static_cast<const CellT*>(cells), ncx, ncy, r, T,
+                      static_cast<const WT*>(w), bias, nx, ny, S, n_items, static_cast<OutT*>(scores));
 }
 
 template <typename CellT>

@@ -182,6 +182,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_trigger();
+    pdl_wait();  // set-up above read only the weights; the cell rows come from the predecessor
 
     const int n_stage_loads = (G.rows + kRowsPerStage - 1) / kRowsPerStage;
     const int valid_cells = min(G.row_cells, ncx - px0);  // > 0: px0 < nx <= ncx
@@ -305,9 +307,8 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     dim3 grid((nx + kM - 1) / kM, (ny + Tc * r - 1) / (Tc * r));
-    kern<<<grid, kThreads, smem, st>>>(cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias, nx, ny,
-                                      static_cast<OutT*>(scores), status);
-    return check_launch();
+    return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias,
+                      nx, ny, static_cast<OutT*>(scores), status);
 }
 
 }  // namespace
