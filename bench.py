@@ -67,6 +67,30 @@ def peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+def profiled_traffic(stage: str, workload: str):
+    """DRAM bytes per launch of `stage` from the committed ncu capture, or None
+    when there is none for this workload or the kernel source has changed
+    since it was taken (profiles/traffic.txt records a hash of the source)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        if ln.startswith("#") or not ln.strip():
+            continue
+        st, wl_, nbytes, src, sha = ln.split()
+        if st == stage and wl_ == workload:
+            try:
+                cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+            except OSError:
+                return None
+            return int(nbytes) if cur == sha else None
+    return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -338,8 +362,9 @@ def main():
         "windows_per_s": round(world * windows / (ms_per_step * 1e-3), 1),
         "stages_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": None, "peak_source": src,
-                     "algorithmic_bytes_per_launch": alg_bytes[dom]},
+                     "frac": round(achieved / hbm, 4), "traffic": profiled_traffic(dom, f"{W}x{H}"),
+                     "peak_source": src, "algorithmic_bytes_per_launch": alg_bytes[dom],
+                     "traffic_source": "profiles/traffic.txt (ncu, summed over the stage's kernels)"},
         "e2e": {"value": round(replicas.aggregate_rate(px, e2e_s, world) / 1e6, 2), "unit": "Mpixel/s",
                 "h2d_bytes_per_step": pipe.h2d_bytes(), "d2h_bytes_per_step": int(statistics.mean(d2h))},
         "gpu_launches": launches_per_step * args.steps,
