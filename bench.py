@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the fused-path and 1080p-batch figures (the main line is unchanged)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     return ap.parse_args()
 
@@ -241,6 +243,57 @@ def graph_step(torch, fns, between: bool):
     return step, read_times, mode
 
 
+def time_steps(torch, step, read, flush, steps, warmup):
+    """Mean device time (ms) of `steps` replays, each after an L2 flush."""
+    for _ in range(max(warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    total = 0.0
+    for k in range(steps):
+        flush.fill_(k)
+        step()
+        torch.cuda.synchronize()
+        total += read()[1]
+    return total / steps
+
+
+def batch_1080p(torch, fh, wl, replicas, flush, args, world):
+    """The 1080p batch: 32 RGB 1920x1080 images per step (N_b = 8, stride 4),
+    bf16 cell maps and bf16 weights, so the score runs on the tensor cores.
+    All 32 images' calls are recorded in one CUDA graph."""
+    n_img, W, H = 32, 1920, 1080
+    rng = wl.rng_for(3)
+    w = wl.weights_f32(8, rng)
+    pipes = []
+    for i in range(n_img):
+        p = fh.HogPipeline(W, H, 3, 8, 4, cell_dtype=fh.HOG_BF16, w_dtype=fh.HOG_BF16)
+        p.set_weights(w, 0.0, 0.5)
+        p.set_image(wl.rgb_smooth_shapes(W, H, rng))
+        pipes.append(p)
+    out = {}
+    for label, fused in (("separate_calls", False), ("fused_cells", True)):
+        fns = []
+        for p in pipes:
+            p.fused = fused
+            fns += ([p.stage_cells_fused] if fused else [p.stage_bin_map, p.stage_integral, p.stage_cell_hist])
+            fns += [p.stage_score, p.stage_detect]
+        for p in pipes:
+            p.run_eager()
+        torch.cuda.synchronize()
+        step, read, _ = graph_step(torch, fns, between=False)
+        ms = replicas.max_over_ranks(time_steps(torch, step, read, flush, max(args.steps // 10, 5), args.warmup),
+                                     "cuda")
+        windows = n_img * pipes[0].nx * pipes[0].ny
+        out[label] = {"value": round(replicas.aggregate_rate(n_img * W * H, ms * 1e-3, world) / 1e6, 1),
+                      "unit": "Mpixel/s", "ms_per_step": round(ms, 4),
+                      "windows_per_s": round(replicas.aggregate_rate(windows, ms * 1e-3, world), 1)}
+    out["workload"] = "32 RGB 1920x1080 images per step, N_b=8, stride 4, bf16 cells x bf16 weights (tensor cores)"
+    del pipes
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -325,6 +378,19 @@ def main():
     value = replicas.aggregate_rate(px, ms_per_step * 1e-3, world) / 1e6
     windows = pipe.nx * pipe.ny
 
+    # the same step with the fused image-to-cells kernel (no bin map or integral planes in HBM)
+    fused = None
+    if not args.no_extras:
+        pipe.fused = True
+        fstep, fread, _ = graph_step(torch, [pipe.stage_cells_fused, pipe.stage_score, pipe.stage_detect],
+                                     between=False)
+        fused_ms = time_steps(torch, fstep, fread, flush, args.steps, args.warmup)
+        pipe.fused = False
+        fused = {"value": round(replicas.aggregate_rate(W * H, replicas.max_over_ranks(fused_ms, "cuda") * 1e-3,
+                                                        world) / 1e6, 2),
+                 "unit": "Mpixel/s", "ms_per_step": round(fused_ms, 5),
+                 "calls": "hog_cell_hist_fused + hog_window_score + hog_detect"}
+
     # end to end through the public API, from pinned host memory (graph replay)
     pipe.capture()
     for _ in range(3):
@@ -370,6 +436,8 @@ def main():
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "device_status": status,
+        "fused": fused,
+        "batch_1080p": None if args.no_extras else batch_1080p(torch, fh, wl, replicas, flush, args, world),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(img, c, args.cpu_seconds)

@@ -177,6 +177,27 @@ hog_status hog_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype,
                          int stride, int cell_dtype, void* cells, hog_stream_t stream);
 
 /*
+ * hog_cell_hist_fused -- the cell map of hog_cell_hist straight from the image
+ * (paper Sections 2 and 3 in one kernel).
+ *
+ * Produces exactly hog_cell_hist(hog_integral(hog_bin_map(img))) for the
+ * same arguments, without writing the bin map or the integral planes to
+ * memory: each block of stride x stride pixels is binned (Eq. 1 and the
+ * table) and counted, a tile-local integral image is formed at the block
+ * corners (Eq. 5), and every cell is its four-corner sum (Eq. 6).  Box sums
+ * are unchanged by the per-tile offset of a tile-local integral image.
+ *
+ *   img, W, H, channels, pitch_bytes, lut, n_bins   as for hog_bin_map
+ *   cell, stride, cell_dtype, cells                 as for hog_cell_hist
+ * Supported: n_bins 8 or 16, stride 4 or 8, cell a multiple of stride with
+ * cell / stride <= 4; other valid arguments return HOG_ERR_UNSUPPORTED (use
+ * the three separate calls).
+ */
+hog_status hog_cell_hist_fused(const uint8_t* img, int W, int H, int channels, size_t pitch_bytes,
+                               const uint8_t* lut, int n_bins, int cell, int stride, int cell_dtype, void* cells,
+                               hog_stream_t stream);
+
+/*
  * hog_window_score -- linear objectness score of every window position
  * (paper Section 1: the cached histograms feed a score at every scan
  * position; Section 4: that score is an inner product of the window feature

@@ -71,6 +71,7 @@ def _load() -> ctypes.CDLL:
         "hog_detect_workspace_bytes": (Z, [I, I]),
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
+        "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -82,7 +83,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
-            "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc")
+            "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused")
 
 
 def lib() -> ctypes.CDLL:
@@ -148,6 +149,12 @@ def hog_cell_hist(ii, W: int, H: int, n_bins: int, ii_dtype: int, cell: int, str
                   cells, stream=None) -> None:
     _check("hog_cell_hist", _lib.hog_cell_hist(_ptr(ii), W, H, n_bins, ii_dtype, cell, stride, cell_dtype,
                                                _ptr(cells), _stream(stream)))
+
+
+def hog_cell_hist_fused(img, W: int, H: int, channels: int, pitch_bytes: int, lut, n_bins: int, cell: int,
+                        stride: int, cell_dtype: int, cells, stream=None) -> None:
+    _check("hog_cell_hist_fused", _lib.hog_cell_hist_fused(_ptr(img), W, H, channels, pitch_bytes, _ptr(lut), n_bins,
+                                                           cell, stride, cell_dtype, _ptr(cells), _stream(stream)))
 
 
 def hog_window_score(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, cells_x: int, cells_y: int,

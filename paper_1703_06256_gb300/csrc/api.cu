@@ -165,6 +165,24 @@ hog_status hog_cell_hist(const void* ii, int W, int H, int n_bins, int ii_dtype,
                             reinterpret_cast<cudaStream_t>(stream));
 }
 
+hog_status hog_cell_hist_fused(const uint8_t* img, int W, int H, int channels, size_t pitch_bytes,
+                               const uint8_t* lut, int n_bins, int cell, int stride, int cell_dtype, void* cells,
+                               hog_stream_t stream) {
+    if (img == nullptr || lut == nullptr || cells == nullptr) return HOG_ERR_ARG;
+    if (!size_ok(W, H) || (channels != 1 && channels != 3)) return HOG_ERR_ARG;
+    if (pitch_bytes < (size_t)W * channels || n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(lut) % 16 != 0) return HOG_ERR_ARG;
+    if (cell < 1 || cell > 64 || stride < 1 || stride > cell) return HOG_ERR_ARG;
+    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
+    if (cell_dtype == HOG_BF16 && cell > 16) return HOG_ERR_ARG;
+    if (!cells_fused_supported(n_bins, cell, stride)) return HOG_ERR_UNSUPPORTED;
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    return launch_cells_fused(img, W, H, channels, pitch_bytes, lut, n_bins, cell, stride, cell_dtype, cells, status,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
+
 hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int cells_x, int cells_y,
                             int cell, int stride, const void* w, int w_dtype, float bias, void* scores,
                             hog_stream_t stream) {

@@ -1,0 +1,113 @@
+// bin_core.cuh -- per-pixel orientation bins of a quad of 4 pixels (paper
+// Section 2, Eq. 1 and the table lookup), shared by the bin-map kernel and
+// the fused image-to-cells kernel.  See bin_map.cu for the method.
+#pragma once
+
+#include "internal.cuh"
+
+namespace fasthog {
+
+// The 32-bit word at byte offset `off` of a row of `row_bytes` bytes; bytes
+// outside the row read as 0.
+__device__ __forceinline__ uint32_t row_word(const uint8_t* __restrict__ row, long off, long row_bytes, bool aligned) {
+    if (aligned && off >= 0 && off + 4 <= row_bytes) return __ldg(reinterpret_cast<const uint32_t*>(row + off));
+    uint32_t w = 0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (off + b >= 0 && off + b < row_bytes) w |= (uint32_t)__ldg(row + off + b) << (8 * b);
+    return w;
+}
+
+// Byte i of a little-endian word array, i a compile-time constant.
+template <int N>
+__device__ __forceinline__ int byte_of(const uint32_t (&w)[N], int i) {
+    return (int)((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+}
+
+template <int CH>
+struct QuadWords {
+    static constexpr int NC = CH == 3 ? 5 : 3;  // centre-row words, from byte CH*x - 4
+    static constexpr int NV = CH == 3 ? 3 : 1;  // rows above / below: the quad's own bytes
+    uint32_t wc[NC], wu[NV], wd[NV];
+};
+
+// Load the words of quad (x, y), 0 < y < H-1.  Interior quads of aligned
+// images load without bounds tests.
+template <int CH>
+__device__ __forceinline__ void load_quad(const uint8_t* __restrict__ img, size_t pitch, long row_bytes, bool aligned,
+                                          int x, int y, QuadWords<CH>& q) {
+    using Q = QuadWords<CH>;
+    const uint8_t* mid = img + (size_t)y * pitch;
+    const uint8_t* up = mid - pitch;
+    const uint8_t* dn = mid + pitch;
+    const long o = (long)x * CH;
+    if (aligned && x >= 4 && o + 4 * Q::NC - 4 <= row_bytes) {
+        const uint32_t* m4 = reinterpret_cast<const uint32_t*>(mid + o - 4);
+        const uint32_t* u4 = reinterpret_cast<const uint32_t*>(up + o);
+        const uint32_t* d4 = reinterpret_cast<const uint32_t*>(dn + o);
+#pragma unroll
+        for (int k = 0; k < Q::NC; ++k) q.wc[k] = __ldg(m4 + k);
+#pragma unroll
+        for (int k = 0; k < Q::NV; ++k) {
+            q.wu[k] = __ldg(u4 + k);
+            q.wd[k] = __ldg(d4 + k);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < Q::NC; ++k) q.wc[k] = row_word(mid, o - 4 + 4 * k, row_bytes, aligned);
+#pragma unroll
+        for (int k = 0; k < Q::NV; ++k) {
+            q.wu[k] = row_word(up, o + 4 * k, row_bytes, aligned);
+            q.wd[k] = row_word(dn, o + 4 * k, row_bytes, aligned);
+        }
+    }
+}
+
+// Eq. 1 and the table lookup for the 4 pixels of quad x (row loaded in q).
+// Channel c of pixel x + p: right neighbour at byte 4 + (p+1)*CH + c of wc,
+// left at 4 + (p-1)*CH + c, below / above at byte p*CH + c of wd / wu.
+template <int CH, bool QUAD>
+__device__ __forceinline__ uint32_t bins_of_quad(const QuadWords<CH>& q, int x, int W, const uint8_t* __restrict__ lutq,
+                                                 const uint8_t* __restrict__ lut, int nb, int nb4) {
+    uint32_t packed = 0;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        uint32_t bin = kNoBin;
+        const int xp = x + p;
+        if (xp > 0 && xp < W - 1) {
+            int dx = byte_of(q.wc, 4 + (p + 1) * CH) - byte_of(q.wc, 4 + (p - 1) * CH);
+            int dy = byte_of(q.wd, p * CH) - byte_of(q.wu, p * CH);
+            if (CH == 3) {
+                int best = dx * dx + dy * dy;
+#pragma unroll
+                for (int c = 1; c < 3; ++c) {
+                    const int ddx = byte_of(q.wc, 4 + (p + 1) * CH + c) - byte_of(q.wc, 4 + (p - 1) * CH + c);
+                    const int ddy = byte_of(q.wd, p * CH + c) - byte_of(q.wu, p * CH + c);
+                    const int m = ddx * ddx + ddy * ddy;
+                    if (m > best) {  // strict: ties keep the lower channel
+                        best = m;
+                        dx = ddx;
+                        dy = ddy;
+                    }
+                }
+            }
+            if (dx != 0 || dy != 0) {
+                if (QUAD) {
+                    int qd, u, v;  // quadrant and quadrant-0 coordinates
+                    if (dx > 0 && dy >= 0) { qd = 0; u = dx; v = dy; }
+                    else if (dx <= 0 && dy > 0) { qd = 1; u = dy; v = -dx; }
+                    else if (dx < 0 && dy <= 0) { qd = 2; u = -dx; v = -dy; }
+                    else { qd = 3; u = -dy; v = dx; }
+                    const int t = lutq[v * 256 + u - 1] + qd * nb4;
+                    bin = t >= nb ? t - nb : t;
+                } else {
+                    bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
+                }
+            }
+        }
+        packed |= bin << (8 * p);
+    }
+    return packed;
+}
+
+}  // namespace fasthog

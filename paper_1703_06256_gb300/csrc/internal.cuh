@@ -60,6 +60,11 @@ hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_b
                            int cells_y, int r, const void* w, int w_dtype, float bias,
                            void* scores, cudaStream_t st);
 
+bool cells_fused_supported(int n_bins, int cell, int stride);
+hog_status launch_cells_fused(const uint8_t* img, int W, int H, int channels, size_t pitch, const uint8_t* lut,
+                              int n_bins, int cell, int stride, int cell_dtype, void* cells, unsigned int* status,
+                              cudaStream_t st);
+
 size_t detect_workspace_bytes(int nx, int ny);
 hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
                          int image, int level, hog_det* out, int max_out, int32_t* d_count, void* ws,

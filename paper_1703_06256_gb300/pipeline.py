@@ -15,8 +15,9 @@ import numpy as np
 import torch
 
 from . import (DET_BYTES, HOG_BF16, HOG_F32, HOG_I8, HOG_I32, HOG_LUT_BYTES, HOG_U16, TORCH_DTYPE,
-               dets_to_numpy, grid_shapes, hog_bin_map, hog_build_lut, hog_cell_hist, hog_detect,
-               hog_detect_workspace_bytes, hog_integral, hog_integral_workspace_bytes, hog_window_score)
+               dets_to_numpy, grid_shapes, hog_bin_map, hog_build_lut, hog_cell_hist, hog_cell_hist_fused,
+               hog_detect, hog_detect_workspace_bytes, hog_integral, hog_integral_workspace_bytes,
+               hog_window_score)
 
 _W_DTYPE = {HOG_F32: torch.float32, HOG_BF16: torch.bfloat16, HOG_I8: torch.int8}
 
@@ -88,11 +89,24 @@ class HogPipeline:
         hog_detect(self.scores, self.score_dtype, self.nx, self.ny, self.stride, self.thr, 0, 0, self.det,
                    self.max_out, self.count, self.ws_det, self.ws_det_bytes, stream)
 
+    def stage_cells_fused(self, stream=None):
+        """Bin map, integral images and cell histograms in one call (the bin
+        map and the integral planes are not written)."""
+        hog_cell_hist_fused(self.img, self.W, self.H, self.channels, self.W * self.channels, self.lut, self.n_bins,
+                            self.cell, self.stride, self.cell_dtype, self.cells, stream)
+
+    fused = False
+
     def run_eager(self, stream=None) -> None:
-        """Enqueue the five calls for the image already in ``self.img``."""
-        self.stage_bin_map(stream)
-        self.stage_integral(stream)
-        self.stage_cell_hist(stream)
+        """Enqueue the calls for the image already in ``self.img``: the five
+        separate stages, or (fused=True) the fused image-to-cells call, the
+        score and the list."""
+        if self.fused:
+            self.stage_cells_fused(stream)
+        else:
+            self.stage_bin_map(stream)
+            self.stage_integral(stream)
+            self.stage_cell_hist(stream)
         self.stage_score(stream)
         self.stage_detect(stream)
 

@@ -313,3 +313,38 @@ def test_score_bf16_error_against_f32_weights(fh, g):
     err = np.abs(got - ref)
     assert np.all(err <= (2.0 ** -8 + 1e-5) * mass)
     print(f"bf16 scores: max abs error {err.max():.3g}, max relative to sum|w|h {(err / mass).max():.3g}")
+
+
+# ---------------------------------------------------------------- fused image -> cells
+@pytest.mark.parametrize("ch", [1, 3])
+@pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (8, 8, 8), (16, 8, 4), (8, 16, 4), (8, 16, 8)])
+def test_cells_fused(fh, g, ch, nb, cell, stride):
+    """hog_cell_hist_fused equals the oracle's Eq. 6 cell map of the oracle's
+    bins, bit for bit, on images spanning several tiles with ragged edges."""
+    for i, (H, W) in enumerate([(77, 300), (240, 320), (131, 517), (16, 16)]):
+        img = rand_img(H, W, ch, 1000 + 10 * nb + i)
+        ref = oracle.cell_hist_ii(oracle.integral(oracle.bin_map(img, nb), nb), nb, cell, stride)
+        ncy, ncx = ref.shape[:2]
+        lut = g.gpu_lut(nb)
+        d = g.dev(img.reshape(-1))
+        for cd in (fh.HOG_I32, fh.HOG_F32, fh.HOG_BF16):
+            out = torch.full((max(ncx * ncy * nb, 1),), -1, dtype=fh.TORCH_DTYPE[cd], device="cuda")
+            fh.hog_cell_hist_fused(d, W, H, ch, W * ch, lut, nb, cell, stride, cd, out)
+            got = out.float().cpu().numpy()[: ncx * ncy * nb].reshape(ncy, ncx, nb)
+            assert np.array_equal(got, ref), (H, W, cd)
+
+
+def test_pipeline_fused_config1(fh, g):
+    c = wl.config1()
+    img = c["images"][0]
+    pipe = fh.HogPipeline(800, 600, 3, 8, 4)
+    pipe.fused = True
+    pipe.set_weights(c["w"], 0.0, c["thr"])
+    pipe.set_image(img)
+    pipe.run()
+    got = pipe.results()
+    ref = oracle.pipeline(img, 8, c["w"], 0.0, 4, c["thr"])
+    assert np.array_equal(got["cells"], ref["cells"])
+    tol = g.score_tolerance(ref["cells"], c["w"], 0.0, stride=4)
+    assert np.all(np.abs(got["scores"] - ref["scores"]) <= tol)
+    g.check_detections(got["detections"], got["count"], got["scores"], ref["scores"], tol, c["thr"], 4)
