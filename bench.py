@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the fused-path and 1080p-batch figures (the main line is unchanged)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
+    ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
     return ap.parse_args()
 
 
@@ -292,6 +293,63 @@ def batch_1080p(torch, fh, wl, replicas, flush, args, world):
     return out
 
 
+def serving(torch, wl, args):
+    """Continuous batching against the plain per-image path.
+
+    Requests: RGB images, width and height uniform over multiples of 8 in
+    320..3840 x 240..2160, Poisson arrivals, N_b = 8, stride 4, bf16 weights.
+    The images cycle through 128 pinned host images, cropped at random
+    offsets from one generated 3840x2160 image at the sizes of the stream's first 128
+    requests.  The plain path is the same server with one stream (one request
+    on the GPU at a time, FIFO); its capacity is measured by a back-to-back
+    run, and the Poisson stream arrives at 0.8 x that capacity for both.
+    Latency is arrival to detections on the host."""
+    from paper_1703_06256_gb300.serve import HogServer, Request, latency_summary
+    import paper_1703_06256_gb300 as fh
+
+    n_req = args.serve_requests
+    rng = wl.rng_for(5)
+    w = wl.weights_f32(8, rng)
+    stream = wl.request_stream(n_req, rate_per_s=1.0)
+    base = wl.rgb_smooth_shapes(3840, 2160, rng, n_shapes=12)
+    pool = []
+    for k in range(min(128, n_req)):
+        Wk, Hk = stream[k]["W"], stream[k]["H"]
+        y, x = int(rng.integers(0, 2160 - Hk + 1)), int(rng.integers(0, 3840 - Wk + 1))
+        pool.append(torch.from_numpy(np.ascontiguousarray(base[y:y + Hk, x:x + Wk])).pin_memory())
+    del base
+    kw = dict(n_bins=8, stride=4, thr=0.5, w_dtype=fh.HOG_BF16, budget_bytes=8 << 30, fused=True)
+    served = HogServer(w, n_streams=16, **kw)
+    plain = HogServer(w, n_streams=1, **kw)
+
+    def run(srv, reqs):
+        t0 = time.perf_counter()
+        res = srv.serve(reqs, keep=False)
+        return res, time.perf_counter() - t0
+
+    burst = [Request(i, pool[i % len(pool)], 0.0) for i in range(min(1000, n_req))]
+    for srv in (served, plain):  # warm-up: every kernel loaded, allocator pools filled
+        run(srv, burst[: len(pool)])
+    torch.cuda.synchronize()
+    _, t_plain = run(plain, burst)
+    _, t_served = run(served, burst)
+    cap_plain, cap_served = len(burst) / t_plain, len(burst) / t_served
+    rate = 0.8 * cap_plain
+    reqs = [Request(i, pool[i % len(pool)], stream[i]["t"] / rate) for i in range(n_req)]
+    out = {"workload": ("Poisson arrivals at 0.8 x the plain path's capacity; RGB images, W, H uniform over multiples "
+                        "of 8 in 320..3840 x 240..2160 (128 distinct pinned host images, cycled); N_b=8, stride 4, "
+                        "bf16 cells x bf16 weights; 8 GB device budget; latency = arrival to detections on the host"),
+           "requests": n_req, "rate_per_s": round(rate, 1),
+           "mean_mpixel_per_request": round(sum(int(t.numel()) for t in pool) / 3 / len(pool) / 1e6, 3),
+           "capacity_images_per_s": {"plain": round(cap_plain, 1), "served": round(cap_served, 1)}}
+    for label, srv, streams in (("served", served, 16), ("plain", plain, 1)):
+        res, wall = run(srv, reqs)
+        out[label] = dict(latency_summary(res, wall), streams=streams, fused=srv.fused)
+    del served, plain, pool
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -436,6 +494,8 @@ def main():
         "device_status": status,
         "fused": fused,
         "batch_1080p": None if args.no_extras else batch_1080p(torch, fh, wl, replicas, flush, args, world),
+        "serving": (serving(torch, wl, args) if not args.no_extras and world == 1 and args.serve_requests > 0
+                    else None),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(img, c, args.cpu_seconds)

@@ -237,6 +237,9 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
  *
  *   scores, score_dtype  [ny][nx] of HOG_F32 or HOG_I32
  *   image, level         copied into every detection (caller's tags)
+ *   out, d_count         device memory, or page-locked host memory mapped into
+ *                        the device's address space (the list is written with
+ *                        plain coalesced stores, no atomics); out 4-byte aligned
  *   workspace            at least hog_detect_workspace_bytes(nx, ny) bytes of
  *                        scratch; contents ignored on entry
  */

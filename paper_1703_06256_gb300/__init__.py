@@ -41,6 +41,22 @@ class HogDet(ctypes.Structure):
 DET_BYTES = ctypes.sizeof(HogDet)  # 20
 
 
+class HogServerConfig(ctypes.Structure):
+    """hog_server_config of include/fasthog_server.h."""
+    _fields_ = [("n_bins", ctypes.c_int), ("cell", ctypes.c_int), ("stride", ctypes.c_int),
+                ("cells_x", ctypes.c_int), ("cells_y", ctypes.c_int), ("w_dtype", ctypes.c_int),
+                ("bias", ctypes.c_float), ("thr", ctypes.c_float), ("fused", ctypes.c_int),
+                ("ii_dtype", ctypes.c_int), ("n_slots", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
+                ("max_W", ctypes.c_int), ("max_H", ctypes.c_int)]
+
+
+class HogServerResult(ctypes.Structure):
+    """hog_server_result of include/fasthog_server.h."""
+    _fields_ = [("rid", ctypes.c_int32), ("status", ctypes.c_int32), ("count", ctypes.c_int32),
+                ("token", ctypes.c_int32), ("W", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("dets", ctypes.c_void_p)]
+
+
 class HogError(RuntimeError):
     def __init__(self, fn: str, status: int, cuda_error: int = 0):
         self.status = status
@@ -72,6 +88,13 @@ def _load() -> ctypes.CDLL:
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
         "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
+        "hog_server_create": (I, [P, P, P]),
+        "hog_server_destroy": (I, [P]),
+        "hog_server_request_bytes": (Z, [P, I, I, I]),
+        "hog_server_submit": (I, [P, ctypes.c_int32, P, I, I, I, P]),
+        "hog_server_poll": (I, [P, P, I, P]),
+        "hog_server_release": (I, [P, ctypes.c_int32]),
+        "hog_server_stats": (I, [P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -83,7 +106,9 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
-            "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused")
+            "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
+            "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
+            "hog_server_poll", "hog_server_release", "hog_server_stats")
 
 
 def lib() -> ctypes.CDLL:
@@ -98,6 +123,17 @@ def _ptr(x) -> int | None:
             raise ValueError("libfasthog takes CUDA tensors (device memory); got a CPU tensor")
         return x.data_ptr()
     return int(x)
+
+
+def _host_ptr(x) -> int:
+    """Address of a contiguous HOST buffer (numpy array or CPU tensor)."""
+    if isinstance(x, torch.Tensor):
+        if x.device.type != "cpu" or not x.is_contiguous():
+            raise ValueError("expected a contiguous CPU tensor (host memory)")
+        return x.data_ptr()
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a C-contiguous numpy array")
+    return x.ctypes.data
 
 
 def _stream(stream) -> int | None:
@@ -187,6 +223,51 @@ def hog_detect_noalloc(scores, score_dtype: int, nx: int, ny: int, stride: int, 
 HOG_DETECT_NOALLOC_MAX_SCORES = 16384 * 2048
 
 
+# ---- request server (include/fasthog_server.h) -------------------------------
+
+def hog_server_create(cfg: HogServerConfig, w_host) -> ctypes.c_void_p:
+    """`w_host`: a contiguous host numpy array (or CPU tensor) of the
+    weights, of the type cfg.w_dtype names.  Returns the server handle."""
+    h = ctypes.c_void_p()
+    _check("hog_server_create", _lib.hog_server_create(ctypes.byref(cfg), _host_ptr(w_host), ctypes.byref(h)))
+    return h
+
+
+def hog_server_destroy(handle) -> None:
+    _check("hog_server_destroy", _lib.hog_server_destroy(handle))
+
+
+def hog_server_request_bytes(handle, W: int, H: int, channels: int) -> int:
+    return _lib.hog_server_request_bytes(handle, W, H, channels)
+
+
+def hog_server_submit(handle, rid: int, img_host, W: int, H: int, channels: int) -> bool:
+    """True if the request was admitted; `img_host` must stay alive and
+    unchanged until its result has been polled."""
+    ok = ctypes.c_int(0)
+    _check("hog_server_submit", _lib.hog_server_submit(handle, rid, _host_ptr(img_host), W, H, channels,
+                                                       ctypes.byref(ok)))
+    return bool(ok.value)
+
+
+def hog_server_poll(handle, out, max_out: int) -> int:
+    """Fill `out` (a ctypes array of HogServerResult) and return how many."""
+    n = ctypes.c_int(0)
+    _check("hog_server_poll", _lib.hog_server_poll(handle, out, max_out, ctypes.byref(n)))
+    return n.value
+
+
+def hog_server_release(handle, token: int) -> None:
+    _check("hog_server_release", _lib.hog_server_release(handle, token))
+
+
+def hog_server_stats(handle) -> tuple[int, int, int]:
+    """(requests on the GPU, arena bytes in use, free slots)."""
+    a, b, c = ctypes.c_int(0), ctypes.c_size_t(0), ctypes.c_int(0)
+    _check("hog_server_stats", _lib.hog_server_stats(handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
 # ---- shapes (host arithmetic only) --------------------------------------------
 
 def n_positions(extent: int, box: int, stride: int) -> int:
@@ -201,13 +282,15 @@ def grid_shapes(W: int, H: int, cell: int = 8, stride: int = 8, cells_x: int = 8
     return ncx, ncy, nx, ny
 
 
-def dets_to_numpy(raw: torch.Tensor, count: int):
-    """Unpack `count` hog_det records from a uint8 tensor (host or device)."""
+def dets_to_numpy(raw, count: int):
+    """Unpack `count` hog_det records from a uint8 tensor (host or device) or
+    a bytes object."""
     import numpy as np
 
     dt = np.dtype([("x", "<i4"), ("y", "<i4"), ("score", "<f4"), ("image", "<i4"), ("level", "<i4")])
-    a = raw[: count * DET_BYTES].cpu().numpy().view(dt)
-    return a
+    if isinstance(raw, (bytes, bytearray)):
+        return np.frombuffer(raw, dtype=np.uint8, count=count * DET_BYTES).view(dt)
+    return raw[: count * DET_BYTES].cpu().numpy().view(dt)
 
 
 from .pipeline import HogPipeline  # noqa: E402  (after the entry points it calls)

@@ -215,6 +215,7 @@ hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int s
                       hog_stream_t stream) {
     if (scores == nullptr || d_count == nullptr || workspace == nullptr) return HOG_ERR_ARG;
     if (out == nullptr && max_out > 0) return HOG_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(out) % alignof(hog_det) != 0) return HOG_ERR_ARG;
     if (nx < 0 || ny < 0 || (long)nx * ny >= (1L << 31) || stride < 1 || max_out < 0) return HOG_ERR_ARG;
     if (score_dtype != HOG_F32 && score_dtype != HOG_I32) return HOG_ERR_ARG;
     if (std::isnan(thr)) return HOG_ERR_ARG;

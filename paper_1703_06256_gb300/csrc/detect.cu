@@ -7,8 +7,9 @@
 //            windows with score >= thr to the workspace;
 //   scatter  one CTA per tile sums the counts of the tiles before it (a block
 //            reduction over at most a few thousand ints), scans its own flags
-//            (warp shuffles + one cross-warp step) and writes its detections
-//            at their final positions.  The last tile writes the total.
+//            (warp shuffles + one cross-warp step), builds its run of the
+//            list in shared memory and writes it with coalesced stores.  The
+//            last tile writes the total.
 // A map of a single tile skips the count launch.  Integer scores compare
 // against ceil(thr), which for integers is the same test as >= thr.
 #include <cmath>
@@ -23,6 +24,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPer = 8;
 constexpr int kTile = kThreads * kPer;
+constexpr int kDetWords = sizeof(hog_det) / 4;  // x, y, score, image, level
+static_assert(sizeof(hog_det) == 20, "hog_det is five 32-bit words");
 
 template <typename T>
 __device__ __forceinline__ bool pass(T v, float thr_f, int thr_i);
@@ -72,6 +75,7 @@ __global__ void __launch_bounds__(kThreads)
                           int max_out, int* __restrict__ d_count) {
     __shared__ int red[kThreads / 32];
     __shared__ int wsum[kThreads / 32];
+    __shared__ uint32_t stage[kTile * kDetWords];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     pdl_trigger();
     pdl_wait();
@@ -99,30 +103,35 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    int off = before + incl - mine;
+    int loc = incl - mine;  // this thread's first slot in the tile's list
     int tile_total = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) {
-        if (w < warp) off += wsum[w];
+        if (w < warp) loc += wsum[w];
         tile_total += wsum[w];
     }
+    // The tile's detections are contiguous in the output: build them in
+    // shared memory, then write the whole run with coalesced word stores
+    // (full 128-byte lines, whether `out` is device or mapped host memory).
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
         if (flags & (1u << e)) {
-            if (off < max_out) {
-                const long i = base + e;
-                const int py = (int)(i / nx), px = (int)(i - (long)py * nx);
-                hog_det d;
-                d.x = px * stride;
-                d.y = py * stride;
-                d.score = (float)v[e];
-                d.image = image;
-                d.level = level;
-                out[off] = d;
-            }
-            ++off;
+            const long i = base + e;
+            const int py = (int)(i / nx), px = (int)(i - (long)py * nx);
+            uint32_t* d = stage + loc * kDetWords;
+            d[0] = (uint32_t)(px * stride);
+            d[1] = (uint32_t)(py * stride);
+            d[2] = __float_as_uint((float)v[e]);
+            d[3] = (uint32_t)image;
+            d[4] = (uint32_t)level;
+            ++loc;
         }
     }
+    __syncthreads();
+    const int room = max_out - before;
+    const int keep = tile_total < room ? tile_total : (room > 0 ? room : 0);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(out + (room > 0 ? before : 0));
+    for (int j = threadIdx.x; j < keep * kDetWords; j += kThreads) dst[j] = stage[j];
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) *d_count = before + tile_total;
 }
 

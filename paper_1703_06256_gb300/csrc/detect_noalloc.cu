@@ -63,6 +63,7 @@ extern "C" hog_status hog_detect_noalloc(const void* scores, int score_dtype, in
                                          hog_stream_t stream) {
     if (scores == nullptr || d_count == nullptr) return HOG_ERR_ARG;
     if (out == nullptr && max_out > 0) return HOG_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(out) % alignof(hog_det) != 0) return HOG_ERR_ARG;
     if (nx < 0 || ny < 0 || stride < 1 || max_out < 0) return HOG_ERR_ARG;
     if ((long)nx * ny > (long)HOG_DETECT_NOALLOC_MAX_SCORES) return HOG_ERR_ARG;  // beyond the fixed scratch
     if (score_dtype != HOG_F32 && score_dtype != HOG_I32) return HOG_ERR_ARG;

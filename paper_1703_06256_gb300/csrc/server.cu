@@ -1,0 +1,407 @@
+// server.cu -- hog_server (include/fasthog_server.h): continuous batching of
+// detection requests over the per-image calls of fasthog.h.  Host code only;
+// every step of a request runs in the library's kernels through the public
+// entry points.
+//
+// A request's life: submit takes a free slot (stream, event, host detection
+// buffer) and a first-fit block of the device arena, then enqueues on the
+// slot's stream the host-to-device copy of the image, the cell-map call(s),
+// the window score and the detection list, which hog_detect writes straight
+// into the slot's page-locked host buffer (mapped into the device's address
+// space), and records the slot's event.  poll queries the events of the
+// requests on the GPU; a finished request gives its arena block back at once
+// and hands its host buffer to the caller until release.
+#include <atomic>
+#include <cmath>
+#include <iterator>
+#include <map>
+#include <new>
+#include <vector>
+
+#include "../../include/fasthog_server.h"
+#include "internal.cuh"
+
+namespace {
+
+using fasthog::cuda_fail;
+
+constexpr size_t kAlign = 256;
+constexpr int kMaxSlots = 64;
+constexpr int kCountStride = 16;  // int32 counters 64 bytes apart, one per slot
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+int n_pos(int extent, int box, int stride) { return extent < box ? 0 : (extent - box) / stride + 1; }
+bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 65535 && H <= 65535 && (long)W * H < (1L << 31); }
+
+// First-fit sub-allocator over one device allocation.  Free extents are kept
+// by offset and merged with their neighbours when a block comes back.
+class Arena {
+  public:
+    void reset(size_t size) {
+        free_.clear();
+        if (size) free_[0] = size;
+        used_ = 0;
+    }
+    bool take(size_t n, size_t* off) {
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second < n) continue;
+            *off = it->first;
+            const size_t rest = it->second - n, start = it->first + n;
+            free_.erase(it);
+            if (rest) free_[start] = rest;
+            used_ += n;
+            return true;
+        }
+        return false;
+    }
+    void give(size_t off, size_t n) {
+        used_ -= n;
+        auto next = free_.lower_bound(off);
+        if (next != free_.end() && off + n == next->first) {
+            n += next->second;
+            next = free_.erase(next);
+        }
+        if (next != free_.begin()) {
+            auto prev = std::prev(next);
+            if (prev->first + prev->second == off) {
+                prev->second += n;
+                return;
+            }
+        }
+        free_[off] = n;
+    }
+    size_t used() const { return used_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0;
+};
+
+// Switches to the server's device for the duration of a call.
+class DeviceGuard {
+  public:
+    explicit DeviceGuard(int dev) : dev_(dev) {
+        err_ = cudaGetDevice(&prev_);
+        if (err_ == cudaSuccess && prev_ != dev_) err_ = cudaSetDevice(dev_);
+    }
+    ~DeviceGuard() {
+        if (err_ == cudaSuccess && prev_ != dev_) cudaSetDevice(prev_);
+    }
+    cudaError_t error() const { return err_; }
+
+  private:
+    int dev_, prev_ = -1;
+    cudaError_t err_;
+};
+
+// Byte offsets of one request's buffers inside its arena block.
+struct Layout {
+    int ncx, ncy, nx, ny;
+    size_t img, cells, scores, ws_det, ws_det_bytes, bins, ii, ws_ii, ws_ii_bytes, total;
+};
+
+enum class SlotState { kFree, kBusy, kHeld };
+
+struct Slot {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    hog_det* dets_host = nullptr;  // page-locked, mapped
+    hog_det* dets_dev = nullptr;   // the same memory, as the device addresses it
+    SlotState state = SlotState::kFree;
+    size_t off = 0, bytes = 0;
+    int32_t rid = 0;
+    int W = 0, H = 0;
+};
+
+}  // namespace
+
+struct hog_server {
+    hog_server_config cfg;
+    int device = 0;
+    int cell_dtype = HOG_F32, score_dtype = HOG_F32;
+    bool fused = false;
+    size_t max_windows = 0;
+    uint8_t* arena_base = nullptr;
+    uint8_t* lut = nullptr;
+    void* w = nullptr;
+    int32_t* counts_host = nullptr;  // page-locked, mapped; slot i at [i * kCountStride]
+    int32_t* counts_dev = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::vector<int> free_slots;  // stack of free slot indices
+    std::vector<int> busy;        // slots on the GPU, in submission order
+
+    Layout plan(int W, int H, int channels) const {
+        Layout L{};
+        const hog_server_config& c = cfg;
+        L.ncx = n_pos(W, c.cell, c.stride);
+        L.ncy = n_pos(H, c.cell, c.stride);
+        const int r = c.cell / c.stride;
+        L.nx = L.ncx - (c.cells_x - 1) * r > 0 ? L.ncx - (c.cells_x - 1) * r : 0;
+        L.ny = L.ncy - (c.cells_y - 1) * r > 0 ? L.ncy - (c.cells_y - 1) * r : 0;
+        const size_t cell_bytes = cell_dtype == HOG_BF16 ? 2 : 4;
+        const size_t windows = (size_t)L.nx * L.ny;
+        size_t o = 0;
+        L.img = o;
+        o += align_up((size_t)W * H * channels);
+        L.cells = o;
+        o += align_up((size_t)L.ncx * L.ncy * c.n_bins * cell_bytes + 1);
+        L.scores = o;
+        o += align_up(windows * 4 + 1);
+        L.ws_det = o;
+        L.ws_det_bytes = hog_detect_workspace_bytes(L.nx, L.ny);
+        o += align_up(L.ws_det_bytes);
+        L.bins = L.ii = L.ws_ii = L.ws_ii_bytes = 0;
+        if (!fused) {
+            L.bins = o;
+            o += align_up((size_t)W * H);
+            L.ii = o;
+            o += align_up((size_t)c.n_bins * W * H * (c.ii_dtype == HOG_U16 ? 2 : 4));
+            L.ws_ii = o;
+            L.ws_ii_bytes = hog_integral_workspace_bytes(W, H, c.n_bins);
+            o += align_up(L.ws_ii_bytes);
+        }
+        L.total = o;
+        return L;
+    }
+
+    // Enqueue one request's work on its slot's stream.
+    hog_status enqueue(const Slot& sl, const Layout& L, const uint8_t* img, int W, int H, int channels,
+                       int32_t* count_dev) {
+        const hog_server_config& c = cfg;
+        uint8_t* base = arena_base + sl.off;
+        hog_stream_t st = reinterpret_cast<hog_stream_t>(sl.stream);
+        const int windows = L.nx * L.ny;
+        if (windows > 0) {
+            const cudaError_t e = cudaMemcpyAsync(base + L.img, img, (size_t)W * H * channels,
+                                                  cudaMemcpyHostToDevice, sl.stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+            hog_status s;
+            if (fused) {
+                s = hog_cell_hist_fused(base + L.img, W, H, channels, (size_t)W * channels, lut, c.n_bins, c.cell,
+                                        c.stride, cell_dtype, base + L.cells, st);
+            } else {
+                s = hog_bin_map(base + L.img, W, H, channels, (size_t)W * channels, lut, c.n_bins, base + L.bins,
+                                st);
+                if (s == HOG_OK)
+                    s = hog_integral(base + L.bins, W, H, c.n_bins, c.ii_dtype, base + L.ii, base + L.ws_ii,
+                                     L.ws_ii_bytes, st);
+                if (s == HOG_OK)
+                    s = hog_cell_hist(base + L.ii, W, H, c.n_bins, c.ii_dtype, c.cell, c.stride, cell_dtype,
+                                      base + L.cells, st);
+            }
+            if (s != HOG_OK) return s;
+            s = hog_window_score(base + L.cells, cell_dtype, L.ncx, L.ncy, c.n_bins, c.cells_x, c.cells_y, c.cell,
+                                 c.stride, w, c.w_dtype, c.bias, base + L.scores, st);
+            if (s != HOG_OK) return s;
+        }
+        // With no window position the list call still runs: it writes the count 0.
+        return hog_detect(base + L.scores, score_dtype, L.nx, L.ny, c.stride, c.thr, sl.rid, 0, sl.dets_dev,
+                          windows, count_dev, base + L.ws_det, L.ws_det_bytes, st);
+    }
+
+    void release_all() {
+        for (Slot& sl : slots) {
+            if (sl.state == SlotState::kBusy && sl.done) cudaEventSynchronize(sl.done);
+            if (sl.done) cudaEventDestroy(sl.done);
+            if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.dets_host) cudaFreeHost(sl.dets_host);
+        }
+        slots.clear();
+        if (counts_host) cudaFreeHost(counts_host);
+        if (arena_base) cudaFree(arena_base);
+        if (lut) cudaFree(lut);
+        if (w) cudaFree(w);
+        counts_host = nullptr;
+        arena_base = lut = nullptr;
+        w = nullptr;
+    }
+};
+
+namespace {
+
+hog_status check_config(const hog_server_config* c) {
+    if (c->n_bins < 1 || c->n_bins > 64) return HOG_ERR_ARG;
+    if (c->cell < 1 || c->cell > 64 || c->stride < 1 || c->cell % c->stride != 0) return HOG_ERR_ARG;
+    if (c->cells_x < 1 || c->cells_y < 1 || c->cells_x > 64 || c->cells_y > 64) return HOG_ERR_ARG;
+    if (c->w_dtype != HOG_F32 && c->w_dtype != HOG_BF16 && c->w_dtype != HOG_I8) return HOG_ERR_ARG;
+    if (!std::isfinite(c->bias) || std::isnan(c->thr)) return HOG_ERR_ARG;
+    if (c->fused < -1 || c->fused > 1) return HOG_ERR_ARG;
+    if (c->ii_dtype != HOG_I32 && c->ii_dtype != HOG_U16) return HOG_ERR_ARG;
+    if (c->n_slots < 1 || c->n_slots > kMaxSlots || c->budget_bytes == 0) return HOG_ERR_ARG;
+    if (!size_ok(c->max_W, c->max_H)) return HOG_ERR_ARG;
+    if (c->fused == 1 && !fasthog::cells_fused_supported(c->n_bins, c->cell, c->stride)) return HOG_ERR_UNSUPPORTED;
+    return HOG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+hog_status hog_server_create(const hog_server_config* cfg, const void* w, hog_server** out) {
+    if (out == nullptr) return HOG_ERR_ARG;
+    *out = nullptr;
+    if (cfg == nullptr || w == nullptr) return HOG_ERR_ARG;
+    hog_status st = check_config(cfg);
+    if (st != HOG_OK) return st;
+    hog_server* s = new (std::nothrow) hog_server();
+    if (s == nullptr) return HOG_ERR_ARG;
+    s->cfg = *cfg;
+    const hog_server_config& c = s->cfg;
+    // Histogram counts of cells up to 16 x 16 are exact in bf16; the tensor-core score takes bf16 cells.
+    s->cell_dtype = (c.w_dtype != HOG_F32 && c.cell <= 16) ? HOG_BF16 : HOG_F32;
+    s->score_dtype = c.w_dtype == HOG_I8 ? HOG_I32 : HOG_F32;
+    s->fused = c.fused == 1 || (c.fused == -1 && fasthog::cells_fused_supported(c.n_bins, c.cell, c.stride));
+    const int r = c.cell / c.stride;
+    const long mx = n_pos(c.max_W, c.cell, c.stride) - (long)(c.cells_x - 1) * r;
+    const long my = n_pos(c.max_H, c.cell, c.stride) - (long)(c.cells_y - 1) * r;
+    s->max_windows = (size_t)(mx > 0 ? mx : 0) * (size_t)(my > 0 ? my : 0);
+
+    cudaError_t e = cudaGetDevice(&s->device);
+    const size_t w_elems = (size_t)c.cells_x * c.cells_y * c.n_bins;
+    const size_t w_bytes = w_elems * (c.w_dtype == HOG_F32 ? 4 : (c.w_dtype == HOG_BF16 ? 2 : 1));
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->arena_base), c.budget_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(reinterpret_cast<void**>(&s->lut), HOG_LUT_BYTES);
+    if (e == cudaSuccess) e = cudaMalloc(&s->w, w_bytes);
+    if (e == cudaSuccess) e = cudaMemcpy(s->w, w, w_bytes, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void**>(&s->counts_host), sizeof(int32_t) * kCountStride * c.n_slots,
+                          cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&s->counts_dev), s->counts_host, 0);
+    s->slots.resize(c.n_slots);
+    for (int i = 0; i < c.n_slots && e == cudaSuccess; ++i) {
+        Slot& sl = s->slots[i];
+        e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming);
+        const size_t det_bytes = (s->max_windows > 0 ? s->max_windows : 1) * sizeof(hog_det);
+        if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&sl.dets_host), det_bytes, cudaHostAllocMapped);
+        if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sl.dets_dev), sl.dets_host, 0);
+    }
+    if (e != cudaSuccess) {
+        st = cuda_fail(e);
+        s->release_all();
+        delete s;
+        return st;
+    }
+    st = hog_build_lut(c.n_bins, s->lut, reinterpret_cast<hog_stream_t>(s->slots[0].stream));
+    if (st == HOG_OK) {
+        e = cudaStreamSynchronize(s->slots[0].stream);
+        if (e != cudaSuccess) st = cuda_fail(e);
+    }
+    if (st != HOG_OK) {
+        s->release_all();
+        delete s;
+        return st;
+    }
+    s->arena.reset(c.budget_bytes);
+    for (int i = c.n_slots - 1; i >= 0; --i) s->free_slots.push_back(i);
+    s->busy.reserve(c.n_slots);
+    *out = s;
+    return HOG_OK;
+}
+
+hog_status hog_server_destroy(hog_server* s) {
+    if (s == nullptr) return HOG_OK;
+    DeviceGuard g(s->device);
+    s->release_all();
+    delete s;
+    return g.error() == cudaSuccess ? HOG_OK : cuda_fail(g.error());
+}
+
+size_t hog_server_request_bytes(const hog_server* s, int W, int H, int channels) {
+    if (s == nullptr || !size_ok(W, H) || (channels != 1 && channels != 3)) return 0;
+    return s->plan(W, H, channels).total;
+}
+
+hog_status hog_server_submit(hog_server* s, int32_t rid, const uint8_t* img, int W, int H, int channels,
+                             int* admitted) {
+    if (s == nullptr || img == nullptr || admitted == nullptr) return HOG_ERR_ARG;
+    *admitted = 0;
+    if (!size_ok(W, H) || (channels != 1 && channels != 3)) return HOG_ERR_ARG;
+    if (W > s->cfg.max_W || H > s->cfg.max_H) return HOG_ERR_ARG;
+    const Layout L = s->plan(W, H, channels);
+    if (L.total > s->cfg.budget_bytes) return HOG_ERR_ARG;
+    if (s->free_slots.empty()) return HOG_OK;
+    size_t off = 0;
+    if (!s->arena.take(L.total, &off)) return HOG_OK;
+    DeviceGuard g(s->device);
+    if (g.error() != cudaSuccess) {
+        s->arena.give(off, L.total);
+        return cuda_fail(g.error());
+    }
+    const int i = s->free_slots.back();
+    Slot& sl = s->slots[i];
+    sl.off = off;
+    sl.bytes = L.total;
+    sl.rid = rid;
+    sl.W = W;
+    sl.H = H;
+    s->counts_host[i * kCountStride] = -1;
+    hog_status st = s->enqueue(sl, L, img, W, H, channels, s->counts_dev + i * kCountStride);
+    if (st == HOG_OK) {
+        const cudaError_t e = cudaEventRecord(sl.done, sl.stream);
+        if (e != cudaSuccess) st = cuda_fail(e);
+    }
+    if (st != HOG_OK) {
+        // Part of the work may be enqueued: let it finish before the block is reused.
+        cudaStreamSynchronize(sl.stream);
+        s->arena.give(off, L.total);
+        return st;
+    }
+    s->free_slots.pop_back();
+    sl.state = SlotState::kBusy;
+    s->busy.push_back(i);
+    *admitted = 1;
+    return HOG_OK;
+}
+
+hog_status hog_server_poll(hog_server* s, hog_server_result* out, int max_out, int* n_out) {
+    if (s == nullptr || n_out == nullptr || max_out < 0 || (out == nullptr && max_out > 0)) return HOG_ERR_ARG;
+    *n_out = 0;
+    DeviceGuard g(s->device);
+    if (g.error() != cudaSuccess) return cuda_fail(g.error());
+    int n = 0;
+    size_t keep = 0;
+    for (size_t k = 0; k < s->busy.size(); ++k) {
+        const int i = s->busy[k];
+        Slot& sl = s->slots[i];
+        cudaError_t e = n < max_out ? cudaEventQuery(sl.done) : cudaErrorNotReady;
+        if (e == cudaErrorNotReady) {
+            s->busy[keep++] = i;
+            continue;
+        }
+        std::atomic_thread_fence(std::memory_order_acquire);
+        hog_server_result& r = out[n++];
+        r.rid = sl.rid;
+        r.status = e == cudaSuccess ? HOG_OK : cuda_fail(e);
+        r.count = e == cudaSuccess ? *static_cast<volatile int32_t*>(s->counts_host + i * kCountStride) : 0;
+        r.token = i;
+        r.W = sl.W;
+        r.H = sl.H;
+        r.dets = sl.dets_host;
+        s->arena.give(sl.off, sl.bytes);
+        sl.state = SlotState::kHeld;
+    }
+    s->busy.resize(keep);
+    *n_out = n;
+    return HOG_OK;
+}
+
+hog_status hog_server_release(hog_server* s, int32_t token) {
+    if (s == nullptr || token < 0 || token >= (int32_t)s->slots.size()) return HOG_ERR_ARG;
+    Slot& sl = s->slots[token];
+    if (sl.state != SlotState::kHeld) return HOG_ERR_ARG;
+    sl.state = SlotState::kFree;
+    s->free_slots.push_back(token);
+    return HOG_OK;
+}
+
+hog_status hog_server_stats(const hog_server* s, int* in_flight, size_t* bytes_in_use, int* free_slots) {
+    if (s == nullptr) return HOG_ERR_ARG;
+    if (in_flight) *in_flight = (int)s->busy.size();
+    if (bytes_in_use) *bytes_in_use = s->arena.used();
+    if (free_slots) *free_slots = (int)s->free_slots.size();
+    return HOG_OK;
+}
+
+}  // extern "C"

@@ -1,19 +1,20 @@
-"""The C-ABI library loads and exports every entry point include/fasthog.h
+"""The C-ABI library loads and exports every entry point that include/*.h
 declares; host-side argument checks reject bad calls before touching CUDA.
 No compute call is made here (this runs without a GPU)."""
 
 import ctypes
+import glob
 import os
 import re
 
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "fasthog.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\*?\s+\*?(hog_[a-z_0-9]+)\s*\(", src, flags=re.M)))
 
@@ -82,3 +83,29 @@ def test_argument_errors_need_no_gpu(fh):
     assert L.hog_detect(4096, fh.HOG_BF16, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 256, None) == ARG
     assert L.hog_detect(None, fh.HOG_F32, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 256, None) == ARG
     assert L.hog_device_status(None, 0) == ARG
+
+
+def test_server_argument_errors_need_no_gpu(fh):
+    L = fh.lib()
+    ARG = fh.HOG_ERR_ARG
+    good = dict(n_bins=8, cell=8, stride=4, cells_x=8, cells_y=16, w_dtype=fh.HOG_BF16, bias=0.0, thr=0.5,
+                fused=-1, ii_dtype=fh.HOG_I32, n_slots=4, budget_bytes=1 << 20, max_W=640, max_H=480)
+    h = ctypes.c_void_p(1)
+    w = (ctypes.c_uint16 * (8 * 16 * 8))()
+    assert L.hog_server_create(None, w, ctypes.byref(h)) == ARG and h.value is None
+    assert L.hog_server_create(ctypes.byref(fh.HogServerConfig(**good)), None, ctypes.byref(h)) == ARG
+    for bad in (dict(n_bins=0), dict(stride=3), dict(cells_x=0), dict(w_dtype=fh.HOG_U8), dict(fused=2),
+                dict(ii_dtype=fh.HOG_F32), dict(n_slots=0), dict(n_slots=65), dict(budget_bytes=0),
+                dict(max_W=0), dict(thr=float("nan")), dict(bias=float("inf"))):
+        cfg = fh.HogServerConfig(**{**good, **bad})
+        assert L.hog_server_create(ctypes.byref(cfg), w, ctypes.byref(h)) == ARG, bad
+    cfg = fh.HogServerConfig(**{**good, "fused": 1, "n_bins": 9})  # the fused call takes N_b 8 or 16
+    assert L.hog_server_create(ctypes.byref(cfg), w, ctypes.byref(h)) == fh.HOG_ERR_UNSUPPORTED
+    ok = ctypes.c_int(7)
+    assert L.hog_server_submit(None, 0, 4096, 64, 128, 3, ctypes.byref(ok)) == ARG
+    n = ctypes.c_int(0)
+    assert L.hog_server_poll(None, None, 0, ctypes.byref(n)) == ARG
+    assert L.hog_server_release(None, 0) == ARG
+    assert L.hog_server_stats(None, None, None, None) == ARG
+    assert L.hog_server_request_bytes(None, 64, 128, 3) == 0
+    assert L.hog_server_destroy(None) == fh.HOG_OK

@@ -227,6 +227,31 @@ def test_detect_float_and_overflow(fh, g):
     assert n2 == len(xs) and len(det) == 100 and np.array_equal(det["x"], xs[:100])
 
 
+def test_detect_truncation_and_offsets(fh, g):
+    """The list stops at max_out exactly (at tile boundaries and inside a
+    tile), nothing past it is written, and any 4-byte-aligned start works."""
+    rng = np.random.default_rng(13)
+    S = rng.normal(0, 1, size=(97, 211)).astype(np.float32)  # ~20.5k scores: 11 tiles of 2048
+    xs, ys, sc = oracle.detect(S.astype(np.float64), 4, 0.0)
+    n_ref = len(xs)
+    s = torch.from_numpy(S.reshape(-1)).cuda()
+    ws_b = fh.hog_detect_workspace_bytes(211, 97)
+    ws = torch.empty(ws_b, dtype=torch.uint8, device="cuda")
+    for max_out in (0, 1, 1023, 1024, 1025, 5000, n_ref - 1, n_ref, n_ref + 7):
+        for shift in (0, 4, 8, 12):
+            total = (n_ref + 16) * fh.DET_BYTES + 64
+            buf = torch.full((total,), 0x5A, dtype=torch.uint8, device="cuda")
+            cnt = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+            fh.hog_detect(s, fh.HOG_F32, 211, 97, 4, 0.0, 1, 0, buf.data_ptr() + shift, max_out, cnt, ws, ws_b)
+            host = buf.cpu().numpy()
+            assert int(cnt.item()) == n_ref
+            k = min(max_out, n_ref)
+            det = host[shift: shift + k * fh.DET_BYTES].copy().view(fh.dets_to_numpy(b"", 0).dtype)
+            assert np.array_equal(det["x"], xs[:k]) and np.array_equal(det["y"], ys[:k])
+            assert np.array_equal(det["score"], sc[:k].astype(np.float32))
+            assert np.all(host[:shift] == 0x5A) and np.all(host[shift + k * fh.DET_BYTES:] == 0x5A)
+
+
 # ---------------------------------------------------------------- whole path
 def compare_pipeline(fh, g, img, nb, stride, w, bias, thr, ii_dtype, cell_dtype):
     H, W = img.shape[:2]
