@@ -13,12 +13,15 @@
 // same amount, so each CTA builds G from its own tile only ("tile-local"
 // integral image), as a 2-D prefix sum of its block histograms.
 //
-// Per tile of BX x BY cells (origins), a CTA
+// Per tile of BX x BY cells (origins), a CTA of 512 threads
 //   1. computes the bins of the tile's (BX + r - 1) x (BY + r - 1) blocks with
 //      the same quad code and shared-memory table quadrant as the bin-map
-//      kernel, and counts them per block (8-bit fields, s^2 <= 64 for s = 4, 8);
-//   2. forms G over those blocks in shared memory (16-bit fields);
-//   3. writes each cell's histogram from four corners of G.
+//      kernel, one quad (4 pixels of a row) per task, and adds them into
+//      per-block counters (8-bit fields, s^2 <= 64 for s = 4, 8) with
+//      shared-memory atomics;
+//   2. forms G over those blocks in shared memory (16-bit fields): warp
+//      scans along block rows, then running sums down the columns;
+//   3. writes each cell's histogram from four corners of G (16-byte stores).
 // Tiles overlap by r - 1 blocks, whose bins are computed twice.  The grid is
 // persistent so that each CTA stages the table quadrant once.
 #include <type_traits>
@@ -31,19 +34,29 @@ namespace fasthog {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kBX = 32, kBY = 8;        // cells per tile (= 256 threads in step 3)
+constexpr int kThreads = 512;
 constexpr int kQuadBytes = 256 * 256;
 constexpr int kMaxR = 4;
 
-template <int NB>
+// Tile of BX x BY cell origins per CTA.  Its blocks span (BX + r - 1) s by
+// (BY + r - 1) s pixels, at most 140 x 76 (s = 4) or 152 x 152 (s = 8) for
+// r <= 4: below 2^15 pixels, so every corner value of the tile-local integral
+// image fits a 16-bit field with a spare bit, and (a + d) - (b + c) of Eq. 6
+// never carries or borrows between fields.
+template <int S>
+struct TileShape {
+    static constexpr int BX = S == 4 ? 32 : 16;
+    static constexpr int BY = 16;
+};
+
+template <int NB, int S>
 struct FusedSmem {
-    static constexpr int NW8 = NB / 4;                 // 8-bit-field words per block histogram
-    static constexpr int NW16 = NB / 2;                // 16-bit-field words per G entry
-    static constexpr int BXB = kBX + kMaxR - 1;        // blocks per tile row (max)
-    static constexpr int BYB = kBY + kMaxR - 1;
-    uint32_t bh[BYB][BXB][NW8];                        // block histograms
-    uint32_t g[BYB + 1][BXB + 1][NW16];                // corner-sampled tile integral image
+    static constexpr int NW8 = NB / 4;                      // 8-bit-field words per block histogram
+    static constexpr int NW16 = NB / 2;                     // 16-bit-field words per G entry
+    static constexpr int BXB = TileShape<S>::BX + kMaxR - 1;  // blocks per tile row (max)
+    static constexpr int BYB = TileShape<S>::BY + kMaxR - 1;
+    uint32_t g[BYB + 1][BXB + 1][NW16];                     // corner-sampled tile integral image
+    uint32_t bh[BYB][BXB][NW8];                             // block histograms
 };
 
 template <typename OutT>
@@ -55,18 +68,30 @@ __device__ __forceinline__ OutT as_count(uint32_t v) {
     }
 }
 
-template <int CH, int NB, typename OutT>
-__global__ void __launch_bounds__(kThreads)
+// A count as the 32-bit pattern of a 4-byte OutT (float or int32).
+template <typename OutT>
+__device__ __forceinline__ uint32_t out_bits(uint32_t v) {
+    if constexpr (std::is_same<OutT, float>::value) {
+        return __float_as_uint((float)v);
+    } else {
+        return v;
+    }
+}
+
+template <int CH, int NB, int S, typename OutT>
+__global__ void __launch_bounds__(kThreads, 2)
     cells_fused_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
-                       const uint8_t* __restrict__ lut, int s, int r, int ncx, int ncy, OutT* __restrict__ cells,
-                       unsigned int* status) {
-    using S = FusedSmem<NB>;
+                       const uint8_t* __restrict__ lut, int r, int ncx, int ncy, OutT* __restrict__ cells,
+                       int out_align, unsigned int* status) {
+    using F = FusedSmem<NB, S>;
+    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    constexpr int QPR = S / 4;  // quads in one block row
     extern __shared__ __align__(128) uint8_t smem[];
     uint8_t* lutq = smem;
-    S& sm = *reinterpret_cast<S*>(smem + kQuadBytes);
+    F& sm = *reinterpret_cast<F*>(smem + kQuadBytes);
     __shared__ __align__(8) uint64_t lut_bar;
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     if (tid == 0) {
         ptx::mbar_init(&lut_bar, 1);
         ptx::fence_mbar_init();
@@ -84,116 +109,155 @@ __global__ void __launch_bounds__(kThreads)
         return;
     }
 
-    const int tiles_x = (ncx + kBX - 1) / kBX, tiles_y = (ncy + kBY - 1) / kBY;
-    const int bxn = kBX + r - 1, byn = kBY + r - 1;  // blocks of a tile
+    const int tiles_x = (ncx + BX - 1) / BX, tiles_y = (ncy + BY - 1) / BY;
+    const int bxn = BX + r - 1, byn = BY + r - 1;  // blocks of a tile
     const long row_bytes = (long)W * CH;
-    const int quads_per_brow = s / 4;                // quads in one block row
+    const int row_tasks = bxn * QPR;               // quads in one pixel row of the tile
+    const int n_tasks = byn * S * row_tasks;
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
-        const int bx0 = (t % tiles_x) * kBX, by0 = (t / tiles_x) * kBY;
-        __syncthreads();  // the previous tile's G reads are done
-        // 1. block histograms
-        for (int blk = tid; blk < bxn * byn; blk += kThreads) {
-            const int bi = blk % bxn, bj = blk / bxn;
-            uint32_t h[S::NW8];
+        const int bx0 = (t % tiles_x) * BX, by0 = (t / tiles_x) * BY;
+        __syncthreads();  // the previous tile's reads of g and bh are done
+        for (int k = tid; k < byn * F::BXB * F::NW8; k += kThreads) (&sm.bh[0][0][0])[k] = 0;
+        __syncthreads();
+        // 1. block histograms: one quad (4 pixels of one row) per task; the
+        //    8-bit fields of a block's words collect at most s^2 <= 64 pixels.
+        for (int task = tid; task < n_tasks; task += kThreads) {
+            const int prow = task / row_tasks, qc = task - prow * row_tasks;
+            const int y = by0 * S + prow, x = bx0 * S + 4 * qc;
+            if (y <= 0 || y >= H - 1 || x >= W) continue;  // border rows, or outside the image: no bins
+            QuadWords<CH> q;
+            load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
+            const uint32_t packed = bins_of_quad<CH, true>(q, x, W, lutq, lut, NB, NB / 4);
+            uint32_t h[F::NW8];
 #pragma unroll
-            for (int k = 0; k < S::NW8; ++k) h[k] = 0;
-            const int x_blk = (bx0 + bi) * s, y_blk = (by0 + bj) * s;
-            for (int yy = 0; yy < s; ++yy) {
-                const int y = y_blk + yy;
-                if (y <= 0 || y >= H - 1) continue;  // border rows, or below the image: no bins
-                for (int qq = 0; qq < quads_per_brow; ++qq) {
-                    const int x = x_blk + 4 * qq;
-                    if (x >= W) break;
-                    QuadWords<CH> q;
-                    load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
-                    const uint32_t packed = bins_of_quad<CH, true>(q, x, W, lutq, lut, NB, NB / 4);
+            for (int k = 0; k < F::NW8; ++k) h[k] = 0;
 #pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        const uint32_t v = (packed >> (8 * p)) & 0xFFu;
-                        const uint32_t inc = 1u << ((v & 3) << 3);
+            for (int p = 0; p < 4; ++p) {
+                const uint32_t v = (packed >> (8 * p)) & 0xFFu;
+                const uint32_t inc = 1u << ((v & 3) << 3);
 #pragma unroll
-                        for (int k = 0; k < S::NW8; ++k) h[k] += ((v >> 2) == (uint32_t)k) ? inc : 0u;  // 0xFF: none
-                    }
-                }
+                for (int k = 0; k < F::NW8; ++k) h[k] += ((v >> 2) == (uint32_t)k) ? inc : 0u;  // 0xFF: none
             }
+            uint32_t* dst = sm.bh[prow / S][qc / QPR];
 #pragma unroll
-            for (int k = 0; k < S::NW8; ++k) sm.bh[bj][bi][k] = h[k];
+            for (int k = 0; k < F::NW8; ++k)
+                if (h[k]) atomicAdd(dst + k, h[k]);
         }
         __syncthreads();
-        // 2. G: exclusive 2-D prefix of the block histograms, widened to
-        //    16-bit fields (bins 2e, 2e+1 in word e).  First the prefix along
-        //    each block row (G row J+1 holds the rows < J+1), then down columns.
-        for (int task = tid; task < (byn + 1) * S::NW16; task += kThreads) {
-            const int J = task / S::NW16, e = task % S::NW16;
-            uint32_t run = 0;
-            sm.g[J][0][e] = 0;
-            for (int I = 0; I < bxn; ++I) {
-                if (J > 0) {
+        // 2. G: exclusive 2-D prefix of the block histograms in 16-bit fields
+        //    (bins 2e, 2e+1 in word e).  Along block rows with warp scans (G row
+        //    J + 1 holds block row J), then down the columns.
+        for (int task = wid; task < byn * F::NW16; task += kThreads / 32) {
+            const int J = 1 + task / F::NW16, e = task % F::NW16;
+            uint32_t carry = 0;
+            for (int I0 = 0; I0 < bxn; I0 += 32) {
+                const int I = I0 + lane;
+                uint32_t v = 0;
+                if (I < bxn) {
                     const uint32_t w8 = sm.bh[J - 1][I][e >> 1];
                     const uint32_t two = (e & 1) ? (w8 >> 16) : (w8 & 0xFFFFu);  // bins 2e, 2e+1 (8-bit each)
-                    run += (two & 0xFFu) | ((two >> 8) << 16);
+                    v = (two & 0xFFu) | ((two >> 8) << 16);
                 }
-                sm.g[J][I + 1][e] = run;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                    if (lane >= d) v += u;
+                }
+                if (I < bxn) sm.g[J][I + 1][e] = v + carry;
+                carry += __shfl_sync(0xffffffffu, v, 31);
             }
+            if (lane == 0) sm.g[J][0][e] = 0;
         }
+        for (int k = tid; k < (bxn + 1) * F::NW16; k += kThreads) sm.g[0][k / F::NW16][k % F::NW16] = 0;
         __syncthreads();
-        for (int task = tid; task < (bxn + 1) * S::NW16; task += kThreads) {
-            const int I = task / S::NW16, e = task % S::NW16;
+        for (int task = tid; task < (bxn + 1) * F::NW16; task += kThreads) {
+            const int I = task / F::NW16, e = task % F::NW16;
             uint32_t run = 0;
-            for (int J = 0; J <= byn; ++J) {
+            for (int J = 1; J <= byn; ++J) {
                 run += sm.g[J][I][e];
                 sm.g[J][I][e] = run;
             }
         }
         __syncthreads();
         // 3. cells: Eq. 6 on the corner-sampled integral image
-        {
-            const int ci = tid % kBX, cj = tid / kBX;
+        if (tid < BX * BY) {
+            const int ci = tid % BX, cj = tid / BX;
             const int i = bx0 + ci, j = by0 + cj;
             if (i < ncx && j < ncy) {
-                OutT* out = cells + ((size_t)j * ncx + i) * NB;
+                // the cell's NB counts as OutT, packed into 32-bit words (bf16: two per word)
+                constexpr int NWORDS = NB * (int)sizeof(OutT) / 4;
+                uint32_t words[NWORDS];
 #pragma unroll
-                for (int e = 0; e < S::NW16; ++e) {
-                    // (a + d) - (b + c) per 16-bit field: no field borrows
+                for (int e = 0; e < F::NW16; ++e) {
+                    // (a + d) - (b + c) per 16-bit field: no field carries or borrows
                     const uint32_t v = (sm.g[cj + r][ci + r][e] + sm.g[cj][ci][e]) -
                                        (sm.g[cj][ci + r][e] + sm.g[cj + r][ci][e]);
-                    out[2 * e] = as_count<OutT>(v & 0xFFFFu);
-                    out[2 * e + 1] = as_count<OutT>(v >> 16);
+                    if constexpr (sizeof(OutT) == 2) {
+                        words[e] = (uint32_t)as_count<OutT>(v & 0xFFFFu) | ((uint32_t)as_count<OutT>(v >> 16) << 16);
+                    } else {
+                        words[2 * e] = out_bits<OutT>(v & 0xFFFFu);
+                        words[2 * e + 1] = out_bits<OutT>(v >> 16);
+                    }
+                }
+                OutT* out = cells + ((size_t)j * ncx + i) * NB;
+                if (out_align == 16) {
+#pragma unroll
+                    for (int k = 0; k < NWORDS / 4; ++k)
+                        reinterpret_cast<uint4*>(out)[k] =
+                            make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+                } else if (out_align == 4) {
+#pragma unroll
+                    for (int k = 0; k < NWORDS; ++k) reinterpret_cast<uint32_t*>(out)[k] = words[k];
+                } else {  // a 2-byte-aligned bf16 map
+#pragma unroll
+                    for (int k = 0; k < 2 * NWORDS; ++k)
+                        reinterpret_cast<uint16_t*>(out)[k] = (uint16_t)(words[k >> 1] >> (16 * (k & 1)));
                 }
             }
         }
     }
 }
 
-template <int CH, int NB, typename OutT>
-hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int s, int r, int ncx, int ncy,
+template <int CH, int NB, int S, typename OutT>
+hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
                     void* cells, unsigned int* status, cudaStream_t st) {
-    const size_t smem = kQuadBytes + sizeof(FusedSmem<NB>);
-    auto kern = cells_fused_kernel<CH, NB, OutT>;
+    const size_t smem = kQuadBytes + sizeof(FusedSmem<NB, S>);
+    auto kern = cells_fused_kernel<CH, NB, S, OutT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    const int tiles = ((ncx + kBX - 1) / kBX) * ((ncy + kBY - 1) / kBY);
-    const int cap = 2 * sm_count();
+    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    const int tiles = ((ncx + BX - 1) / BX) * ((ncy + BY - 1) / BY);
+    const int cap = 2 * sm_count();  // two CTAs of this size fit an SM
     const int grid = tiles < cap ? tiles : cap;
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
-    return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, img, W, H, pitch, aligned, lut, s, r, ncx, ncy,
-                      static_cast<OutT*>(cells), status);
+    // every cell starts a multiple of 16 bytes after `cells`
+    const uintptr_t c = reinterpret_cast<uintptr_t>(cells);
+    const int out_align = c % 16 == 0 ? 16 : (c % 4 == 0 ? 4 : 2);
+    return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, img, W, H, pitch, aligned, lut, r, ncx, ncy,
+                      static_cast<OutT*>(cells), out_align, status);
+}
+
+template <int CH, int NB, int S>
+hog_status by_out(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
+                  int cell_dtype, void* cells, unsigned int* status, cudaStream_t st) {
+    if (cell_dtype == HOG_BF16)
+        return launch_t<CH, NB, S, uint16_t>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    if (cell_dtype == HOG_F32)
+        return launch_t<CH, NB, S, float>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    return launch_t<CH, NB, S, int32_t>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
 }
 
 template <int CH, int NB>
-hog_status by_out(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int s, int r, int ncx, int ncy,
-                  int cell_dtype, void* cells, unsigned int* status, cudaStream_t st) {
-    if (cell_dtype == HOG_BF16)
-        return launch_t<CH, NB, uint16_t>(img, W, H, pitch, lut, s, r, ncx, ncy, cells, status, st);
-    if (cell_dtype == HOG_F32)
-        return launch_t<CH, NB, float>(img, W, H, pitch, lut, s, r, ncx, ncy, cells, status, st);
-    return launch_t<CH, NB, int32_t>(img, W, H, pitch, lut, s, r, ncx, ncy, cells, status, st);
+hog_status by_stride(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int s, int r, int ncx,
+                     int ncy, int cell_dtype, void* cells, unsigned int* status, cudaStream_t st) {
+    if (s == 4) return by_out<CH, NB, 4>(img, W, H, pitch, lut, r, ncx, ncy, cell_dtype, cells, status, st);
+    return by_out<CH, NB, 8>(img, W, H, pitch, lut, r, ncx, ncy, cell_dtype, cells, status, st);
 }
 
 }  // namespace
 
 bool cells_fused_supported(int n_bins, int cell, int stride) {
-    // 16-bit corner sums stay below 2^15 per tile for strides 4 and 8 with r <= 4
+    // tile shapes keep 16-bit corner sums below 2^15 for strides 4 and 8 with r <= 4
     return (n_bins == 8 || n_bins == 16) && (stride == 4 || stride == 8) && cell % stride == 0 &&
            cell / stride <= kMaxR;
 }
@@ -206,10 +270,10 @@ hog_status launch_cells_fused(const uint8_t* img, int W, int H, int channels, si
     if (ncx == 0 || ncy == 0) return HOG_OK;
     const int r = cell / stride;
     if (channels == 1)
-        return n_bins == 8 ? by_out<1, 8>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st)
-                           : by_out<1, 16>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st);
-    return n_bins == 8 ? by_out<3, 8>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st)
-                       : by_out<3, 16>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st);
+        return n_bins == 8 ? by_stride<1, 8>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st)
+                           : by_stride<1, 16>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st);
+    return n_bins == 8 ? by_stride<3, 8>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st)
+                       : by_stride<3, 16>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st);
 }
 
 }  // namespace fasthog

@@ -28,7 +28,9 @@
 // band of cell row rho' is the same planes with the descriptor start moved
 // back 16 bytes per row (LBO = plane size, SBO = 128 bytes).
 //
-// One CTA: 128 windows (one TMEM lane each) by Tc * r output rows; 4 warps.
+// One CTA: 128 windows (one TMEM lane each) by the Tc output rows of one
+// residue class (blockIdx.z = phi), so the r classes of a row band run in
+// separate CTAs and read disjoint cell rows; 4 warps.
 // Warp 0 lane 0 streams cell rows into a ring of shared-memory stages with
 // bulk async copies (mbarrier full/empty pipeline), warp 1 lane 0 issues
 // the MMAs (the first of each class overwrites its columns, the rest
@@ -96,19 +98,43 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The 8 bins of filter cell c (weights 8c .. 8c + 7) as 8 bf16 values.
 template <typename WT>
-__device__ __forceinline__ uint16_t weight_bf16(const WT* w, int k);
+__device__ __forceinline__ uint4 load_weight_cell(const WT* w, int c);
 template <>
-__device__ __forceinline__ uint16_t weight_bf16<uint16_t>(const uint16_t* w, int k) {
-    return __ldg(w + k);
+__device__ __forceinline__ uint4 load_weight_cell<uint16_t>(const uint16_t* w, int c) {
+    const uint16_t* p = w + (size_t)c * kNB;
+    if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) return __ldg(reinterpret_cast<const uint4*>(p));
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = (uint32_t)__ldg(p + 2 * k) | ((uint32_t)__ldg(p + 2 * k + 1) << 16);
+    return make_uint4(h[0], h[1], h[2], h[3]);
 }
 template <>
-__device__ __forceinline__ uint16_t weight_bf16<int8_t>(const int8_t* w, int k) {
-    return f32_to_bf16_exact_int((float)__ldg(w + k));  // |w| <= 127: exact in bf16
+__device__ __forceinline__ uint4 load_weight_cell<int8_t>(const int8_t* w, int c) {
+    const int8_t* p = w + (size_t)c * kNB;
+    int8_t b[8];
+    if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            b[k] = (int8_t)(v.x >> (8 * k));
+            b[k + 4] = (int8_t)(v.y >> (8 * k));
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) b[k] = __ldg(p + k);
+    }
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)  // |w| <= 127: exact in bf16
+        h[k] = (uint32_t)f32_to_bf16_exact_int((float)b[2 * k]) |
+               ((uint32_t)f32_to_bf16_exact_int((float)b[2 * k + 1]) << 16);
+    return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
 struct TcGeom {
-    int r, Tc, rows;      // residue count, outputs per class per CTA, cell rows per CTA
+    int r, Tc, rows;      // residue count, output rows per CTA (one class), cell rows per CTA
     int row_cells;        // cells staged per cell row: kM + (kCX - 1) r
     int row_bytes;        // row_cells * 16
     int stage_bytes;      // kRowsPerStage rows
@@ -117,7 +143,7 @@ struct TcGeom {
     int band_bytes;       // kCX planes
     int cols;             // TMEM columns allocated (power of two >= 32)
     __host__ __device__ TcGeom(int r_, int Tc_) : r(r_), Tc(Tc_) {
-        rows = (Tc + kCY - 1) * r;
+        rows = Tc + kCY - 1;
         row_cells = kM + (kCX - 1) * r;
         row_bytes = row_cells * 16;
         stage_bytes = kRowsPerStage * row_bytes;
@@ -125,7 +151,7 @@ struct TcGeom {
         plane_bytes = plane_rows * 16;
         band_bytes = kCX * plane_bytes;
         cols = 32;
-        while (cols < r * Tc) cols *= 2;
+        while (cols < Tc) cols *= 2;
     }
     __host__ __device__ size_t smem_bytes() const {
         return 1024 + (size_t)band_bytes + (size_t)kStages * stage_bytes + 256;
@@ -151,14 +177,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int px0 = blockIdx.x * kM;
-    const int py_lo = blockIdx.y * Tc * r;
+    const int phi = blockIdx.z;                    // residue class of this CTA
+    const int py_lo = blockIdx.y * Tc * r + phi;   // first output row; rows step by r
 
-    // band planes: plane_i[v][b] = w[Tc + 14 - v][i][b] for filter rows 0..15, zero elsewhere
-    for (int e = tid; e < kCX * G.plane_rows * kNB; e += kThreads) {
-        const int b = e % kNB, v = (e / kNB) % G.plane_rows, i = e / (kNB * G.plane_rows);
-        const int j = Tc + 14 - v;
-        reinterpret_cast<uint16_t*>(band)[e] =
-            (j >= 0 && j < kCY) ? weight_bf16<WT>(w, (j * kCX + i) * kNB + b) : (uint16_t)0;
+    // band planes: plane_i[v][b] = w[Tc + 14 - v][i][b] for filter rows 0..15, zero elsewhere.
+    // Thread t < 128 moves the 8 bins of filter cell (j, i) = (t / 8, t % 8) in one load; the
+    // rows of the planes that hold no filter row are zeroed by 16-byte stores.
+    {
+        const int j = tid / kCX, i = tid % kCX;
+        uint4 v = load_weight_cell<WT>(w, tid);
+        *reinterpret_cast<uint4*>(band + (size_t)i * G.plane_bytes + (size_t)(Tc + 14 - j) * 16) = v;
+        const int zero_rows = G.plane_rows - kCY;  // v < Tc - 1 or v > Tc + 14
+        for (int e = tid; e < kCX * zero_rows; e += kThreads) {
+            const int pi = e / zero_rows, zr = e % zero_rows;
+            const int vrow = zr < Tc - 1 ? zr : zr + kCY;
+            *reinterpret_cast<uint4*>(band + (size_t)pi * G.plane_bytes + (size_t)vrow * 16) = make_uint4(0, 0, 0, 0);
+        }
     }
     if (tid == 0) {
         aborted = 0;
@@ -188,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int n_stage_loads = (G.rows + kRowsPerStage - 1) / kRowsPerStage;
     const int valid_cells = min(G.row_cells, ncx - px0);  // > 0: px0 < nx <= ncx
     if (warp == 0 && lane == 0) {
-        // producer: cell rows py_lo .. py_lo + rows - 1 into the stage ring
+        // producer: cell rows py_lo + r rho (rho < rows) into the stage ring
         int armed = 0;  // stages whose copies were issued
         for (int k = 0; k < n_stage_loads; ++k) {
             const int s = k % kStages;
@@ -199,12 +233,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             uint32_t bytes = 0;
             for (int q = 0; q < kRowsPerStage; ++q) {
-                const int row = py_lo + k * kRowsPerStage + q;
+                const int row = py_lo + r * (k * kRowsPerStage + q);
                 if (k * kRowsPerStage + q < G.rows && row < ncy) bytes += (uint32_t)valid_cells * 16;
             }
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
             for (int q = 0; q < kRowsPerStage; ++q) {
-                const int row = py_lo + k * kRowsPerStage + q;
+                const int row = py_lo + r * (k * kRowsPerStage + q);
                 if (k * kRowsPerStage + q < G.rows && row < ncy)
                     ptx::bulk_g2s(stages + (size_t)s * G.stage_bytes + (size_t)q * G.row_bytes,
                                   cells + ((size_t)row * ncx + px0) * kNB, (uint32_t)valid_cells * 16, &full[s]);
@@ -230,10 +264,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_after();
             for (int q = 0; q < kRowsPerStage; ++q) {
-                const int rr = k * kRowsPerStage + q;  // cell row within the CTA
-                if (rr >= G.rows) break;
-                const int phi = rr % r, rho = rr / r;
-                const uint32_t dcol = (uint32_t)(phi * Tc);
+                const int rho = k * kRowsPerStage + q;  // cell row within the class
+                if (rho >= G.rows) break;
                 const uint32_t a_addr = ptx::smem_addr(stages + (size_t)s * G.stage_bytes + (size_t)q * G.row_bytes);
                 const uint32_t b_row = band_addr + (uint32_t)((Tc + 14 - rho) * 16);
 #pragma unroll
@@ -242,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * r * 16), (uint32_t)(r * 16), 128);
                     const uint64_t bd =
                         smem_desc(b_row + (uint32_t)(2 * ks * G.plane_bytes), (uint32_t)G.plane_bytes, 128);
-                    mma_bf16(tmem + dcol, ad, bd, idesc, (rho == 0 && ks == 0) ? 0u : 1u);
+                    mma_bf16(tmem, ad, bd, idesc, (rho == 0 && ks == 0) ? 0u : 1u);
                 }
             }
             mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
@@ -258,20 +290,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     const int px = px0 + warp * 32 + lane;
     if (ok && !*reinterpret_cast<volatile int*>(&aborted)) {
-        for (int phi = 0; phi < r; ++phi) {
-            for (int c0 = 0; c0 < Tc; c0 += 16) {
-                uint32_t v[16];
-                tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(phi * Tc + c0), v);
+        for (int c0 = 0; c0 < Tc; c0 += 16) {
+            uint32_t v[16];
+            tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    const int py = py_lo + phi + r * (c0 + c);
-                    if (px < nx && py < ny) {
-                        const float sc = __uint_as_float(v[c]) + bias;
-                        if constexpr (std::is_same<OutT, int32_t>::value) {
-                            scores[(size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
-                        } else {
-                            scores[(size_t)py * nx + px] = sc;
-                        }
+            for (int c = 0; c < 16; ++c) {
+                const int py = py_lo + r * (c0 + c);
+                if (px < nx && py < ny) {
+                    const float sc = __uint_as_float(v[c]) + bias;
+                    if constexpr (std::is_same<OutT, int32_t>::value) {
+                        scores[(size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
+                    } else {
+                        scores[(size_t)py * nx + px] = sc;
                     }
                 }
             }
@@ -285,9 +315,9 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 int choose_tc(int nx, int ny, int r) {
-    // 32 output rows per class per CTA when that still gives every SM a CTA, else 16
+    // 32 output rows per CTA when that still gives every SM a CTA, else 16
     const long tiles_x = (nx + kM - 1) / kM;
-    const long ctas32 = tiles_x * ((ny + 32 * r - 1) / (32 * r));
+    const long ctas32 = tiles_x * ((ny + 32 * r - 1) / (32 * r)) * r;
     return ctas32 >= sm_count() ? 32 : 16;
 }
 
@@ -306,7 +336,7 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     auto kern = score_tc_kernel<WT, OutT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    dim3 grid((nx + kM - 1) / kM, (ny + Tc * r - 1) / (Tc * r));
+    dim3 grid((nx + kM - 1) / kM, (ny + Tc * r - 1) / (Tc * r), r);
     return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias,
                       nx, ny, static_cast<OutT*>(scores), status);
 }

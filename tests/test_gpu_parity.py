@@ -359,6 +359,32 @@ def test_cells_fused(fh, g, ch, nb, cell, stride):
             assert np.array_equal(got, ref), (H, W, cd)
 
 
+@pytest.mark.parametrize("cell,stride", [(16, 4), (32, 8)])
+def test_cells_fused_single_bin_extremes(fh, g, cell, stride):
+    """A diagonal ramp puts every interior pixel in one bin, so the tile-local
+    corner sums reach their largest values (r = 4, the largest tiles); the
+    counts must still be exact, written at 2-, 4- and 16-byte aligned
+    addresses."""
+    H, W = 300, 700
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = ((xx + 2 * yy) % 256).astype(np.uint8)  # (dx, dy) = (2, 4) except at the wrap
+    ref = oracle.cell_hist_ii(oracle.integral(oracle.bin_map(img, 8), 8), 8, cell, stride)
+    ncy, ncx = ref.shape[:2]
+    lut = g.gpu_lut(8)
+    d = g.dev(img.reshape(-1))
+    n = ncx * ncy * 8
+    for cd, shifts in ((fh.HOG_BF16, (0, 1, 2)), (fh.HOG_F32, (0, 1)), (fh.HOG_I32, (0, 3))):
+        if cd == fh.HOG_BF16 and cell > 16:
+            continue  # counts above 256 are not exact in bf16: the call refuses that combination
+        esz = torch.empty(0, dtype=fh.TORCH_DTYPE[cd]).element_size()
+        for sh in shifts:  # offsets in elements: 16-byte, 4-byte and 2-byte aligned starts
+            buf = torch.full((n + 16,), -1, dtype=fh.TORCH_DTYPE[cd], device="cuda")
+            fh.hog_cell_hist_fused(d, W, H, 1, W, lut, 8, cell, stride, cd, buf.data_ptr() + sh * esz)
+            host = buf.float().cpu().numpy()
+            assert np.array_equal(host[sh: sh + n].reshape(ncy, ncx, 8), ref), (cd, sh)
+            assert np.all(host[:sh] == -1) and np.all(host[sh + n:] == -1)
+
+
 def test_pipeline_fused_config1(fh, g):
     c = wl.config1()
     img = c["images"][0]
