@@ -41,6 +41,13 @@ class HogDet(ctypes.Structure):
 DET_BYTES = ctypes.sizeof(HogDet)  # 20
 
 
+class HogBatchItem(ctypes.Structure):
+    """hog_batch_item of include/fasthog_batch.h."""
+    _fields_ = [("img", ctypes.c_void_p), ("pitch", ctypes.c_size_t), ("W", ctypes.c_int), ("H", ctypes.c_int),
+                ("cells", ctypes.c_void_p), ("scores", ctypes.c_void_p), ("image", ctypes.c_int),
+                ("level", ctypes.c_int)]
+
+
 class HogServerConfig(ctypes.Structure):
     """hog_server_config of include/fasthog_server.h."""
     _fields_ = [("n_bins", ctypes.c_int), ("cell", ctypes.c_int), ("stride", ctypes.c_int),
@@ -88,6 +95,14 @@ def _load() -> ctypes.CDLL:
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
         "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
+        "hog_batch_plan_bytes": (Z, [I]),
+        "hog_batch_plan": (I, [P, I, I, I, I, I, I, I, P, Z]),
+        "hog_cell_hist_fused_batch": (I, [P, P, P, I, P]),
+        "hog_window_score_batch": (I, [P, P, I, P, I, F, P]),
+        "hog_detect_batch_workspace_bytes": (Z, [P]),
+        "hog_detect_batch": (I, [P, P, I, F, P, I, P, P, P, Z, P]),
+        "hog_pyramid_bytes": (Z, [I, I, I, I]),
+        "hog_pyramid": (I, [P, I, I, I, Z, I, P, P]),
         "hog_server_create": (I, [P, P, P]),
         "hog_server_destroy": (I, [P]),
         "hog_server_request_bytes": (Z, [P, I, I, I]),
@@ -107,6 +122,8 @@ _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
+            "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
+            "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
             "hog_server_poll", "hog_server_release", "hog_server_stats")
 
@@ -221,6 +238,57 @@ def hog_detect_noalloc(scores, score_dtype: int, nx: int, ny: int, stride: int, 
 
 
 HOG_DETECT_NOALLOC_MAX_SCORES = 16384 * 2048
+
+
+# ---- batches of images and pyramid levels (include/fasthog_batch.h) ---------
+
+def hog_batch_plan_bytes(n_items: int) -> int:
+    return _lib.hog_batch_plan_bytes(n_items)
+
+
+def hog_batch_plan(items, channels: int, n_bins: int, cell: int, stride: int, cells_x: int, cells_y: int):
+    """Plan of a batch of HogBatchItem (a sequence).  Returns the host copy (a
+    ctypes buffer; ``bytes(plan)`` are the bytes to copy to device memory)."""
+    arr = (HogBatchItem * len(items))(*items)
+    nbytes = _lib.hog_batch_plan_bytes(len(items))
+    buf = (ctypes.c_uint64 * ((nbytes + 7) // 8))()
+    _check("hog_batch_plan", _lib.hog_batch_plan(arr, len(items), channels, n_bins, cell, stride, cells_x, cells_y,
+                                                 buf, nbytes))
+    return buf
+
+
+def hog_cell_hist_fused_batch(plan, plan_dev, lut, cell_dtype: int, stream=None) -> None:
+    _check("hog_cell_hist_fused_batch", _lib.hog_cell_hist_fused_batch(_plan_ptr(plan), _ptr(plan_dev), _ptr(lut),
+                                                                       cell_dtype, _stream(stream)))
+
+
+def hog_window_score_batch(plan, plan_dev, cell_dtype: int, w, w_dtype: int, bias: float,
+                           stream=None) -> None:
+    _check("hog_window_score_batch", _lib.hog_window_score_batch(_plan_ptr(plan), _ptr(plan_dev), cell_dtype, _ptr(w),
+                                                                 w_dtype, float(bias), _stream(stream)))
+
+
+def hog_detect_batch_workspace_bytes(plan) -> int:
+    return _lib.hog_detect_batch_workspace_bytes(_plan_ptr(plan))
+
+
+def hog_detect_batch(plan, plan_dev, score_dtype: int, thr: float, out, max_out: int, d_count, item_counts,
+                     workspace, workspace_bytes: int, stream=None) -> None:
+    _check("hog_detect_batch", _lib.hog_detect_batch(_plan_ptr(plan), _ptr(plan_dev), score_dtype, float(thr),
+                                                     _ptr(out), max_out, _ptr(d_count), _ptr(item_counts),
+                                                     _ptr(workspace), workspace_bytes, _stream(stream)))
+
+
+def hog_pyramid_bytes(W: int, H: int, channels: int, levels: int) -> int:
+    return _lib.hog_pyramid_bytes(W, H, channels, levels)
+
+
+def hog_pyramid(img, W: int, H: int, channels: int, pitch: int, levels: int, out, stream=None) -> None:
+    _check("hog_pyramid", _lib.hog_pyramid(_ptr(img), W, H, channels, pitch, levels, _ptr(out), _stream(stream)))
+
+
+def _plan_ptr(plan) -> int:
+    return ctypes.addressof(plan)
 
 
 # ---- request server (include/fasthog_server.h) -------------------------------

@@ -26,6 +26,7 @@
 // persistent so that each CTA stages the table quadrant once.
 #include <type_traits>
 
+#include "batch_plan.cuh"
 #include "bin_core.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
@@ -78,143 +79,186 @@ __device__ __forceinline__ uint32_t out_bits(uint32_t v) {
     }
 }
 
+// Stage the shared-memory quadrant of the table (one bulk copy, bounded wait).
+__device__ __forceinline__ bool stage_lut(uint8_t* lutq, const uint8_t* __restrict__ lut, uint64_t* bar,
+                                          unsigned int* status) {
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        ptx::mbar_init(bar, 1);
+        ptx::fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        ptx::mbar_arrive_expect_tx(bar, kQuadBytes);
+        ptx::bulk_g2s(lutq, lut + kLutQuadOffset, kQuadBytes, bar);
+    }
+    pdl_trigger();
+    pdl_wait();
+    const bool ok = ptx::mbar_wait_bounded(bar, 0, kWaitLimitNs);
+    if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
+    return ok;
+}
+
+// One tile of cell origins [bx0, bx0 + BX) x [by0, by0 + BY) of one image:
+// steps 1-3 above.  Called by every thread of the CTA.
+template <int CH, int NB, int S, typename OutT>
+__device__ __forceinline__ void fused_tile(FusedSmem<NB, S>& sm, const uint8_t* lutq, const uint8_t* __restrict__ lut,
+                                           const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
+                                           int r, int ncx, int ncy, OutT* __restrict__ cells, int out_align, int bx0,
+                                           int by0) {
+    using F = FusedSmem<NB, S>;
+    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    constexpr int QPR = S / 4;  // quads in one block row
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int bxn = BX + r - 1, byn = BY + r - 1;  // blocks of a tile
+    const long row_bytes = (long)W * CH;
+    const int row_tasks = bxn * QPR;               // quads in one pixel row of the tile
+    const int n_tasks = byn * S * row_tasks;
+    __syncthreads();  // the previous tile's reads of g and bh are done
+    for (int k = tid; k < byn * F::BXB * F::NW8; k += kThreads) (&sm.bh[0][0][0])[k] = 0;
+    __syncthreads();
+    // 1. block histograms: one quad (4 pixels of one row) per task; the
+    //    8-bit fields of a block's words collect at most s^2 <= 64 pixels.
+    for (int task = tid; task < n_tasks; task += kThreads) {
+        const int prow = task / row_tasks, qc = task - prow * row_tasks;
+        const int y = by0 * S + prow, x = bx0 * S + 4 * qc;
+        if (y <= 0 || y >= H - 1 || x >= W) continue;  // border rows, or outside the image: no bins
+        QuadWords<CH> q;
+        load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
+        const uint32_t packed = bins_of_quad<CH, true>(q, x, W, lutq, lut, NB, NB / 4);
+        uint32_t h[F::NW8];
+#pragma unroll
+        for (int k = 0; k < F::NW8; ++k) h[k] = 0;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            const uint32_t v = (packed >> (8 * p)) & 0xFFu;
+            const uint32_t inc = 1u << ((v & 3) << 3);
+#pragma unroll
+            for (int k = 0; k < F::NW8; ++k) h[k] += ((v >> 2) == (uint32_t)k) ? inc : 0u;  // 0xFF: none
+        }
+        uint32_t* dst = sm.bh[prow / S][qc / QPR];
+#pragma unroll
+        for (int k = 0; k < F::NW8; ++k)
+            if (h[k]) atomicAdd(dst + k, h[k]);
+    }
+    __syncthreads();
+    // 2. G: exclusive 2-D prefix of the block histograms in 16-bit fields
+    //    (bins 2e, 2e+1 in word e).  Along block rows with warp scans (G row
+    //    J + 1 holds block row J), then down the columns.
+    for (int task = wid; task < byn * F::NW16; task += kThreads / 32) {
+        const int J = 1 + task / F::NW16, e = task % F::NW16;
+        uint32_t carry = 0;
+        for (int I0 = 0; I0 < bxn; I0 += 32) {
+            const int I = I0 + lane;
+            uint32_t v = 0;
+            if (I < bxn) {
+                const uint32_t w8 = sm.bh[J - 1][I][e >> 1];
+                const uint32_t two = (e & 1) ? (w8 >> 16) : (w8 & 0xFFFFu);  // bins 2e, 2e+1 (8-bit each)
+                v = (two & 0xFFu) | ((two >> 8) << 16);
+            }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
+                if (lane >= d) v += u;
+            }
+            if (I < bxn) sm.g[J][I + 1][e] = v + carry;
+            carry += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) sm.g[J][0][e] = 0;
+    }
+    for (int k = tid; k < (bxn + 1) * F::NW16; k += kThreads) sm.g[0][k / F::NW16][k % F::NW16] = 0;
+    __syncthreads();
+    for (int task = tid; task < (bxn + 1) * F::NW16; task += kThreads) {
+        const int I = task / F::NW16, e = task % F::NW16;
+        uint32_t run = 0;
+        for (int J = 1; J <= byn; ++J) {
+            run += sm.g[J][I][e];
+            sm.g[J][I][e] = run;
+        }
+    }
+    __syncthreads();
+    // 3. cells: Eq. 6 on the corner-sampled integral image
+    if (tid < BX * BY) {
+        const int ci = tid % BX, cj = tid / BX;
+        const int i = bx0 + ci, j = by0 + cj;
+        if (i < ncx && j < ncy) {
+            // the cell's NB counts as OutT, packed into 32-bit words (bf16: two per word)
+            constexpr int NWORDS = NB * (int)sizeof(OutT) / 4;
+            uint32_t words[NWORDS];
+#pragma unroll
+            for (int e = 0; e < F::NW16; ++e) {
+                // (a + d) - (b + c) per 16-bit field: no field carries or borrows
+                const uint32_t v = (sm.g[cj + r][ci + r][e] + sm.g[cj][ci][e]) -
+                                   (sm.g[cj][ci + r][e] + sm.g[cj + r][ci][e]);
+                if constexpr (sizeof(OutT) == 2) {
+                    words[e] = (uint32_t)as_count<OutT>(v & 0xFFFFu) | ((uint32_t)as_count<OutT>(v >> 16) << 16);
+                } else {
+                    words[2 * e] = out_bits<OutT>(v & 0xFFFFu);
+                    words[2 * e + 1] = out_bits<OutT>(v >> 16);
+                }
+            }
+            OutT* out = cells + ((size_t)j * ncx + i) * NB;
+            if (out_align == 16) {
+#pragma unroll
+                for (int k = 0; k < NWORDS / 4; ++k)
+                    reinterpret_cast<uint4*>(out)[k] =
+                        make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
+            } else if (out_align == 4) {
+#pragma unroll
+                for (int k = 0; k < NWORDS; ++k) reinterpret_cast<uint32_t*>(out)[k] = words[k];
+            } else {  // a 2-byte-aligned bf16 map
+#pragma unroll
+                for (int k = 0; k < 2 * NWORDS; ++k)
+                    reinterpret_cast<uint16_t*>(out)[k] = (uint16_t)(words[k >> 1] >> (16 * (k & 1)));
+            }
+        }
+    }
+}
+
+// Output alignment class of a cell map: every cell starts a multiple of 16
+// bytes after the map's start.
+__host__ __device__ inline int cells_alignment(const void* cells) {
+    const uintptr_t c = reinterpret_cast<uintptr_t>(cells);
+    return c % 16 == 0 ? 16 : (c % 4 == 0 ? 4 : 2);
+}
+
 template <int CH, int NB, int S, typename OutT>
 __global__ void __launch_bounds__(kThreads, 2)
     cells_fused_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                        const uint8_t* __restrict__ lut, int r, int ncx, int ncy, OutT* __restrict__ cells,
                        int out_align, unsigned int* status) {
-    using F = FusedSmem<NB, S>;
-    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
-    constexpr int QPR = S / 4;  // quads in one block row
     extern __shared__ __align__(128) uint8_t smem[];
-    uint8_t* lutq = smem;
-    F& sm = *reinterpret_cast<F*>(smem + kQuadBytes);
     __shared__ __align__(8) uint64_t lut_bar;
-
-    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    if (tid == 0) {
-        ptx::mbar_init(&lut_bar, 1);
-        ptx::fence_mbar_init();
-    }
-    __syncthreads();
-    if (tid == 0) {
-        ptx::mbar_arrive_expect_tx(&lut_bar, kQuadBytes);
-        ptx::bulk_g2s(lutq, lut + kLutQuadOffset, kQuadBytes, &lut_bar);
-    }
-    pdl_trigger();
-    pdl_wait();
-    const bool lut_ok = ptx::mbar_wait_bounded(&lut_bar, 0, kWaitLimitNs);
-    if (!lut_ok) {
-        if (tid == 0) atomicOr(status, kStatusTimeout);
-        return;
-    }
-
+    auto& sm = *reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
+    if (!stage_lut(smem, lut, &lut_bar, status)) return;
+    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
     const int tiles_x = (ncx + BX - 1) / BX, tiles_y = (ncy + BY - 1) / BY;
-    const int bxn = BX + r - 1, byn = BY + r - 1;  // blocks of a tile
-    const long row_bytes = (long)W * CH;
-    const int row_tasks = bxn * QPR;               // quads in one pixel row of the tile
-    const int n_tasks = byn * S * row_tasks;
-    for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
-        const int bx0 = (t % tiles_x) * BX, by0 = (t / tiles_x) * BY;
-        __syncthreads();  // the previous tile's reads of g and bh are done
-        for (int k = tid; k < byn * F::BXB * F::NW8; k += kThreads) (&sm.bh[0][0][0])[k] = 0;
-        __syncthreads();
-        // 1. block histograms: one quad (4 pixels of one row) per task; the
-        //    8-bit fields of a block's words collect at most s^2 <= 64 pixels.
-        for (int task = tid; task < n_tasks; task += kThreads) {
-            const int prow = task / row_tasks, qc = task - prow * row_tasks;
-            const int y = by0 * S + prow, x = bx0 * S + 4 * qc;
-            if (y <= 0 || y >= H - 1 || x >= W) continue;  // border rows, or outside the image: no bins
-            QuadWords<CH> q;
-            load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
-            const uint32_t packed = bins_of_quad<CH, true>(q, x, W, lutq, lut, NB, NB / 4);
-            uint32_t h[F::NW8];
-#pragma unroll
-            for (int k = 0; k < F::NW8; ++k) h[k] = 0;
-#pragma unroll
-            for (int p = 0; p < 4; ++p) {
-                const uint32_t v = (packed >> (8 * p)) & 0xFFu;
-                const uint32_t inc = 1u << ((v & 3) << 3);
-#pragma unroll
-                for (int k = 0; k < F::NW8; ++k) h[k] += ((v >> 2) == (uint32_t)k) ? inc : 0u;  // 0xFF: none
-            }
-            uint32_t* dst = sm.bh[prow / S][qc / QPR];
-#pragma unroll
-            for (int k = 0; k < F::NW8; ++k)
-                if (h[k]) atomicAdd(dst + k, h[k]);
-        }
-        __syncthreads();
-        // 2. G: exclusive 2-D prefix of the block histograms in 16-bit fields
-        //    (bins 2e, 2e+1 in word e).  Along block rows with warp scans (G row
-        //    J + 1 holds block row J), then down the columns.
-        for (int task = wid; task < byn * F::NW16; task += kThreads / 32) {
-            const int J = 1 + task / F::NW16, e = task % F::NW16;
-            uint32_t carry = 0;
-            for (int I0 = 0; I0 < bxn; I0 += 32) {
-                const int I = I0 + lane;
-                uint32_t v = 0;
-                if (I < bxn) {
-                    const uint32_t w8 = sm.bh[J - 1][I][e >> 1];
-                    const uint32_t two = (e & 1) ? (w8 >> 16) : (w8 & 0xFFFFu);  // bins 2e, 2e+1 (8-bit each)
-                    v = (two & 0xFFu) | ((two >> 8) << 16);
-                }
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t u = __shfl_up_sync(0xffffffffu, v, d);
-                    if (lane >= d) v += u;
-                }
-                if (I < bxn) sm.g[J][I + 1][e] = v + carry;
-                carry += __shfl_sync(0xffffffffu, v, 31);
-            }
-            if (lane == 0) sm.g[J][0][e] = 0;
-        }
-        for (int k = tid; k < (bxn + 1) * F::NW16; k += kThreads) sm.g[0][k / F::NW16][k % F::NW16] = 0;
-        __syncthreads();
-        for (int task = tid; task < (bxn + 1) * F::NW16; task += kThreads) {
-            const int I = task / F::NW16, e = task % F::NW16;
-            uint32_t run = 0;
-            for (int J = 1; J <= byn; ++J) {
-                run += sm.g[J][I][e];
-                sm.g[J][I][e] = run;
-            }
-        }
-        __syncthreads();
-        // 3. cells: Eq. 6 on the corner-sampled integral image
-        if (tid < BX * BY) {
-            const int ci = tid % BX, cj = tid / BX;
-            const int i = bx0 + ci, j = by0 + cj;
-            if (i < ncx && j < ncy) {
-                // the cell's NB counts as OutT, packed into 32-bit words (bf16: two per word)
-                constexpr int NWORDS = NB * (int)sizeof(OutT) / 4;
-                uint32_t words[NWORDS];
-#pragma unroll
-                for (int e = 0; e < F::NW16; ++e) {
-                    // (a + d) - (b + c) per 16-bit field: no field carries or borrows
-                    const uint32_t v = (sm.g[cj + r][ci + r][e] + sm.g[cj][ci][e]) -
-                                       (sm.g[cj][ci + r][e] + sm.g[cj + r][ci][e]);
-                    if constexpr (sizeof(OutT) == 2) {
-                        words[e] = (uint32_t)as_count<OutT>(v & 0xFFFFu) | ((uint32_t)as_count<OutT>(v >> 16) << 16);
-                    } else {
-                        words[2 * e] = out_bits<OutT>(v & 0xFFFFu);
-                        words[2 * e + 1] = out_bits<OutT>(v >> 16);
-                    }
-                }
-                OutT* out = cells + ((size_t)j * ncx + i) * NB;
-                if (out_align == 16) {
-#pragma unroll
-                    for (int k = 0; k < NWORDS / 4; ++k)
-                        reinterpret_cast<uint4*>(out)[k] =
-                            make_uint4(words[4 * k], words[4 * k + 1], words[4 * k + 2], words[4 * k + 3]);
-                } else if (out_align == 4) {
-#pragma unroll
-                    for (int k = 0; k < NWORDS; ++k) reinterpret_cast<uint32_t*>(out)[k] = words[k];
-                } else {  // a 2-byte-aligned bf16 map
-#pragma unroll
-                    for (int k = 0; k < 2 * NWORDS; ++k)
-                        reinterpret_cast<uint16_t*>(out)[k] = (uint16_t)(words[k >> 1] >> (16 * (k & 1)));
-                }
-            }
-        }
+    for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x)
+        fused_tile<CH, NB, S, OutT>(sm, smem, lut, img, W, H, pitch, aligned, r, ncx, ncy, cells, out_align,
+                                    (t % tiles_x) * BX, (t / tiles_x) * BY);
+}
+
+// The same over every item of a batch plan: the persistent CTAs walk the
+// batch's tiles, item by item.
+template <int CH, int NB, int S, typename OutT>
+__global__ void __launch_bounds__(kThreads, 2)
+    cells_fused_batch_kernel(const PlanItem* __restrict__ items, int n_items, int total_tiles,
+                             const uint8_t* __restrict__ lut, int r, unsigned int* status) {
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t lut_bar;
+    auto& sm = *reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
+    if (!stage_lut(smem, lut, &lut_bar, status)) return;
+    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
+        const PlanItem* it = items + find_item<Stage::kCells>(items, n_items, t);
+        const hog_batch_item item = it->it;
+        const int local = t - it->cells_t0, tx = it->cells_tx;
+        const uint8_t* img = item.img;
+        OutT* cells = static_cast<OutT*>(item.cells);
+        const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (item.pitch % 4 == 0);
+        fused_tile<CH, NB, S, OutT>(sm, smem, lut, img, item.W, item.H, item.pitch, aligned, r, it->ncx, it->ncy,
+                                    cells, cells_alignment(cells),
+                                    (local % tx) * BX, (local / tx) * BY);
     }
 }
 
@@ -230,9 +274,7 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     const int cap = 2 * sm_count();  // two CTAs of this size fit an SM
     const int grid = tiles < cap ? tiles : cap;
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
-    // every cell starts a multiple of 16 bytes after `cells`
-    const uintptr_t c = reinterpret_cast<uintptr_t>(cells);
-    const int out_align = c % 16 == 0 ? 16 : (c % 4 == 0 ? 4 : 2);
+    const int out_align = cells_alignment(cells);
     return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, img, W, H, pitch, aligned, lut, r, ncx, ncy,
                       static_cast<OutT*>(cells), out_align, status);
 }
@@ -274,6 +316,58 @@ hog_status launch_cells_fused(const uint8_t* img, int W, int H, int channels, si
                            : by_stride<1, 16>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st);
     return n_bins == 8 ? by_stride<3, 8>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st)
                        : by_stride<3, 16>(img, W, H, pitch, lut, stride, r, ncx, ncy, cell_dtype, cells, status, st);
+}
+
+int cells_fused_tiles_x(int ncx, int stride) {
+    const int bx = stride == 4 ? TileShape<4>::BX : TileShape<8>::BX;
+    return (ncx + bx - 1) / bx;
+}
+
+int cells_fused_tiles(int ncx, int ncy, int stride) {
+    const int by = stride == 4 ? TileShape<4>::BY : TileShape<8>::BY;
+    return cells_fused_tiles_x(ncx, stride) * ((ncy + by - 1) / by);
+}
+
+namespace {
+
+template <int CH, int NB, int S, typename OutT>
+hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, unsigned int* status,
+                          cudaStream_t st) {
+    const size_t smem = kQuadBytes + sizeof(FusedSmem<NB, S>);
+    auto kern = cells_fused_batch_kernel<CH, NB, S, OutT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int cap = 2 * sm_count();
+    const int grid = h.cells_tiles < cap ? h.cells_tiles : cap;
+    return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, plan_items(plan_dev), h.n_items, h.cells_tiles,
+                      lut, h.r, status);
+}
+
+template <int CH, int NB, int S>
+hog_status batch_by_out(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, int cell_dtype,
+                        unsigned int* status, cudaStream_t st) {
+    if (cell_dtype == HOG_BF16) return launch_batch_t<CH, NB, S, uint16_t>(h, plan_dev, lut, status, st);
+    if (cell_dtype == HOG_F32) return launch_batch_t<CH, NB, S, float>(h, plan_dev, lut, status, st);
+    return launch_batch_t<CH, NB, S, int32_t>(h, plan_dev, lut, status, st);
+}
+
+template <int CH, int NB>
+hog_status batch_by_stride(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, int cell_dtype,
+                           unsigned int* status, cudaStream_t st) {
+    if (h.stride == 4) return batch_by_out<CH, NB, 4>(h, plan_dev, lut, cell_dtype, status, st);
+    return batch_by_out<CH, NB, 8>(h, plan_dev, lut, cell_dtype, status, st);
+}
+
+}  // namespace
+
+hog_status launch_cells_fused_batch(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, int cell_dtype,
+                                    unsigned int* status, cudaStream_t st) {
+    if (h.cells_tiles == 0) return HOG_OK;
+    if (h.channels == 1)
+        return h.n_bins == 8 ? batch_by_stride<1, 8>(h, plan_dev, lut, cell_dtype, status, st)
+                             : batch_by_stride<1, 16>(h, plan_dev, lut, cell_dtype, status, st);
+    return h.n_bins == 8 ? batch_by_stride<3, 8>(h, plan_dev, lut, cell_dtype, status, st)
+                         : batch_by_stride<3, 16>(h, plan_dev, lut, cell_dtype, status, st);
 }
 
 }  // namespace fasthog

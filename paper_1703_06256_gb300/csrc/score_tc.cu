@@ -45,6 +45,7 @@
 // exact in any order and the int32 scores are bit-exact.
 #include <type_traits>
 
+#include "batch_plan.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
 
@@ -158,10 +159,15 @@ struct TcGeom {
     }
 };
 
-template <typename WT, typename OutT>
+// BATCH = false: one image, CTA (blockIdx.x, .y, .z) = (window column, row
+// band, residue class).  BATCH = true: the CTAs of every item of a batch
+// plan in one 1-D grid; each CTA finds its item and its (column, band,
+// class) from the plan and overrides the image arguments.
+template <typename WT, typename OutT, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const uint16_t* __restrict__ cells, int ncx, int ncy, int r, int Tc, const WT* __restrict__ w,
-                    float bias, int nx, int ny, OutT* __restrict__ scores, unsigned int* status) {
+                    float bias, int nx, int ny, OutT* __restrict__ scores, const PlanItem* __restrict__ items,
+                    int n_items, unsigned int* status) {
     extern __shared__ uint8_t smem_raw[];
     const TcGeom G(r, Tc);
     // 1024-byte aligned working area: band planes, A stages, barriers
@@ -176,9 +182,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     __shared__ int aborted;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int px0 = blockIdx.x * kM;
-    const int phi = blockIdx.z;                    // residue class of this CTA
-    const int py_lo = blockIdx.y * Tc * r + phi;   // first output row; rows step by r
+    int xt = blockIdx.x, yband = blockIdx.y, phi = blockIdx.z;  // phi: residue class of this CTA
+    if constexpr (BATCH) {
+        const PlanItem* it = items + find_item<Stage::kScore>(items, n_items, (int)blockIdx.x);
+        const int local = (int)blockIdx.x - it->score_c0, tx = it->score_tx, bands = it->score_bands;
+        xt = local % tx;
+        yband = (local / tx) % bands;
+        phi = local / (tx * bands);
+        cells = static_cast<const uint16_t*>(it->it.cells);
+        scores = static_cast<OutT*>(it->it.scores);
+        ncx = it->ncx;
+        ncy = it->ncy;
+        nx = it->nx;
+        ny = it->ny;
+    }
+    const int px0 = xt * kM;
+    const int py_lo = yband * Tc * r + phi;  // first output row; rows step by r
 
     // band planes: plane_i[v][b] = w[Tc + 14 - v][i][b] for filter rows 0..15, zero elsewhere.
     // Thread t < 128 moves the 8 bins of filter cell (j, i) = (t / 8, t % 8) in one load; the
@@ -333,15 +352,41 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     const TcGeom G(r, Tc);
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
-    auto kern = score_tc_kernel<WT, OutT>;
+    auto kern = score_tc_kernel<WT, OutT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     dim3 grid((nx + kM - 1) / kM, (ny + Tc * r - 1) / (Tc * r), r);
     return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias,
-                      nx, ny, static_cast<OutT*>(scores), status);
+                      nx, ny, static_cast<OutT*>(scores), static_cast<const PlanItem*>(nullptr), 0, status);
+}
+
+template <typename WT, typename OutT>
+hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void* w, float bias, cudaStream_t st) {
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    const TcGeom G(h.r, h.score_tc);
+    if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
+    const size_t smem = G.smem_bytes();
+    auto kern = score_tc_kernel<WT, OutT, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    return launch_pdl(kern, dim3(h.score_ctas), dim3(kThreads), smem, st, static_cast<const uint16_t*>(nullptr), 0,
+                      0, h.r, h.score_tc, static_cast<const WT*>(w), bias, 0, 0, static_cast<OutT*>(nullptr),
+                      plan_items(plan_dev), h.n_items, status);
 }
 
 }  // namespace
+
+hog_status launch_score_tc_batch(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
+                                 cudaStream_t st) {
+    if (h.score_ctas == 0) return HOG_OK;
+    if (w_dtype == HOG_BF16) return launch_batch_t<uint16_t, float>(h, plan_dev, w, bias, st);
+    if (w_dtype == HOG_I8) return launch_batch_t<int8_t, int32_t>(h, plan_dev, w, bias, st);
+    return HOG_ERR_UNSUPPORTED;
+}
+
+int score_tc_rows_for(long ctas32) { return ctas32 >= kNumSMs ? 32 : 16; }
 
 bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx) {
     (void)ncx;

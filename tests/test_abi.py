@@ -109,3 +109,32 @@ def test_server_argument_errors_need_no_gpu(fh):
     assert L.hog_server_stats(None, None, None, None) == ARG
     assert L.hog_server_request_bytes(None, 64, 128, 3) == 0
     assert L.hog_server_destroy(None) == fh.HOG_OK
+
+
+def test_batch_plan_on_the_host(fh):
+    """hog_batch_plan is host arithmetic; bad plans and arguments are refused
+    before anything is enqueued."""
+    item = fh.HogBatchItem(4096, 640 * 3, 640, 480, 4096, 8192, 0, 0)
+    small = fh.HogBatchItem(4096, 60 * 3, 60, 100, 4096, 0, 1, 0)  # smaller than a window: no scores needed
+    plan = fh.hog_batch_plan([item, small], 3, 8, 8, 4, 8, 16)
+    assert len(bytes(plan)) == fh.hog_batch_plan_bytes(2) == 64 + 2 * 96
+    with pytest.raises(fh.HogError):
+        fh.hog_batch_plan([item], 3, 9, 8, 4, 8, 16)  # N_b 9: no fused kernel
+    with pytest.raises(fh.HogError):
+        fh.hog_batch_plan([fh.HogBatchItem(4096, 100, 640, 480, 4096, 8192, 0, 0)], 3, 8, 8, 4, 8, 16)  # pitch
+    with pytest.raises(fh.HogError):
+        fh.hog_batch_plan([fh.HogBatchItem(4096, 640 * 3, 640, 480, 4096, 0, 0, 0)], 3, 8, 8, 4, 8, 16)  # scores
+    assert fh.hog_batch_plan_bytes(0) == 0
+    junk = (ctypes.c_uint64 * 32)()
+    L = fh.lib()
+    ARG = fh.HOG_ERR_ARG
+    assert L.hog_cell_hist_fused_batch(junk, 4096, 4096, fh.HOG_BF16, None) == ARG  # not a plan
+    assert L.hog_cell_hist_fused_batch(plan, 4100, 4096, fh.HOG_BF16, None) == ARG  # device copy misaligned
+    assert L.hog_cell_hist_fused_batch(plan, 4096, 4100, fh.HOG_BF16, None) == ARG  # table misaligned
+    assert L.hog_window_score_batch(plan, 4096, fh.HOG_BF16, None, fh.HOG_BF16, 0.0, None) == ARG
+    assert fh.hog_detect_batch_workspace_bytes(plan) > 0
+    assert L.hog_detect_batch(plan, 4096, fh.HOG_F32, 0.5, 4096, 10, 4096, None, 4096, 0, None) == ARG  # workspace
+    assert fh.hog_pyramid_bytes(640, 480, 3, 3) == 320 * 240 * 3 + 160 * 120 * 3
+    assert fh.hog_pyramid_bytes(640, 480, 3, 1) == 0
+    assert L.hog_pyramid(None, 640, 480, 3, 1920, 3, 4096, None) == ARG
+    assert L.hog_pyramid(4096, 640, 480, 3, 100, 3, 4096, None) == ARG  # pitch
