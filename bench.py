@@ -350,6 +350,80 @@ def serving(torch, wl, args):
     return out
 
 
+def batch_pyramid(torch, fh, wl, replicas, flush, args, world):
+    """The mixed-size pyramid batch: 64 RGB images, sizes drawn from
+    {640x480, 800x600, 1280x720, 1920x1080}, each with a 3-level 2:1 pyramid
+    (192 items), stride 4.  Images are crops, at random offsets, of one
+    generated 1920x1080 image (generating 64 images on the host would take
+    longer than the whole benchmark).  Mpixel/s counts input pixels (level 0);
+    windows/s counts windows over all levels.
+
+      batched_nb8   one launch per stage for the whole batch (pyramids: one
+                    per image), bf16 cells x bf16 weights on the tensor cores
+      batched_nb16  the same with N_b = 16 (the score runs per item on CUDA cores)
+      graph_nb8     per-item calls (fused cells, score, detect), one graph
+                    over 8 streams
+      unfused_i32 / unfused_u16   per-item five calls with int32 / uint16
+                    integral images, one graph over 8 streams"""
+    from paper_1703_06256_gb300.batch import HogBatch, HogPlanBatch
+
+    rng = wl.rng_for(2)
+    sizes = [wl.BATCH_SIZES[int(i)] for i in rng.integers(0, len(wl.BATCH_SIZES), size=64)]
+    base = wl.rgb_smooth_shapes(1920, 1080, rng)
+    imgs = []
+    for (W, H) in sizes:
+        y, x = int(rng.integers(0, 1080 - H + 1)), int(rng.integers(0, 1920 - W + 1))
+        imgs.append(np.ascontiguousarray(base[y:y + H, x:x + W]))
+    px = sum(W * H for (W, H) in sizes)
+    steps = max(args.steps // 10, 5)
+    out = {}
+
+    def timed(label, run_fn, evs, windows, extra=None):
+        ms = replicas.max_over_ranks(
+            time_steps(torch, run_fn, lambda: (None, evs[0].elapsed_time(evs[1])), flush, steps, args.warmup),
+            "cuda")
+        out[label] = dict({"value": round(replicas.aggregate_rate(px, ms * 1e-3, world) / 1e6, 1),
+                           "unit": "Mpixel/s", "ms_per_step": round(ms, 4),
+                           "windows_per_s": round(replicas.aggregate_rate(windows, ms * 1e-3, world), 1)},
+                          **(extra or {}))
+
+    for nb in (8, 16):
+        w = wl.weights_f32(nb, rng)
+        b = HogPlanBatch(sizes, channels=3, levels=3, n_bins=nb, stride=4, w_dtype=fh.HOG_BF16)
+        b.set_images(imgs)
+        b.set_weights(w, 0.0, 0.5)
+        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        b.capture(evs)
+        timed(f"batched_nb{nb}", b.run, evs, b.windows, {"items": len(b.items), "launches": b.launches()})
+        windows = b.windows
+        del b
+    torch.cuda.empty_cache()
+    # per-item pipelines over the same items (levels decimated on the host: every 2^l-th row and column)
+    w = wl.weights_f32(8, rng)
+    for label, fused, ii in (("graph_nb8", True, fh.HOG_I32), ("unfused_i32", False, fh.HOG_I32),
+                             ("unfused_u16", False, fh.HOG_U16)):
+        pipes = []
+        for img in imgs:
+            H, W = img.shape[:2]
+            for lv in range(3):
+                lvl = np.ascontiguousarray(img[:: 1 << lv, :: 1 << lv][: H >> lv, : W >> lv])
+                p = fh.HogPipeline(W >> lv, H >> lv, 3, 8, 4, ii_dtype=ii, cell_dtype=fh.HOG_BF16,
+                                   w_dtype=fh.HOG_BF16)
+                p.set_weights(w, 0.0, 0.5)
+                p.set_image(lvl)
+                pipes.append(p)
+        hb = HogBatch(pipes, n_streams=8, fused=fused)
+        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        hb.capture(evs)
+        timed(label, hb.run, evs, windows)
+        del hb, pipes
+        torch.cuda.empty_cache()
+    out["workload"] = ("64 RGB images, sizes from {640x480, 800x600, 1280x720, 1920x1080} (crops of one generated "
+                       "1920x1080 image), 3-level 2:1 pyramid (192 items), stride 4, bf16 cells x bf16 weights, "
+                       "thr 0.5; Mpixel/s over level-0 pixels")
+    return out
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -494,6 +568,7 @@ def main():
         "device_status": status,
         "fused": fused,
         "batch_1080p": None if args.no_extras else batch_1080p(torch, fh, wl, replicas, flush, args, world),
+        "batch_pyramid": None if args.no_extras else batch_pyramid(torch, fh, wl, replicas, flush, args, world),
         "serving": (serving(torch, wl, args) if not args.no_extras and world == 1 and args.serve_requests > 0
                     else None),
     }

@@ -216,11 +216,13 @@ hog_status hog_cell_hist_fused(const uint8_t* img, int W, int H, int channels, s
  *   cell, stride       as given to hog_cell_hist; stride must divide cell
  *   w, w_dtype         cells_x * cells_y * n_bins weights:
  *                      HOG_F32  -> FP32 arithmetic on CUDA cores, scores f32
- *                      HOG_BF16 -> tensor cores (tcgen05, bf16 x bf16 -> f32),
- *                                  scores f32; needs HOG_BF16 cells and
- *                                  n_bins a multiple of 8
- *                      HOG_I8   -> tensor cores, exact; scores int32 (the bias
- *                                  is rounded to the nearest integer)
+ *                      HOG_BF16 -> bf16 x bf16 -> f32, scores f32
+ *                      HOG_I8   -> exact; scores int32 (the bias is rounded to
+ *                                  the nearest integer)
+ *                      BF16 and I8 weights run on the tensor cores (tcgen05)
+ *                      for 16-byte-aligned HOG_BF16 cells, n_bins 8 or 16, an
+ *                      8 x 16-cell window and r = 1, 2 or 4; otherwise on CUDA
+ *                      cores with the same results
  *   scores             out: [ny][nx], f32 (F32/BF16 weights) or int32 (I8)
  */
 hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins,

@@ -191,7 +191,7 @@ class HogPlanBatch:
         from . import HOG_BF16, HOG_F32
 
         n_pyr = len(self.sizes) if self.levels > 1 else 0
-        tc = (self.w_dtype != HOG_F32 and self.cell_dtype == HOG_BF16 and self.n_bins == 8
+        tc = (self.w_dtype != HOG_F32 and self.cell_dtype == HOG_BF16 and self.n_bins in (8, 16)
               and (self.cells_x, self.cells_y) == (8, 16) and self.cell // self.stride in (1, 2, 4))
         score = 1 if tc else sum(1 for m in self.item_meta if m["nx"] * m["ny"] > 0)
         return n_pyr + 1 + score + (3 if self.windows > 0 else 1)

@@ -42,6 +42,7 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
     if (cell < 1 || stride < 1 || cell % stride != 0) return HOG_ERR_ARG;
     if (!cells_fused_supported(n_bins, cell, stride)) return HOG_ERR_UNSUPPORTED;
     const int r = cell / stride;
+    const int wpc = score_tc_windows(n_bins);
     // first pass: sizes, and the tensor-core row count the whole batch supports
     long ctas32 = 0;
     for (int i = 0; i < n_items; ++i) {
@@ -54,7 +55,7 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
         const int nx = ncx - (cells_x - 1) * r, ny = ncy - (cells_y - 1) * r;
         if (nx > 0 && ny > 0) {
             if (it.scores == nullptr) return HOG_ERR_ARG;
-            ctas32 += (long)((nx + kScoreTcWindows - 1) / kScoreTcWindows) * ((ny + 32 * r - 1) / (32 * r)) * r;
+            ctas32 += (long)((nx + wpc - 1) / wpc) * ((ny + 32 * r - 1) / (32 * r)) * r;
         }
     }
     const int Tc = score_tc_rows_for(ctas32);
@@ -76,7 +77,7 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
         p.cells_tx = p.ncx > 0 ? cells_fused_tiles_x(p.ncx, stride) : 1;
         cells_t += p.ncx > 0 && p.ncy > 0 ? cells_fused_tiles(p.ncx, p.ncy, stride) : 0;
         p.score_c0 = (int)score_c;
-        p.score_tx = (p.nx + kScoreTcWindows - 1) / kScoreTcWindows;
+        p.score_tx = (p.nx + wpc - 1) / wpc;
         p.score_bands = (p.ny + Tc * r - 1) / (Tc * r);
         score_c += (long)p.score_tx * p.score_bands * r;
         p.detect_t0 = (int)detect_t;

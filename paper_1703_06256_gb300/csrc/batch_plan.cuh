@@ -64,7 +64,7 @@ __device__ __forceinline__ int find_item(const PlanItem* items, int n, int t) {
 // Geometry helpers of the per-stage kernels, used by the planner.
 int cells_fused_tiles_x(int ncx, int stride);
 int cells_fused_tiles(int ncx, int ncy, int stride);
-constexpr int kScoreTcWindows = 128;  // windows per tensor-core CTA
+int score_tc_windows(int n_bins);  // windows per tensor-core CTA
 int detect_tiles(long n_scores);
 
 // Batch launchers (kernels in cells_fused.cu, score_tc.cu, detect.cu).

@@ -2,7 +2,7 @@
 // GEMM (the paper's linear score, Sections 1 and 4: the inner product of the
 // window feature with a weight vector at every scan position).
 //
-//   S[py][px] = bias + sum_{j<16} sum_{i<8} sum_{b<8} w[j][i][b] * C[py + j r][px + i r][b]
+//   S[py][px] = bias + sum_{j<16} sum_{i<8} sum_{b<N_b} w[j][i][b] * C[py + j r][px + i r][b]
 //
 // Output rows split into r residue classes: class phi holds the rows
 // py = py_lo + phi + r t (t < Tc), and they read only the cell rows
@@ -12,24 +12,30 @@
 //   S[t][px] += sum_{i, b} C_rho'[px + i r][b] * Wband_rho'[t][(i, b)],
 //   Wband_rho'[t][(i, b)] = w[rho' - t][i][b]  (0 unless 0 <= rho' - t < 16)
 //
-// is a GEMM with M = 128 windows px, N = Tc output rows, K = 8 cells x 8
-// bins = 64, accumulated over the Tc + 15 cell rows of the class into one
-// fixed block of Tc TMEM columns.
+// is a GEMM with M = windows px, N = Tc output rows, K = 8 cells x N_b bins,
+// accumulated over the Tc + 15 cell rows of the class into one fixed block
+// of TMEM columns.
 //
 // Neither operand is materialised per row.  A: in shared memory a cell row is
-// kept as in HBM, [px][8 bins] bf16 = 16 bytes per cell, so the 8 x 16-byte
-// core matrix (windows px0 + 8g .. +7, cell i) starts at byte (8g + i r) * 16:
-// the descriptor of an MMA over cells i, i+1 points at cell i r with a
-// K-direction core-matrix stride (LBO) of r * 16 bytes and an M-direction
-// stride (SBO) of 128 bytes -- an im2col done by the descriptor.  B: for each
-// cell i the 16 filter rows sit in a zero-padded, reversed plane
-// plane_i[v] = w[Tc + 14 - v][i] (16 bytes each); rows t = 0..Tc-1 of
-// Wband_rho' are the consecutive plane rows v = Tc + 14 - rho' + t, so the
-// band of cell row rho' is the same planes with the descriptor start moved
-// back 16 bytes per row (LBO = plane size, SBO = 128 bytes).
+// kept as in HBM, [px][N_b bins] bf16.  With N_b = 8 a cell is 16 bytes, so
+// the 8 x 16-byte core matrix (windows px0 + 8g .. +7, cell i) starts at
+// byte (8g + i r) * 16: the descriptor of an MMA over cells i, i+1 points at
+// cell i r with a K-direction core-matrix stride (LBO) of r * 16 bytes and an
+// M-direction stride (SBO) of 128 bytes -- an im2col done by the descriptor.
+// With N_b = 16 a cell is two 16-byte halves (bins 0-7, 8-15); the same
+// descriptor over 16-byte rows makes A row m half m % 2 of window m / 2, so
+// a CTA covers 64 windows, and each half h of the weights gets its own MMA
+// into its own Tc columns: only half h of the rows in those columns is kept,
+// and the epilogue adds the two halves of a window (neighbouring lanes).
+// B: for each cell i and half h the 16 filter rows sit in a zero-padded,
+// reversed plane plane_{i,h}[v] = w[Tc + 14 - v][i][8h .. 8h + 7] (16 bytes);
+// rows t = 0..Tc-1 of Wband_rho' are the consecutive plane rows
+// v = Tc + 14 - rho' + t, so the band of cell row rho' is the same planes
+// with the descriptor start moved back 16 bytes per row (LBO = distance
+// between the planes of cells i and i + 1, SBO = 128 bytes).
 //
-// One CTA: 128 windows (one TMEM lane each) by the Tc output rows of one
-// residue class (blockIdx.z = phi), so the r classes of a row band run in
+// One CTA: 128 accumulator rows (one TMEM lane each) by the Tc output rows of
+// one residue class (blockIdx.z = phi), so the r classes of a row band run in
 // separate CTAs and read disjoint cell rows; 4 warps.
 // Warp 0 lane 0 streams cell rows into a ring of shared-memory stages with
 // bulk async copies (mbarrier full/empty pipeline), warp 1 lane 0 issues
@@ -41,8 +47,9 @@
 //
 // Exactness: bin counts (<= 64) are exact in bf16, products of bf16 values
 // are exact in fp32.  With int8 weights (exact in bf16) every partial sum is
-// an integer of magnitude <= 127 * 8192 < 2^24, so the fp32 accumulation is
-// exact in any order and the int32 scores are bit-exact.
+// an integer of magnitude <= 127 * 8192 (a window has 8192 pixels, each in
+// at most one bin) < 2^24, so the fp32 accumulation is exact in any order
+// and the int32 scores are bit-exact.
 #include <type_traits>
 
 #include "batch_plan.cuh"
@@ -53,7 +60,7 @@ namespace fasthog {
 
 namespace {
 
-constexpr int kNB = 8, kCX = 8, kCY = 16;
+constexpr int kCX = 8, kCY = 16;
 constexpr int kM = 128;                   // windows per CTA (TMEM lanes)
 constexpr int kThreads = 128;
 constexpr int kStages = 4;
@@ -99,12 +106,12 @@ __device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// The 8 bins of filter cell c (weights 8c .. 8c + 7) as 8 bf16 values.
+// Weights off .. off + 7 (off a multiple of 8) as 8 bf16 values.
 template <typename WT>
-__device__ __forceinline__ uint4 load_weight_cell(const WT* w, int c);
+__device__ __forceinline__ uint4 load_weight8(const WT* w, int off);
 template <>
-__device__ __forceinline__ uint4 load_weight_cell<uint16_t>(const uint16_t* w, int c) {
-    const uint16_t* p = w + (size_t)c * kNB;
+__device__ __forceinline__ uint4 load_weight8<uint16_t>(const uint16_t* w, int off) {
+    const uint16_t* p = w + off;
     if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) return __ldg(reinterpret_cast<const uint4*>(p));
     uint32_t h[4];
 #pragma unroll
@@ -112,8 +119,8 @@ __device__ __forceinline__ uint4 load_weight_cell<uint16_t>(const uint16_t* w, i
     return make_uint4(h[0], h[1], h[2], h[3]);
 }
 template <>
-__device__ __forceinline__ uint4 load_weight_cell<int8_t>(const int8_t* w, int c) {
-    const int8_t* p = w + (size_t)c * kNB;
+__device__ __forceinline__ uint4 load_weight8<int8_t>(const int8_t* w, int off) {
+    const int8_t* p = w + off;
     int8_t b[8];
     if ((reinterpret_cast<uintptr_t>(p) & 7) == 0) {
         const uint2 v = __ldg(reinterpret_cast<const uint2*>(p));
@@ -136,23 +143,26 @@ __device__ __forceinline__ uint4 load_weight_cell<int8_t>(const int8_t* w, int c
 
 struct TcGeom {
     int r, Tc, rows;      // residue count, output rows per CTA (one class), cell rows per CTA
-    int row_cells;        // cells staged per cell row: kM + (kCX - 1) r
-    int row_bytes;        // row_cells * 16
+    int halves;           // N_b / 8: 16-byte halves of a cell (1 or 2)
+    int wpc;              // windows per CTA: 128 / halves
+    int row_cells;        // cells staged per cell row: wpc + (kCX - 1) r
+    int row_bytes;        // row_cells * 16 * halves
     int stage_bytes;      // kRowsPerStage rows
     int plane_rows;       // rows of one band plane: 2 Tc + 16
     int plane_bytes;      // plane_rows * 16
     int band_bytes;       // kCX planes
     int cols;             // TMEM columns allocated (power of two >= 32)
-    __host__ __device__ TcGeom(int r_, int Tc_) : r(r_), Tc(Tc_) {
+    __host__ __device__ TcGeom(int r_, int Tc_, int halves_) : r(r_), Tc(Tc_), halves(halves_) {
         rows = Tc + kCY - 1;
-        row_cells = kM + (kCX - 1) * r;
-        row_bytes = row_cells * 16;
+        wpc = kM / halves;
+        row_cells = wpc + (kCX - 1) * r;
+        row_bytes = row_cells * 16 * halves;
         stage_bytes = kRowsPerStage * row_bytes;
         plane_rows = 2 * Tc + 16;
         plane_bytes = plane_rows * 16;
-        band_bytes = kCX * plane_bytes;
+        band_bytes = kCX * halves * plane_bytes;
         cols = 32;
-        while (cols < Tc) cols *= 2;
+        while (cols < halves * Tc) cols *= 2;
     }
     __host__ __device__ size_t smem_bytes() const {
         return 1024 + (size_t)band_bytes + (size_t)kStages * stage_bytes + 256;
@@ -163,13 +173,14 @@ struct TcGeom {
 // band, residue class).  BATCH = true: the CTAs of every item of a batch
 // plan in one 1-D grid; each CTA finds its item and its (column, band,
 // class) from the plan and overrides the image arguments.
-template <typename WT, typename OutT, bool BATCH>
+template <int NB, typename WT, typename OutT, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const uint16_t* __restrict__ cells, int ncx, int ncy, int r, int Tc, const WT* __restrict__ w,
                     float bias, int nx, int ny, OutT* __restrict__ scores, const PlanItem* __restrict__ items,
                     int n_items, unsigned int* status) {
     extern __shared__ uint8_t smem_raw[];
-    const TcGeom G(r, Tc);
+    constexpr int HALVES = NB / 8, CB = NB * 2;  // 16-byte halves per cell, bytes per cell
+    const TcGeom G(r, Tc, HALVES);
     // 1024-byte aligned working area: band planes, A stages, barriers
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* band = base;
@@ -196,18 +207,23 @@ __global__ void __launch_bounds__(kThreads, 1)
         nx = it->nx;
         ny = it->ny;
     }
-    const int px0 = xt * kM;
+    const int px0 = xt * G.wpc;
     const int py_lo = yband * Tc * r + phi;  // first output row; rows step by r
 
-    // band planes: plane_i[v][b] = w[Tc + 14 - v][i][b] for filter rows 0..15, zero elsewhere.
-    // Thread t < 128 moves the 8 bins of filter cell (j, i) = (t / 8, t % 8) in one load; the
-    // rows of the planes that hold no filter row are zeroed by 16-byte stores.
+    // band planes, one per (cell i, half h): plane_{i,h}[v][b] = w[Tc + 14 - v][i][8h + b]
+    // for filter rows 0..15, zero elsewhere.  Thread t < 128 moves the bins of filter cell
+    // (j, i) = (t / 8, t % 8), 8 per load; the rows of the planes that hold no filter row are
+    // zeroed by 16-byte stores.
     {
         const int j = tid / kCX, i = tid % kCX;
-        uint4 v = load_weight_cell<WT>(w, tid);
-        *reinterpret_cast<uint4*>(band + (size_t)i * G.plane_bytes + (size_t)(Tc + 14 - j) * 16) = v;
+#pragma unroll
+        for (int h = 0; h < HALVES; ++h) {
+            const uint4 v = load_weight8<WT>(w, (j * kCX + i) * NB + 8 * h);
+            *reinterpret_cast<uint4*>(band + (size_t)(i * HALVES + h) * G.plane_bytes + (size_t)(Tc + 14 - j) * 16) =
+                v;
+        }
         const int zero_rows = G.plane_rows - kCY;  // v < Tc - 1 or v > Tc + 14
-        for (int e = tid; e < kCX * zero_rows; e += kThreads) {
+        for (int e = tid; e < kCX * HALVES * zero_rows; e += kThreads) {
             const int pi = e / zero_rows, zr = e % zero_rows;
             const int vrow = zr < Tc - 1 ? zr : zr + kCY;
             *reinterpret_cast<uint4*>(band + (size_t)pi * G.plane_bytes + (size_t)vrow * 16) = make_uint4(0, 0, 0, 0);
@@ -253,14 +269,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t bytes = 0;
             for (int q = 0; q < kRowsPerStage; ++q) {
                 const int row = py_lo + r * (k * kRowsPerStage + q);
-                if (k * kRowsPerStage + q < G.rows && row < ncy) bytes += (uint32_t)valid_cells * 16;
+                if (k * kRowsPerStage + q < G.rows && row < ncy) bytes += (uint32_t)valid_cells * CB;
             }
             ptx::mbar_arrive_expect_tx(&full[s], bytes);
             for (int q = 0; q < kRowsPerStage; ++q) {
                 const int row = py_lo + r * (k * kRowsPerStage + q);
                 if (k * kRowsPerStage + q < G.rows && row < ncy)
                     ptx::bulk_g2s(stages + (size_t)s * G.stage_bytes + (size_t)q * G.row_bytes,
-                                  cells + ((size_t)row * ncx + px0) * kNB, (uint32_t)valid_cells * 16, &full[s]);
+                                  cells + ((size_t)row * ncx + px0) * NB, (uint32_t)valid_cells * CB, &full[s]);
             }
             armed = k + 1;
         }
@@ -289,11 +305,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t b_row = band_addr + (uint32_t)((Tc + 14 - rho) * 16);
 #pragma unroll
                 for (int ks = 0; ks < kCX / 2; ++ks) {
-                    // cells 2ks, 2ks+1: A at cell 2ks*r, B at plane 2ks
-                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * r * 16), (uint32_t)(r * 16), 128);
-                    const uint64_t bd =
-                        smem_desc(b_row + (uint32_t)(2 * ks * G.plane_bytes), (uint32_t)G.plane_bytes, 128);
-                    mma_bf16(tmem, ad, bd, idesc, (rho == 0 && ks == 0) ? 0u : 1u);
+                    // cells 2ks, 2ks+1: A at cell 2ks*r (with two halves, A row m is half m % 2 of
+                    // window m / 2), B at the planes of half h of cells 2ks, 2ks+1, D at h * Tc
+                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * r * CB), (uint32_t)(r * CB), 128);
+#pragma unroll
+                    for (int h = 0; h < HALVES; ++h) {
+                        const uint64_t bd = smem_desc(b_row + (uint32_t)((2 * ks * HALVES + h) * G.plane_bytes),
+                                                      (uint32_t)(HALVES * G.plane_bytes), 128);
+                        mma_bf16(tmem + (uint32_t)(h * Tc), ad, bd, idesc, (rho == 0 && ks == 0) ? 0u : 1u);
+                    }
                 }
             }
             mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
@@ -307,15 +327,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (!ok) atomicOr(status, kStatusTimeout);
     tc_fence_after();
     __syncthreads();
-    const int px = px0 + warp * 32 + lane;
+    // lane m of the accumulator: window px0 + m (one half) or px0 + m / 2, half m % 2 (two
+    // halves, whose valid sums are columns [0, Tc) of even rows and [Tc, 2 Tc) of odd rows)
+    const int m = warp * 32 + lane;
+    const int px = px0 + m / HALVES;
+    const bool writer = HALVES == 1 || (lane & 1) == 0;
     if (ok && !*reinterpret_cast<volatile int*>(&aborted)) {
         for (int c0 = 0; c0 < Tc; c0 += 16) {
             uint32_t v[16];
             tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            if constexpr (HALVES == 2) {
+                uint32_t u[16];
+                tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(Tc + c0), u);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    const float mine = __uint_as_float((lane & 1) ? u[c] : v[c]);
+                    const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                    v[c] = __float_as_uint((lane & 1) ? other + mine : mine + other);  // half 0 + half 1
+                }
+            }
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 const int py = py_lo + r * (c0 + c);
-                if (px < nx && py < ny) {
+                if (writer && px < nx && py < ny) {
                     const float sc = __uint_as_float(v[c]) + bias;
                     if constexpr (std::is_same<OutT, int32_t>::value) {
                         scores[(size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
@@ -333,14 +367,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-int choose_tc(int nx, int ny, int r) {
+int choose_tc(int nx, int ny, int r, int wpc) {
     // 32 output rows per CTA when that still gives every SM a CTA, else 16
-    const long tiles_x = (nx + kM - 1) / kM;
+    const long tiles_x = (nx + wpc - 1) / wpc;
     const long ctas32 = tiles_x * ((ny + 32 * r - 1) / (32 * r)) * r;
     return ctas32 >= sm_count() ? 32 : 16;
 }
 
-template <typename WT, typename OutT>
+template <int NB, typename WT, typename OutT>
 hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* w, float bias, void* scores,
                     cudaStream_t st) {
     const int nx = ncx - (kCX - 1) * r, ny = ncy - (kCY - 1) * r;
@@ -348,27 +382,28 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     unsigned int* status = nullptr;
     hog_status s = device_status_word(&status);
     if (s != HOG_OK) return s;
-    const int Tc = choose_tc(nx, ny, r);
-    const TcGeom G(r, Tc);
+    const int wpc = kM / (NB / 8);
+    const int Tc = choose_tc(nx, ny, r, wpc);
+    const TcGeom G(r, Tc, NB / 8);
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
-    auto kern = score_tc_kernel<WT, OutT, false>;
+    auto kern = score_tc_kernel<NB, WT, OutT, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    dim3 grid((nx + kM - 1) / kM, (ny + Tc * r - 1) / (Tc * r), r);
+    dim3 grid((nx + wpc - 1) / wpc, (ny + Tc * r - 1) / (Tc * r), r);
     return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias,
                       nx, ny, static_cast<OutT*>(scores), static_cast<const PlanItem*>(nullptr), 0, status);
 }
 
-template <typename WT, typename OutT>
+template <int NB, typename WT, typename OutT>
 hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void* w, float bias, cudaStream_t st) {
     unsigned int* status = nullptr;
     hog_status s = device_status_word(&status);
     if (s != HOG_OK) return s;
-    const TcGeom G(h.r, h.score_tc);
+    const TcGeom G(h.r, h.score_tc, NB / 8);
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
-    auto kern = score_tc_kernel<WT, OutT, true>;
+    auto kern = score_tc_kernel<NB, WT, OutT, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     return launch_pdl(kern, dim3(h.score_ctas), dim3(kThreads), smem, st, static_cast<const uint16_t*>(nullptr), 0,
@@ -376,32 +411,48 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void*
                       plan_items(plan_dev), h.n_items, status);
 }
 
+template <int NB>
+hog_status batch_by_w(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
+                      cudaStream_t st) {
+    if (w_dtype == HOG_BF16) return launch_batch_t<NB, uint16_t, float>(h, plan_dev, w, bias, st);
+    if (w_dtype == HOG_I8) return launch_batch_t<NB, int8_t, int32_t>(h, plan_dev, w, bias, st);
+    return HOG_ERR_UNSUPPORTED;
+}
+
+template <int NB>
+hog_status by_w(const uint16_t* cells, int ncx, int ncy, int r, const void* w, int w_dtype, float bias, void* scores,
+                cudaStream_t st) {
+    if (w_dtype == HOG_BF16) return launch_t<NB, uint16_t, float>(cells, ncx, ncy, r, w, bias, scores, st);
+    if (w_dtype == HOG_I8) return launch_t<NB, int8_t, int32_t>(cells, ncx, ncy, r, w, bias, scores, st);
+    return HOG_ERR_UNSUPPORTED;
+}
+
 }  // namespace
 
 hog_status launch_score_tc_batch(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
                                  cudaStream_t st) {
     if (h.score_ctas == 0) return HOG_OK;
-    if (w_dtype == HOG_BF16) return launch_batch_t<uint16_t, float>(h, plan_dev, w, bias, st);
-    if (w_dtype == HOG_I8) return launch_batch_t<int8_t, int32_t>(h, plan_dev, w, bias, st);
-    return HOG_ERR_UNSUPPORTED;
+    return h.n_bins == 16 ? batch_by_w<16>(h, plan_dev, w, w_dtype, bias, st)
+                          : batch_by_w<8>(h, plan_dev, w, w_dtype, bias, st);
 }
 
 int score_tc_rows_for(long ctas32) { return ctas32 >= kNumSMs ? 32 : 16; }
 
+int score_tc_windows(int n_bins) { return kM / (n_bins == 16 ? 2 : 1); }
+
 bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx) {
     (void)ncx;
-    return cell_dtype == HOG_BF16 && n_bins == kNB && cells_x == kCX && cells_y == kCY && (r == 1 || r == 2 || r == 4);
+    return cell_dtype == HOG_BF16 && (n_bins == 8 || n_bins == 16) && cells_x == kCX && cells_y == kCY &&
+           (r == 1 || r == 2 || r == 4);
 }
 
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x, int cells_y, int r,
                            const void* w, int w_dtype, float bias, void* scores, cudaStream_t st) {
-    (void)n_bins;
     (void)cells_x;
     (void)cells_y;
     if (reinterpret_cast<uintptr_t>(cells_bf16) % 16 != 0) return HOG_ERR_UNSUPPORTED;
-    if (w_dtype == HOG_BF16) return launch_t<uint16_t, float>(cells_bf16, ncx, ncy, r, w, bias, scores, st);
-    if (w_dtype == HOG_I8) return launch_t<int8_t, int32_t>(cells_bf16, ncx, ncy, r, w, bias, scores, st);
-    return HOG_ERR_UNSUPPORTED;
+    return n_bins == 16 ? by_w<16>(cells_bf16, ncx, ncy, r, w, w_dtype, bias, scores, st)
+                        : by_w<8>(cells_bf16, ncx, ncy, r, w, w_dtype, bias, scores, st);
 }
 
 }  // namespace fasthog

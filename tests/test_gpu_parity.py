@@ -302,22 +302,24 @@ def test_pipeline_end_to_end_host(fh, g):
 
 
 # ---------------------------------------------------------------- tensor-core scores
+@pytest.mark.parametrize("nb", [8, 16])
 @pytest.mark.parametrize("stride", [8, 4, 2])
-def test_score_tensor_cores(fh, g, stride):
-    """bf16 cell map -> the tcgen05 implicit-GEMM kernel.  bf16 weights: within
-    the FP32-path bound of the oracle run on the same bf16-rounded weights;
-    int8 weights: bit-exact.  The image spans several 128-window tiles and
-    row bands, with ragged ends in both directions."""
-    rng = np.random.default_rng(20 + stride)
+def test_score_tensor_cores(fh, g, stride, nb):
+    """bf16 cell map -> the tcgen05 implicit-GEMM kernel (N_b = 16: two cell
+    halves per window).  bf16 weights: within the FP32-path bound of the
+    oracle run on the same bf16-rounded weights; int8 weights: bit-exact.  The
+    image spans several window tiles and row bands, with ragged ends in both
+    directions."""
+    rng = np.random.default_rng(20 + stride + nb)
     img = rand_img(520, 700, 3, 40 + stride)
-    cells = cells_of(img, 8, stride)
-    w = rng.normal(0, 0.01, 1024).astype(np.float32)
+    cells = cells_of(img, nb, stride)
+    w = rng.normal(0, 0.01, 128 * nb).astype(np.float32)
     w_bf = torch.from_numpy(w).to(torch.bfloat16).float().numpy()
     ref = oracle.window_score(cells, w_bf, 0.25, stride=stride)
     got = g.gpu_scores(cells, w, fh.HOG_BF16, 0.25, stride=stride, cell_dtype=fh.HOG_BF16)
     assert got.shape == ref.shape
     assert np.all(np.abs(got - ref) <= g.score_tolerance(cells, w_bf, 0.25, stride=stride))
-    wi = rng.integers(-127, 128, 1024).astype(np.int8)
+    wi = rng.integers(-127, 128, 128 * nb).astype(np.int8)
     ref_i = oracle.window_score(cells, wi, 3.0, stride=stride)
     got_i = g.gpu_scores(cells, wi, fh.HOG_I8, 3.0, stride=stride, cell_dtype=fh.HOG_BF16)
     assert got_i.dtype == np.int32 and np.array_equal(got_i, ref_i.astype(np.int64))
