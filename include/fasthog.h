@@ -277,6 +277,35 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
                               int image, int level, hog_det* out, int max_out, int32_t* d_count,
                               hog_stream_t stream);
 
+/*
+ * Launch-shape knobs, read by the launches made after they are set (a CUDA
+ * graph keeps the shapes it was captured with).  None of them changes any
+ * result: they pick tile shapes, schedules and grid sizes only.  0 restores
+ * the library's own choice.  Process-wide; set them from one thread while no
+ * other thread is launching.  The paper has no counterpart: they exist for
+ * the autotuner (paper_1703_06256_gb300/autotune.py).
+ *
+ *   HOG_TUNE_INTEGRAL_BAND_ROWS   rows per tile of the integral-image scan:
+ *                                 4, 8, 16 or 32 (hog_integral_workspace_bytes
+ *                                 covers every choice)
+ *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
+ *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
+ *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 16 or 32
+ *
+ * hog_tune_set returns HOG_ERR_ARG for an unknown knob or a value outside its
+ * range (nothing changes); hog_tune_get returns the current value (0 = the
+ * library's choice), or -1 for an unknown knob.
+ */
+typedef enum {
+    HOG_TUNE_INTEGRAL_BAND_ROWS = 0,
+    HOG_TUNE_BINMAP_CTAS_PER_SM = 1,
+    HOG_TUNE_FUSED_CTAS_PER_SM = 2,
+    HOG_TUNE_SCORE_TC_ROWS = 3,
+    HOG_TUNE_KNOBS = 4
+} hog_tune_knob;
+hog_status hog_tune_set(int knob, int value);
+int hog_tune_get(int knob);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,6 +28,8 @@ HOG_LUT_PITCH = 512
 HOG_LUT_QUAD_OFFSET = HOG_LUT_SIDE * HOG_LUT_PITCH
 HOG_LUT_BYTES = HOG_LUT_QUAD_OFFSET + 256 * 256
 HOG_STATUS_TIMEOUT = 1
+(HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_FUSED_CTAS_PER_SM,
+ HOG_TUNE_SCORE_TC_ROWS) = range(4)
 
 TORCH_DTYPE = {HOG_U8: torch.uint8, HOG_I32: torch.int32, HOG_BF16: torch.bfloat16, HOG_F32: torch.float32,
                HOG_I8: torch.int8, HOG_U16: torch.uint16 if hasattr(torch, "uint16") else torch.int16}
@@ -95,6 +97,8 @@ def _load() -> ctypes.CDLL:
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
         "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
+        "hog_tune_set": (I, [I, I]),
+        "hog_tune_get": (I, [I]),
         "hog_batch_plan_bytes": (Z, [I]),
         "hog_batch_plan": (I, [P, I, I, I, I, I, I, I, P, Z]),
         "hog_cell_hist_fused_batch": (I, [P, P, P, I, P]),
@@ -122,7 +126,7 @@ _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
-            "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
+            "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
             "hog_server_poll", "hog_server_release", "hog_server_stats")
@@ -238,6 +242,16 @@ def hog_detect_noalloc(scores, score_dtype: int, nx: int, ny: int, stride: int, 
 
 
 HOG_DETECT_NOALLOC_MAX_SCORES = 16384 * 2048
+
+
+# ---- launch-shape knobs -------------------------------------------------------
+
+def hog_tune_set(knob: int, value: int) -> None:
+    _check("hog_tune_set", _lib.hog_tune_set(knob, value))
+
+
+def hog_tune_get(knob: int) -> int:
+    return _lib.hog_tune_get(knob)
 
 
 # ---- batches of images and pyramid levels (include/fasthog_batch.h) ---------

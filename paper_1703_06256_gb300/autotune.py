@@ -1,0 +1,164 @@
+"""Autotuner for the library's launch-shape knobs (``hog_tune_*`` in
+include/fasthog.h): the integral-image scan's band height (rows per tile),
+the bin-map and fused-cells grid caps, and the tensor-core score's rows per
+CTA.  None of them changes a result; they change only how the work is cut.
+
+The tuner times each candidate on the caller's own workload through the
+library's calls -- the per-image path captured as a CUDA graph, CUDA events
+around each replay, the L2 flushed between replays -- and keeps the fastest.
+The search is coordinate descent from the library's defaults (value 0 for
+every knob): one knob at a time over its candidates, the others held at the
+best so far, repeated until a sweep changes nothing.  Results are cached in
+a JSON file per device and workload.
+"""
+
+from __future__ import annotations
+
+import json
+import os
+import statistics
+
+from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_INTEGRAL_BAND_ROWS,
+               HOG_TUNE_SCORE_TC_ROWS, hog_tune_get, hog_tune_set)
+
+# knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
+KNOBS = {
+    "integral_band_rows": (HOG_TUNE_INTEGRAL_BAND_ROWS, (0, 4, 8, 16, 32)),
+    "binmap_ctas_per_sm": (HOG_TUNE_BINMAP_CTAS_PER_SM, (0, 1, 2, 4)),
+    "fused_ctas_per_sm": (HOG_TUNE_FUSED_CTAS_PER_SM, (0, 1)),
+    "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 16, 32)),
+}
+# the knobs each path's launches read
+PATH_KNOBS = {
+    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "score_tc_rows"),
+    "fused": ("fused_ctas_per_sm", "score_tc_rows"),
+}
+
+
+def apply(config: dict) -> None:
+    """Set every knob named in `config` (others keep their value)."""
+    for name, value in config.items():
+        hog_tune_set(KNOBS[name][0], int(value))
+
+
+def current() -> dict:
+    return {name: hog_tune_get(k) for name, (k, _) in KNOBS.items()}
+
+
+def reset() -> None:
+    apply({name: 0 for name in KNOBS})
+
+
+def search(candidates: dict, measure, max_sweeps: int = 3):
+    """Coordinate descent over `candidates` (name -> values) with `measure`
+    (config -> time, lower is better).  Starts from the first value of every
+    knob.  Returns (best config, best time, {config key: time} of every
+    measurement)."""
+    best = {name: vals[0] for name, vals in candidates.items()}
+    seen: dict = {}
+
+    def timed(cfg):
+        key = json.dumps(cfg, sort_keys=True)
+        if key not in seen:
+            seen[key] = measure(dict(cfg))
+        return seen[key]
+
+    best_t = timed(best)
+    for _ in range(max_sweeps):
+        changed = False
+        for name, vals in candidates.items():
+            for v in vals:
+                if v == best[name]:
+                    continue
+                cfg = dict(best, **{name: v})
+                t = timed(cfg)
+                if t < best_t:
+                    best, best_t, changed = cfg, t, True
+        if not changed:
+            break
+    return best, best_t, seen
+
+
+class Autotuner:
+    """Cached tuning: ``tune(workload, measure, knobs)`` returns the best
+    knob values for `workload` (a dict naming it), measuring only on a cache
+    miss."""
+
+    def __init__(self, cache_path: str | None = None, device_name: str | None = None):
+        self.cache_path = cache_path
+        self.device_name = device_name or _device_name()
+        self.cache: dict = {}
+        if cache_path and os.path.exists(cache_path):
+            with open(cache_path) as f:
+                self.cache = json.load(f)
+
+    def key(self, workload: dict) -> str:
+        return json.dumps({"device": self.device_name, **workload}, sort_keys=True)
+
+    def tune(self, workload: dict, measure, knobs) -> dict:
+        k = self.key(workload)
+        hit = self.cache.get(k)
+        if hit is not None:
+            return hit
+        cand = {name: KNOBS[name][1] for name in knobs}
+        best, best_t, seen = search(cand, measure)
+        default_t = seen[json.dumps({name: 0 for name in knobs}, sort_keys=True)]
+        entry = {"config": best, "ms": best_t, "default_ms": default_t, "measured": len(seen)}
+        self.cache[k] = entry
+        if self.cache_path:
+            tmp = self.cache_path + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(self.cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, self.cache_path)
+        return entry
+
+
+def _device_name() -> str:
+    import torch
+
+    return torch.cuda.get_device_name(0) if torch.cuda.is_available() else "cpu"
+
+
+def pipeline_measure(pipe, reps: int = 20, flush_bytes: int = 256 << 20):
+    """A `measure` for `search`: apply the knobs, recapture `pipe`'s graph
+    (launch shapes are fixed at capture), and return the median device time
+    (ms) of `reps` replays, each after an L2 flush."""
+    import torch
+
+    flush = torch.empty(flush_bytes // 4, dtype=torch.int32, device=pipe.device)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def measure(cfg: dict) -> float:
+        apply(cfg)
+        pipe.graph = None
+        pipe.capture()
+        times = []
+        for k in range(reps + 3):
+            flush.fill_(k)
+            ev[0].record()
+            pipe.run()
+            ev[1].record()
+            torch.cuda.synchronize(pipe.device)
+            if k >= 3:
+                times.append(ev[0].elapsed_time(ev[1]))
+        return statistics.median(times)
+
+    return measure
+
+
+def tune_pipeline(pipe, tuner: Autotuner | None = None, reps: int = 20) -> dict:
+    """Tune the knobs of `pipe`'s path (HogPipeline, image and weights set)
+    and leave the best values applied.  Returns the cache entry."""
+    tuner = tuner or Autotuner()
+    path = "fused" if pipe.fused else "separate"
+    workload = {"W": pipe.W, "H": pipe.H, "channels": pipe.channels, "n_bins": pipe.n_bins, "stride": pipe.stride,
+                "cell": pipe.cell, "ii_dtype": pipe.ii_dtype, "cell_dtype": pipe.cell_dtype,
+                "w_dtype": pipe.w_dtype, "path": path}
+    entry = tuner.tune(workload, pipeline_measure(pipe, reps), PATH_KNOBS[path])
+    apply(entry["config"])
+    pipe.graph = None
+    return entry
+
+
+__all__ = ["KNOBS", "PATH_KNOBS", "Autotuner", "apply", "current", "reset", "search", "pipeline_measure",
+           "tune_pipeline"]

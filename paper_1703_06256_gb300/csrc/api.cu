@@ -2,6 +2,7 @@
 // argument checks, then one launcher per stage.  No entry point allocates,
 // synchronises or falls back to the host: a stage runs on the GPU or the
 // call returns an error without enqueueing anything.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -10,6 +11,7 @@
 namespace fasthog {
 
 namespace {
+std::atomic<int> g_tune[HOG_TUNE_KNOBS];
 thread_local int t_last_cuda_error = 0;
 constexpr int kMaxDevices = 64;
 int g_sm_count[kMaxDevices] = {0};
@@ -58,6 +60,10 @@ hog_status device_status_word(unsigned int** out) {
     return HOG_OK;
 }
 
+int tune_get(int knob) {
+    return knob >= 0 && knob < HOG_TUNE_KNOBS ? g_tune[knob].load(std::memory_order_relaxed) : 0;
+}
+
 static int n_pos(int extent, int box, int stride) { return extent < box ? 0 : (extent - box) / stride + 1; }
 
 static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 65535 && H <= 65535 && (long)W * H < (1L << 31); }
@@ -67,6 +73,24 @@ static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 65535 && H <
 using namespace fasthog;
 
 extern "C" {
+
+hog_status hog_tune_set(int knob, int value) {
+    bool ok = value == 0;
+    switch (knob) {
+        case HOG_TUNE_INTEGRAL_BAND_ROWS: ok = ok || value == 4 || value == 8 || value == 16 || value == 32; break;
+        case HOG_TUNE_BINMAP_CTAS_PER_SM: ok = ok || (value >= 1 && value <= 8); break;
+        case HOG_TUNE_FUSED_CTAS_PER_SM: ok = ok || value == 1 || value == 2; break;
+        case HOG_TUNE_SCORE_TC_ROWS: ok = ok || value == 16 || value == 32; break;
+        default: return HOG_ERR_ARG;
+    }
+    if (!ok) return HOG_ERR_ARG;
+    g_tune[knob].store(value, std::memory_order_relaxed);
+    return HOG_OK;
+}
+
+int hog_tune_get(int knob) {
+    return knob >= 0 && knob < HOG_TUNE_KNOBS ? g_tune[knob].load(std::memory_order_relaxed) : -1;
+}
 
 const char* hog_status_string(hog_status s) {
     switch (s) {

@@ -124,7 +124,8 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     const long n_quads = (long)((W + 3) / 4) * H;
     // at least 4 quads per thread, so each staged table copy serves a fair share of pixels
     const long need = (n_quads + 4 * kThreads - 1) / (4 * kThreads);
-    const long cap = (long)sm_count() * (QUAD ? 3 : 8);
+    const int per_sm = tune_get(HOG_TUNE_BINMAP_CTAS_PER_SM);
+    const long cap = (long)sm_count() * (per_sm > 0 ? per_sm : (QUAD ? 3 : 8));
     const int grid = (int)(need < cap ? need : cap);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
     const bool word_stores = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (W % 4 == 0);

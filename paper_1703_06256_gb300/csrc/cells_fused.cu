@@ -271,7 +271,8 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     if (e != cudaSuccess) return cuda_fail(e);
     constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
     const int tiles = ((ncx + BX - 1) / BX) * ((ncy + BY - 1) / BY);
-    const int cap = 2 * sm_count();  // two CTAs of this size fit an SM
+    const int per_sm = tune_get(HOG_TUNE_FUSED_CTAS_PER_SM);
+    const int cap = (per_sm > 0 ? per_sm : 2) * sm_count();  // two CTAs of this size fit an SM
     const int grid = tiles < cap ? tiles : cap;
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
     const int out_align = cells_alignment(cells);
@@ -337,7 +338,8 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const uint8
     auto kern = cells_fused_batch_kernel<CH, NB, S, OutT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    const int cap = 2 * sm_count();
+    const int per_sm = tune_get(HOG_TUNE_FUSED_CTAS_PER_SM);
+    const int cap = (per_sm > 0 ? per_sm : 2) * sm_count();
     const int grid = h.cells_tiles < cap ? h.cells_tiles : cap;
     return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, plan_items(plan_dev), h.n_items, h.cells_tiles,
                       lut, h.r, status);

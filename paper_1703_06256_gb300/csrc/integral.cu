@@ -53,19 +53,26 @@ struct Plan {
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
-Plan make_plan(int W, int H, int n_bins) {
+// Band height h (rows per tile): the tuned value if one is set (force > 0
+// overrides both), else the tallest band that still gives every SM four
+// tiles (16 warps).
+Plan make_plan(int W, int H, int n_bins, int force = 0) {
     Plan p{};
     p.W = W;
     p.H = H;
     p.n_groups = ceil_div(W, kGroup);
-    // The tallest band that still gives every SM four tiles (16 warps).
-    const int target = 4 * sm_count();
-    p.h = 4;
-    for (int h : {32, 16, 8})
-        if ((long)ceil_div(H, h) * p.n_groups >= target) {
-            p.h = h;
-            break;
-        }
+    const int tuned = force > 0 ? force : tune_get(HOG_TUNE_INTEGRAL_BAND_ROWS);
+    if (tuned > 0) {
+        p.h = tuned;
+    } else {
+        const int target = 4 * sm_count();
+        p.h = 4;
+        for (int h : {32, 16, 8})
+            if ((long)ceil_div(H, h) * p.n_groups >= target) {
+                p.h = h;
+                break;
+            }
+    }
     p.n_bands = ceil_div(H, p.h);
     p.win = n_bins <= 4 ? 4 : (n_bins <= 8 ? 8 : 16);
     p.n_windows = ceil_div(n_bins, p.win);
@@ -539,8 +546,14 @@ hog_status run_all(const Plan& p, const uint8_t* bins, int n_bins, OutT* ii, con
 }  // namespace
 
 size_t integral_workspace_bytes(int W, int H, int n_bins) {
-    const Plan p = make_plan(W, H, n_bins);
-    return p.colcnt_bytes + p.rowcnt_bytes + p.bt_bytes + p.carry_bytes + p.gv_bytes;
+    // enough for every band height, so a workspace stays valid whatever the tuning
+    size_t most = 0;
+    for (int h : {4, 8, 16, 32}) {
+        const Plan p = make_plan(W, H, n_bins, h);
+        const size_t b = p.colcnt_bytes + p.rowcnt_bytes + p.bt_bytes + p.carry_bytes + p.gv_bytes;
+        most = b > most ? b : most;
+    }
+    return most;
 }
 
 hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii, void* ws,

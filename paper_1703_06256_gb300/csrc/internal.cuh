@@ -25,6 +25,8 @@ hog_status cuda_fail(cudaError_t e);
 hog_status check_launch();
 // Number of SMs of the current device (cached per device).
 int sm_count();
+// Current value of a launch-shape knob (hog_tune_knob); 0 = the library's choice.
+int tune_get(int knob);
 // Device address of the library's status word on the current device.
 hog_status device_status_word(unsigned int** out);
 
