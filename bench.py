@@ -47,7 +47,9 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0, help="CPU-baseline sample length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the fused-path and 1080p-batch figures (the main line is unchanged)")
+                    help="skip every extra figure (the main line is unchanged)")
+    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,serving",
+                    help="comma-separated extra figures to run (default: all)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
@@ -427,6 +429,7 @@ def batch_pyramid(torch, fh, wl, replicas, flush, args, world):
 
 def main():
     args = parse()
+    extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -515,7 +518,7 @@ def main():
 
     # the same step with the fused image-to-cells kernel (no bin map or integral planes in HBM)
     fused = None
-    if not args.no_extras:
+    if "fused" in extras:
         pipe.fused = True
         ftuned = None if args.no_tune else autotune.tune_pipeline(pipe, autotune.Autotuner(), reps=10)
         fstep, fread, _ = graph_step(torch, [pipe.stage_cells_fused, pipe.stage_score, pipe.stage_detect],
@@ -575,9 +578,10 @@ def main():
         "clocks": clocks,
         "device_status": status,
         "fused": fused,
-        "batch_1080p": None if args.no_extras else batch_1080p(torch, fh, wl, replicas, flush, args, world),
-        "batch_pyramid": None if args.no_extras else batch_pyramid(torch, fh, wl, replicas, flush, args, world),
-        "serving": (serving(torch, wl, args) if not args.no_extras and world == 1 and args.serve_requests > 0
+        "batch_1080p": batch_1080p(torch, fh, wl, replicas, flush, args, world) if "batch_1080p" in extras else None,
+        "batch_pyramid": (batch_pyramid(torch, fh, wl, replicas, flush, args, world) if "batch_pyramid" in extras
+                          else None),
+        "serving": (serving(torch, wl, args) if "serving" in extras and world == 1 and args.serve_requests > 0
                     else None),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
