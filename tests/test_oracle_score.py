@@ -85,3 +85,30 @@ def test_decimate(oracle_mod):
     d = oracle_mod.decimate(img)
     assert d.shape == (3, 4, 3)
     assert np.array_equal(d, img[0:6:2, 0:8:2])
+
+
+def test_multi_filter_linearity_and_order(oracle_mod):
+    """Several filters: filter f of the result is filter f's own score with
+    bias f.  Checked by exact integer linearity (f2 = 3 f0 - 2 f1), one-hot
+    filters that read single cell counts, and the all-ones filter, which
+    counts the binned pixels of the window (closed form)."""
+    rng = np.random.default_rng(31)
+    img = rng.integers(0, 256, size=(200, 120), dtype=np.uint8)
+    bins = oracle_mod.bin_map(img, 8)
+    cells = oracle_mod.cell_hist_direct(bins, 8, 8, 4)
+    K = 8 * 16 * 8
+    w0 = rng.integers(-5, 6, K).astype(np.float64)
+    w1 = rng.integers(-5, 6, K).astype(np.float64)
+    onehot = np.zeros(K)
+    onehot[(3 * 8 + 5) * 8 + 6] = 1.0  # cell (cx, cy) = (5, 3), bin 6
+    W = np.stack([w0, w1, 3 * w0 - 2 * w1, onehot, np.ones(K)])
+    B = np.array([0.5, -1.0, 3.5, 0.0, 0.0])
+    S = oracle_mod.window_score_multi(cells, W, B, stride=4)
+    assert S.shape[0] == 5
+    assert np.array_equal(S[2] - 3.5, 3 * (S[0] - 0.5) - 2 * (S[1] + 1.0))
+    ny, nx = S.shape[1:]
+    assert np.array_equal(S[3], cells[3 * 2: 3 * 2 + ny, 5 * 2: 5 * 2 + nx, 6].astype(np.float64))
+    for py in (0, ny // 2, ny - 1):
+        for px in (0, nx - 1):
+            win = bins[py * 4: py * 4 + 128, px * 4: px * 4 + 64]
+            assert S[4, py, px] == np.count_nonzero(win < 8)
