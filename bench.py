@@ -36,6 +36,7 @@ METRIC = "Mpixel/s & windows/s (800×600, 1080p batch), % HBM peak; served p50/p
 WORKLOAD = "800x600 RGB uint8, N_b=8, 8x8 cells, 64x128 window, stride 4, f32 weights, thr 0.5"
 L2_FLUSH_BYTES = 256 << 20
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0
 
 
 def parse():
@@ -48,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra figure (the main line is unchanged)")
-    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,serving",
+    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,multi_filter,serving",
                     help="comma-separated extra figures to run (default: all)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
@@ -71,6 +72,15 @@ def peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return FALLBACK_HBM_GBS, "fallback"
+
+
+def bf16_peak():
+    """Measured dense bf16 peak (TFLOP/s, burst: the score is timed alone), or the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return FALLBACK_BF16_TFLOPS
 
 
 def profiled_traffic(stage: str, workload: str):
@@ -427,6 +437,48 @@ def batch_pyramid(torch, fh, wl, replicas, flush, args, world):
     return out
 
 
+def multi_filter(torch, fh, wl, flush, args, bf16_peak):
+    """Several filters on one 1920x1080 RGB image (stride 4, N_b = 8, bf16
+    cells x bf16 weights): the score call alone (hog_window_score_multi, one
+    tensor-core launch per filter group), cells computed beforehand.  Reports
+    the dense-equivalent FLOP rate 2 * 1024 * windows * F / t against the
+    measured bf16 peak: the banded implicit GEMM spends N = Tc output rows per
+    MMA per filter, so its ceiling is far below dense peak; the figure shows
+    how several filters raise it."""
+    W, H = 1920, 1080
+    rng = wl.rng_for(3)
+    img = wl.rgb_smooth_shapes(W, H, rng)
+    p = fh.HogPipeline(W, H, 3, 8, 4, cell_dtype=fh.HOG_BF16, w_dtype=fh.HOG_BF16)
+    p.set_image(img)
+    p.stage_cells_fused()
+    torch.cuda.synchronize()
+    windows = p.nx * p.ny
+    out = {"workload": "1920x1080 RGB, N_b=8, stride 4, bf16 cells x bf16 weights; score call only"}
+    steps = max(args.steps // 4, 10)
+    for F in (1, 4, 16):
+        w = torch.from_numpy(rng.normal(0, 0.01, (F, 1024)).astype(np.float32)).to(torch.bfloat16).cuda()
+        scores = torch.empty(F * windows, dtype=torch.float32, device="cuda")
+        biases = [0.0] * F
+        evs = [torch.cuda.Event(enable_timing=True, external=True) for _ in range(2)]
+        call = lambda: fh.hog_window_score_multi(p.cells, fh.HOG_BF16, p.ncx, p.ncy, 8, 8, 16, 8, 4, w,  # noqa: E731
+                                                 fh.HOG_BF16, F, biases, scores)
+        call()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            evs[0].record()
+            call()
+            evs[1].record()
+        ms = time_steps(torch, g.replay, lambda: (None, evs[0].elapsed_time(evs[1])), flush, steps, args.warmup)
+        tflops = 2.0 * 1024 * windows * F / (ms * 1e-3) / 1e12
+        out[f"filters_{F}"] = {"ms": round(ms, 5), "filter_windows_per_s": round(windows * F / (ms * 1e-3), 1),
+                               "tflops": round(tflops, 2),
+                               "frac_of_bf16_peak": round(tflops / bf16_peak, 4) if bf16_peak else None}
+    del p
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     args = parse()
     extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
@@ -581,6 +633,8 @@ def main():
         "batch_1080p": batch_1080p(torch, fh, wl, replicas, flush, args, world) if "batch_1080p" in extras else None,
         "batch_pyramid": (batch_pyramid(torch, fh, wl, replicas, flush, args, world) if "batch_pyramid" in extras
                           else None),
+        "multi_filter": (multi_filter(torch, fh, wl, flush, args, bf16_peak()) if "multi_filter" in extras
+                         else None),
         "serving": (serving(torch, wl, args) if "serving" in extras and world == 1 and args.serve_requests > 0
                     else None),
     }

@@ -230,6 +230,24 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
                             int w_dtype, float bias, void* scores, hog_stream_t stream);
 
 /*
+ * hog_window_score_multi -- several linear filters over the same windows:
+ *   scores[f][py][px] = biases[f] + sum_k w[f][k] * feature_k(px, py),
+ * each filter exactly as hog_window_score would score it alone.  The paper
+ * scores one filter; several filters (one detector per class or pose) share
+ * every cell row the kernel loads, and on the tensor cores they widen the
+ * contraction (one MMA per filter per step into its own accumulator block).
+ *
+ *   w        device [n_filters][cells_y * cells_x * n_bins] of w_dtype
+ *   biases   HOST array of n_filters floats, read during the call (rounded to
+ *            the nearest integer, halves away from zero, for HOG_I8 weights)
+ *   scores   device [n_filters][ny][nx], f32 (int32 for HOG_I8 weights)
+ *   n_filters 1..1024; everything else as in hog_window_score.
+ */
+hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int cells_x,
+                                  int cells_y, int cell, int stride, const void* w, int w_dtype, int n_filters,
+                                  const float* biases, void* scores, hog_stream_t stream);
+
+/*
  * hog_detect -- threshold and ordered compaction of the score map.
  *
  * Every window with score >= thr is written to out[] in row-major (py, px)

@@ -97,6 +97,7 @@ def _load() -> ctypes.CDLL:
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
         "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
+        "hog_window_score_multi": (I, [P, I, I, I, I, I, I, I, I, P, I, I, P, P, P]),
         "hog_tune_set": (I, [I, I]),
         "hog_tune_get": (I, [I]),
         "hog_batch_plan_bytes": (Z, [I]),
@@ -126,7 +127,7 @@ _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
-            "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
+            "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
             "hog_server_poll", "hog_server_release", "hog_server_stats")
@@ -219,6 +220,17 @@ def hog_window_score(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, ce
     _check("hog_window_score", _lib.hog_window_score(_ptr(cells), cell_dtype, ncx, ncy, n_bins, cells_x, cells_y,
                                                      cell, stride, _ptr(w), w_dtype, float(bias), _ptr(scores),
                                                      _stream(stream)))
+
+
+def hog_window_score_multi(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, cells_x: int, cells_y: int,
+                           cell: int, stride: int, w, w_dtype: int, n_filters: int, biases, scores,
+                           stream=None) -> None:
+    """Several filters: `w` [n_filters][K] on the device, `biases` host
+    floats (a sequence), `scores` [n_filters][ny][nx] on the device."""
+    b = (ctypes.c_float * n_filters)(*[float(x) for x in biases])
+    _check("hog_window_score_multi", _lib.hog_window_score_multi(_ptr(cells), cell_dtype, ncx, ncy, n_bins, cells_x,
+                                                                 cells_y, cell, stride, _ptr(w), w_dtype, n_filters,
+                                                                 b, _ptr(scores), _stream(stream)))
 
 
 def hog_detect_workspace_bytes(nx: int, ny: int) -> int:

@@ -229,6 +229,38 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
                                    st);
 }
 
+hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int cells_x,
+                                  int cells_y, int cell, int stride, const void* w, int w_dtype, int n_filters,
+                                  const float* biases, void* scores, hog_stream_t stream) {
+    if (cells == nullptr || w == nullptr || scores == nullptr || biases == nullptr) return HOG_ERR_ARG;
+    if (n_filters < 1 || n_filters > 1024) return HOG_ERR_ARG;
+    if (ncx < 0 || ncy < 0 || n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
+    if (cells_x < 1 || cells_y < 1 || cells_x > 64 || cells_y > 64) return HOG_ERR_ARG;
+    if (cell < 1 || stride < 1 || cell % stride != 0) return HOG_ERR_ARG;
+    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
+    if (w_dtype != HOG_F32 && w_dtype != HOG_BF16 && w_dtype != HOG_I8) return HOG_ERR_ARG;
+    for (int f = 0; f < n_filters; ++f)
+        if (!std::isfinite(biases[f])) return HOG_ERR_ARG;
+    const int r = cell / stride;
+    const long nx = (long)ncx - (long)(cells_x - 1) * r, ny = (long)ncy - (long)(cells_y - 1) * r;
+    if (nx <= 0 || ny <= 0) return HOG_OK;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (w_dtype != HOG_F32 && score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx) &&
+        reinterpret_cast<uintptr_t>(cells) % 16 == 0)
+        return launch_score_tc_multi(static_cast<const uint16_t*>(cells), ncx, ncy, n_bins, r, w, w_dtype, n_filters,
+                                     biases, scores, st);
+    // otherwise the single-filter kernels, one filter at a time
+    const size_t esize = w_dtype == HOG_F32 ? 4 : (w_dtype == HOG_BF16 ? 2 : 1);
+    const size_t k = (size_t)cells_x * cells_y * n_bins;
+    for (int f = 0; f < n_filters; ++f) {
+        hog_status s = hog_window_score(cells, cell_dtype, ncx, ncy, n_bins, cells_x, cells_y, cell, stride,
+                                        static_cast<const uint8_t*>(w) + f * k * esize, w_dtype, biases[f],
+                                        static_cast<uint8_t*>(scores) + (size_t)f * nx * ny * 4, stream);
+        if (s != HOG_OK) return s;
+    }
+    return HOG_OK;
+}
+
 size_t hog_detect_workspace_bytes(int nx, int ny) {
     if (nx < 0 || ny < 0) return 0;
     return detect_workspace_bytes(nx, ny);

@@ -50,6 +50,7 @@
 // an integer of magnitude <= 127 * 8192 (a window has 8192 pixels, each in
 // at most one bin) < 2^24, so the fp32 accumulation is exact in any order
 // and the int32 scores are bit-exact.
+#include <cmath>
 #include <type_traits>
 
 #include "batch_plan.cuh"
@@ -141,18 +142,28 @@ __device__ __forceinline__ uint4 load_weight8<int8_t>(const int8_t* w, int off) 
     return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
+constexpr int kMaxFilters = 32;  // filters per launch (a group; the API splits larger sets)
+constexpr size_t kMaxSmem = 227 * 1024;
+
+// Per-filter biases, passed by value (captured with the launch).
+struct FilterBias {
+    float b[kMaxFilters];
+};
+
 struct TcGeom {
     int r, Tc, rows;      // residue count, output rows per CTA (one class), cell rows per CTA
     int halves;           // N_b / 8: 16-byte halves of a cell (1 or 2)
+    int filters;          // filters scored by one CTA
     int wpc;              // windows per CTA: 128 / halves
     int row_cells;        // cells staged per cell row: wpc + (kCX - 1) r
     int row_bytes;        // row_cells * 16 * halves
     int stage_bytes;      // kRowsPerStage rows
     int plane_rows;       // rows of one band plane: 2 Tc + 16
     int plane_bytes;      // plane_rows * 16
-    int band_bytes;       // kCX planes
+    int band_bytes;       // filters * kCX * halves planes
     int cols;             // TMEM columns allocated (power of two >= 32)
-    __host__ __device__ TcGeom(int r_, int Tc_, int halves_) : r(r_), Tc(Tc_), halves(halves_) {
+    __host__ __device__ TcGeom(int r_, int Tc_, int halves_, int filters_ = 1)
+        : r(r_), Tc(Tc_), halves(halves_), filters(filters_) {
         rows = Tc + kCY - 1;
         wpc = kM / halves;
         row_cells = wpc + (kCX - 1) * r;
@@ -160,9 +171,9 @@ struct TcGeom {
         stage_bytes = kRowsPerStage * row_bytes;
         plane_rows = 2 * Tc + 16;
         plane_bytes = plane_rows * 16;
-        band_bytes = kCX * halves * plane_bytes;
+        band_bytes = filters * kCX * halves * plane_bytes;
         cols = 32;
-        while (cols < halves * Tc) cols *= 2;
+        while (cols < filters * halves * Tc) cols *= 2;
     }
     __host__ __device__ size_t smem_bytes() const {
         return 1024 + (size_t)band_bytes + (size_t)kStages * stage_bytes + 256;
@@ -176,11 +187,12 @@ struct TcGeom {
 template <int NB, typename WT, typename OutT, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 1)
     score_tc_kernel(const uint16_t* __restrict__ cells, int ncx, int ncy, int r, int Tc, const WT* __restrict__ w,
-                    float bias, int nx, int ny, OutT* __restrict__ scores, const PlanItem* __restrict__ items,
-                    int n_items, unsigned int* status) {
+                    float bias, int n_filters, const __grid_constant__ FilterBias fbias, int nx, int ny,
+                    OutT* __restrict__ scores,
+                    const PlanItem* __restrict__ items, int n_items, unsigned int* status) {
     extern __shared__ uint8_t smem_raw[];
     constexpr int HALVES = NB / 8, CB = NB * 2;  // 16-byte halves per cell, bytes per cell
-    const TcGeom G(r, Tc, HALVES);
+    const TcGeom G(r, Tc, HALVES, n_filters);
     // 1024-byte aligned working area: band planes, A stages, barriers
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* band = base;
@@ -214,16 +226,19 @@ __global__ void __launch_bounds__(kThreads, 1)
     // for filter rows 0..15, zero elsewhere.  Thread t < 128 moves the bins of filter cell
     // (j, i) = (t / 8, t % 8), 8 per load; the rows of the planes that hold no filter row are
     // zeroed by 16-byte stores.
+    // With several filters, filter f's planes follow filter f - 1's.
     {
         const int j = tid / kCX, i = tid % kCX;
+        for (int f = 0; f < n_filters; ++f) {
 #pragma unroll
-        for (int h = 0; h < HALVES; ++h) {
-            const uint4 v = load_weight8<WT>(w, (j * kCX + i) * NB + 8 * h);
-            *reinterpret_cast<uint4*>(band + (size_t)(i * HALVES + h) * G.plane_bytes + (size_t)(Tc + 14 - j) * 16) =
-                v;
+            for (int h = 0; h < HALVES; ++h) {
+                const uint4 v = load_weight8<WT>(w, f * (kCX * kCY * NB) + (j * kCX + i) * NB + 8 * h);
+                *reinterpret_cast<uint4*>(band + (size_t)((f * kCX + i) * HALVES + h) * G.plane_bytes +
+                                          (size_t)(Tc + 14 - j) * 16) = v;
+            }
         }
         const int zero_rows = G.plane_rows - kCY;  // v < Tc - 1 or v > Tc + 14
-        for (int e = tid; e < kCX * HALVES * zero_rows; e += kThreads) {
+        for (int e = tid; e < n_filters * kCX * HALVES * zero_rows; e += kThreads) {
             const int pi = e / zero_rows, zr = e % zero_rows;
             const int vrow = zr < Tc - 1 ? zr : zr + kCY;
             *reinterpret_cast<uint4*>(band + (size_t)pi * G.plane_bytes + (size_t)vrow * 16) = make_uint4(0, 0, 0, 0);
@@ -308,11 +323,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // cells 2ks, 2ks+1: A at cell 2ks*r (with two halves, A row m is half m % 2 of
                     // window m / 2), B at the planes of half h of cells 2ks, 2ks+1, D at h * Tc
                     const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * r * CB), (uint32_t)(r * CB), 128);
+                    for (int f = 0; f < n_filters; ++f) {
 #pragma unroll
-                    for (int h = 0; h < HALVES; ++h) {
-                        const uint64_t bd = smem_desc(b_row + (uint32_t)((2 * ks * HALVES + h) * G.plane_bytes),
-                                                      (uint32_t)(HALVES * G.plane_bytes), 128);
-                        mma_bf16(tmem + (uint32_t)(h * Tc), ad, bd, idesc, (rho == 0 && ks == 0) ? 0u : 1u);
+                        for (int h = 0; h < HALVES; ++h) {
+                            const int plane = ((f * kCX + 2 * ks) * HALVES + h);
+                            const uint64_t bd = smem_desc(b_row + (uint32_t)(plane * G.plane_bytes),
+                                                          (uint32_t)(HALVES * G.plane_bytes), 128);
+                            mma_bf16(tmem + (uint32_t)((f * HALVES + h) * Tc), ad, bd, idesc,
+                                     (rho == 0 && ks == 0) ? 0u : 1u);
+                        }
                     }
                 }
             }
@@ -333,28 +352,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int px = px0 + m / HALVES;
     const bool writer = HALVES == 1 || (lane & 1) == 0;
     if (ok && !*reinterpret_cast<volatile int*>(&aborted)) {
-        for (int c0 = 0; c0 < Tc; c0 += 16) {
-            uint32_t v[16];
-            tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-            if constexpr (HALVES == 2) {
-                uint32_t u[16];
-                tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(Tc + c0), u);
+        for (int f = 0; f < n_filters; ++f) {
+            const float bias_f = n_filters == 1 ? bias : fbias.b[f];
+            OutT* out = scores + (size_t)f * nx * ny;
+            const uint32_t col0 = (uint32_t)(f * HALVES * Tc);
+            for (int c0 = 0; c0 < Tc; c0 += 16) {
+                uint32_t v[16];
+                tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)c0, v);
+                if constexpr (HALVES == 2) {
+                    uint32_t u[16];
+                    tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)(Tc + c0), u);
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) {
+                        const float mine = __uint_as_float((lane & 1) ? u[c] : v[c]);
+                        const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                        v[c] = __float_as_uint((lane & 1) ? other + mine : mine + other);  // half 0 + half 1
+                    }
+                }
 #pragma unroll
                 for (int c = 0; c < 16; ++c) {
-                    const float mine = __uint_as_float((lane & 1) ? u[c] : v[c]);
-                    const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                    v[c] = __float_as_uint((lane & 1) ? other + mine : mine + other);  // half 0 + half 1
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                const int py = py_lo + r * (c0 + c);
-                if (writer && px < nx && py < ny) {
-                    const float sc = __uint_as_float(v[c]) + bias;
-                    if constexpr (std::is_same<OutT, int32_t>::value) {
-                        scores[(size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
-                    } else {
-                        scores[(size_t)py * nx + px] = sc;
+                    const int py = py_lo + r * (c0 + c);
+                    if (writer && px < nx && py < ny) {
+                        const float sc = __uint_as_float(v[c]) + bias_f;
+                        if constexpr (std::is_same<OutT, int32_t>::value) {
+                            out[(size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
+                        } else {
+                            out[(size_t)py * nx + px] = sc;
+                        }
                     }
                 }
             }
@@ -394,7 +418,8 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     if (e != cudaSuccess) return cuda_fail(e);
     dim3 grid((nx + wpc - 1) / wpc, (ny + Tc * r - 1) / (Tc * r), r);
     return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias,
-                      nx, ny, static_cast<OutT*>(scores), static_cast<const PlanItem*>(nullptr), 0, status);
+                      1, FilterBias{}, nx, ny, static_cast<OutT*>(scores), static_cast<const PlanItem*>(nullptr), 0,
+                      status);
 }
 
 template <int NB, typename WT, typename OutT>
@@ -409,8 +434,65 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void*
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     return launch_pdl(kern, dim3(h.score_ctas), dim3(kThreads), smem, st, static_cast<const uint16_t*>(nullptr), 0,
-                      0, h.r, h.score_tc, static_cast<const WT*>(w), bias, 0, 0, static_cast<OutT*>(nullptr),
-                      plan_items(plan_dev), h.n_items, status);
+                      0, h.r, h.score_tc, static_cast<const WT*>(w), bias, 1, FilterBias{}, 0, 0,
+                      static_cast<OutT*>(nullptr), plan_items(plan_dev), h.n_items, status);
+}
+
+// Several filters: groups of filters per launch, as many as the shared
+// memory (their weight planes) and the TMEM columns allow.
+template <int NB, typename WT, typename OutT>
+hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, int r, const WT* w, int n_filters,
+                          const float* biases, OutT* scores, cudaStream_t st) {
+    const int nx = ncx - (kCX - 1) * r, ny = ncy - (kCY - 1) * r;
+    if (nx <= 0 || ny <= 0) return HOG_OK;
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    const int wpc = kM / (NB / 8);
+    int Tc = choose_tc(nx, ny, r, wpc);
+    auto fits = [&](int tc, int g) {
+        const TcGeom G(r, tc, NB / 8, g);
+        return G.cols <= 512 && G.smem_bytes() <= kMaxSmem;
+    };
+    int group = kMaxFilters < n_filters ? kMaxFilters : n_filters;
+    while (group > 1 && !fits(Tc, group)) --group;
+    if (!fits(Tc, group) && Tc == 32) {
+        Tc = 16;
+        group = kMaxFilters < n_filters ? kMaxFilters : n_filters;
+        while (group > 1 && !fits(Tc, group)) --group;
+    }
+    if (!fits(Tc, group)) return HOG_ERR_UNSUPPORTED;
+    auto kern = score_tc_kernel<NB, WT, OutT, false>;
+    const size_t smem_max = TcGeom(r, Tc, NB / 8, group).smem_bytes();
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const dim3 grid((nx + wpc - 1) / wpc, (ny + Tc * r - 1) / (Tc * r), r);
+    const size_t per_filter = (size_t)kCX * kCY * NB;
+    for (int f0 = 0; f0 < n_filters; f0 += group) {
+        const int g = n_filters - f0 < group ? n_filters - f0 : group;
+        FilterBias fb{};
+        for (int k = 0; k < g; ++k) {
+            const float b = biases[f0 + k];
+            fb.b[k] = std::is_same<OutT, int32_t>::value ? (float)std::llround((double)b) : b;
+        }
+        s = launch_pdl(kern, grid, dim3(kThreads), TcGeom(r, Tc, NB / 8, g).smem_bytes(), st, cells, ncx, ncy, r, Tc,
+                       w + f0 * per_filter, fb.b[0], g, fb, nx, ny, scores + (size_t)f0 * nx * ny,
+                       static_cast<const PlanItem*>(nullptr), 0, status);
+        if (s != HOG_OK) return s;
+    }
+    return HOG_OK;
+}
+
+template <int NB>
+hog_status multi_by_w(const uint16_t* cells, int ncx, int ncy, int r, const void* w, int w_dtype, int n_filters,
+                      const float* biases, void* scores, cudaStream_t st) {
+    if (w_dtype == HOG_BF16)
+        return launch_multi_t<NB, uint16_t, float>(cells, ncx, ncy, r, static_cast<const uint16_t*>(w), n_filters,
+                                                   biases, static_cast<float*>(scores), st);
+    if (w_dtype == HOG_I8)
+        return launch_multi_t<NB, int8_t, int32_t>(cells, ncx, ncy, r, static_cast<const int8_t*>(w), n_filters,
+                                                   biases, static_cast<int32_t*>(scores), st);
+    return HOG_ERR_UNSUPPORTED;
 }
 
 template <int NB>
@@ -449,6 +531,13 @@ bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, in
     (void)ncx;
     return cell_dtype == HOG_BF16 && (n_bins == 8 || n_bins == 16) && cells_x == kCX && cells_y == kCY &&
            (r == 1 || r == 2 || r == 4);
+}
+
+hog_status launch_score_tc_multi(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int r, const void* w,
+                                 int w_dtype, int n_filters, const float* biases, void* scores, cudaStream_t st) {
+    if (reinterpret_cast<uintptr_t>(cells_bf16) % 16 != 0) return HOG_ERR_UNSUPPORTED;
+    return n_bins == 16 ? multi_by_w<16>(cells_bf16, ncx, ncy, r, w, w_dtype, n_filters, biases, scores, st)
+                        : multi_by_w<8>(cells_bf16, ncx, ncy, r, w, w_dtype, n_filters, biases, scores, st);
 }
 
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x, int cells_y, int r,

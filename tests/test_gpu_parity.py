@@ -325,6 +325,60 @@ def test_score_tensor_cores(fh, g, stride, nb):
     assert got_i.dtype == np.int32 and np.array_equal(got_i, ref_i.astype(np.int64))
 
 
+@pytest.mark.parametrize("nb,stride,F", [(8, 4, 1), (8, 4, 5), (8, 8, 17), (16, 4, 3), (8, 2, 9)])
+def test_score_multi_filter(fh, g, nb, stride, F):
+    """Several filters in one call: each filter's map equals the oracle's
+    (bf16 weights: within the FP32-path bound on the bf16-rounded weights;
+    int8: exact) and is bit-identical to scoring that filter alone.  17
+    filters exceed one launch group, so the call splits them."""
+    rng = np.random.default_rng(200 + 10 * nb + F)
+    img = rand_img(330, 420, 3, 60 + stride)
+    cells = cells_of(img, nb, stride)
+    ncy, ncx, _ = cells.shape
+    K = 128 * nb
+    r = 8 // stride
+    nx, ny = ncx - 7 * r, ncy - 15 * r
+    c = torch.from_numpy(cells.astype(np.float32).reshape(-1)).to(torch.bfloat16).cuda()
+    W = rng.normal(0, 0.01, (F, K)).astype(np.float32)
+    B = rng.normal(0, 0.5, F).astype(np.float32)
+    W_bf = torch.from_numpy(W).to(torch.bfloat16)
+    ref = oracle.window_score_multi(cells, W_bf.double().numpy(), B, stride=stride)
+    out = torch.zeros(F * nx * ny, dtype=torch.float32, device="cuda")
+    fh.hog_window_score_multi(c, fh.HOG_BF16, ncx, ncy, nb, 8, 16, 8, stride, W_bf.cuda(), fh.HOG_BF16, F, B, out)
+    got = out.cpu().numpy().reshape(F, ny, nx)
+    for f in range(F):
+        tol = g.score_tolerance(cells, W_bf[f].double().numpy(), float(B[f]), stride=stride)
+        assert np.all(np.abs(got[f] - ref[f]) <= tol), f
+        one = g.gpu_scores(cells, W[f], fh.HOG_BF16, float(B[f]), stride=stride, cell_dtype=fh.HOG_BF16)
+        assert np.array_equal(one, got[f]), f
+    Wi = rng.integers(-127, 128, (F, K)).astype(np.int8)
+    Bi = np.round(rng.normal(0, 20, F)).astype(np.float32)
+    out_i = torch.zeros(F * nx * ny, dtype=torch.int32, device="cuda")
+    fh.hog_window_score_multi(c, fh.HOG_BF16, ncx, ncy, nb, 8, 16, 8, stride, torch.from_numpy(Wi).cuda(),
+                              fh.HOG_I8, F, Bi, out_i)
+    ref_i = oracle.window_score_multi(cells, Wi.astype(np.float64), Bi, stride=stride)
+    assert np.array_equal(out_i.cpu().numpy().reshape(F, ny, nx), ref_i.astype(np.int64))
+
+
+def test_score_multi_filter_f32(fh, g):
+    """f32 weights: the CUDA-core kernel per filter, within the FP32 bound."""
+    rng = np.random.default_rng(301)
+    img = rand_img(300, 260, 3, 9)
+    cells = cells_of(img, 8, 4)
+    ncy, ncx, _ = cells.shape
+    nx, ny = ncx - 14, ncy - 30
+    F = 4
+    W = rng.normal(0, 0.01, (F, 1024)).astype(np.float32)
+    B = [0.0, 0.5, -0.25, 2.0]
+    out = torch.zeros(F * nx * ny, dtype=torch.float32, device="cuda")
+    fh.hog_window_score_multi(g.dev(cells.astype(np.float32).reshape(-1)), fh.HOG_F32, ncx, ncy, 8, 8, 16, 8, 4,
+                              g.dev(W.reshape(-1)), fh.HOG_F32, F, B, out)
+    got = out.cpu().numpy().reshape(F, ny, nx)
+    ref = oracle.window_score_multi(cells, W, B, stride=4)
+    for f in range(F):
+        assert np.all(np.abs(got[f] - ref[f]) <= g.score_tolerance(cells, W[f], B[f], stride=4))
+
+
 def test_score_bf16_error_against_f32_weights(fh, g):
     """The bf16 path against the FP64 oracle with the original f32 weights:
     the error is the weight rounding (bf16 keeps 8 significant bits, so at
