@@ -73,6 +73,7 @@ def _load():
                 "oracle_window_score_from_bins": (I, [P, I, I, I, I, I, I, I, P, D, P]),
                 "oracle_detect": (L, [P, I, I, I, D, P, P, P, L]),
                 "oracle_decimate": (I, [P, I, I, I, L, P]),
+                "oracle_block_norm": (I, [P, I, I, I, I, D, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -226,6 +227,32 @@ def detect(S: np.ndarray, stride: int, thr: float):
     n = _load().oracle_detect(_ptr(S), nx, ny, int(stride), float(thr), _ptr(xs), _ptr(ys),
                               _ptr(sc), cap)
     return xs[:n].copy(), ys[:n].copy(), sc[:n].copy()
+
+
+def block_norm(cells: np.ndarray, r: int, eps: float) -> np.ndarray:
+    """Overlapping 2x2-cell blocks, L2-normalised: [ncy-r][ncx-r][4 nb] FP64
+    (quadrant q = 2 cy + cx of the block holds cell (i + cx r, j + cy r))."""
+    cells = np.ascontiguousarray(cells, dtype=np.int32)
+    ncy, ncx, nb = cells.shape
+    out = np.zeros((max(ncy - r, 0), max(ncx - r, 0), 4 * nb), np.float64)
+    _check(_load().oracle_block_norm(_ptr(cells), ncx, ncy, nb, r, float(eps), _ptr(out)), "block_norm")
+    return out
+
+
+def block_window_score(blocks: np.ndarray, w: np.ndarray, bias: float = 0.0, blocks_x: int = 7,
+                       blocks_y: int = 15, r: int = 2) -> np.ndarray:
+    """Linear score over windows of blocks_x x blocks_y blocks, block step r
+    positions (one cell): the window score of the block map with 4 nb
+    'bins' per entry, in FP64."""
+    blocks = np.ascontiguousarray(blocks, dtype=np.float64)
+    nby, nbx, k = blocks.shape
+    w64 = np.asarray(w, dtype=np.float64).reshape(blocks_y, blocks_x, k)
+    ny, nx = nby - (blocks_y - 1) * r, nbx - (blocks_x - 1) * r
+    S = np.full((max(ny, 0), max(nx, 0)), float(bias))
+    for by in range(blocks_y):
+        for bx in range(blocks_x):
+            S += blocks[by * r: by * r + ny, bx * r: bx * r + nx, :] @ w64[by, bx]
+    return S
 
 
 def decimate(img: np.ndarray) -> np.ndarray:

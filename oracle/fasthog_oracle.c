@@ -313,6 +313,35 @@ long oracle_detect(const double* S, int nx, int ny, int stride, double thr, int3
     return n;
 }
 
+/* Overlapping blocks (the "four overlapped sub areas" of a region, Section
+ * 3, Fig. 4's caption), read as blocks of 2 x 2 cells with a stride of one
+ * cell: block (i, j) of the cell map (positions at the scan stride, r = cell
+ * / stride positions per cell) concatenates the histograms of cells (i, j),
+ * (i + r, j), (i, j + r), (i + r, j + r) -- quadrant q = 2 cy + cx -- and
+ * divides the 4 nb values by sqrt(sum of their squares + eps^2).
+ * blocks: [ncy - r][ncx - r][4 nb] doubles. */
+int oracle_block_norm(const int32_t* cells, int ncx, int ncy, int nb, int r, double eps, double* blocks) {
+    int nbx = ncx - r, nby = ncy - r;
+    if (r < 1 || nb < 1) return -1;
+    if (nbx <= 0 || nby <= 0) return 0;
+    for (int j = 0; j < nby; ++j)
+        for (int i = 0; i < nbx; ++i) {
+            double* out = blocks + ((long)j * nbx + i) * 4 * nb;
+            double ss = 0.0;
+            for (int q = 0; q < 4; ++q) {
+                int ci = i + (q & 1) * r, cj = j + (q >> 1) * r;
+                for (int b = 0; b < nb; ++b) {
+                    double v = (double)cells[((long)cj * ncx + ci) * nb + b];
+                    out[q * nb + b] = v;
+                    ss += v * v;
+                }
+            }
+            double norm = sqrt(ss + eps * eps);
+            for (int k = 0; k < 4 * nb; ++k) out[k] = norm > 0.0 ? out[k] / norm : 0.0;
+        }
+    return 0;
+}
+
 /* Image pyramid level by 2:1 decimation: level l+1 keeps the pixels (2x, 2y)
  * of level l; sizes floor(W/2) x floor(H/2).  dst is packed (pitch W/2*ch). */
 int oracle_decimate(const uint8_t* src, int W, int H, int channels, long pitch, uint8_t* dst) {

@@ -112,3 +112,60 @@ def test_multi_filter_linearity_and_order(oracle_mod):
         for px in (0, nx - 1):
             win = bins[py * 4: py * 4 + 128, px * 4: px * 4 + 64]
             assert S[4, py, px] == np.count_nonzero(win < 8)
+
+
+def test_block_norm_from_pixels(oracle_mod):
+    """Overlapping 2x2-cell blocks counted straight from the bin map (16x16
+    pixels at the scan stride, four 8x8 quadrants) and L2-normalised equal the
+    oracle's blocks built from the cell map."""
+    rng = np.random.default_rng(41)
+    img = rng.integers(0, 256, size=(90, 70, 3), dtype=np.uint8)
+    bins = oracle_mod.bin_map(img, 8)
+    cells = oracle_mod.cell_hist_direct(bins, 8, 8, 4)
+    eps = 0.7
+    B = oracle_mod.block_norm(cells, 2, eps)
+    nby, nbx, k = B.shape
+    assert k == 32 and (nby, nbx) == (cells.shape[0] - 2, cells.shape[1] - 2)
+    for j in range(0, nby, 3):
+        for i in range(0, nbx, 2):
+            v = []
+            for q in range(4):
+                y0, x0 = 4 * j + 8 * (q >> 1), 4 * i + 8 * (q & 1)
+                blk = bins[y0: y0 + 8, x0: x0 + 8]
+                v += [np.count_nonzero(blk == b) for b in range(8)]
+            v = np.array(v, np.float64)
+            assert np.allclose(B[j, i], v / np.sqrt(v @ v + eps * eps), rtol=0, atol=1e-15)
+
+
+def test_block_norm_closed_forms(oracle_mod):
+    """A ramp puts every interior pixel in one bin: each quadrant of an
+    interior block holds 64 counts of that bin, so the block is
+    64 / sqrt(4 * 64^2 + eps^2) at the four entries of that bin and 0
+    elsewhere; with eps = 0 every non-empty block has unit norm, and a block
+    without binned pixels is all zero."""
+    _, xx = np.mgrid[0:64, 0:80]
+    img = (3 * xx).astype(np.uint8)  # (dx, dy) = (6, 0) inside: bin 0
+    bins = oracle_mod.bin_map(img, 8)
+    cells = oracle_mod.cell_hist_direct(bins, 8, 8, 4)
+    B = oracle_mod.block_norm(cells, 2, 2.0)
+    v = B[5, 5].reshape(4, 8)
+    want = 64 / np.sqrt(4 * 64.0 ** 2 + 4.0)
+    assert np.allclose(v[:, 0], want, atol=1e-15) and np.all(v[:, 1:] == 0)
+    B0 = oracle_mod.block_norm(cells, 2, 0.0)
+    n = np.sqrt((B0 ** 2).sum(axis=2))
+    assert np.allclose(n[n > 0], 1.0, atol=1e-15)
+    empty = np.zeros_like(cells)
+    assert np.all(oracle_mod.block_norm(empty, 2, 0.0) == 0)
+
+
+def test_block_window_score_indexing(oracle_mod):
+    """A one-hot weight on block (bx, by), entry k picks that block entry
+    of every window; the bias is added once."""
+    rng = np.random.default_rng(42)
+    B = rng.random((50, 30, 32))
+    w = np.zeros((15, 7, 32))
+    w[11, 4, 19] = 1.0
+    S = oracle_mod.block_window_score(B, w, 0.25, r=2)
+    ny, nx = S.shape
+    assert (ny, nx) == (50 - 28, 30 - 12)
+    assert np.array_equal(S, B[22: 22 + ny, 8: 8 + nx, 19] + 0.25)
