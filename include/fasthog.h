@@ -230,6 +230,30 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
                             int w_dtype, float bias, void* scores, hog_stream_t stream);
 
 /*
+ * hog_block_norm -- overlapping blocks of 2 x 2 cells, L2-normalised.
+ *
+ * The paper forms a region's feature from the histograms of four overlapped
+ * sub-areas (Section 3, Fig. 4's caption; the figure is missing).  Read here
+ * as the classic layout: a block is 2 x 2 cells, blocks step by one cell,
+ * and each block's 4 n_bins counts are divided by sqrt(sum of squares +
+ * eps^2).  Block (i, j) of the map holds cells (i + cx r, j + cy r) of the
+ * cell map, r = cell / stride, in quadrant order q = 2 cy + cx:
+ *   blocks[j][i][q * n_bins + b] = cells[j + cy r][i + cx r][b] / norm(i, j)
+ * (0 for a block with no binned pixel and eps = 0).
+ *
+ *   cells, cell_dtype  [ncy][ncx][n_bins] of HOG_I32, HOG_F32 or HOG_BF16
+ *   r                  block step in cell-map positions (cell / stride), >= 1
+ *   eps                >= 0
+ *   blocks             out: float [ncy - r][ncx - r][4 * n_bins]
+ *
+ * Score the block map with hog_window_score as a map with 4 * n_bins values
+ * per entry and a window of 7 x 15 blocks (64 x 128 pixels), with the same
+ * cell and stride: ncx, ncy of that call are ncx - r, ncy - r.
+ */
+hog_status hog_block_norm(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int r, float eps,
+                          float* blocks, hog_stream_t stream);
+
+/*
  * hog_window_score_multi -- several linear filters over the same windows:
  *   scores[f][py][px] = biases[f] + sum_k w[f][k] * feature_k(px, py),
  * each filter exactly as hog_window_score would score it alone.  The paper

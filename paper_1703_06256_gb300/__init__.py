@@ -97,6 +97,7 @@ def _load() -> ctypes.CDLL:
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
         "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
+        "hog_block_norm": (I, [P, I, I, I, I, I, F, P, P]),
         "hog_window_score_multi": (I, [P, I, I, I, I, I, I, I, I, P, I, I, P, P, P]),
         "hog_tune_set": (I, [I, I]),
         "hog_tune_get": (I, [I]),
@@ -127,7 +128,7 @@ _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
-            "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
+            "hog_block_norm", "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
             "hog_server_poll", "hog_server_release", "hog_server_stats")
@@ -220,6 +221,12 @@ def hog_window_score(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, ce
     _check("hog_window_score", _lib.hog_window_score(_ptr(cells), cell_dtype, ncx, ncy, n_bins, cells_x, cells_y,
                                                      cell, stride, _ptr(w), w_dtype, float(bias), _ptr(scores),
                                                      _stream(stream)))
+
+
+def hog_block_norm(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, r: int, eps: float, blocks,
+                   stream=None) -> None:
+    _check("hog_block_norm", _lib.hog_block_norm(_ptr(cells), cell_dtype, ncx, ncy, n_bins, r, float(eps),
+                                                 _ptr(blocks), _stream(stream)))
 
 
 def hog_window_score_multi(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, cells_x: int, cells_y: int,

@@ -229,6 +229,17 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
                                    st);
 }
 
+hog_status hog_block_norm(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int r, float eps,
+                          float* blocks, hog_stream_t stream) {
+    if (cells == nullptr || blocks == nullptr) return HOG_ERR_ARG;
+    if (ncx < 0 || ncy < 0 || n_bins < 1 || n_bins > kMaxBins || r < 1) return HOG_ERR_ARG;
+    if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
+    if (!(eps >= 0.f) || !std::isfinite(eps)) return HOG_ERR_ARG;
+    if ((long)(ncx - r > 0 ? ncx - r : 0) * (ncy - r > 0 ? ncy - r : 0) * 4 * n_bins >= (1L << 31)) return HOG_ERR_ARG;
+    return launch_block_norm(cells, cell_dtype, ncx, ncy, n_bins, r, eps, blocks,
+                             reinterpret_cast<cudaStream_t>(stream));
+}
+
 hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int cells_x,
                                   int cells_y, int cell, int stride, const void* w, int w_dtype, int n_filters,
                                   const float* biases, void* scores, hog_stream_t stream) {

@@ -61,6 +61,8 @@ bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, in
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x,
                            int cells_y, int r, const void* w, int w_dtype, float bias,
                            void* scores, cudaStream_t st);
+hog_status launch_block_norm(const void* cells, int cell_dtype, int ncx, int ncy, int nb, int r, float eps,
+                             float* blocks, cudaStream_t st);
 hog_status launch_score_tc_multi(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int r, const void* w,
                                  int w_dtype, int n_filters, const float* biases, void* scores, cudaStream_t st);
 

@@ -379,6 +379,40 @@ def test_score_multi_filter_f32(fh, g):
         assert np.all(np.abs(got[f] - ref[f]) <= g.score_tolerance(cells, W[f], B[f], stride=4))
 
 
+@pytest.mark.parametrize("nb,stride,eps", [(8, 4, 1.0), (16, 4, 0.0), (8, 8, 0.5), (9, 2, 2.0)])
+def test_block_norm_and_block_score(fh, g, nb, stride, eps):
+    """Overlapping L2-normalised blocks: the block map within 2 ulp-scale of
+    the FP64 oracle for every cell dtype, and the 7 x 15-block window score
+    (hog_window_score on the block map) within the FP32-path bound."""
+    rng = np.random.default_rng(400 + nb + stride)
+    img = rand_img(300, 230, 3, 70 + nb)
+    cells = cells_of(img, nb, stride)
+    ncy, ncx, _ = cells.shape
+    r = 8 // stride
+    ref = oracle.block_norm(cells, r, eps)
+    nby, nbx, k = ref.shape
+    for cd in (fh.HOG_I32, fh.HOG_F32, fh.HOG_BF16):
+        if cd == fh.HOG_BF16:
+            c = torch.from_numpy(cells.astype(np.float32).reshape(-1)).to(torch.bfloat16).cuda()
+        else:
+            c = g.dev(cells.astype(np.int32 if cd == fh.HOG_I32 else np.float32).reshape(-1))
+        out = torch.full((nby * nbx * k + 8,), -3.0, dtype=torch.float32, device="cuda")
+        fh.hog_block_norm(c, cd, ncx, ncy, nb, r, eps, out)
+        got = out.cpu().numpy()
+        assert np.all(got[nby * nbx * k:] == -3.0)
+        got = got[: nby * nbx * k].reshape(nby, nbx, k)
+        assert np.all(np.abs(got - ref) <= 4e-7 * np.maximum(np.abs(ref), 1e-30) + 1e-12), cd
+    w = rng.normal(0, 0.01, 15 * 7 * k).astype(np.float32)
+    bl = torch.from_numpy(got.reshape(-1).copy()).cuda()
+    ny, nx = nby - 14 * r, nbx - 6 * r
+    sc = torch.zeros(max(nx * ny, 1), dtype=torch.float32, device="cuda")
+    fh.hog_window_score(bl, fh.HOG_F32, nbx, nby, k, 7, 15, 8, stride, g.dev(w), fh.HOG_F32, 0.3, sc)
+    S = sc.cpu().numpy()[: nx * ny].reshape(ny, nx)
+    S64 = oracle.block_window_score(ref, w, 0.3, r=r)
+    mass = oracle.block_window_score(np.abs(ref), np.abs(w.astype(np.float64)), 0.3, r=r)
+    assert np.all(np.abs(S - S64) <= 1e-5 * mass + 1e-6)
+
+
 def test_score_bf16_error_against_f32_weights(fh, g):
     """The bf16 path against the FP64 oracle with the original f32 weights:
     the error is the weight rounding (bf16 keeps 8 significant bits, so at
