@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra figure (the main line is unchanged)")
-    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,multi_filter,serving",
+    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,multi_filter,blocks,serving",
                     help="comma-separated extra figures to run (default: all)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
@@ -479,6 +479,50 @@ def multi_filter(torch, fh, wl, flush, args, bf16_peak):
     return out
 
 
+def blocks_variant(torch, fh, wl, flush, args):
+    """Overlapping L2-normalised 2x2-cell blocks on the benchmark image
+    (800x600 RGB, N_b = 8, stride 4, eps = 1): cells from the five-call path,
+    then hog_block_norm and the 7 x 15-block window score (f32 weights, 3360
+    per window).  Times the two block calls as one graph."""
+    c = wl.config1()
+    img = c["images"][0]
+    H, W = img.shape[:2]
+    p = fh.HogPipeline(W, H, 3, 8, 4)
+    p.set_image(img)
+    p.run_eager()
+    torch.cuda.synchronize()
+    r = 2
+    nbx, nby = p.ncx - r, p.ncy - r
+    k = 32
+    blocks = torch.empty(nbx * nby * k, dtype=torch.float32, device="cuda")
+    nx, ny = nbx - 6 * r, nby - 14 * r
+    w = torch.from_numpy(wl.rng_for(14).normal(0, 0.01, 15 * 7 * k).astype(np.float32)).cuda()
+    scores = torch.empty(max(nx * ny, 1), dtype=torch.float32, device="cuda")
+    calls = [lambda: fh.hog_block_norm(p.cells, fh.HOG_F32, p.ncx, p.ncy, 8, r, 1.0, blocks),
+             lambda: fh.hog_window_score(blocks, fh.HOG_F32, nbx, nby, k, 7, 15, 8, 4, w, fh.HOG_F32, 0.0, scores)]
+    for fn in calls:  # load the kernels before the capture
+        fn()
+    torch.cuda.synchronize()
+    step, read, _ = graph_step(torch, calls, between=True)
+    steps = max(args.steps // 4, 10)
+    ms = [0.0, 0.0]
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    for kk in range(steps):
+        flush.fill_(kk)
+        step()
+        torch.cuda.synchronize()
+        st, _ = read()
+        ms = [a + b for a, b in zip(ms, st)]
+    ms = [m / steps for m in ms]
+    return {"workload": "800x600 RGB, N_b=8, stride 4, 2x2-cell blocks at one-cell steps, L2 norm (eps 1), "
+                        "7x15-block window, f32 weights",
+            "block_norm_ms": round(ms[0], 5), "block_score_ms": round(ms[1], 5), "blocks": nbx * nby,
+            "windows": nx * ny, "windows_per_s": round(nx * ny / (sum(ms) * 1e-3), 1)}
+
+
 def main():
     args = parse()
     extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
@@ -635,6 +679,7 @@ def main():
                           else None),
         "multi_filter": (multi_filter(torch, fh, wl, flush, args, bf16_peak()) if "multi_filter" in extras
                          else None),
+        "blocks": blocks_variant(torch, fh, wl, flush, args) if "blocks" in extras else None,
         "serving": (serving(torch, wl, args) if "serving" in extras and world == 1 and args.serve_requests > 0
                     else None),
     }

@@ -4,7 +4,8 @@
 //
 //   S[py][px] = bias + sum_{cy, cx, b} w[(cy*cells_x + cx)*nb + b] * C[py + cy*r][px + cx*r][b]
 //
-// One thread per window; a CTA owns 32 x 8 windows.  It stages the cell-map
+// One thread per window; a CTA owns 32 x TY windows, TY = 8, 4, 2 or 1: the
+// tallest tile whose staged region fits in shared memory.  It stages the cell-map
 // region those windows touch, converted to float, in shared memory as
 // [row][bin/4][column] float4 (consecutive threads read consecutive
 // float4s: no bank conflicts), and the weights as float4s that every thread
@@ -13,8 +14,8 @@
 // int8 weights every product and partial sum is an integer below 2^24, so
 // the float arithmetic is exact and the score is returned as int32.
 //
-// When the staged region would not fit in shared memory (strides well below
-// the cell size), the kernel reads the cells from global memory instead.
+// When even a one-row tile would not fit (strides well below the cell size,
+// very long features), the kernel reads the cells from global memory instead.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -23,7 +24,7 @@ namespace fasthog {
 
 namespace {
 
-constexpr int kTX = 32, kTY = 8;
+constexpr int kTX = 32;
 constexpr int kSmemLimit = 200 * 1024;
 
 struct ScoreGeom {
@@ -32,11 +33,11 @@ struct ScoreGeom {
     size_t cells_bytes, w_bytes;
 };
 
-ScoreGeom geom(int nb, int cells_x, int cells_y, int r) {
+ScoreGeom geom(int nb, int cells_x, int cells_y, int r, int ty) {
     ScoreGeom g;
     g.nb4 = (nb + 3) / 4;
     g.rw = kTX + (cells_x - 1) * r;
-    g.rh = kTY + (cells_y - 1) * r;
+    g.rh = ty + (cells_y - 1) * r;
     g.cells_bytes = (size_t)g.rh * g.nb4 * g.rw * 16;
     g.w_bytes = (size_t)cells_x * cells_y * g.nb4 * 16;
     return g;
@@ -72,29 +73,29 @@ __device__ __forceinline__ float weight_val<int8_t>(const int8_t* w, int k) {
     return (float)__ldg(w + k);
 }
 
-template <typename CellT, typename WT, typename OutT, bool SMEM>
-__global__ void __launch_bounds__(kTX* kTY)
+template <typename CellT, typename WT, typename OutT, bool SMEM, int TY>
+__global__ void __launch_bounds__(kTX* TY)
     score_kernel(const CellT* __restrict__ cells, int ncx, int ncy, int nb, int cells_x, int cells_y, int r,
                  const WT* __restrict__ w, float bias, int nx, int ny, OutT* __restrict__ scores) {
     extern __shared__ __align__(16) float4 smem4[];
     const int nb4 = (nb + 3) / 4;
     const int rw = kTX + (cells_x - 1) * r;
-    const int rh = kTY + (cells_y - 1) * r;
+    const int rh = TY + (cells_y - 1) * r;
     const int K4 = cells_x * cells_y * nb4;
     float4* w_s = smem4;          // [cells_y*cells_x][nb4]
     float4* c_s = smem4 + K4;     // [rh][nb4][rw]
     const int tid = threadIdx.y * kTX + threadIdx.x;
-    const int px0 = blockIdx.x * kTX, py0 = blockIdx.y * kTY;
+    const int px0 = blockIdx.x * kTX, py0 = blockIdx.y * TY;
     pdl_trigger();
     pdl_wait();
 
     // weights, padded per cell to nb4 float4s
-    for (int i = tid; i < K4 * 4; i += kTX * kTY) {
+    for (int i = tid; i < K4 * 4; i += kTX * TY) {
         const int cellk = i / (nb4 * 4), b = i - cellk * nb4 * 4;
         reinterpret_cast<float*>(w_s)[i] = b < nb ? weight_val<WT>(w, cellk * nb + b) : 0.f;
     }
     if (SMEM) {
-        for (int i = tid; i < rh * nb4 * rw * 4; i += kTX * kTY) {
+        for (int i = tid; i < rh * nb4 * rw * 4; i += kTX * TY) {
             // i enumerates [row][b4][col][lane]
             const int lanei = i & 3;
             const int t = i >> 2;
@@ -149,30 +150,41 @@ __global__ void __launch_bounds__(kTX* kTY)
     }
 }
 
+template <typename CellT, typename WT, typename OutT, bool SMEM, int TY>
+hog_status launch_ty(const void* cells, int ncx, int ncy, int nb, int cells_x, int cells_y, int r, const void* w,
+                     float bias, void* scores, int nx, int ny, size_t smem, cudaStream_t st) {
+    auto k = score_kernel<CellT, WT, OutT, SMEM, TY>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    dim3 grid(ceil_div(nx, kTX), ceil_div(ny, TY)), block(kTX, TY);
+    return launch_pdl(k, grid, block, smem, st, static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y, r,
+                      static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
+}
+
 template <typename CellT, typename WT, typename OutT>
 hog_status launch_t(const void* cells, int ncx, int ncy, int nb, int cells_x, int cells_y, int r, const void* w,
                     float bias, void* scores, cudaStream_t st) {
     const int nx = ncx - (cells_x - 1) * r, ny = ncy - (cells_y - 1) * r;
     if (nx <= 0 || ny <= 0) return HOG_OK;
-    const ScoreGeom g = geom(nb, cells_x, cells_y, r);
-    const bool use_smem = g.cells_bytes + g.w_bytes <= (size_t)kSmemLimit;
-    const size_t smem = g.w_bytes + (use_smem ? g.cells_bytes : 0);
-    if (smem > (size_t)kSmemLimit) return HOG_ERR_UNSUPPORTED;
-    dim3 grid(ceil_div(nx, kTX), ceil_div(ny, kTY)), block(kTX, kTY);
-    cudaError_t e;
-    if (use_smem) {
-        auto k = score_kernel<CellT, WT, OutT, true>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e);
-        return launch_pdl(k, grid, block, smem, st, static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y,
-                          r, static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
-    } else {
-        auto k = score_kernel<CellT, WT, OutT, false>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return cuda_fail(e);
-        return launch_pdl(k, grid, block, smem, st, static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y,
-                          r, static_cast<const WT*>(w), bias, nx, ny, static_cast<OutT*>(scores));
+    for (int ty : {8, 4, 2, 1}) {
+        const ScoreGeom g = geom(nb, cells_x, cells_y, r, ty);
+        const size_t smem = g.w_bytes + g.cells_bytes;
+        if (smem > (size_t)kSmemLimit) continue;
+        switch (ty) {
+            case 8: return launch_ty<CellT, WT, OutT, true, 8>(cells, ncx, ncy, nb, cells_x, cells_y, r, w, bias,
+                                                               scores, nx, ny, smem, st);
+            case 4: return launch_ty<CellT, WT, OutT, true, 4>(cells, ncx, ncy, nb, cells_x, cells_y, r, w, bias,
+                                                               scores, nx, ny, smem, st);
+            case 2: return launch_ty<CellT, WT, OutT, true, 2>(cells, ncx, ncy, nb, cells_x, cells_y, r, w, bias,
+                                                               scores, nx, ny, smem, st);
+            default: return launch_ty<CellT, WT, OutT, true, 1>(cells, ncx, ncy, nb, cells_x, cells_y, r, w, bias,
+                                                                scores, nx, ny, smem, st);
+        }
     }
+    const ScoreGeom g = geom(nb, cells_x, cells_y, r, 8);
+    if (g.w_bytes > (size_t)kSmemLimit) return HOG_ERR_UNSUPPORTED;
+    return launch_ty<CellT, WT, OutT, false, 8>(cells, ncx, ncy, nb, cells_x, cells_y, r, w, bias, scores, nx, ny,
+                                                g.w_bytes, st);
 }
 
 template <typename CellT>
