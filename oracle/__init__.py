@@ -74,6 +74,8 @@ def _load():
                 "oracle_detect": (L, [P, I, I, I, D, P, P, P, L]),
                 "oracle_decimate": (I, [P, I, I, I, L, P]),
                 "oracle_block_norm": (I, [P, I, I, I, I, D, P]),
+                "oracle_soft_lut": (I, [I, I, P, P]),
+                "oracle_soft_votes": (I, [P, I, I, I, L, I, I, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(lib, name)
@@ -227,6 +229,42 @@ def detect(S: np.ndarray, stride: int, thr: float):
     n = _load().oracle_detect(_ptr(S), nx, ny, int(stride), float(thr), _ptr(xs), _ptr(ys),
                               _ptr(sc), cap)
     return xs[:n].copy(), ys[:n].copy(), sc[:n].copy()
+
+
+SOFT_Q = 64  # vote units per pixel
+
+
+def soft_lut(nb: int, q: int = SOFT_Q):
+    """Soft-vote table [511][511] uint16 (k0 | a << 8, 0xFFFF at (0, 0)) and
+    the smallest distance of q * alpha from a rounding tie over the table."""
+    out = np.empty(511 * 511, np.uint16)
+    m = ctypes.c_double(0.0)
+    _check(_load().oracle_soft_lut(nb, q, _ptr(out), ctypes.addressof(m)), "soft_lut")
+    return out.reshape(511, 511), m.value
+
+
+def soft_votes(img: np.ndarray, nb: int, q: int = SOFT_Q) -> np.ndarray:
+    """Per-pixel two-bin votes [H][W][nb] int32 (q units per voting pixel)."""
+    img = np.ascontiguousarray(img, dtype=np.uint8)
+    H, W = img.shape[:2]
+    ch = 1 if img.ndim == 2 else img.shape[2]
+    out = np.empty((H, W, nb), np.int32)
+    _check(_load().oracle_soft_votes(_ptr(img), W, H, ch, W * ch, nb, q, _ptr(out)), "soft_votes")
+    return out
+
+
+def soft_cells(img: np.ndarray, nb: int, cell: int = 8, stride: int = 8, q: int = SOFT_Q) -> np.ndarray:
+    """Soft-vote cell histograms [ncy][ncx][nb] by direct summation of each
+    cell's pixel votes."""
+    v = soft_votes(img, nb, q)
+    H, W = v.shape[:2]
+    ncx = 0 if W < cell else (W - cell) // stride + 1
+    ncy = 0 if H < cell else (H - cell) // stride + 1
+    out = np.zeros((ncy, ncx, nb), np.int64)
+    for j in range(ncy):
+        for i in range(ncx):
+            out[j, i] = v[j * stride: j * stride + cell, i * stride: i * stride + cell].sum(axis=(0, 1))
+    return out
 
 
 def block_norm(cells: np.ndarray, r: int, eps: float) -> np.ndarray:

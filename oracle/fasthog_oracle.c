@@ -313,6 +313,90 @@ long oracle_detect(const double* S, int nx, int ny, int stride, double thr, int3
     return n;
 }
 
+/* Soft votes: the two-bin vote of Section 2 (OpenCV's way, which the paper
+ * sets aside for single-bin unit votes).  The gradient angle phi in [0, 2 pi)
+ * is placed among the bin centres c_k = (k + 1/2) 2 pi / nb:
+ *   t = phi nb / (2 pi) - 1/2,  k0 = floor(t) mod nb,  alpha = t - floor(t),
+ * and the pixel (unit magnitude) votes q - a to bin k0 and a to bin k0 + 1
+ * (mod nb), a = round(q alpha) to nearest.  a = q is written as (k0 + 1, 0),
+ * so that an angle on a bin centre has one encoding.  The distance of
+ * q alpha from the nearest half-integer is recorded (oracle_soft_lut returns
+ * its minimum): a rounding tie would make the vote depend on the last bit
+ * of atan2, and the tables' lattice points keep far from one.
+ * Operation order is fixed (FP contraction off): ((phi * nb) / 2pi) - 1/2. */
+static const double ORACLE_TWO_PI = 6.283185307179586; /* 2 pi rounded to double */
+
+static int soft_vote(int dx, int dy, int nb, int q, int* k0_out, double* margin) {
+    double phi = atan2((double)dy, (double)dx);
+    if (phi < 0.0) phi += ORACLE_TWO_PI;
+    double t = phi * (double)nb / ORACLE_TWO_PI - 0.5;
+    double fl = floor(t);
+    double x = (double)q * (t - fl);
+    double m = fabs(x - floor(x) - 0.5);
+    if (margin && m < *margin) *margin = m;
+    int a = (int)floor(x + 0.5);
+    int k0 = (int)fl % nb;
+    if (k0 < 0) k0 += nb;
+    if (a >= q) {
+        a = 0;
+        k0 = (k0 + 1) % nb;
+    }
+    *k0_out = k0;
+    return a;
+}
+
+/* The soft table: entry (dy + 255) * 511 + (dx + 255) = k0 | a << 8, or
+ * 0xFFFF for (0, 0).  *margin receives the smallest distance of q alpha from
+ * a half-integer over the table. */
+int oracle_soft_lut(int nb, int q, uint16_t* lut, double* margin) {
+    if (nb < 1 || nb > 64 || q < 2 || q > 255) return -1;
+    double m = 1.0;
+    for (int dy = -ORACLE_DMAX; dy <= ORACLE_DMAX; ++dy)
+        for (int dx = -ORACLE_DMAX; dx <= ORACLE_DMAX; ++dx) {
+            long idx = (long)(dy + ORACLE_DMAX) * (2 * ORACLE_DMAX + 1) + (dx + ORACLE_DMAX);
+            if (dx == 0 && dy == 0) {
+                lut[idx] = 0xFFFF;
+                continue;
+            }
+            int k0;
+            int a = soft_vote(dx, dy, nb, q, &k0, &m);
+            lut[idx] = (uint16_t)(k0 | (a << 8));
+        }
+    if (margin) *margin = m;
+    return 0;
+}
+
+/* Per-pixel soft votes [H][W][nb]: Eq. 1 gradients with the strongest
+ * channel (as oracle_bin_map), then the two-bin vote; border pixels and
+ * (0, 0) gradients vote nothing. */
+int oracle_soft_votes(const uint8_t* img, int W, int H, int channels, long pitch, int nb, int q, int32_t* votes) {
+    if (channels != 1 && channels != 3) return -1;
+    if (nb < 1 || nb > 64 || q < 2 || q > 255) return -1;
+    memset(votes, 0, sizeof(int32_t) * (size_t)W * H * nb);
+    for (int y = 1; y < H - 1; ++y)
+        for (int x = 1; x < W - 1; ++x) {
+            int best_dx = 0, best_dy = 0;
+            long best_mag = -1;
+            for (int c = 0; c < channels; ++c) {
+                int dx = img[y * pitch + (long)channels * (x + 1) + c] - img[y * pitch + (long)channels * (x - 1) + c];
+                int dy = img[(y + 1) * pitch + (long)channels * x + c] - img[(y - 1) * pitch + (long)channels * x + c];
+                long mag = (long)dx * dx + (long)dy * dy;
+                if (mag > best_mag) { /* strict: ties keep the lower channel */
+                    best_mag = mag;
+                    best_dx = dx;
+                    best_dy = dy;
+                }
+            }
+            if (best_dx == 0 && best_dy == 0) continue;
+            int k0;
+            int a = soft_vote(best_dx, best_dy, nb, q, &k0, NULL);
+            int32_t* v = votes + ((long)y * W + x) * nb;
+            v[k0] += q - a;
+            v[(k0 + 1) % nb] += a;
+        }
+    return 0;
+}
+
 /* Overlapping blocks (the "four overlapped sub areas" of a region, Section
  * 3, Fig. 4's caption), read as blocks of 2 x 2 cells with a stride of one
  * cell: block (i, j) of the cell map (positions at the scan stride, r = cell
