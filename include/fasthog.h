@@ -230,6 +230,33 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
                             int w_dtype, float bias, void* scores, hog_stream_t stream);
 
 /*
+ * Soft votes -- the two-bin vote that Section 2 mentions (OpenCV spreads each
+ * pixel over two bins) and the paper sets aside for single-bin unit votes.
+ * Each pixel with a gradient (unit magnitude) splits HOG_SOFT_Q vote units
+ * between the two bins whose centres c_k = (k + 1/2) 2 pi / N_b flank its
+ * angle phi, linearly in angle: with t = phi N_b / (2 pi) - 1/2,
+ * k0 = floor(t) mod N_b and alpha = t - floor(t), bin k0 gets q - a and bin
+ * k0 + 1 (mod N_b) gets a = round(q alpha).  Integral images and Eq. 6 still
+ * apply: they sum vote units instead of counts, exactly.
+ *
+ * hog_build_soft_lut -- the soft table: 511 rows (dy + 255) of HOG_LUT_PITCH
+ *   uint16 entries (dx + 255), entry = k0 | a << 8 (an angle on a bin centre
+ *   is (k, 0)), 0xFFFF at (0, 0) and in the pad column.  FP64, fixed
+ *   operation order; n_bins 1..64; lut 4-byte aligned, HOG_SOFT_LUT_BYTES.
+ * hog_cell_hist_soft -- the cell histograms of the soft votes straight from
+ *   the image, in one kernel (as hog_cell_hist_fused): cells[j][i][b] = the
+ *   vote units of bin b from the cell's pixels.  n_bins 2..16, stride 4 or 8,
+ *   cell = r * stride with r <= 4; cell_dtype HOG_I32 or HOG_F32 (a cell
+ *   holds up to cell^2 * HOG_SOFT_Q units).
+ */
+#define HOG_SOFT_Q 64
+#define HOG_SOFT_LUT_BYTES (HOG_LUT_SIDE * HOG_LUT_PITCH * 2)
+hog_status hog_build_soft_lut(int n_bins, uint16_t* lut, hog_stream_t stream);
+hog_status hog_cell_hist_soft(const uint8_t* img, int W, int H, int channels, size_t pitch_bytes,
+                              const uint16_t* soft_lut, int n_bins, int cell, int stride, int cell_dtype,
+                              void* cells, hog_stream_t stream);
+
+/*
  * hog_block_norm -- overlapping blocks of 2 x 2 cells, L2-normalised.
  *
  * The paper forms a region's feature from the histograms of four overlapped

@@ -28,6 +28,8 @@ HOG_LUT_PITCH = 512
 HOG_LUT_QUAD_OFFSET = HOG_LUT_SIDE * HOG_LUT_PITCH
 HOG_LUT_BYTES = HOG_LUT_QUAD_OFFSET + 256 * 256
 HOG_STATUS_TIMEOUT = 1
+HOG_SOFT_Q = 64
+HOG_SOFT_LUT_BYTES = HOG_LUT_SIDE * HOG_LUT_PITCH * 2
 (HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_FUSED_CTAS_PER_SM,
  HOG_TUNE_SCORE_TC_ROWS) = range(4)
 
@@ -97,6 +99,8 @@ def _load() -> ctypes.CDLL:
         "hog_detect": (I, [P, I, I, I, I, F, I, I, P, I, P, P, Z, P]),
         "hog_detect_noalloc": (I, [P, I, I, I, I, F, I, I, P, I, P, P]),
         "hog_cell_hist_fused": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
+        "hog_build_soft_lut": (I, [I, P, P]),
+        "hog_cell_hist_soft": (I, [P, I, I, I, Z, P, I, I, I, I, P, P]),
         "hog_block_norm": (I, [P, I, I, I, I, I, F, P, P]),
         "hog_window_score_multi": (I, [P, I, I, I, I, I, I, I, I, P, I, I, P, P, P]),
         "hog_tune_set": (I, [I, I]),
@@ -128,7 +132,7 @@ _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
-            "hog_block_norm", "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
+            "hog_build_soft_lut", "hog_cell_hist_soft", "hog_block_norm", "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
             "hog_server_poll", "hog_server_release", "hog_server_stats")
@@ -221,6 +225,17 @@ def hog_window_score(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, ce
     _check("hog_window_score", _lib.hog_window_score(_ptr(cells), cell_dtype, ncx, ncy, n_bins, cells_x, cells_y,
                                                      cell, stride, _ptr(w), w_dtype, float(bias), _ptr(scores),
                                                      _stream(stream)))
+
+
+def hog_build_soft_lut(n_bins: int, lut, stream=None) -> None:
+    _check("hog_build_soft_lut", _lib.hog_build_soft_lut(n_bins, _ptr(lut), _stream(stream)))
+
+
+def hog_cell_hist_soft(img, W: int, H: int, channels: int, pitch_bytes: int, soft_lut, n_bins: int, cell: int,
+                       stride: int, cell_dtype: int, cells, stream=None) -> None:
+    _check("hog_cell_hist_soft", _lib.hog_cell_hist_soft(_ptr(img), W, H, channels, pitch_bytes, _ptr(soft_lut),
+                                                         n_bins, cell, stride, cell_dtype, _ptr(cells),
+                                                         _stream(stream)))
 
 
 def hog_block_norm(cells, cell_dtype: int, ncx: int, ncy: int, n_bins: int, r: int, eps: float, blocks,

@@ -229,6 +229,27 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
                                    st);
 }
 
+hog_status hog_build_soft_lut(int n_bins, uint16_t* lut, hog_stream_t stream) {
+    if (lut == nullptr || reinterpret_cast<uintptr_t>(lut) % 4 != 0) return HOG_ERR_ARG;
+    if (n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
+    return launch_build_soft_lut(n_bins, lut, reinterpret_cast<cudaStream_t>(stream));
+}
+
+hog_status hog_cell_hist_soft(const uint8_t* img, int W, int H, int channels, size_t pitch_bytes,
+                              const uint16_t* soft_lut, int n_bins, int cell, int stride, int cell_dtype,
+                              void* cells, hog_stream_t stream) {
+    if (img == nullptr || soft_lut == nullptr || cells == nullptr) return HOG_ERR_ARG;
+    if (!size_ok(W, H) || (channels != 1 && channels != 3)) return HOG_ERR_ARG;
+    if (pitch_bytes < (size_t)W * channels || n_bins < 1 || n_bins > kMaxBins) return HOG_ERR_ARG;
+    if (cell < 1 || cell > 64 || stride < 1 || stride > cell) return HOG_ERR_ARG;
+    if (cell_dtype != HOG_I32 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(cells) % 4 != 0 || reinterpret_cast<uintptr_t>(soft_lut) % 4 != 0)
+        return HOG_ERR_ARG;
+    if (!cells_soft_supported(n_bins, cell, stride)) return HOG_ERR_UNSUPPORTED;
+    return launch_cells_soft(img, W, H, channels, pitch_bytes, soft_lut, n_bins, cell, stride, cell_dtype, cells,
+                             reinterpret_cast<cudaStream_t>(stream));
+}
+
 hog_status hog_block_norm(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins, int r, float eps,
                           float* blocks, hog_stream_t stream) {
     if (cells == nullptr || blocks == nullptr) return HOG_ERR_ARG;

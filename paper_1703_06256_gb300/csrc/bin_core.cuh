@@ -1,6 +1,7 @@
-// bin_core.cuh -- per-pixel orientation bins of a quad of 4 pixels (paper
-// Section 2, Eq. 1 and the table lookup), shared by the bin-map kernel and
-// the fused image-to-cells kernel.  See bin_map.cu for the method.
+// bin_core.cuh -- per-pixel gradients and orientation bins of a quad of 4
+// pixels (paper Section 2, Eq. 1 and the table lookup), shared by the
+// bin-map kernel, the fused image-to-cells kernel and the soft-vote kernel.
+// See bin_map.cu for the method.
 #pragma once
 
 #include "internal.cuh"
@@ -63,9 +64,32 @@ __device__ __forceinline__ void load_quad(const uint8_t* __restrict__ img, size_
     }
 }
 
+// Eq. 1 for pixel p (a compile-time constant after unrolling) of the quad in
+// q: central differences, and for RGB the channel with the largest
+// dx^2 + dy^2 (ties keep the lower channel).  Channel c of pixel x + p:
+// right neighbour at byte 4 + (p+1)*CH + c of wc, left at 4 + (p-1)*CH + c,
+// below / above at byte p*CH + c of wd / wu.
+template <int CH>
+__device__ __forceinline__ void quad_gradient(const QuadWords<CH>& q, int p, int& dx, int& dy) {
+    dx = byte_of(q.wc, 4 + (p + 1) * CH) - byte_of(q.wc, 4 + (p - 1) * CH);
+    dy = byte_of(q.wd, p * CH) - byte_of(q.wu, p * CH);
+    if (CH == 3) {
+        int best = dx * dx + dy * dy;
+#pragma unroll
+        for (int c = 1; c < 3; ++c) {
+            const int ddx = byte_of(q.wc, 4 + (p + 1) * CH + c) - byte_of(q.wc, 4 + (p - 1) * CH + c);
+            const int ddy = byte_of(q.wd, p * CH + c) - byte_of(q.wu, p * CH + c);
+            const int m = ddx * ddx + ddy * ddy;
+            if (m > best) {  // strict: ties keep the lower channel
+                best = m;
+                dx = ddx;
+                dy = ddy;
+            }
+        }
+    }
+}
+
 // Eq. 1 and the table lookup for the 4 pixels of quad x (row loaded in q).
-// Channel c of pixel x + p: right neighbour at byte 4 + (p+1)*CH + c of wc,
-// left at 4 + (p-1)*CH + c, below / above at byte p*CH + c of wd / wu.
 template <int CH, bool QUAD>
 __device__ __forceinline__ uint32_t bins_of_quad(const QuadWords<CH>& q, int x, int W, const uint8_t* __restrict__ lutq,
                                                  const uint8_t* __restrict__ lut, int nb, int nb4) {
@@ -75,22 +99,8 @@ __device__ __forceinline__ uint32_t bins_of_quad(const QuadWords<CH>& q, int x, 
         uint32_t bin = kNoBin;
         const int xp = x + p;
         if (xp > 0 && xp < W - 1) {
-            int dx = byte_of(q.wc, 4 + (p + 1) * CH) - byte_of(q.wc, 4 + (p - 1) * CH);
-            int dy = byte_of(q.wd, p * CH) - byte_of(q.wu, p * CH);
-            if (CH == 3) {
-                int best = dx * dx + dy * dy;
-#pragma unroll
-                for (int c = 1; c < 3; ++c) {
-                    const int ddx = byte_of(q.wc, 4 + (p + 1) * CH + c) - byte_of(q.wc, 4 + (p - 1) * CH + c);
-                    const int ddy = byte_of(q.wd, p * CH + c) - byte_of(q.wu, p * CH + c);
-                    const int m = ddx * ddx + ddy * ddy;
-                    if (m > best) {  // strict: ties keep the lower channel
-                        best = m;
-                        dx = ddx;
-                        dy = ddy;
-                    }
-                }
-            }
+            int dx, dy;
+            quad_gradient<CH>(q, p, dx, dy);
             if (dx != 0 || dy != 0) {
                 if (QUAD) {
                     int qd, u, v;  // quadrant and quadrant-0 coordinates

@@ -61,6 +61,10 @@ bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, in
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x,
                            int cells_y, int r, const void* w, int w_dtype, float bias,
                            void* scores, cudaStream_t st);
+bool cells_soft_supported(int n_bins, int cell, int stride);
+hog_status launch_build_soft_lut(int n_bins, uint16_t* lut, cudaStream_t st);
+hog_status launch_cells_soft(const uint8_t* img, int W, int H, int channels, size_t pitch, const uint16_t* lut,
+                             int n_bins, int cell, int stride, int cell_dtype, void* cells, cudaStream_t st);
 hog_status launch_block_norm(const void* cells, int cell_dtype, int ncx, int ncy, int nb, int r, float eps,
                              float* blocks, cudaStream_t st);
 hog_status launch_score_tc_multi(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int r, const void* w,

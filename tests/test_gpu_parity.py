@@ -413,6 +413,46 @@ def test_block_norm_and_block_score(fh, g, nb, stride, eps):
     assert np.all(np.abs(S - S64) <= 1e-5 * mass + 1e-6)
 
 
+# ---------------------------------------------------------------- soft votes
+@pytest.mark.parametrize("nb", [4, 8, 9, 16, 64])
+def test_soft_lut_exhaustive(fh, g, nb):
+    buf = torch.empty(fh.HOG_SOFT_LUT_BYTES // 2, dtype=torch.int16, device="cuda")
+    fh.hog_build_soft_lut(nb, buf)
+    tab = buf.cpu().numpy().view(np.uint16).reshape(511, 512)
+    ref, margin = oracle.soft_lut(nb)
+    assert margin > 1e-9
+    assert np.all(tab[:, 511] == 0xFFFF)
+    assert np.array_equal(tab[:, :511], ref)
+
+
+@pytest.mark.parametrize("ch", [1, 3])
+@pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (8, 8, 8), (16, 8, 4), (9, 16, 4), (8, 32, 8)])
+def test_cells_soft(fh, g, ch, nb, cell, stride):
+    """Soft-vote cells from the image in one kernel equal the oracle's direct
+    sums of per-pixel votes, on images spanning several tiles with ragged
+    edges; the window score over them is within the FP32 bound."""
+    buf = torch.empty(fh.HOG_SOFT_LUT_BYTES // 2, dtype=torch.int16, device="cuda")
+    fh.hog_build_soft_lut(nb, buf)
+    for i, (H, W) in enumerate([(77, 300), (240, 330), (131, 517)]):
+        img = rand_img(H, W, ch, 3000 + 10 * nb + i)
+        ref = oracle.soft_cells(img, nb, cell, stride)
+        ncy, ncx = ref.shape[:2]
+        d = g.dev(img.reshape(-1))
+        for cd in (fh.HOG_I32, fh.HOG_F32):
+            out = torch.full((max(ncx * ncy * nb, 1) + 4,), -1, dtype=fh.TORCH_DTYPE[cd], device="cuda")
+            fh.hog_cell_hist_soft(d, W, H, ch, W * ch, buf, nb, cell, stride, cd, out)
+            host = out.cpu().numpy()
+            assert np.all(host[ncx * ncy * nb:] == -1)
+            got = host[: ncx * ncy * nb].astype(np.int64).reshape(ncy, ncx, nb)
+            assert np.array_equal(got, ref), (H, W, cd)
+    if cell == 8 and stride == 4:
+        rng = np.random.default_rng(nb)
+        w = rng.normal(0, 0.001, 128 * nb).astype(np.float32)
+        S64 = oracle.window_score(ref, w, 0.1, stride=4)
+        S = g.gpu_scores(ref, w, fh.HOG_F32, 0.1, stride=4, cell_dtype=fh.HOG_F32)
+        assert np.all(np.abs(S - S64) <= g.score_tolerance(ref, w, 0.1, stride=4))
+
+
 def test_score_bf16_error_against_f32_weights(fh, g):
     """The bf16 path against the FP64 oracle with the original f32 weights:
     the error is the weight rounding (bf16 keeps 8 significant bits, so at
