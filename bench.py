@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra figure (the main line is unchanged)")
-    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,multi_filter,blocks,serving",
+    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,multi_filter,blocks,soft,serving",
                     help="comma-separated extra figures to run (default: all)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
@@ -479,6 +479,29 @@ def multi_filter(torch, fh, wl, flush, args, bf16_peak):
     return out
 
 
+def soft_variant(torch, fh, wl, flush, args):
+    """Two-bin soft votes on the benchmark image (800x600 RGB, N_b = 8,
+    stride 4): hog_cell_hist_soft (one kernel from the image) and the window
+    score over its f32 cells (f32 weights), as one graph."""
+    c = wl.config1()
+    img = c["images"][0]
+    H, W = img.shape[:2]
+    p = fh.HogPipeline(W, H, 3, 8, 4)
+    p.set_weights(c["w"], 0.0, c["thr"])
+    p.set_image(img)
+    lut = torch.empty(fh.HOG_SOFT_LUT_BYTES // 2, dtype=torch.int16, device="cuda")
+    fh.hog_build_soft_lut(8, lut)
+    calls = [lambda: fh.hog_cell_hist_soft(p.img, W, H, 3, W * 3, lut, 8, 8, 4, fh.HOG_F32, p.cells),
+             p.stage_score]
+    for fn in calls:
+        fn()
+    torch.cuda.synchronize()
+    step, read, _ = graph_step(torch, calls, between=False)
+    ms = time_steps(torch, step, read, flush, max(args.steps // 4, 10), args.warmup)
+    return {"workload": "800x600 RGB, N_b=8, stride 4, soft votes (64 units per pixel), f32 weights",
+            "ms_per_step": round(ms, 5), "mpixel_per_s": round(W * H / (ms * 1e-3) / 1e6, 1)}
+
+
 def blocks_variant(torch, fh, wl, flush, args):
     """Overlapping L2-normalised 2x2-cell blocks on the benchmark image
     (800x600 RGB, N_b = 8, stride 4, eps = 1): cells from the five-call path,
@@ -680,6 +703,7 @@ def main():
         "multi_filter": (multi_filter(torch, fh, wl, flush, args, bf16_peak()) if "multi_filter" in extras
                          else None),
         "blocks": blocks_variant(torch, fh, wl, flush, args) if "blocks" in extras else None,
+        "soft": soft_variant(torch, fh, wl, flush, args) if "soft" in extras else None,
         "serving": (serving(torch, wl, args) if "serving" in extras and world == 1 and args.serve_requests > 0
                     else None),
     }

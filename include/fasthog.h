@@ -360,6 +360,13 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
  *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 16 or 32
+ *   HOG_TUNE_TABLE                where the bin-map and fused-cells kernels read
+ *                                 the gradient table: 1 = a quadrant staged in
+ *                                 shared memory (N_b a multiple of 4), 2 = the
+ *                                 whole table through the read-only cache; the
+ *                                 library's choice is 1 for the bin map and 2
+ *                                 for the fused kernel (measured on natural-image
+ *                                 gradients, which cluster in the table)
  *
  * hog_tune_set returns HOG_ERR_ARG for an unknown knob or a value outside its
  * range (nothing changes); hog_tune_get returns the current value (0 = the
@@ -370,7 +377,8 @@ typedef enum {
     HOG_TUNE_BINMAP_CTAS_PER_SM = 1,
     HOG_TUNE_FUSED_CTAS_PER_SM = 2,
     HOG_TUNE_SCORE_TC_ROWS = 3,
-    HOG_TUNE_KNOBS = 4
+    HOG_TUNE_TABLE = 4,
+    HOG_TUNE_KNOBS = 5
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

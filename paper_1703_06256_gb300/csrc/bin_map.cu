@@ -137,7 +137,8 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
 
 hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t pitch, const uint8_t* lut,
                           int n_bins, uint8_t* bins, unsigned int* status, cudaStream_t st) {
-    const bool quad = (n_bins % 4 == 0);
+    // the shared-memory quadrant needs 4 | N_b; it is the default here
+    const bool quad = (n_bins % 4 == 0) && tune_get(HOG_TUNE_TABLE) != 2;
     if (channels == 1)
         return quad ? launch_t<1, true>(img, W, H, pitch, lut, n_bins, bins, status, st)
                     : launch_t<1, false>(img, W, H, pitch, lut, n_bins, bins, status, st);

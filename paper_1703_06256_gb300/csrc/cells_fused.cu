@@ -101,7 +101,7 @@ __device__ __forceinline__ bool stage_lut(uint8_t* lutq, const uint8_t* __restri
 
 // One tile of cell origins [bx0, bx0 + BX) x [by0, by0 + BY) of one image:
 // steps 1-3 above.  Called by every thread of the CTA.
-template <int CH, int NB, int S, typename OutT>
+template <int CH, int NB, int S, typename OutT, bool QUAD>
 __device__ __forceinline__ void fused_tile(FusedSmem<NB, S>& sm, const uint8_t* lutq, const uint8_t* __restrict__ lut,
                                            const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                                            int r, int ncx, int ncy, OutT* __restrict__ cells, int out_align, int bx0,
@@ -125,7 +125,7 @@ __device__ __forceinline__ void fused_tile(FusedSmem<NB, S>& sm, const uint8_t* 
         if (y <= 0 || y >= H - 1 || x >= W) continue;  // border rows, or outside the image: no bins
         QuadWords<CH> q;
         load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
-        const uint32_t packed = bins_of_quad<CH, true>(q, x, W, lutq, lut, NB, NB / 4);
+        const uint32_t packed = bins_of_quad<CH, QUAD>(q, x, W, lutq, lut, NB, NB / 4);
         uint32_t h[F::NW8];
 #pragma unroll
         for (int k = 0; k < F::NW8; ++k) h[k] = 0;
@@ -222,32 +222,48 @@ __host__ __device__ inline int cells_alignment(const void* cells) {
     return c % 16 == 0 ? 16 : (c % 4 == 0 ? 4 : 2);
 }
 
-template <int CH, int NB, int S, typename OutT>
+// The table: QUAD = true stages its quadrant in shared memory (one bulk
+// copy per CTA, quarter-turn lookups); QUAD = false reads the whole table
+// through the read-only cache and leaves the shared memory to the tile.
+template <bool QUAD, int NB, int S>
+__device__ __forceinline__ FusedSmem<NB, S>* fused_prologue(uint8_t* smem, const uint8_t* lut, uint64_t* bar,
+                                                            unsigned int* status) {
+    if constexpr (QUAD) {
+        if (!stage_lut(smem, lut, bar, status)) return nullptr;
+        return reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
+    } else {
+        pdl_trigger();
+        pdl_wait();
+        return reinterpret_cast<FusedSmem<NB, S>*>(smem);
+    }
+}
+
+template <int CH, int NB, int S, typename OutT, bool QUAD>
 __global__ void __launch_bounds__(kThreads, 2)
     cells_fused_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                        const uint8_t* __restrict__ lut, int r, int ncx, int ncy, OutT* __restrict__ cells,
                        int out_align, unsigned int* status) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t lut_bar;
-    auto& sm = *reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
-    if (!stage_lut(smem, lut, &lut_bar, status)) return;
+    FusedSmem<NB, S>* sm = fused_prologue<QUAD, NB, S>(smem, lut, &lut_bar, status);
+    if (sm == nullptr) return;
     constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
     const int tiles_x = (ncx + BX - 1) / BX, tiles_y = (ncy + BY - 1) / BY;
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x)
-        fused_tile<CH, NB, S, OutT>(sm, smem, lut, img, W, H, pitch, aligned, r, ncx, ncy, cells, out_align,
-                                    (t % tiles_x) * BX, (t / tiles_x) * BY);
+        fused_tile<CH, NB, S, OutT, QUAD>(*sm, smem, lut, img, W, H, pitch, aligned, r, ncx, ncy, cells, out_align,
+                                          (t % tiles_x) * BX, (t / tiles_x) * BY);
 }
 
 // The same over every item of a batch plan: the persistent CTAs walk the
 // batch's tiles, item by item.
-template <int CH, int NB, int S, typename OutT>
+template <int CH, int NB, int S, typename OutT, bool QUAD>
 __global__ void __launch_bounds__(kThreads, 2)
     cells_fused_batch_kernel(const PlanItem* __restrict__ items, int n_items, int total_tiles,
                              const uint8_t* __restrict__ lut, int r, unsigned int* status) {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t lut_bar;
-    auto& sm = *reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
-    if (!stage_lut(smem, lut, &lut_bar, status)) return;
+    FusedSmem<NB, S>* sm = fused_prologue<QUAD, NB, S>(smem, lut, &lut_bar, status);
+    if (sm == nullptr) return;
     constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
     for (int t = blockIdx.x; t < total_tiles; t += gridDim.x) {
         const PlanItem* it = items + find_item<Stage::kCells>(items, n_items, t);
@@ -256,17 +272,21 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint8_t* img = item.img;
         OutT* cells = static_cast<OutT*>(item.cells);
         const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (item.pitch % 4 == 0);
-        fused_tile<CH, NB, S, OutT>(sm, smem, lut, img, item.W, item.H, item.pitch, aligned, r, it->ncx, it->ncy,
-                                    cells, cells_alignment(cells),
-                                    (local % tx) * BX, (local / tx) * BY);
+        fused_tile<CH, NB, S, OutT, QUAD>(*sm, smem, lut, img, item.W, item.H, item.pitch, aligned, r, it->ncx,
+                                          it->ncy, cells, cells_alignment(cells), (local % tx) * BX,
+                                          (local / tx) * BY);
     }
 }
 
-template <int CH, int NB, int S, typename OutT>
-hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
+// Table placement for a launch: the tuned choice, else the whole table
+// through the read-only cache.
+inline bool use_quad_table() { return tune_get(HOG_TUNE_TABLE) == 1; }
+
+template <int CH, int NB, int S, typename OutT, bool QUAD>
+hog_status launch_q(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
                     void* cells, unsigned int* status, cudaStream_t st) {
-    const size_t smem = kQuadBytes + sizeof(FusedSmem<NB, S>);
-    auto kern = cells_fused_kernel<CH, NB, S, OutT>;
+    const size_t smem = (QUAD ? kQuadBytes : 0) + sizeof(FusedSmem<NB, S>);
+    auto kern = cells_fused_kernel<CH, NB, S, OutT, QUAD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
@@ -278,6 +298,14 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     const int out_align = cells_alignment(cells);
     return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, img, W, H, pitch, aligned, lut, r, ncx, ncy,
                       static_cast<OutT*>(cells), out_align, status);
+}
+
+template <int CH, int NB, int S, typename OutT>
+hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
+                    void* cells, unsigned int* status, cudaStream_t st) {
+    if (use_quad_table())
+        return launch_q<CH, NB, S, OutT, true>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    return launch_q<CH, NB, S, OutT, false>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
 }
 
 template <int CH, int NB, int S>
@@ -331,11 +359,11 @@ int cells_fused_tiles(int ncx, int ncy, int stride) {
 
 namespace {
 
-template <int CH, int NB, int S, typename OutT>
-hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, unsigned int* status,
+template <int CH, int NB, int S, typename OutT, bool QUAD>
+hog_status launch_batch_q(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, unsigned int* status,
                           cudaStream_t st) {
-    const size_t smem = kQuadBytes + sizeof(FusedSmem<NB, S>);
-    auto kern = cells_fused_batch_kernel<CH, NB, S, OutT>;
+    const size_t smem = (QUAD ? kQuadBytes : 0) + sizeof(FusedSmem<NB, S>);
+    auto kern = cells_fused_batch_kernel<CH, NB, S, OutT, QUAD>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     const int per_sm = tune_get(HOG_TUNE_FUSED_CTAS_PER_SM);
@@ -343,6 +371,13 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const uint8
     const int grid = h.cells_tiles < cap ? h.cells_tiles : cap;
     return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, plan_items(plan_dev), h.n_items, h.cells_tiles,
                       lut, h.r, status);
+}
+
+template <int CH, int NB, int S, typename OutT>
+hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, unsigned int* status,
+                          cudaStream_t st) {
+    if (use_quad_table()) return launch_batch_q<CH, NB, S, OutT, true>(h, plan_dev, lut, status, st);
+    return launch_batch_q<CH, NB, S, OutT, false>(h, plan_dev, lut, status, st);
 }
 
 template <int CH, int NB, int S>

@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import collections
 import ctypes
+import gc
 import time
 from dataclasses import dataclass, field
 
@@ -136,15 +137,21 @@ class HogServer:
         """Replay `requests` at their arrival times (seconds from now),
         admitting each as soon as it has arrived and fits; returns the
         results in completion order."""
-        t0 = time.perf_counter()
-        clock = lambda: time.perf_counter() - t0  # noqa: E731
         queue = collections.deque(sorted(requests, key=lambda r: r.arrival))
         results: list[Result] = []
-        while queue or self._inflight:
-            now = clock()
-            while queue and queue[0].arrival <= now and self.try_submit(queue[0], now):
-                queue.popleft()
-            results += self.poll(clock, keep)
+        gc_was_on = gc.isenabled()
+        gc.disable()  # a collection pause would land in some request's latency
+        try:
+            t0 = time.perf_counter()
+            clock = lambda: time.perf_counter() - t0  # noqa: E731
+            while queue or self._inflight:
+                now = clock()
+                while queue and queue[0].arrival <= now and self.try_submit(queue[0], now):
+                    queue.popleft()
+                results += self.poll(clock, keep)
+        finally:
+            if gc_was_on:
+                gc.enable()
         return results
 
     def run_one(self, image, rid: int = 0) -> Result:

@@ -62,6 +62,21 @@ def test_bin_map_random(fh, g, nb, ch):
         assert np.array_equal(g.gpu_bins(img, nb), oracle.bin_map(img, nb)), (H, W)
 
 
+@pytest.mark.parametrize("table", [1, 2])
+@pytest.mark.parametrize("nb", [8, 16, 4])
+@pytest.mark.parametrize("ch", [1, 3])
+def test_bin_map_table_placements(fh, g, nb, ch, table):
+    """The bin map with the table quadrant staged in shared memory (1) and
+    with the whole table read through the cache (2) equals the oracle's."""
+    fh.hog_tune_set(fh.HOG_TUNE_TABLE, table)
+    try:
+        for i, (H, W) in enumerate(SHAPES):
+            img = rand_img(H, W, ch, 700 * nb + 10 * ch + i)
+            assert np.array_equal(g.gpu_bins(img, nb), oracle.bin_map(img, nb)), (H, W)
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_TABLE, 0)
+
+
 @pytest.mark.parametrize("ch", [1, 3])
 def test_bin_map_pitch_and_alignment(fh, g, ch):
     img = rand_img(45, 203, ch, 5)
@@ -471,11 +486,14 @@ def test_score_bf16_error_against_f32_weights(fh, g):
 
 
 # ---------------------------------------------------------------- fused image -> cells
+@pytest.mark.parametrize("table", [1, 2])
 @pytest.mark.parametrize("ch", [1, 3])
 @pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (8, 8, 8), (16, 8, 4), (8, 16, 4), (8, 16, 8)])
-def test_cells_fused(fh, g, ch, nb, cell, stride):
+def test_cells_fused(fh, g, ch, nb, cell, stride, table):
     """hog_cell_hist_fused equals the oracle's Eq. 6 cell map of the oracle's
-    bins, bit for bit, on images spanning several tiles with ragged edges."""
+    bins, bit for bit, on images spanning several tiles with ragged edges,
+    with the table staged in shared memory (1) or read through the cache (2)."""
+    fh.hog_tune_set(fh.HOG_TUNE_TABLE, table)
     for i, (H, W) in enumerate([(77, 300), (240, 320), (131, 517), (16, 16)]):
         img = rand_img(H, W, ch, 1000 + 10 * nb + i)
         ref = oracle.cell_hist_ii(oracle.integral(oracle.bin_map(img, nb), nb), nb, cell, stride)
@@ -487,6 +505,7 @@ def test_cells_fused(fh, g, ch, nb, cell, stride):
             fh.hog_cell_hist_fused(d, W, H, ch, W * ch, lut, nb, cell, stride, cd, out)
             got = out.float().cpu().numpy()[: ncx * ncy * nb].reshape(ncy, ncx, nb)
             assert np.array_equal(got, ref), (H, W, cd)
+    fh.hog_tune_set(fh.HOG_TUNE_TABLE, 0)
 
 
 @pytest.mark.parametrize("cell,stride", [(16, 4), (32, 8)])
