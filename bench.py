@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra figure (the main line is unchanged)")
-    ap.add_argument("--extras", default="fused,batch_1080p,batch_pyramid,multi_filter,blocks,soft,serving",
+    ap.add_argument("--extras",
+                    default="fused,stages_4k,batch_1080p,batch_pyramid,multi_filter,blocks,soft,serving",
                     help="comma-separated extra figures to run (default: all)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
@@ -324,13 +325,12 @@ def serving(torch, wl, args):
     rng = wl.rng_for(5)
     w = wl.weights_f32(8, rng)
     stream = wl.request_stream(n_req, rate_per_s=1.0)
-    base = wl.rgb_smooth_shapes(3840, 2160, rng, n_shapes=12)
+    base = base_4k(wl)
     pool = []
     for k in range(min(128, n_req)):
         Wk, Hk = stream[k]["W"], stream[k]["H"]
         y, x = int(rng.integers(0, 2160 - Hk + 1)), int(rng.integers(0, 3840 - Wk + 1))
         pool.append(torch.from_numpy(np.ascontiguousarray(base[y:y + Hk, x:x + Wk])).pin_memory())
-    del base
     kw = dict(n_bins=8, stride=4, thr=0.5, w_dtype=fh.HOG_BF16, budget_bytes=8 << 30, fused=True)
     served = HogServer(w, n_streams=16, **kw)
     plain = HogServer(w, n_streams=1, **kw)
@@ -474,6 +474,59 @@ def multi_filter(torch, fh, wl, flush, args, bf16_peak):
         out[f"filters_{F}"] = {"ms": round(ms, 5), "filter_windows_per_s": round(windows * F / (ms * 1e-3), 1),
                                "tflops": round(tflops, 2),
                                "frac_of_bf16_peak": round(tflops / bf16_peak, 4) if bf16_peak else None}
+    del p
+    torch.cuda.empty_cache()
+    return out
+
+
+_BASE_4K = None
+
+
+def base_4k(wl):
+    """One generated 3840x2160 RGB image, shared by the figures that crop from it."""
+    global _BASE_4K
+    if _BASE_4K is None:
+        _BASE_4K = wl.rgb_smooth_shapes(3840, 2160, wl.rng_for(5))
+    return _BASE_4K
+
+
+def stage_rooflines(torch, fh, wl, flush, args, hbm):
+    """The five-call step on one 3840x2160 RGB image (the size at which the
+    memory-bound stages leave L2): each stage's algorithmic bytes over its
+    mean time (events between the stages inside one graph), against the
+    measured HBM peak.  N_b = 8, stride 4, int32 integral images and cells."""
+    W, H = 3840, 2160
+    p = fh.HogPipeline(W, H, 3, 8, 4)
+    p.set_weights(wl.weights_f32(8, wl.rng_for(1)), 0.0, 0.5)
+    p.set_image(base_4k(wl))
+    fns = [p.stage_bin_map, p.stage_integral, p.stage_cell_hist, p.stage_score, p.stage_detect]
+    names = ["bin_map", "integral", "cell_hist", "score", "detect"]
+    p.run_eager()
+    torch.cuda.synchronize()
+    step, read, _ = graph_step(torch, fns, between=True)
+    steps = max(args.steps // 10, 10)
+    for _ in range(max(args.warmup, 3)):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+    ms = [0.0] * 5
+    for k in range(steps):
+        flush.fill_(k)
+        step()
+        torch.cuda.synchronize()
+        st, _ = read()
+        ms = [a + b for a, b in zip(ms, st)]
+    ms = [m / steps for m in ms]
+    px, nb = W * H, 8
+    windows = p.nx * p.ny
+    alg = {"bin_map": px * (3 + 1), "integral": px * (1 + 4 * nb),
+           "cell_hist": p.ncx * p.ncy * nb * (4 * 4 + 4), "score": p.ncx * p.ncy * nb * 4 + windows * 4,
+           "detect": windows * 4}
+    out = {"workload": "3840x2160 RGB, N_b=8, stride 4, int32 integral images, int32 cells, f32 weights",
+           "peak_gbs": hbm}
+    for n, t in zip(names, ms):
+        gbs = alg[n] / (t * 1e-3) / 1e9
+        out[n] = {"ms": round(t, 5), "algorithmic_bytes": alg[n], "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)}
     del p
     torch.cuda.empty_cache()
     return out
@@ -697,6 +750,7 @@ def main():
         "clocks": clocks,
         "device_status": status,
         "fused": fused,
+        "stages_4k": stage_rooflines(torch, fh, wl, flush, args, hbm) if "stages_4k" in extras else None,
         "batch_1080p": batch_1080p(torch, fh, wl, replicas, flush, args, world) if "batch_1080p" in extras else None,
         "batch_pyramid": (batch_pyramid(torch, fh, wl, replicas, flush, args, world) if "batch_pyramid" in extras
                           else None),

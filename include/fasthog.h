@@ -360,6 +360,10 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
  *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 16 or 32
+ *   HOG_TUNE_CELL_ROWS            cell rows per CTA of the cell-histogram kernel
+ *                                 that stages the integral-image samples in
+ *                                 shared memory: 4, 8 or 16; 1 = one thread per
+ *                                 cell reading its corners directly
  *   HOG_TUNE_TABLE                where the bin-map and fused-cells kernels read
  *                                 the gradient table: 1 = a quadrant staged in
  *                                 shared memory (N_b a multiple of 4), 2 = the
@@ -378,7 +382,8 @@ typedef enum {
     HOG_TUNE_FUSED_CTAS_PER_SM = 2,
     HOG_TUNE_SCORE_TC_ROWS = 3,
     HOG_TUNE_TABLE = 4,
-    HOG_TUNE_KNOBS = 5
+    HOG_TUNE_CELL_ROWS = 5,
+    HOG_TUNE_KNOBS = 6
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

@@ -1,7 +1,8 @@
 """Autotuner for the library's launch-shape knobs (``hog_tune_*`` in
 include/fasthog.h): the integral-image scan's band height (rows per tile),
 the bin-map and fused-cells grid caps, where those two kernels read the
-gradient table, and the tensor-core score's rows per CTA.  None of them changes a result; they change only how the work is cut.
+gradient table, the cell-histogram kernel's tile height (or its per-cell
+form), and the tensor-core score's rows per CTA.  None of them changes a result; they change only how the work is cut.
 
 The tuner times each candidate on the caller's own workload through the
 library's calls -- the per-image path captured as a CUDA graph, CUDA events
@@ -18,7 +19,7 @@ import json
 import os
 import statistics
 
-from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
+from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_CELL_ROWS, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
                HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_SCORE_TC_ROWS, hog_tune_get, hog_tune_set)
 
 # knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
@@ -28,10 +29,11 @@ KNOBS = {
     "fused_ctas_per_sm": (HOG_TUNE_FUSED_CTAS_PER_SM, (0, 1)),
     "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
+    "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
 }
 # the knobs each path's launches read
 PATH_KNOBS = {
-    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "score_tc_rows", "table"),
+    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_tc_rows", "table"),
     "fused": ("fused_ctas_per_sm", "score_tc_rows", "table"),
 }
 

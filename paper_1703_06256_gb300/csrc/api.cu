@@ -82,6 +82,7 @@ hog_status hog_tune_set(int knob, int value) {
         case HOG_TUNE_FUSED_CTAS_PER_SM: ok = ok || value == 1 || value == 2; break;
         case HOG_TUNE_SCORE_TC_ROWS: ok = ok || value == 16 || value == 32; break;
         case HOG_TUNE_TABLE: ok = ok || value == 1 || value == 2; break;
+        case HOG_TUNE_CELL_ROWS: ok = ok || value == 1 || value == 4 || value == 8 || value == 16; break;
         default: return HOG_ERR_ARG;
     }
     if (!ok) return HOG_ERR_ARG;

@@ -11,6 +11,10 @@
 //
 // With uint16 integral images the four-term sum is taken modulo 2^16, which
 // is exact because a cell holds fewer than 65536 pixels.
+//
+// For cells made of whole strides (cell = r * stride) and 8 or 16 bins a
+// streaming variant (below) reads only the grid of integral-image samples
+// Eq. 6 uses, through shared memory.
 #include <type_traits>
 
 #include "internal.cuh"
@@ -75,9 +79,110 @@ __global__ void __launch_bounds__(128)
     }
 }
 
+// Streaming variant for cell = r * stride.  Eq. 6 only reads the integral
+// image on a grid: with S[k][m] = ii(s m - 1, s k - 1) (0 for k = 0 or
+// m = 0), cell (i, j) = S[j+r][i+r] - S[j][i+r] - S[j+r][i] + S[j][i].  A CTA
+// owns TJ x kTI cells, loads its (TJ + r) x (kTI + r) samples of every bin
+// into shared memory (many independent loads in flight; the sample rows of
+// neighbouring tiles overlap by r), then forms and writes its cells in
+// output order.  Shared rows are padded to NB + 1 words per sample so that
+// the loads (consecutive samples of a row) do not collide in banks.
+constexpr int kTI = 64;
+constexpr int kStreamThreads = 256;
+
+template <typename InT, typename OutT, int NB>
+__global__ void __launch_bounds__(kStreamThreads)
+    cell_hist_stream_kernel(const InT* __restrict__ ii, int W, int H, int s, int r, int ncx, int ncy, int TJ,
+                            OutT* __restrict__ cells) {
+    extern __shared__ uint32_t S[];  // [TJ + r][kTI + r][NB + 1]
+    pdl_trigger();
+    pdl_wait();
+    const int i0 = blockIdx.x * kTI, j0 = blockIdx.y * TJ;
+    const int rows = TJ + r, cols = kTI + r;
+    const int kmax = ncy - 1 + r, mmax = ncx - 1 + r;  // last sample rows / columns any cell reads
+    const size_t plane = (size_t)W * H;
+    // one warp per (sample row, bin) line, lanes over the line's samples
+    // (cols <= kTI + 8 < 3 * 32); a warp issues the loads of kLines lines
+    // before it stores any of them, so their latencies overlap
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kWarps = kStreamThreads / 32, kLines = 8, kPerLane = 3;
+    for (int l0 = warp * kLines; l0 < rows * NB; l0 += kWarps * kLines) {
+        uint32_t v[kLines][kPerLane];
+#pragma unroll
+        for (int q = 0; q < kLines; ++q) {
+            const int line = l0 + q;
+            const int kk = line / NB, b = line - kk * NB;
+            const int k = j0 + kk;
+            const bool row_ok = line < rows * NB && k > 0 && k <= kmax;
+            const InT* src = ii + b * plane + (size_t)(s * k - 1) * W - 1;  // sample m at src + s * m
+#pragma unroll
+            for (int t = 0; t < kPerLane; ++t) {
+                const int mm = lane + 32 * t, m = i0 + mm;
+                v[q][t] = (row_ok && mm < cols && m > 0 && m <= mmax) ? (uint32_t)__ldg(src + (size_t)s * m) : 0u;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kLines; ++q) {
+            const int line = l0 + q;
+            if (line >= rows * NB) break;
+            const int kk = line / NB, b = line - kk * NB;
+            uint32_t* dst = S + (size_t)kk * cols * (NB + 1) + b;
+#pragma unroll
+            for (int t = 0; t < kPerLane; ++t) {
+                const int mm = lane + 32 * t;
+                if (mm < cols) dst[mm * (NB + 1)] = v[q][t];
+            }
+        }
+    }
+    __syncthreads();
+    const int outs = TJ * kTI * NB;
+    for (int e = threadIdx.x; e < outs; e += kStreamThreads) {
+        const int b = e % NB, rest = e / NB;
+        const int ci = rest % kTI, cj = rest / kTI;
+        const int i = i0 + ci, j = j0 + cj;
+        if (i >= ncx || j >= ncy) continue;
+        const uint32_t a = S[((cj + r) * cols + ci + r) * (NB + 1) + b];
+        const uint32_t d = S[(cj * cols + ci) * (NB + 1) + b];
+        const uint32_t bb = S[(cj * cols + ci + r) * (NB + 1) + b];
+        const uint32_t c = S[((cj + r) * cols + ci) * (NB + 1) + b];
+        uint32_t v = (a + d) - (bb + c);
+        if (sizeof(InT) == 2) v &= 0xFFFFu;
+        cells[((size_t)j * ncx + i) * NB + b] = count_as<OutT>(v);
+    }
+}
+
+// Rows of cells per streaming CTA: the tuned value (1 = the per-cell kernel),
+// else 8 when that still gives every SM two CTAs, else 4 (measured best of
+// 4, 8 and 16 from 800x600 to 3840x2160).
+int stream_rows(int ncx, int ncy) {
+    const int tuned = tune_get(HOG_TUNE_CELL_ROWS);
+    if (tuned > 0) return tuned;
+    const long tx = (ncx + kTI - 1) / kTI;
+    return tx * ((ncy + 7) / 8) >= 2L * sm_count() ? 8 : 4;
+}
+
+template <typename InT, typename OutT, int NB>
+hog_status launch_stream(const void* ii, int W, int H, int stride, int r, int ncx, int ncy, int TJ, void* cells,
+                         cudaStream_t st) {
+    const size_t smem = sizeof(uint32_t) * (size_t)(TJ + r) * (kTI + r) * (NB + 1);
+    auto kern = cell_hist_stream_kernel<InT, OutT, NB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    dim3 grid(ceil_div(ncx, kTI), ceil_div(ncy, TJ));
+    return launch_pdl(kern, grid, dim3(kStreamThreads), smem, st, static_cast<const InT*>(ii), W, H, stride, r, ncx,
+                      ncy, TJ, static_cast<OutT*>(cells));
+}
+
 template <typename InT, typename OutT>
 hog_status launch_t(const void* ii, int W, int H, int nb, int cell, int stride, int ncx, int ncy, void* cells,
                     cudaStream_t st) {
+    if ((nb == 8 || nb == 16) && cell % stride == 0 && cell / stride <= 8) {
+        const int TJ = stream_rows(ncx, ncy);
+        const int r = cell / stride;
+        if (TJ > 1)
+            return nb == 8 ? launch_stream<InT, OutT, 8>(ii, W, H, stride, r, ncx, ncy, TJ, cells, st)
+                           : launch_stream<InT, OutT, 16>(ii, W, H, stride, r, ncx, ncy, TJ, cells, st);
+    }
     dim3 grid(ceil_div(ncx, 128), ncy);
     const InT* src = static_cast<const InT*>(ii);
     OutT* dst = static_cast<OutT*>(cells);

@@ -146,6 +146,25 @@ def test_cell_hist(fh, g, stride, cell_dtype):
         assert np.array_equal(g.gpu_cells(ii, 8, 8, stride, cell_dtype=cd), ref), (H, W)
 
 
+@pytest.mark.parametrize("rows", [1, 4, 8, 16])
+@pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (16, 8, 4), (8, 16, 8), (8, 8, 2), (16, 32, 4)])
+def test_cell_hist_launch_shapes(fh, g, rows, nb, cell, stride):
+    """Every cell-histogram launch shape (HOG_TUNE_CELL_ROWS: 1 = per-cell
+    corner reads, 4/8/16 = staged sample grid) gives the oracle's cells from
+    int32 and uint16 integral images, on maps spanning several tiles."""
+    fh.hog_tune_set(fh.HOG_TUNE_CELL_ROWS, rows)
+    try:
+        for i, (H, W) in enumerate([(150, 700), (301, 233)]):
+            bins = oracle_bins(H, W, nb, 50 * nb + rows + i)
+            ii = oracle.integral(bins, nb)
+            ref = oracle.cell_hist_ii(ii, nb, cell, stride)
+            assert np.array_equal(g.gpu_cells(ii, nb, cell, stride), ref), (H, W)
+            got16 = g.gpu_cells((ii & 0xFFFF).astype(np.uint16), nb, cell, stride, ii_dtype=fh.HOG_U16)
+            assert np.array_equal(got16, ref), (H, W)
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_CELL_ROWS, 0)
+
+
 def test_cell_hist_from_uint16(fh, g):
     bins = oracle_bins(600, 800, 8, 99, p_none=0.02)
     ii = oracle.integral(bins, 8)
