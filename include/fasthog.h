@@ -219,10 +219,12 @@ hog_status hog_cell_hist_fused(const uint8_t* img, int W, int H, int channels, s
  *                      HOG_BF16 -> bf16 x bf16 -> f32, scores f32
  *                      HOG_I8   -> exact; scores int32 (the bias is rounded to
  *                                  the nearest integer)
- *                      BF16 and I8 weights run on the tensor cores (tcgen05)
- *                      for 16-byte-aligned HOG_BF16 cells, n_bins 8 or 16, an
- *                      8 x 16-cell window and r = 1, 2 or 4; otherwise on CUDA
- *                      cores with the same results
+ *                      All three run on the tensor cores (tcgen05) for
+ *                      16-byte-aligned HOG_BF16 cells, n_bins 8 or 16, an
+ *                      8 x 16-cell window and r = 1, 2 or 4 (f32 weights as
+ *                      three exact bf16 parts accumulated in f32, so the
+ *                      products are the f32 products); otherwise on CUDA
+ *                      cores with the same accuracy
  *   scores             out: [ny][nx], f32 (F32/BF16 weights) or int32 (I8)
  */
 hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy, int n_bins,
@@ -348,9 +350,12 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
 
 /*
  * Launch-shape knobs, read by the launches made after they are set (a CUDA
- * graph keeps the shapes it was captured with).  None of them changes any
- * result: they pick tile shapes, schedules and grid sizes only.  0 restores
- * the library's own choice.  Process-wide; set them from one thread while no
+ * graph keeps the shapes it was captured with).  They pick tile shapes,
+ * schedules, grid sizes and engines only: integer results (bins, integral
+ * images, cells, int8 scores, lists from integer scores) never change;
+ * HOG_TUNE_SCORE_PATH changes the order of the f32 additions of float scores
+ * (both engines stay within the FP32 bound of hog_window_score), every other
+ * knob leaves float scores bit-identical.  0 restores the library's choice.  Process-wide; set them from one thread while no
  * other thread is launching.  The paper has no counterpart: they exist for
  * the autotuner (paper_1703_06256_gb300/autotune.py).
  *
@@ -364,6 +369,12 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 that stages the integral-image samples in
  *                                 shared memory: 4, 8 or 16; 1 = one thread per
  *                                 cell reading its corners directly
+ *   HOG_TUNE_SCORE_PATH           the single-image score's engine where both apply:
+ *                                 1 = CUDA cores, 2 = tensor cores; the
+ *                                 library's choice is the tensor cores for bf16
+ *                                 and int8 weights, and for f32 weights (three
+ *                                 MMAs per step) only when the tensor-core grid
+ *                                 alone gives every SM a CTA
  *   HOG_TUNE_TABLE                where the bin-map and fused-cells kernels read
  *                                 the gradient table: 1 = a quadrant staged in
  *                                 shared memory (N_b a multiple of 4), 2 = the
@@ -383,7 +394,8 @@ typedef enum {
     HOG_TUNE_SCORE_TC_ROWS = 3,
     HOG_TUNE_TABLE = 4,
     HOG_TUNE_CELL_ROWS = 5,
-    HOG_TUNE_KNOBS = 6
+    HOG_TUNE_SCORE_PATH = 6,
+    HOG_TUNE_KNOBS = 7
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

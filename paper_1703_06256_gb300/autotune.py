@@ -2,7 +2,8 @@
 include/fasthog.h): the integral-image scan's band height (rows per tile),
 the bin-map and fused-cells grid caps, where those two kernels read the
 gradient table, the cell-histogram kernel's tile height (or its per-cell
-form), and the tensor-core score's rows per CTA.  None of them changes a result; they change only how the work is cut.
+form), the score's engine (CUDA or tensor cores) and the tensor-core score's
+rows per CTA.  None of them changes a result; they change only how the work is cut.
 
 The tuner times each candidate on the caller's own workload through the
 library's calls -- the per-image path captured as a CUDA graph, CUDA events
@@ -20,7 +21,7 @@ import os
 import statistics
 
 from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_CELL_ROWS, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
-               HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_SCORE_TC_ROWS, hog_tune_get, hog_tune_set)
+               HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_SCORE_PATH, HOG_TUNE_SCORE_TC_ROWS, hog_tune_get, hog_tune_set)
 
 # knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
 KNOBS = {
@@ -30,11 +31,12 @@ KNOBS = {
     "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
+    "score_path": (HOG_TUNE_SCORE_PATH, (0, 1, 2)),
 }
 # the knobs each path's launches read
 PATH_KNOBS = {
-    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_tc_rows", "table"),
-    "fused": ("fused_ctas_per_sm", "score_tc_rows", "table"),
+    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_path", "score_tc_rows", "table"),
+    "fused": ("fused_ctas_per_sm", "score_path", "score_tc_rows", "table"),
 }
 
 

@@ -83,6 +83,7 @@ hog_status hog_tune_set(int knob, int value) {
         case HOG_TUNE_SCORE_TC_ROWS: ok = ok || value == 16 || value == 32; break;
         case HOG_TUNE_TABLE: ok = ok || value == 1 || value == 2; break;
         case HOG_TUNE_CELL_ROWS: ok = ok || value == 1 || value == 4 || value == 8 || value == 16; break;
+        case HOG_TUNE_SCORE_PATH: ok = ok || value == 1 || value == 2; break;
         default: return HOG_ERR_ARG;
     }
     if (!ok) return HOG_ERR_ARG;
@@ -222,10 +223,17 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
     const int r = cell / stride;
     const float b = w_dtype == HOG_I8 ? (float)std::llround((double)bias) : bias;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (w_dtype != HOG_F32 && score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx))
+    const bool tc = score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx);
+    const bool slide = score_slide_supported(cells, n_bins, cells_x, cells_y, r);
+    const int path = tune_get(HOG_TUNE_SCORE_PATH);
+    // automatic: bf16 and int8 weights on the tensor cores; f32 weights (three MMAs per step) there only
+    // when the map alone fills the GPU, else on the CUDA cores
+    const bool auto_tc = w_dtype != HOG_F32 || !slide || score_tc_fills_gpu(ncx, ncy, n_bins, r);
+    const bool use_tc = tc && (path == 2 || (path == 0 && auto_tc));
+    if (use_tc)
         return launch_score_tc(static_cast<const uint16_t*>(cells), ncx, ncy, n_bins, cells_x, cells_y, r, w,
                                w_dtype, b, scores, st);
-    if (score_slide_supported(cells, n_bins, cells_x, cells_y, r))
+    if (slide)
         return launch_score_slide(cells, cell_dtype, ncx, ncy, r, w, w_dtype, b, scores, st);
     return launch_score_cuda_cores(cells, cell_dtype, ncx, ncy, n_bins, cells_x, cells_y, r, w, w_dtype, b, scores,
                                    st);
@@ -279,7 +287,7 @@ hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, in
     const long nx = (long)ncx - (long)(cells_x - 1) * r, ny = (long)ncy - (long)(cells_y - 1) * r;
     if (nx <= 0 || ny <= 0) return HOG_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    if (w_dtype != HOG_F32 && score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx) &&
+    if (score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx) &&
         reinterpret_cast<uintptr_t>(cells) % 16 == 0)
         return launch_score_tc_multi(static_cast<const uint16_t*>(cells), ncx, ncy, n_bins, r, w, w_dtype, n_filters,
                                      biases, scores, st);

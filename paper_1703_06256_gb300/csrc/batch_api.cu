@@ -125,7 +125,7 @@ hog_status hog_window_score_batch(const void* plan, const void* plan_dev, int ce
     if (w_dtype != HOG_F32 && w_dtype != HOG_BF16 && w_dtype != HOG_I8) return HOG_ERR_ARG;
     if (!std::isfinite(bias)) return HOG_ERR_ARG;
     const PlanItem* items = plan_items(plan);
-    bool tc = w_dtype != HOG_F32 && score_tc_supported(cell_dtype, h->n_bins, h->cells_x, h->cells_y, h->r, 0);
+    bool tc = score_tc_supported(cell_dtype, h->n_bins, h->cells_x, h->cells_y, h->r, 0);
     for (int i = 0; i < h->n_items && tc; ++i)
         if (items[i].nx > 0 && reinterpret_cast<uintptr_t>(items[i].it.cells) % 16 != 0) tc = false;
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -58,6 +58,8 @@ bool score_slide_supported(const void* cells, int n_bins, int cells_x, int cells
 hog_status launch_score_slide(const void* cells, int cell_dtype, int ncx, int ncy, int r, const void* w,
                               int w_dtype, float bias, void* scores, cudaStream_t st);
 bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx);
+// Whether the tensor-core score's grid gives every SM a CTA for this map.
+bool score_tc_fills_gpu(int ncx, int ncy, int n_bins, int r);
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x,
                            int cells_y, int r, const void* w, int w_dtype, float bias,
                            void* scores, cudaStream_t st);

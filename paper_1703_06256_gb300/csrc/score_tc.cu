@@ -50,6 +50,8 @@
 // an integer of magnitude <= 127 * 8192 (a window has 8192 pixels, each in
 // at most one bin) < 2^24, so the fp32 accumulation is exact in any order
 // and the int32 scores are bit-exact.
+#include <cuda_bf16.h>
+
 #include <cmath>
 #include <type_traits>
 
@@ -97,15 +99,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_load16(uint32_t taddr, uint32_t (&v)[16]) {
+// 16 consecutive TMEM columns of this warp's 32 lanes; the registers are
+// valid after tmem_wait_ld().
+__device__ __forceinline__ void tmem_load16_async(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
         "%15}, [%16];"
         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Weights off .. off + 7 (off a multiple of 8) as 8 bf16 values.
 template <typename WT>
@@ -142,7 +146,47 @@ __device__ __forceinline__ uint4 load_weight8<int8_t>(const int8_t* w, int off) 
     return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
+// f32 weights: x = p0 + p1 + p2 exactly, each part the bf16 rounding of what
+// the previous parts leave (every residual is exact in f32: it keeps the low
+// bits of x, and 3 x 8 significand bits cover f32's 24).  Counts are exact
+// in bf16 and a count times a bf16 part is exact in f32, so three MMAs per
+// step into one accumulator give the f32 products; only the f32
+// accumulation rounds.
+__device__ __forceinline__ uint32_t bf16_part(float x, int part) {
+    __nv_bfloat16 b = __float2bfloat16_rn(x);
+    for (int k = 0; k < part; ++k) {
+        x = x - __bfloat162float(b);
+        b = __float2bfloat16_rn(x);
+    }
+    return (uint32_t)__bfloat16_as_ushort(b);
+}
+
+// Part `part` of weights off .. off + 7 as 8 bf16 values (bf16 and int8
+// weights have one part).
+template <typename WT>
+__device__ __forceinline__ uint4 load_weight8_part(const WT* w, int off, int part) {
+    (void)part;
+    return load_weight8<WT>(w, off);
+}
+template <>
+__device__ __forceinline__ uint4 load_weight8_part<float>(const float* w, int off, int part) {
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        h[k] = bf16_part(__ldg(w + off + 2 * k), part) | (bf16_part(__ldg(w + off + 2 * k + 1), part) << 16);
+    return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
+template <typename WT>
+__host__ __device__ constexpr int weight_parts() {
+    return std::is_same<WT, float>::value ? 3 : 1;
+}
+
 constexpr int kMaxFilters = 32;  // filters per launch (a group; the API splits larger sets)
+// Independent accumulators: the MMAs of K step ks (cells 2ks, 2ks+1) go to
+// accumulator ks, so consecutive MMAs never wait on each other's result;
+// the epilogue adds the four in a fixed order.
+constexpr int kAcc = 4;
 constexpr size_t kMaxSmem = 227 * 1024;
 
 // Per-filter biases, passed by value (captured with the launch).
@@ -154,6 +198,7 @@ struct TcGeom {
     int r, Tc, rows;      // residue count, output rows per CTA (one class), cell rows per CTA
     int halves;           // N_b / 8: 16-byte halves of a cell (1 or 2)
     int filters;          // filters scored by one CTA
+    int parts;            // bf16 parts per weight (3 for f32 weights, else 1)
     int wpc;              // windows per CTA: 128 / halves
     int row_cells;        // cells staged per cell row: wpc + (kCX - 1) r
     int row_bytes;        // row_cells * 16 * halves
@@ -162,8 +207,8 @@ struct TcGeom {
     int plane_bytes;      // plane_rows * 16
     int band_bytes;       // filters * kCX * halves planes
     int cols;             // TMEM columns allocated (power of two >= 32)
-    __host__ __device__ TcGeom(int r_, int Tc_, int halves_, int filters_ = 1)
-        : r(r_), Tc(Tc_), halves(halves_), filters(filters_) {
+    __host__ __device__ TcGeom(int r_, int Tc_, int halves_, int filters_ = 1, int parts_ = 1)
+        : r(r_), Tc(Tc_), halves(halves_), filters(filters_), parts(parts_) {
         rows = Tc + kCY - 1;
         wpc = kM / halves;
         row_cells = wpc + (kCX - 1) * r;
@@ -171,14 +216,29 @@ struct TcGeom {
         stage_bytes = kRowsPerStage * row_bytes;
         plane_rows = 2 * Tc + 16;
         plane_bytes = plane_rows * 16;
-        band_bytes = filters * kCX * halves * plane_bytes;
+        band_bytes = filters * parts * kCX * halves * plane_bytes;
         cols = 32;
-        while (cols < filters * halves * Tc) cols *= 2;
+        while (cols < kAcc * filters * halves * Tc) cols *= 2;
     }
     __host__ __device__ size_t smem_bytes() const {
         return 1024 + (size_t)band_bytes + (size_t)kStages * stage_bytes + 256;
     }
 };
+
+// Columns c0 .. c0 + 15 of filter f, half h: the sum of the kAcc accumulators
+// ((d0 + d1) + (d2 + d3)), as f32 bit patterns.
+__device__ __forceinline__ void acc_sum(uint32_t lane_base, int f, int h, int n_filters, int halves, int Tc, int c0,
+                                        uint32_t (&v)[16]) {
+    uint32_t d[kAcc][16];
+#pragma unroll
+    for (int a = 0; a < kAcc; ++a)
+        tmem_load16_async(lane_base + (uint32_t)(((a * n_filters + f) * halves + h) * Tc + c0), d[a]);
+    tmem_wait_ld();
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        v[c] = __float_as_uint((__uint_as_float(d[0][c]) + __uint_as_float(d[1][c])) +
+                               (__uint_as_float(d[2][c]) + __uint_as_float(d[3][c])));
+}
 
 // BATCH = false: one image, CTA (blockIdx.x, .y, .z) = (window column, row
 // band, residue class).  BATCH = true: the CTAs of every item of a batch
@@ -192,7 +252,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const PlanItem* __restrict__ items, int n_items, unsigned int* status) {
     extern __shared__ uint8_t smem_raw[];
     constexpr int HALVES = NB / 8, CB = NB * 2;  // 16-byte halves per cell, bytes per cell
-    const TcGeom G(r, Tc, HALVES, n_filters);
+    constexpr int PARTS = weight_parts<WT>();
+    const TcGeom G(r, Tc, HALVES, n_filters, PARTS);
     // 1024-byte aligned working area: band planes, A stages, barriers
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* band = base;
@@ -231,14 +292,18 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int j = tid / kCX, i = tid % kCX;
         for (int f = 0; f < n_filters; ++f) {
 #pragma unroll
-            for (int h = 0; h < HALVES; ++h) {
-                const uint4 v = load_weight8<WT>(w, f * (kCX * kCY * NB) + (j * kCX + i) * NB + 8 * h);
-                *reinterpret_cast<uint4*>(band + (size_t)((f * kCX + i) * HALVES + h) * G.plane_bytes +
-                                          (size_t)(Tc + 14 - j) * 16) = v;
+            for (int part = 0; part < PARTS; ++part) {
+#pragma unroll
+                for (int h = 0; h < HALVES; ++h) {
+                    const uint4 v =
+                        load_weight8_part<WT>(w, f * (kCX * kCY * NB) + (j * kCX + i) * NB + 8 * h, part);
+                    const int plane = ((f * PARTS + part) * kCX + i) * HALVES + h;
+                    *reinterpret_cast<uint4*>(band + (size_t)plane * G.plane_bytes + (size_t)(Tc + 14 - j) * 16) = v;
+                }
             }
         }
         const int zero_rows = G.plane_rows - kCY;  // v < Tc - 1 or v > Tc + 14
-        for (int e = tid; e < n_filters * kCX * HALVES * zero_rows; e += kThreads) {
+        for (int e = tid; e < n_filters * PARTS * kCX * HALVES * zero_rows; e += kThreads) {
             const int pi = e / zero_rows, zr = e % zero_rows;
             const int vrow = zr < Tc - 1 ? zr : zr + kCY;
             *reinterpret_cast<uint4*>(band + (size_t)pi * G.plane_bytes + (size_t)vrow * 16) = make_uint4(0, 0, 0, 0);
@@ -325,12 +390,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * r * CB), (uint32_t)(r * CB), 128);
                     for (int f = 0; f < n_filters; ++f) {
 #pragma unroll
-                        for (int h = 0; h < HALVES; ++h) {
-                            const int plane = ((f * kCX + 2 * ks) * HALVES + h);
-                            const uint64_t bd = smem_desc(b_row + (uint32_t)(plane * G.plane_bytes),
-                                                          (uint32_t)(HALVES * G.plane_bytes), 128);
-                            mma_bf16(tmem + (uint32_t)((f * HALVES + h) * Tc), ad, bd, idesc,
-                                     (rho == 0 && ks == 0) ? 0u : 1u);
+                        for (int part = 0; part < PARTS; ++part) {
+#pragma unroll
+                            for (int h = 0; h < HALVES; ++h) {
+                                const int plane = ((f * PARTS + part) * kCX + 2 * ks) * HALVES + h;
+                                const uint64_t bd = smem_desc(b_row + (uint32_t)(plane * G.plane_bytes),
+                                                              (uint32_t)(HALVES * G.plane_bytes), 128);
+                                const int acc = (ks * n_filters + f) * HALVES + h;  // accumulator ks
+                                mma_bf16(tmem + (uint32_t)(acc * Tc), ad, bd, idesc,
+                                         (rho == 0 && part == 0) ? 0u : 1u);
+                            }
                         }
                     }
                 }
@@ -355,13 +424,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int f = 0; f < n_filters; ++f) {
             const float bias_f = n_filters == 1 ? bias : fbias.b[f];
             OutT* out = scores + (size_t)f * nx * ny;
-            const uint32_t col0 = (uint32_t)(f * HALVES * Tc);
+            const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
             for (int c0 = 0; c0 < Tc; c0 += 16) {
                 uint32_t v[16];
-                tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)c0, v);
+                acc_sum(lane_base, f, 0, n_filters, HALVES, Tc, c0, v);
                 if constexpr (HALVES == 2) {
                     uint32_t u[16];
-                    tmem_load16(tmem + ((uint32_t)(warp * 32) << 16) + col0 + (uint32_t)(Tc + c0), u);
+                    acc_sum(lane_base, f, 1, n_filters, HALVES, Tc, c0, u);
 #pragma unroll
                     for (int c = 0; c < 16; ++c) {
                         const float mine = __uint_as_float((lane & 1) ? u[c] : v[c]);
@@ -410,7 +479,7 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     if (s != HOG_OK) return s;
     const int wpc = kM / (NB / 8);
     const int Tc = choose_tc(nx, ny, r, wpc);
-    const TcGeom G(r, Tc, NB / 8);
+    const TcGeom G(r, Tc, NB / 8, 1, weight_parts<WT>());
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
     auto kern = score_tc_kernel<NB, WT, OutT, false>;
@@ -427,7 +496,7 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void*
     unsigned int* status = nullptr;
     hog_status s = device_status_word(&status);
     if (s != HOG_OK) return s;
-    const TcGeom G(h.r, h.score_tc, NB / 8);
+    const TcGeom G(h.r, h.score_tc, NB / 8, 1, weight_parts<WT>());
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
     auto kern = score_tc_kernel<NB, WT, OutT, true>;
@@ -451,7 +520,7 @@ hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, int r, const 
     const int wpc = kM / (NB / 8);
     int Tc = choose_tc(nx, ny, r, wpc);
     auto fits = [&](int tc, int g) {
-        const TcGeom G(r, tc, NB / 8, g);
+        const TcGeom G(r, tc, NB / 8, g, weight_parts<WT>());
         return G.cols <= 512 && G.smem_bytes() <= kMaxSmem;
     };
     int group = kMaxFilters < n_filters ? kMaxFilters : n_filters;
@@ -463,7 +532,7 @@ hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, int r, const 
     }
     if (!fits(Tc, group)) return HOG_ERR_UNSUPPORTED;
     auto kern = score_tc_kernel<NB, WT, OutT, false>;
-    const size_t smem_max = TcGeom(r, Tc, NB / 8, group).smem_bytes();
+    const size_t smem_max = TcGeom(r, Tc, NB / 8, group, weight_parts<WT>()).smem_bytes();
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
     if (e != cudaSuccess) return cuda_fail(e);
     const dim3 grid((nx + wpc - 1) / wpc, (ny + Tc * r - 1) / (Tc * r), r);
@@ -475,7 +544,8 @@ hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, int r, const 
             const float b = biases[f0 + k];
             fb.b[k] = std::is_same<OutT, int32_t>::value ? (float)std::llround((double)b) : b;
         }
-        s = launch_pdl(kern, grid, dim3(kThreads), TcGeom(r, Tc, NB / 8, g).smem_bytes(), st, cells, ncx, ncy, r, Tc,
+        s = launch_pdl(kern, grid, dim3(kThreads), TcGeom(r, Tc, NB / 8, g, weight_parts<WT>()).smem_bytes(), st,
+                       cells, ncx, ncy, r, Tc,
                        w + f0 * per_filter, fb.b[0], g, fb, nx, ny, scores + (size_t)f0 * nx * ny,
                        static_cast<const PlanItem*>(nullptr), 0, status);
         if (s != HOG_OK) return s;
@@ -486,6 +556,9 @@ hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, int r, const 
 template <int NB>
 hog_status multi_by_w(const uint16_t* cells, int ncx, int ncy, int r, const void* w, int w_dtype, int n_filters,
                       const float* biases, void* scores, cudaStream_t st) {
+    if (w_dtype == HOG_F32)
+        return launch_multi_t<NB, float, float>(cells, ncx, ncy, r, static_cast<const float*>(w), n_filters, biases,
+                                                static_cast<float*>(scores), st);
     if (w_dtype == HOG_BF16)
         return launch_multi_t<NB, uint16_t, float>(cells, ncx, ncy, r, static_cast<const uint16_t*>(w), n_filters,
                                                    biases, static_cast<float*>(scores), st);
@@ -498,6 +571,7 @@ hog_status multi_by_w(const uint16_t* cells, int ncx, int ncy, int r, const void
 template <int NB>
 hog_status batch_by_w(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
                       cudaStream_t st) {
+    if (w_dtype == HOG_F32) return launch_batch_t<NB, float, float>(h, plan_dev, w, bias, st);
     if (w_dtype == HOG_BF16) return launch_batch_t<NB, uint16_t, float>(h, plan_dev, w, bias, st);
     if (w_dtype == HOG_I8) return launch_batch_t<NB, int8_t, int32_t>(h, plan_dev, w, bias, st);
     return HOG_ERR_UNSUPPORTED;
@@ -506,6 +580,7 @@ hog_status batch_by_w(const PlanHeader& h, const void* plan_dev, const void* w, 
 template <int NB>
 hog_status by_w(const uint16_t* cells, int ncx, int ncy, int r, const void* w, int w_dtype, float bias, void* scores,
                 cudaStream_t st) {
+    if (w_dtype == HOG_F32) return launch_t<NB, float, float>(cells, ncx, ncy, r, w, bias, scores, st);
     if (w_dtype == HOG_BF16) return launch_t<NB, uint16_t, float>(cells, ncx, ncy, r, w, bias, scores, st);
     if (w_dtype == HOG_I8) return launch_t<NB, int8_t, int32_t>(cells, ncx, ncy, r, w, bias, scores, st);
     return HOG_ERR_UNSUPPORTED;
@@ -526,6 +601,14 @@ int score_tc_rows_for(long ctas32) {
 }
 
 int score_tc_windows(int n_bins) { return kM / (n_bins == 16 ? 2 : 1); }
+
+bool score_tc_fills_gpu(int ncx, int ncy, int n_bins, int r) {
+    const long nx = (long)ncx - (kCX - 1) * r, ny = (long)ncy - (kCY - 1) * r;
+    if (nx <= 0 || ny <= 0) return false;
+    const long wpc = score_tc_windows(n_bins);
+    const long ctas = ((nx + wpc - 1) / wpc) * ((ny + 16 * r - 1) / (16 * r)) * r;  // at 16 rows per CTA
+    return ctas >= sm_count();
+}
 
 bool score_tc_supported(int cell_dtype, int n_bins, int cells_x, int cells_y, int r, int ncx) {
     (void)ncx;

@@ -156,6 +156,7 @@ def test_batch_equals_per_image_calls(fh):
     b.set_weights(w, 0.25, 0.5)
     b.run()
     got = b.results()
+    fh.hog_tune_set(fh.HOG_TUNE_SCORE_PATH, 2)  # the batch scores on the tensor cores; so does each item here
     for m, it in zip(b.item_meta, got["items"]):
         lvl = levels_of(imgs[m["image"]], 2)[m["level"]]
         H, W = lvl.shape[:2]
@@ -167,3 +168,4 @@ def test_batch_equals_per_image_calls(fh):
         one = p.results()
         assert np.array_equal(one["cells"], it["cells"])
         assert np.array_equal(one["scores"], it["scores"])
+    fh.hog_tune_set(fh.HOG_TUNE_SCORE_PATH, 0)

@@ -33,6 +33,19 @@ def g(fh):
     return _gpu
 
 
+class score_engine:
+    """Force the single-image score's engine (HOG_TUNE_SCORE_PATH) in a block."""
+
+    def __init__(self, fh, path):
+        self.fh, self.path = fh, path
+
+    def __enter__(self):
+        self.fh.hog_tune_set(self.fh.HOG_TUNE_SCORE_PATH, self.path)
+
+    def __exit__(self, *exc):
+        self.fh.hog_tune_set(self.fh.HOG_TUNE_SCORE_PATH, 0)
+
+
 def rand_img(H, W, ch, seed):
     rng = np.random.default_rng(seed)
     shape = (H, W) if ch == 1 else (H, W, 3)
@@ -350,13 +363,16 @@ def test_score_tensor_cores(fh, g, stride, nb):
     w = rng.normal(0, 0.01, 128 * nb).astype(np.float32)
     w_bf = torch.from_numpy(w).to(torch.bfloat16).float().numpy()
     ref = oracle.window_score(cells, w_bf, 0.25, stride=stride)
-    got = g.gpu_scores(cells, w, fh.HOG_BF16, 0.25, stride=stride, cell_dtype=fh.HOG_BF16)
+    with score_engine(fh, 2):
+        got = g.gpu_scores(cells, w, fh.HOG_BF16, 0.25, stride=stride, cell_dtype=fh.HOG_BF16)
     assert got.shape == ref.shape
     assert np.all(np.abs(got - ref) <= g.score_tolerance(cells, w_bf, 0.25, stride=stride))
     wi = rng.integers(-127, 128, 128 * nb).astype(np.int8)
     ref_i = oracle.window_score(cells, wi, 3.0, stride=stride)
-    got_i = g.gpu_scores(cells, wi, fh.HOG_I8, 3.0, stride=stride, cell_dtype=fh.HOG_BF16)
-    assert got_i.dtype == np.int32 and np.array_equal(got_i, ref_i.astype(np.int64))
+    for engine in (2, 1):  # tensor cores, then CUDA cores where they apply
+        with score_engine(fh, engine):
+            got_i = g.gpu_scores(cells, wi, fh.HOG_I8, 3.0, stride=stride, cell_dtype=fh.HOG_BF16)
+        assert got_i.dtype == np.int32 and np.array_equal(got_i, ref_i.astype(np.int64)), engine
 
 
 @pytest.mark.parametrize("nb,stride,F", [(8, 4, 1), (8, 4, 5), (8, 8, 17), (16, 4, 3), (8, 2, 9)])
@@ -383,7 +399,8 @@ def test_score_multi_filter(fh, g, nb, stride, F):
     for f in range(F):
         tol = g.score_tolerance(cells, W_bf[f].double().numpy(), float(B[f]), stride=stride)
         assert np.all(np.abs(got[f] - ref[f]) <= tol), f
-        one = g.gpu_scores(cells, W[f], fh.HOG_BF16, float(B[f]), stride=stride, cell_dtype=fh.HOG_BF16)
+        with score_engine(fh, 2):
+            one = g.gpu_scores(cells, W[f], fh.HOG_BF16, float(B[f]), stride=stride, cell_dtype=fh.HOG_BF16)
         assert np.array_equal(one, got[f]), f
     Wi = rng.integers(-127, 128, (F, K)).astype(np.int8)
     Bi = np.round(rng.normal(0, 20, F)).astype(np.float32)
@@ -485,6 +502,33 @@ def test_cells_soft(fh, g, ch, nb, cell, stride):
         S64 = oracle.window_score(ref, w, 0.1, stride=4)
         S = g.gpu_scores(ref, w, fh.HOG_F32, 0.1, stride=4, cell_dtype=fh.HOG_F32)
         assert np.all(np.abs(S - S64) <= g.score_tolerance(ref, w, 0.1, stride=4))
+
+
+@pytest.mark.parametrize("nb", [8, 16])
+@pytest.mark.parametrize("stride", [8, 4, 2])
+def test_score_f32_weights_on_tensor_cores(fh, g, stride, nb):
+    """f32 weights with bf16 cells run on the tensor cores as three exact
+    bf16 parts per weight: within the FP32-path bound of the FP64 oracle run
+    on the original f32 weights (no weight rounding), with a large bias too."""
+    rng = np.random.default_rng(500 + stride + nb)
+    img = rand_img(330, 420, 3, 90 + stride)
+    cells = cells_of(img, nb, stride)
+    w = rng.normal(0, 0.01, 128 * nb).astype(np.float32)
+    w[::7] *= 1e3  # mixed magnitudes: the low parts matter
+    for bias in (0.0, -123.25):
+        ref = oracle.window_score(cells, w, bias, stride=stride)
+        with score_engine(fh, 1):
+            cc = g.gpu_scores(cells, w, fh.HOG_F32, bias, stride=stride, cell_dtype=fh.HOG_BF16)
+        assert np.all(np.abs(cc - ref) <= g.score_tolerance(cells, w, bias, stride=stride))
+        with score_engine(fh, 2):
+            got = g.gpu_scores(cells, w, fh.HOG_F32, bias, stride=stride, cell_dtype=fh.HOG_BF16)
+        assert got.shape == ref.shape
+        tol = g.score_tolerance(cells, w, bias, stride=stride)
+        assert np.all(np.abs(got - ref) <= tol)
+        # the same weights rounded to bf16 would be far off: the parts are what make it f32-accurate
+        w_bf = torch.from_numpy(w).to(torch.bfloat16).float().numpy()
+        coarse = oracle.window_score(cells, w_bf, bias, stride=stride)
+        assert np.max(np.abs(coarse - ref) / tol) > 10 * np.max(np.abs(got - ref) / tol)
 
 
 def test_score_bf16_error_against_f32_weights(fh, g):
