@@ -375,6 +375,9 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 and int8 weights, and for f32 weights (three
  *                                 MMAs per step) only when the tensor-core grid
  *                                 alone gives every SM a CTA
+ *   HOG_TUNE_SLIDE_WINDOWS        windows per sequence of the CUDA-core score
+ *                                 (8 or 16): fewer gives more CTAs, more shares
+ *                                 each staged cell row among more windows
  *   HOG_TUNE_TABLE                where the bin-map and fused-cells kernels read
  *                                 the gradient table: 1 = a quadrant staged in
  *                                 shared memory (N_b a multiple of 4), 2 = the
@@ -395,7 +398,8 @@ typedef enum {
     HOG_TUNE_TABLE = 4,
     HOG_TUNE_CELL_ROWS = 5,
     HOG_TUNE_SCORE_PATH = 6,
-    HOG_TUNE_KNOBS = 7
+    HOG_TUNE_SLIDE_WINDOWS = 7,
+    HOG_TUNE_KNOBS = 8
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

@@ -21,7 +21,8 @@ import os
 import statistics
 
 from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_CELL_ROWS, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
-               HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_SCORE_PATH, HOG_TUNE_SCORE_TC_ROWS, hog_tune_get, hog_tune_set)
+               HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_SCORE_PATH, HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_SLIDE_WINDOWS,
+               hog_tune_get, hog_tune_set)
 
 # knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
 KNOBS = {
@@ -32,11 +33,13 @@ KNOBS = {
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
     "score_path": (HOG_TUNE_SCORE_PATH, (0, 1, 2)),
+    "slide_windows": (HOG_TUNE_SLIDE_WINDOWS, (0, 8, 16)),
 }
 # the knobs each path's launches read
 PATH_KNOBS = {
-    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_path", "score_tc_rows", "table"),
-    "fused": ("fused_ctas_per_sm", "score_path", "score_tc_rows", "table"),
+    "separate": ("integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_path", "score_tc_rows",
+                 "slide_windows", "table"),
+    "fused": ("fused_ctas_per_sm", "score_path", "score_tc_rows", "slide_windows", "table"),
 }
 
 

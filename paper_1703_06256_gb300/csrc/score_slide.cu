@@ -178,7 +178,8 @@ hog_status launch_t(const void* cells, int ncx, int ncy, int r, const void* w, f
                     cudaStream_t st) {
     const int nx = ncx - (kCX - 1) * r, ny = ncy - (kCY - 1) * r;
     if (nx <= 0 || ny <= 0) return HOG_OK;
-    const int T = r <= 2 ? 16 : 8;
+    const int tuned = tune_get(HOG_TUNE_SLIDE_WINDOWS);
+    const int T = tuned > 0 ? tuned : (r <= 2 ? 16 : 8);  // windows per sequence
     const SlideGeom G(r, T);
     const int per_class = (nx + r - 1) / r;
     const int S = (per_class + T - 1) / T;
