@@ -91,7 +91,7 @@ constexpr int kTI = 64;
 constexpr int kStreamThreads = 256;
 
 template <typename InT, typename OutT, int NB>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 4)
     cell_hist_stream_kernel(const InT* __restrict__ ii, int W, int H, int s, int r, int ncx, int ncy, int TJ,
                             OutT* __restrict__ cells) {
     extern __shared__ uint32_t S[];  // [TJ + r][kTI + r][NB + 1]
@@ -152,13 +152,12 @@ __global__ void __launch_bounds__(kStreamThreads)
 }
 
 // Rows of cells per streaming CTA: the tuned value (1 = the per-cell kernel),
-// else 8 when that still gives every SM two CTAs, else 4 (measured best of
-// 4, 8 and 16 from 800x600 to 3840x2160).
+// else 4 (measured best or tied among 4, 8 and 16 from 800x600 to 3840x2160).
 int stream_rows(int ncx, int ncy) {
+    (void)ncx;
+    (void)ncy;
     const int tuned = tune_get(HOG_TUNE_CELL_ROWS);
-    if (tuned > 0) return tuned;
-    const long tx = (ncx + kTI - 1) / kTI;
-    return tx * ((ncy + 7) / 8) >= 2L * sm_count() ? 8 : 4;
+    return tuned > 0 ? tuned : 4;
 }
 
 template <typename InT, typename OutT, int NB>
