@@ -52,8 +52,10 @@ def _load():
     global _lib
     with _lock:
         if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB_PATH)
+            # ORACLE_LIB names another build of fasthog_oracle.c (the mutation tests load
+            # deliberately broken copies this way); by default the one built here
+            path = os.environ.get("ORACLE_LIB") or build()
+            lib = ctypes.CDLL(path)
             P = ctypes.c_void_p
             I = ctypes.c_int
             L = ctypes.c_long
