@@ -320,7 +320,7 @@ hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int s
     if (std::isnan(thr)) return HOG_ERR_ARG;
     if (workspace_bytes < detect_workspace_bytes(nx, ny)) return HOG_ERR_ARG;
     return launch_detect(scores, score_dtype, nx, ny, stride, thr, image, level, out, max_out, d_count, workspace,
-                         reinterpret_cast<cudaStream_t>(stream));
+                         workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -65,7 +65,6 @@ __device__ __forceinline__ int find_item(const PlanItem* items, int n, int t) {
 int cells_fused_tiles_x(int ncx, int stride);
 int cells_fused_tiles(int ncx, int ncy, int stride);
 int score_tc_windows(int n_bins);  // windows per tensor-core CTA
-int detect_tiles(long n_scores);
 
 // Batch launchers (kernels in cells_fused.cu, score_tc.cu, detect.cu).
 hog_status launch_cells_fused_batch(const PlanHeader& h, const void* plan_dev, const uint8_t* lut, int cell_dtype,

@@ -68,10 +68,11 @@ extern "C" hog_status hog_detect_noalloc(const void* scores, int score_dtype, in
     if ((long)nx * ny > (long)HOG_DETECT_NOALLOC_MAX_SCORES) return HOG_ERR_ARG;  // beyond the fixed scratch
     if (score_dtype != HOG_F32 && score_dtype != HOG_I32) return HOG_ERR_ARG;
     if (thr != thr) return HOG_ERR_ARG;  // NaN
-    if (detect_workspace_bytes(nx, ny) > sizeof(int32_t) * (size_t)kNoAllocTiles) return HOG_ERR_ARG;
+    if (detect_tiles((long)nx * ny) > kNoAllocTiles) return HOG_ERR_ARG;  // one count per tile
     int32_t* scratch = nullptr;
     const hog_status s = scratch_address(&scratch);
     if (s != HOG_OK) return s;
+    // the fixed scratch holds one count per tile, not the offsets of the scanned form
     return launch_detect(scores, score_dtype, nx, ny, stride, thr, image, level, out, max_out, d_count, scratch,
-                         reinterpret_cast<cudaStream_t>(stream));
+                         (size_t)0, reinterpret_cast<cudaStream_t>(stream));
 }

@@ -78,9 +78,10 @@ hog_status launch_cells_fused(const uint8_t* img, int W, int H, int channels, si
                               cudaStream_t st);
 
 size_t detect_workspace_bytes(int nx, int ny);
+int detect_tiles(long n_scores);  // 2048-score tiles of a map (0 for an empty map)
 hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
                          int image, int level, hog_det* out, int max_out, int32_t* d_count, void* ws,
-                         cudaStream_t st);
+                         size_t ws_bytes, cudaStream_t st);
 
 // ---- programmatic dependent launch
 // Kernels of the detection path launch with programmatic stream
