@@ -6,66 +6,83 @@
 // map on the fly.  The planes are written exactly once, which is the bulk of
 // the work (4 * N_b bytes per pixel for int32, 2 * N_b for uint16).
 //
-// Tiling.  The image is cut into tiles of h rows (a band) by G = 512 columns
-// (a group).  A tile's values need three carries from outside it:
-//   V(x, top-1)      column sums above the band, per column and bin;
-//   RL(y)            per row, the count of each bin left of the group;
-//   corner           ii(group_left - 1, top - 1).
+// Tiling.  One warp owns a tile of h rows (a band) by G columns (a group).
+// Lane L holds the columns 4L..4L+3 of every 128-column slice of the group
+// (one slice, G = 128, in the current tiling), so that a warp's 16-byte
+// stores cover whole sectors.  A tile's values need three carries from
+// outside it:
+//   V(x, top-1)   per column and bin, the count above the band;
+//   RL(y)         per row and bin, the count left of the group;
+//   corner        per bin, ii(group_left - 1, top - 1).
 // With those, ii(x, y) = ii(x, y-1) + RL(y) + (row prefix inside the group),
 // starting from ii(x, top-1) = corner + (prefix of V over the group's
-// columns up to x).  Because V is a whole row vector per band, a chained
-// look-back scan would move tens of KiB per link; the carries come instead
-// from a reduce-then-scan in which no CTA ever waits for another:
+// columns up to x).  V is a whole row vector per band, too large to pass
+// along a look-back chain, so the carries come from a reduce-then-scan in
+// which no warp ever waits for another:
 //
-//   A  tile reduce   per tile: per-column counts over the band's rows
-//                    (8-bit fields), per-row counts over the group's columns
-//                    (16-bit), and the tile's total per bin.
-//   B  carries       (a) per column, the exclusive prefix of the column counts
-//                    over bands = V at every band top, two-level over bands;
-//                    (b) per group and bin, the exclusive prefix of the tile
-//                    totals over bands, a warp shuffle scan in chunks of 32.
-//   C  tile scan     per tile: corner = sum of (b) over the groups to the
-//                    left; RL(y) = sum of the row counts of those groups; one
-//                    block scan of V over the group's columns; then the rows,
-//                    each with a packed 16-bit row prefix (two bins per word:
-//                    thread-local running sums, a warp shuffle scan and one
-//                    cross-warp step, one barrier per row).
+//   A  tile reduce  per tile: per-column counts over the band (8-bit fields,
+//                   4 bins per word), per-row counts over the group (a warp
+//                   reduction per row), and the tile's total per bin.
+//   B  carries      (a) per column: the exclusive prefix of the column counts
+//                   over bands = V at every band top; (b) per group and bin:
+//                   the exclusive prefix of the tile totals over bands (in
+//                   place); (c) per row: the exclusive prefix of the row
+//                   counts over groups = RL (in place, a warp per row).
+//   C  tile scan    per tile: corner = the sum of (b) over the groups to the
+//                   left; acc = corner + prefix of V over the columns;
+//                   then per row the one-hot row's prefix inside each chunk
+//                   (8-bit fields), warp shuffle scans of the chunk totals,
+//                   and acc += RL + those prefixes; each lane stores its
+//                   chunks of every plane.  No barrier inside a row.
+//
+// The one-hot counts come from variable shifts: bin b of a window starting
+// at lo sets byte b - lo - 4m of word m (bins lo + 4m .. lo + 4m + 3) through
+// 1 << 8 (b - lo - 4m); every other bin, and 0xFF, gives a shift outside
+// 0..31, which shl clamps to a zero result.
 //
 // Bins are handled in windows of at most 16; larger N_b runs the phases once
-// per window.  Limits: W, H < 65536 (16-bit fields and carries).
+// per window.  Limits: W, H < 65536 (16-bit row counts and carries).
 #include "internal.cuh"
 
 namespace fasthog {
 
 namespace {
 
-constexpr int kQ = 4;             // columns per thread
-constexpr int kThreads = 128;     // threads per tile CTA
-constexpr int kGroup = kQ * kThreads;  // 512 columns per group
-constexpr int kWarps = kThreads / 32;
-constexpr int kSegments = 32;     // phase B(a): band segments per column
-constexpr int kMaxBand = 32;
+constexpr int kMaxBand = 32;        // rows per tile at most (8-bit column counts)
+constexpr int kCarryThreads = 512;
+constexpr int kSegments = kCarryThreads / 32;  // phase B(a): band segments per column
+constexpr int kSlice = 128;         // columns per slice: 4 per lane
+
+template <int WIN>
+struct Cfg {
+    static constexpr int NCH = 1;                  // 4-column chunks per lane
+    static constexpr int G = kSlice * NCH;         // columns per tile
+    static constexpr int NM = (WIN + 3) / 4;       // 8-bit-field words, 4 bins each
+};
 
 struct Plan {
-    int W, H, h, n_bands, n_groups, win, n_windows;
-    size_t colcnt_bytes, rowcnt_bytes, bt_bytes, carry_bytes, gv_bytes;
+    int W, H, h, n_bands, n_groups, win, n_windows, G;
+    size_t colcnt_bytes, rowcnt_bytes, bt_bytes, carry_bytes;
 };
 
 inline size_t align256(size_t b) { return (b + 255) & ~size_t(255); }
 
 // Band height h (rows per tile): the tuned value if one is set (force > 0
-// overrides both), else the tallest band that still gives every SM four
-// tiles (16 warps).
+// overrides both), else the tallest band that still gives every SM 16 tiles
+// (one warp each).
 Plan make_plan(int W, int H, int n_bins, int force = 0) {
     Plan p{};
     p.W = W;
     p.H = H;
-    p.n_groups = ceil_div(W, kGroup);
+    p.win = n_bins <= 4 ? 4 : (n_bins <= 8 ? 8 : 16);
+    p.n_windows = ceil_div(n_bins, p.win);
+    p.G = p.win == 16 ? Cfg<16>::G : Cfg<8>::G;
+    p.n_groups = ceil_div(W, p.G);
     const int tuned = force > 0 ? force : tune_get(HOG_TUNE_INTEGRAL_BAND_ROWS);
     if (tuned > 0) {
         p.h = tuned;
     } else {
-        const int target = 4 * sm_count();
+        const long target = 16L * sm_count();
         p.h = 4;
         for (int h : {32, 16, 8})
             if ((long)ceil_div(H, h) * p.n_groups >= target) {
@@ -74,22 +91,19 @@ Plan make_plan(int W, int H, int n_bins, int force = 0) {
             }
     }
     p.n_bands = ceil_div(H, p.h);
-    p.win = n_bins <= 4 ? 4 : (n_bins <= 8 ? 8 : 16);
-    p.n_windows = ceil_div(n_bins, p.win);
-    p.colcnt_bytes = align256((size_t)p.n_bands * (p.win / 4) * W * 4);
+    const int nm = (p.win + 3) / 4;
+    p.colcnt_bytes = align256((size_t)p.n_bands * nm * W * 4);
     p.rowcnt_bytes = align256((size_t)H * p.n_groups * p.win * 2);
-    p.bt_bytes = align256((size_t)p.n_groups * p.win * p.n_bands * 4);
-    p.carry_bytes = align256((size_t)p.n_bands * p.win * W * 2);
-    p.gv_bytes = align256((size_t)p.n_bands * p.n_groups * p.win * 4);
+    p.bt_bytes = align256((size_t)p.n_bands * p.n_groups * p.win * 4);
+    p.carry_bytes = align256((size_t)p.n_bands * W * p.win * 2);
     return p;
 }
 
 struct Ws {
-    uint32_t* colcnt;  // [band][win/4][W]       packed 8-bit column counts
-    uint16_t* rowcnt;  // [y][group][win]        row counts inside the group
-    uint32_t* bt;      // [group][win][band]     tile totals
-    uint16_t* carry;   // [band][win][W]         V(x, band top - 1)
-    uint32_t* gv;      // [band][group][win]     sum over bands above of tile totals
+    uint32_t* colcnt;  // [band][NM][W]        8-bit column counts over the band, 4 bins per word
+    uint16_t* rowcnt;  // [y][group][WIN]      row counts inside the group, then RL (in place)
+    uint32_t* bt;      // [band][group][WIN]   tile totals, then their prefix over bands (in place)
+    uint16_t* carry;   // [band][W][WIN]       V(x, band_top - 1)
 };
 
 Ws carve(const Plan& p, void* base) {
@@ -102,231 +116,360 @@ Ws carve(const Plan& p, void* base) {
     w.bt = reinterpret_cast<uint32_t*>(b);
     b += p.bt_bytes;
     w.carry = reinterpret_cast<uint16_t*>(b);
-    b += p.carry_bytes;
-    w.gv = reinterpret_cast<uint32_t*>(b);
     return w;
 }
 
-// Load the bins of this thread's kQ columns of row y (0xFF past the right edge).
-__device__ __forceinline__ void load_bins4(const uint8_t* __restrict__ bins, int W, int y, int x0, int ncol,
-                                           bool vec, uint32_t v[kQ]) {
-    const uint8_t* p = bins + (size_t)y * W + x0;
-    if (vec && ncol == kQ) {
-        const uint32_t w = __ldg(reinterpret_cast<const uint32_t*>(p));
-#pragma unroll
-        for (int c = 0; c < kQ; ++c) v[c] = (w >> (8 * c)) & 0xFFu;
-    } else {
-#pragma unroll
-        for (int c = 0; c < kQ; ++c) v[c] = c < ncol ? (uint32_t)__ldg(p + c) : 0xFFu;
-    }
-}
-
-// Issue the loads of this thread's kQ bins for every row of the band up
-// front, so their latency is paid once per tile rather than once per row,
-// and park them in shared memory (each thread reads back only its own slot).
-__device__ __forceinline__ void stage_band(const uint8_t* __restrict__ bins, int W, int y0, int y1, int x0, int ncol,
-                                           bool vec, uint32_t (*slot)[kThreads]) {
-    for (int y = y0; y < y1; y += 8) {
-        uint32_t w[8];
-#pragma unroll
-        for (int k = 0; k < 8; ++k) {
-            w[k] = 0xFFFFFFFFu;
-            if (y + k < y1) {
-                uint32_t v[kQ];
-                load_bins4(bins, W, y + k, x0, ncol, vec, v);
-                w[k] = v[0] | (v[1] << 8) | (v[2] << 16) | (v[3] << 24);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < 8; ++k)
-            if (y + k < y1) slot[y + k - y0][threadIdx.x] = w[k];
-    }
-}
-
-// SIMD-within-a-register helpers built from single integer instructions
-// (shifts, logic, add, multiply).  A thread's 4 bins sit in one 32-bit word,
-// one byte per column.
-//
-// 1 << n, or 0 when n >= 32 (PTX clamps the shift amount).
+// 1 << n, or 0 when n >= 32 as an unsigned number (PTX clamps the shift amount).
 __device__ __forceinline__ uint32_t bit_or_zero(uint32_t n) {
     uint32_t r;
     asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(n));
     return r;
 }
-// Per-column one-hot masks of the bins [lo, lo + 8): byte c of the result has
-// bit k set iff column c holds bin lo + k (0xFF and bins outside the range
-// set nothing).
-__device__ __forceinline__ uint32_t onehot_cols8(uint32_t w, uint32_t lo) {
-    uint32_t p = 0;
+
+// Byte k of x, zero-extended.
+__device__ __forceinline__ uint32_t byte_at(uint32_t x, int k) { return __byte_perm(x, 0u, 0x4440u | (uint32_t)k); }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c) p |= (bit_or_zero(((w >> (8 * c)) & 0xFFu) - lo) & 0xFFu) << (8 * c);
-    return p;
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) v += t;
+    }
+    return v;
 }
-// Byte c = 1 iff column c holds bin lo + k.
-__device__ __forceinline__ uint32_t col_flags(uint32_t p, int k) { return (p >> k) & 0x01010101u; }
-// The 4 bits of a nibble to the 4 bytes (bit k -> byte k): the products
-// n_k * 2^(7j) land on a multiple of 8 only for j = k, without carries.
-__device__ __forceinline__ uint32_t spread4(uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; }
-// Counts of 4 bins in 8-bit fields (word m: bins 4m..4m+3) widen to 16-bit
-// fields two bins per word, paired as E[2m] = (4m, 4m+2), E[2m+1] = (4m+1, 4m+3).
-__device__ __forceinline__ uint32_t even16(uint32_t t) { return t & 0x00FF00FFu; }
-__device__ __forceinline__ uint32_t odd16(uint32_t t) { return (t >> 8) & 0x00FF00FFu; }
-__host__ __device__ constexpr int e_word(int b) { return 2 * (b >> 2) + (b & 1); }
-__host__ __device__ constexpr int e_half(int b) { return (b >> 1) & 1; }
+
+// The bins of the 4 columns at p (0xFF past the ncol valid ones).
+__device__ __forceinline__ uint32_t load_chunk(const uint8_t* __restrict__ p, int ncol, bool vec) {
+    if (vec && ncol == 4) return __ldg(reinterpret_cast<const uint32_t*>(p));
+    uint32_t w = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) w |= (k < ncol ? (uint32_t)__ldg(p + k) : 0xFFu) << (8 * k);
+    return w;
+}
+
+// Column geometry of this lane's chunks in tile group g.
+template <int NCH>
+struct Chunks {
+    int x[NCH];     // first column of each chunk
+    int ncol[NCH];  // valid columns of each chunk (0..4)
+    __device__ __forceinline__ Chunks(int g, int G, int W) {
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            x[j] = g * G + kSlice * j + 4 * (int)threadIdx.x;
+            ncol[j] = max(0, min(4, W - x[j]));
+        }
+    }
+};
+
+// Park this lane's chunks of rows y0 .. y0 + nrows - 1 in shared memory; the
+// loads of up to 16 rows are issued before any of them is stored.
+template <int NCH>
+__device__ __forceinline__ void stage_rows(const uint8_t* __restrict__ bins, int W, int y0, int nrows,
+                                           const Chunks<NCH>& ch, bool vec, uint32_t (*st)[32][NCH]) {
+    const int lane = threadIdx.x;
+    for (int r0 = 0; r0 < nrows; r0 += 16) {
+        uint32_t v[16][NCH];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint8_t* row = bins + (size_t)(y0 + r0 + k) * W;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) v[k][j] = r0 + k < nrows ? load_chunk(row + ch.x[j], ch.ncol[j], vec) : 0u;
+        }
+#pragma unroll
+        for (int k = 0; k < 16; ++k)
+            if (r0 + k < nrows)
+#pragma unroll
+                for (int j = 0; j < NCH; ++j) st[r0 + k][lane][j] = v[k][j];
+    }
+}
 
 // ---------------------------------------------------------------- phase A
 template <int WIN>
-__global__ void __launch_bounds__(kThreads)
-    ii_tile_reduce_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_bands, int n_groups,
-                          int bin_base, bool vec, Ws ws) {
-    constexpr int NM = WIN / 4;  // 8-bit-field words (4 bins each)
-    constexpr int NE = WIN / 2;  // 16-bit-field words (2 bins each)
-    __shared__ uint32_t row_acc[kMaxBand][NE];
-    __shared__ uint32_t band_bins[kMaxBand][kThreads];
-    const int band = blockIdx.x, g = blockIdx.y;
-    const int tid = threadIdx.x, lane = tid & 31;
-    const int x0 = g * kGroup + tid * kQ;
-    const int ncol = max(0, min(kQ, W - x0));
-    const int y0 = band * h, y1 = min(H, y0 + h);
+__global__ void __launch_bounds__(32)
+    ii_tile_reduce_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_bands, int n_groups, int lo,
+                          bool vec, Ws ws) {
+    using C = Cfg<WIN>;
+    constexpr int NCH = C::NCH, NM = C::NM;
+    __shared__ uint32_t st[kMaxBand][32][NCH];
+    const int tile = blockIdx.x;
+    const int band = tile / n_groups, g = tile - band * n_groups;
+    const int lane = threadIdx.x;
+    const Chunks<NCH> ch(g, C::G, W);
+    const int y0 = band * h, nrows = min(h, H - y0);
 
     pdl_trigger();
     pdl_wait();
-    stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
-    for (int i = tid; i < kMaxBand * NE; i += kThreads) (&row_acc[0][0])[i] = 0;
-    __syncthreads();
+    stage_rows<NCH>(bins, W, y0, nrows, ch, vec, st);
+    __syncwarp();
 
-    // col[c][m]: counts over the band's rows of bins 4m..4m+3 in column c (8-bit fields)
-    uint32_t col[kQ][NM];
+    // col[j][k][m]: counts over the band of bins lo+4m .. lo+4m+3 in column k
+    // of chunk j (8-bit fields: a band has at most 32 rows)
+    uint32_t col[NCH][4][NM];
 #pragma unroll
-    for (int c = 0; c < kQ; ++c)
+    for (int j = 0; j < NCH; ++j)
 #pragma unroll
-        for (int m = 0; m < NM; ++m) col[c][m] = 0;
+        for (int k = 0; k < 4; ++k)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) col[j][k][m] = 0;
+    // rc: lane r keeps row r's counts over the group, 16-bit fields, word i = bins lo+2i, lo+2i+1
+    uint32_t rc[2 * NM];
+#pragma unroll
+    for (int i = 0; i < 2 * NM; ++i) rc[i] = 0;
 
-    for (int y = y0; y < y1; ++y) {
-        const uint32_t w = band_bins[y - y0][tid];
+    for (int r = 0; r < nrows; ++r) {
         uint32_t rowt[NM];
 #pragma unroll
-        for (int g8 = 0; g8 < (WIN + 7) / 8; ++g8) {
-            const uint32_t p = onehot_cols8(w, (uint32_t)(bin_base + 8 * g8));
+        for (int m = 0; m < NM; ++m) rowt[m] = 0;
 #pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-                const int m = 2 * g8 + hh;  // bins 4m..4m+3 = nibble hh of each byte of p
-                if (m < NM) {
-                    uint32_t tsum = 0;
+        for (int j = 0; j < NCH; ++j) {
+            const uint32_t w = st[r][lane][j];
 #pragma unroll
-                    for (int c = 0; c < kQ; ++c) {
-                        const uint32_t t = spread4((p >> (8 * c + 4 * hh)) & 0xFu);
-                        col[c][m] += t;
-                        tsum += t;
-                    }
-                    rowt[m] = tsum;
+            for (int k = 0; k < 4; ++k) {
+                const int b = (int)byte_at(w, k);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const uint32_t oh = bit_or_zero((uint32_t)(8 * (b - lo - 4 * m)));
+                    col[j][k][m] += oh;
+                    rowt[m] += oh;
                 }
             }
         }
+        // sum over the warp in 16-bit fields (a group row holds at most 256 of a bin)
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
-            uint32_t s = rowt[m];  // 8-bit fields: a warp's row count is at most 128
-#pragma unroll
-            for (int d = 16; d > 0; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-            if (lane == 0 && s) {
-                atomicAdd(&row_acc[y - y0][2 * m], even16(s));
-                atomicAdd(&row_acc[y - y0][2 * m + 1], odd16(s));
+            const uint32_t s0 = __reduce_add_sync(0xffffffffu, __byte_perm(rowt[m], 0u, 0x4140u));
+            const uint32_t s1 = __reduce_add_sync(0xffffffffu, __byte_perm(rowt[m], 0u, 0x4342u));
+            if (lane == r) {
+                rc[2 * m] = s0;
+                rc[2 * m + 1] = s1;
             }
         }
     }
+
     // per-column counts of the band
-    if (ncol > 0) {
 #pragma unroll
-        for (int c = 0; c < kQ; ++c)
-            if (c < ncol)
+    for (int j = 0; j < NCH; ++j) {
 #pragma unroll
-                for (int m = 0; m < NM; ++m) ws.colcnt[((size_t)band * NM + m) * W + x0 + c] = col[c][m];
+        for (int m = 0; m < NM; ++m) {
+            uint32_t* dst = ws.colcnt + ((size_t)band * NM + m) * W + ch.x[j];
+            if (vec && ch.ncol[j] == 4) {
+                *reinterpret_cast<uint4*>(dst) = make_uint4(col[j][0][m], col[j][1][m], col[j][2][m], col[j][3][m]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    if (k < ch.ncol[j]) dst[k] = col[j][k][m];
+            }
+        }
     }
-    __syncthreads();
-    // per-row counts of the group, and the tile total
-    for (int i = tid; i < (y1 - y0) * WIN; i += kThreads) {
-        const int r = i / WIN, b = i - r * WIN;
-        const uint32_t v = (row_acc[r][e_word(b)] >> (16 * e_half(b))) & 0xFFFFu;
-        ws.rowcnt[((size_t)(y0 + r) * n_groups + g) * WIN + b] = (uint16_t)v;
+    // per-row counts of the group: WIN consecutive uint16 per row
+    if (lane < nrows) {
+        uint16_t* dst = ws.rowcnt + ((size_t)(y0 + lane) * n_groups + g) * WIN;
+        if (NM == 1) {
+            *reinterpret_cast<uint2*>(dst) = make_uint2(rc[0], rc[1 % (2 * NM)]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < NM / 2; ++k)
+                reinterpret_cast<uint4*>(dst)[k] = make_uint4(rc[4 * k], rc[(4 * k + 1) % (2 * NM)],
+                                                              rc[(4 * k + 2) % (2 * NM)], rc[(4 * k + 3) % (2 * NM)]);
+        }
     }
-    if (tid < WIN) {
-        uint32_t t = 0;
-        for (int r = 0; r < y1 - y0; ++r) t += (row_acc[r][e_word(tid)] >> (16 * e_half(tid))) & 0xFFFFu;
-        ws.bt[((size_t)g * WIN + tid) * n_bands + band] = t;
+    // tile totals (at most 32 * 256 per bin)
+    uint32_t tot[2 * NM];
+#pragma unroll
+    for (int i = 0; i < 2 * NM; ++i) tot[i] = __reduce_add_sync(0xffffffffu, lane < nrows ? rc[i] : 0u);
+    if (lane < WIN) {
+        uint32_t v = 0;
+#pragma unroll
+        for (int i = 0; i < 2 * NM; ++i)
+            if (i == (lane >> 1)) v = tot[i];
+        v = (lane & 1) ? (v >> 16) : (v & 0xFFFFu);
+        ws.bt[((size_t)band * n_groups + g) * WIN + lane] = v;
     }
 }
 
 // ---------------------------------------------------------------- phase B
-// Blocks [0, nb_a): (a) column carries; block b covers 32 columns x one
-//   8-bit word (4 bins); threads (lane, seg).
-// Blocks [nb_a, nb_a + ceil(n_groups*WIN/kSegments)): (b) one warp per
-//   (group, bin), scanning the tile totals over bands in chunks of 32.
+// Blocks [0, na): (a) column carries; block = 32 columns, all bins; threads
+//   (lane = column, warp = segment of bands).
+// Blocks [na, na + nbb): (b) tile-total prefixes; block = 32 (group, bin)
+//   pairs; threads (lane = pair, warp = segment of bands).
+// Blocks [na + nbb, ...): (c) RL; one warp per row, lanes = groups.
 template <int WIN>
-__global__ void __launch_bounds__(32 * kSegments)
-    ii_carry_kernel(int W, int n_bands, int n_groups, int nb_a, Ws ws) {
-    constexpr int NWD = WIN / 4;
-    const int lane = threadIdx.x, seg = threadIdx.y;
+__global__ void __launch_bounds__(kCarryThreads)
+    ii_carry_kernel(int W, int H, int n_bands, int n_groups, int na, int nbb, Ws ws) {
+    constexpr int NM = Cfg<WIN>::NM;
+    constexpr int kWarps = kCarryThreads / 32;
+    constexpr int kPF = 8;  // bands of loads in flight per thread
+    static_assert(kSegments == 16, "the segment scans take half a warp per column");
+    __shared__ uint32_t seg_sum[4][32][kSegments + 1];  // [bin of 4][column][segment]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     pdl_trigger();
     pdl_wait();
-    if ((int)blockIdx.x >= nb_a) {
-        const int pair = (blockIdx.x - nb_a) * kSegments + seg;
-        if (pair >= n_groups * WIN) return;
-        const int g = pair / WIN, b = pair - g * WIN;
-        const uint32_t* src = ws.bt + ((size_t)g * WIN + b) * n_bands;
-        uint32_t run = 0;
-        for (int k0 = 0; k0 < n_bands; k0 += 32) {
-            const int k = k0 + lane;
-            const uint32_t v = k < n_bands ? __ldg(src + k) : 0u;
-            uint32_t s = v;
+
+    if ((int)blockIdx.x >= na + nbb) {
+        // (c) RL(y) = exclusive prefix over groups of the row counts, in place;
+        // 16-bit fields never carry: a row holds at most W < 65536 of a bin
+        const int y = (blockIdx.x - na - nbb) * kWarps + warp;
+        if (y >= H) return;
+        uint16_t* row = ws.rowcnt + (size_t)y * n_groups * WIN;
+        uint32_t before[WIN / 2];
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, s, d);
-                if (lane >= d) s += t;
+        for (int i = 0; i < WIN / 2; ++i) before[i] = 0;
+        for (int g0 = 0; g0 < n_groups; g0 += 32) {
+            const int g = g0 + lane;
+            uint32_t u[WIN / 2];
+#pragma unroll
+            for (int i = 0; i < WIN / 2; ++i) u[i] = 0;
+            uint16_t* src = row + (size_t)g * WIN;
+            if (g < n_groups) {
+                if (WIN == 4) {
+                    const uint2 a = __ldcg(reinterpret_cast<const uint2*>(src));
+                    u[0] = a.x;
+                    u[1 % (WIN / 2)] = a.y;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < WIN / 8; ++q) {
+                        const uint4 a = __ldcg(reinterpret_cast<const uint4*>(src) + q);
+                        u[4 * q] = a.x;
+                        u[(4 * q + 1) % (WIN / 2)] = a.y;
+                        u[(4 * q + 2) % (WIN / 2)] = a.z;
+                        u[(4 * q + 3) % (WIN / 2)] = a.w;
+                    }
+                }
             }
-            if (k < n_bands) ws.gv[((size_t)k * n_groups + g) * WIN + b] = run + s - v;
-            run += __shfl_sync(0xffffffffu, s, 31);
+#pragma unroll
+            for (int i = 0; i < WIN / 2; ++i) {
+                const uint32_t incl = warp_incl_scan(u[i], lane);
+                const uint32_t excl = before[i] + incl - u[i];
+                before[i] += __shfl_sync(0xffffffffu, incl, 31);
+                u[i] = excl;
+            }
+            if (g < n_groups) {
+                if (WIN == 4) {
+                    *reinterpret_cast<uint2*>(src) = make_uint2(u[0], u[1 % (WIN / 2)]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < WIN / 8; ++q)
+                        reinterpret_cast<uint4*>(src)[q] = make_uint4(u[4 * q], u[(4 * q + 1) % (WIN / 2)],
+                                                                      u[(4 * q + 2) % (WIN / 2)],
+                                                                      u[(4 * q + 3) % (WIN / 2)]);
+                }
+            }
         }
         return;
     }
-    __shared__ uint32_t seg_sum[kSegments][32][4];
-    const int words_x = (W + 31) / 32;
-    const int kw = blockIdx.x / words_x;
-    const int x = (blockIdx.x - kw * words_x) * 32 + lane;
+
+    const int seg = warp;
     const int per = (n_bands + kSegments - 1) / kSegments;
-    const int b0 = seg * per, b1 = min(n_bands, b0 + per);
-    constexpr int kPF = 8;  // loads in flight per thread
-    uint32_t s[4] = {0, 0, 0, 0};
-    for (int b = b0; b < b1; b += kPF) {
-        uint32_t wv[kPF];
+    const int b0 = min(n_bands, seg * per), b1 = min(n_bands, b0 + per);
+    // exclusive scan over the segments of the 4 values in s, for the 32
+    // columns of the block: the two halves of warp w scan columns w and w + 16
+    auto segment_scan = [&](const uint32_t (&s)[4], uint32_t (&run)[4]) {
 #pragma unroll
-        for (int k = 0; k < kPF; ++k)
-            wv[k] = (x < W && b + k < b1) ? __ldg(ws.colcnt + ((size_t)(b + k) * NWD + kw) * W + x) : 0u;
+        for (int e = 0; e < 4; ++e) seg_sum[e][lane][seg] = s[e];
+        __syncthreads();
+        const int cx = warp + 16 * (lane >> 4), sg = lane & 15;
 #pragma unroll
-        for (int k = 0; k < kPF; ++k)
+        for (int e = 0; e < 4; ++e) {
+            const uint32_t v = seg_sum[e][cx][sg];
+            uint32_t incl = v;
 #pragma unroll
-            for (int e = 0; e < 4; ++e) s[e] += (wv[k] >> (8 * e)) & 0xFFu;
+            for (int d = 1; d < 16; d <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, d, 16);
+                if (sg >= d) incl += t;
+            }
+            seg_sum[e][cx][sg] = incl - v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 4; ++e) run[e] = seg_sum[e][lane][seg];
+        __syncthreads();
+    };
+
+    if ((int)blockIdx.x >= na) {
+        // (b) per (group, bin) pair: exclusive prefix over bands of the tile totals, in place
+        const int np = n_groups * WIN;
+        const int pi = (blockIdx.x - na) * 32 + lane;
+        uint32_t* t = ws.bt + pi;  // band k at t[k * np]
+        uint32_t s[4] = {0, 0, 0, 0}, run[4];
+        for (int b = b0; b < b1; b += kPF) {
+            uint32_t v[kPF];
+#pragma unroll
+            for (int k = 0; k < kPF; ++k) v[k] = (pi < np && b + k < b1) ? __ldcg(t + (size_t)(b + k) * np) : 0u;
+#pragma unroll
+            for (int k = 0; k < kPF; ++k) s[0] += v[k];
+        }
+        segment_scan(s, run);
+        if (pi >= np) return;
+        for (int b = b0; b < b1; b += kPF) {
+            uint32_t v[kPF];
+#pragma unroll
+            for (int k = 0; k < kPF; ++k) v[k] = b + k < b1 ? __ldcg(t + (size_t)(b + k) * np) : 0u;
+#pragma unroll
+            for (int k = 0; k < kPF; ++k)
+                if (b + k < b1) {
+                    t[(size_t)(b + k) * np] = run[0];
+                    run[0] += v[k];
+                }
+        }
+        return;
     }
+
+    // (a) V at every band top: exclusive prefix over bands of the column counts
+    const int x = blockIdx.x * 32 + lane;
+    uint32_t s[4 * NM];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) seg_sum[seg][lane][e] = s[e];
-    __syncthreads();
-    uint32_t run[4] = {0, 0, 0, 0};
-    for (int t = 0; t < seg; ++t)
+    for (int i = 0; i < 4 * NM; ++i) s[i] = 0;
+    for (int b = b0; b < b1; b += kPF) {
+        uint32_t wv[kPF][NM];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) run[e] += seg_sum[t][lane][e];
+        for (int k = 0; k < kPF; ++k)
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                wv[k][m] = (x < W && b + k < b1) ? __ldcg(ws.colcnt + ((size_t)(b + k) * NM + m) * W + x) : 0u;
+#pragma unroll
+        for (int k = 0; k < kPF; ++k)
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) s[4 * m + e] += byte_at(wv[k][m], e);
+    }
+    uint32_t run[4 * NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        uint32_t s4[4] = {s[4 * m], s[4 * m + 1], s[4 * m + 2], s[4 * m + 3]}, r4[4];
+        segment_scan(s4, r4);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) run[4 * m + e] = r4[e];
+    }
     if (x >= W) return;
     for (int b = b0; b < b1; b += kPF) {
-        uint32_t wv[kPF];
+        uint32_t wv[kPF][NM];
 #pragma unroll
         for (int k = 0; k < kPF; ++k)
-            wv[k] = b + k < b1 ? __ldg(ws.colcnt + ((size_t)(b + k) * NWD + kw) * W + x) : 0u;
+#pragma unroll
+            for (int m = 0; m < NM; ++m)
+                wv[k][m] = b + k < b1 ? __ldcg(ws.colcnt + ((size_t)(b + k) * NM + m) * W + x) : 0u;
 #pragma unroll
         for (int k = 0; k < kPF; ++k) {
             if (b + k < b1) {
+                // V of this column at the top of band b + k, WIN uint16 (bins lo .. lo + WIN - 1)
+                uint32_t u[WIN / 2];
 #pragma unroll
-                for (int e = 0; e < 4; ++e) {
-                    ws.carry[((size_t)(b + k) * WIN + 4 * kw + e) * W + x] = (uint16_t)run[e];
-                    run[e] += (wv[k] >> (8 * e)) & 0xFFu;
+                for (int i = 0; i < WIN / 2; ++i) u[i] = (run[2 * i] & 0xFFFFu) | (run[2 * i + 1] << 16);
+                uint16_t* dst = ws.carry + ((size_t)(b + k) * W + x) * WIN;
+                if (WIN == 4) {
+                    *reinterpret_cast<uint2*>(dst) = make_uint2(u[0], u[1 % (WIN / 2)]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < WIN / 8; ++q)
+                        reinterpret_cast<uint4*>(dst)[q] = make_uint4(u[4 * q], u[(4 * q + 1) % (WIN / 2)],
+                                                                      u[(4 * q + 2) % (WIN / 2)],
+                                                                      u[(4 * q + 3) % (WIN / 2)]);
                 }
+#pragma unroll
+                for (int m = 0; m < NM; ++m)
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) run[4 * m + e] += byte_at(wv[k][m], e);
             }
         }
     }
@@ -334,210 +477,209 @@ __global__ void __launch_bounds__(32 * kSegments)
 
 // ---------------------------------------------------------------- phase C
 template <typename OutT>
-__device__ __forceinline__ void store4(OutT* p, const int* v, int n, bool vec);
-template <>
-__device__ __forceinline__ void store4<int32_t>(int32_t* p, const int* v, int n, bool vec) {
+__device__ __forceinline__ void store_chunk(OutT* p, const int* v, int n, bool vec) {
     if (vec && n == 4) {
-        *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+        if (sizeof(OutT) == 4) {
+            *reinterpret_cast<int4*>(p) = make_int4(v[0], v[1], v[2], v[3]);
+        } else {
+            *reinterpret_cast<uint2*>(p) = make_uint2(__byte_perm((uint32_t)v[0], (uint32_t)v[1], 0x5410u),
+                                                      __byte_perm((uint32_t)v[2], (uint32_t)v[3], 0x5410u));
+        }
     } else {
-        for (int c = 0; c < n; ++c) p[c] = v[c];
-    }
-}
-template <>
-__device__ __forceinline__ void store4<uint16_t>(uint16_t* p, const int* v, int n, bool vec) {
-    if (vec && n == 4) {
-        const uint32_t a = (uint32_t)(v[0] & 0xFFFF) | ((uint32_t)v[1] << 16);
-        const uint32_t b = (uint32_t)(v[2] & 0xFFFF) | ((uint32_t)v[3] << 16);
-        *reinterpret_cast<uint2*>(p) = make_uint2(a, b);
-    } else {
-        for (int c = 0; c < n; ++c) p[c] = (uint16_t)v[c];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (k < n) p[k] = (OutT)v[k];
     }
 }
 
 template <int WIN, typename OutT>
-__global__ void __launch_bounds__(kThreads)
-    ii_tile_scan_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_groups, int bin_base,
-                        int n_bins, bool vec, Ws ws, OutT* __restrict__ ii) {
-    constexpr int NM = WIN / 4;  // 8-bit-field words (4 bins each)
-    constexpr int NE = WIN / 2;  // 16-bit-field words (2 bins each, e_word/e_half pairing)
-    __shared__ int corner_s[WIN];
-    __shared__ uint32_t rl_s[kMaxBand][NE];
-    __shared__ int wtot_init[kWarps][WIN];
-    __shared__ uint32_t wtot[2][kWarps][NM];
+__global__ void __launch_bounds__(32)
+    ii_tile_scan_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_groups, int lo, int n_bins,
+                        bool vec, Ws ws, OutT* __restrict__ ii) {
+    using C = Cfg<WIN>;
+    constexpr int NCH = C::NCH, NM = C::NM;
+    __shared__ uint32_t st[kMaxBand][32][NCH];
+    __shared__ __align__(16) uint32_t rl_s[kMaxBand][WIN];
+    const int tile = blockIdx.x;
+    const int band = tile / n_groups, g = tile - band * n_groups;
+    const int lane = threadIdx.x;
+    const Chunks<NCH> ch(g, C::G, W);
+    const int y0 = band * h, nrows = min(h, H - y0);
+    const int wins = min(WIN, n_bins - lo);
 
-    const int band = blockIdx.x, g = blockIdx.y;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int x0 = g * kGroup + tid * kQ;
-    const int ncol = max(0, min(kQ, W - x0));
-    const int y0 = band * h, y1 = min(H, y0 + h);
-    const int wins = min(WIN, n_bins - bin_base);
-    __shared__ uint32_t band_bins[kMaxBand][kThreads];
     pdl_trigger();
     pdl_wait();
-    stage_band(bins, W, y0, y1, x0, ncol, vec, band_bins);
-
-    // corner = ii(group_left - 1, y0 - 1); RL(y) for the band's rows
-    if (tid < WIN) {
-        uint32_t s = 0;
-        for (int gg = 0; gg < g; ++gg) s += __ldg(ws.gv + ((size_t)band * n_groups + gg) * WIN + tid);
-        corner_s[tid] = (int)s;
-    }
-    for (int i = tid; i < (y1 - y0) * NE; i += kThreads) {
-        const int r = i / NE, k = i - r * NE;
-        const int blo = 4 * (k >> 1) + (k & 1), bhi = blo + 2;  // the bins of E[k]
-        uint32_t lo = 0, hi = 0;
-        const uint16_t* rc = ws.rowcnt + (size_t)(y0 + r) * n_groups * WIN;
-        for (int gg = 0; gg < g; ++gg) {
-            lo += __ldg(rc + gg * WIN + blo);
-            hi += __ldg(rc + gg * WIN + bhi);
-        }
-        rl_s[r][k] = lo | (hi << 16);
-    }
-
-    // ii(x, y0 - 1) = corner + prefix over the group's columns of V(x, y0 - 1)
-    int acc[kQ][WIN];
-    int tot[WIN];
-#pragma unroll
-    for (int b = 0; b < WIN; ++b) {
-        const uint16_t* cp = ws.carry + ((size_t)band * WIN + b) * W + x0;
-        int cv[kQ];
-        if (vec && ncol == kQ) {
-            const uint2 u = __ldg(reinterpret_cast<const uint2*>(cp));
-            cv[0] = (int)(u.x & 0xFFFFu);
-            cv[1] = (int)(u.x >> 16);
-            cv[2] = (int)(u.y & 0xFFFFu);
-            cv[3] = (int)(u.y >> 16);
+    stage_rows<NCH>(bins, W, y0, nrows, ch, vec, st);
+    // RL of the band's rows: lane r fetches row r
+    if (lane < nrows) {
+        const uint16_t* src = ws.rowcnt + ((size_t)(y0 + lane) * n_groups + g) * WIN;
+        uint32_t u[WIN / 2];
+        if (WIN == 4) {
+            const uint2 a = __ldcg(reinterpret_cast<const uint2*>(src));
+            u[0] = a.x;
+            u[1 % (WIN / 2)] = a.y;
         } else {
 #pragma unroll
-            for (int c = 0; c < kQ; ++c) cv[c] = c < ncol ? (int)__ldg(cp + c) : 0;
+            for (int k = 0; k < WIN / 8; ++k) {
+                const uint4 a = __ldcg(reinterpret_cast<const uint4*>(src) + k);
+                u[4 * k] = a.x;
+                u[(4 * k + 1) % (WIN / 2)] = a.y;
+                u[(4 * k + 2) % (WIN / 2)] = a.z;
+                u[(4 * k + 3) % (WIN / 2)] = a.w;
+            }
         }
-        int run = 0;
 #pragma unroll
-        for (int c = 0; c < kQ; ++c) {
-            run += cv[c];
-            acc[c][b] = run;
+        for (int k = 0; k < WIN / 2; ++k) {
+            rl_s[lane][2 * k] = u[k] & 0xFFFFu;
+            rl_s[lane][2 * k + 1] = u[k] >> 16;
         }
-        tot[b] = run;
     }
+    // corner = ii(group_left - 1, y0 - 1): the sum over the groups to the left
+    // of their counts above the band; lanes split the groups, then combine
+    uint32_t corner = 0;
+    {
+        constexpr int kSlots = 32 / WIN;
+        const uint32_t* src = ws.bt + (size_t)band * n_groups * WIN + (lane % WIN);
+        for (int gg = lane / WIN; gg < g; gg += kSlots) corner += __ldcg(src + (size_t)gg * WIN);
 #pragma unroll
-    for (int b = 0; b < WIN; ++b) {
-        int v = tot[b];
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, v, d);
-            if (lane >= d) v += t;
-        }
-        if (lane == 31) wtot_init[warp][b] = v;
-        tot[b] = v - tot[b];
-    }
-    __syncthreads();
-#pragma unroll
-    for (int b = 0; b < WIN; ++b) {
-        int off = corner_s[b] + tot[b];
-        for (int w = 0; w < warp; ++w) off += wtot_init[w][b];
-#pragma unroll
-        for (int c = 0; c < kQ; ++c) acc[c][b] += off;
+        for (int d = WIN; d < 32; d <<= 1) corner += __shfl_xor_sync(0xffffffffu, corner, d);
     }
 
-    // rows of the band: ii(x, y) = ii(x, y-1) + R(x, y), R = row prefix of
-    // the one-hot row = RL(y) + (count left of this thread in the group)
-    //                        + (count in this thread's columns up to x)
-    const size_t plane = (size_t)H * W;
-    OutT* out_row = ii + (size_t)bin_base * plane + (size_t)y0 * W + x0;
-    int buf = 0;
-    for (int y = y0; y < y1; ++y, out_row += W) {
-        const uint32_t w = band_bins[y - y0][tid];
-        // pre4[b] byte c = count of bin b in this thread's columns 0..c
-        uint32_t pre4[WIN];
+    // ii(x, y0 - 1) = corner + prefix over the group's columns of V(x, y0 - 1);
+    // column 4 * j + k of acc is column k of chunk j
+    int acc[WIN][4 * NCH];
 #pragma unroll
-        for (int g8 = 0; g8 < (WIN + 7) / 8; ++g8) {
-            const uint32_t p = onehot_cols8(w, (uint32_t)(bin_base + 8 * g8));
+    for (int j = 0; j < NCH; ++j) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-                if (8 * g8 + k < WIN) pre4[8 * g8 + k] = col_flags(p, k) * 0x01010101u;
-        }
-        // thread totals (8-bit fields) and their inclusive warp scan
-        uint32_t T[NM], S[NM];
+        for (int k = 0; k < 4; ++k) {
+            uint32_t u[WIN / 2];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            T[m] = __byte_perm(__byte_perm(pre4[4 * m], pre4[4 * m + 1], 0x0073),
-                               __byte_perm(pre4[4 * m + 2], pre4[4 * m + 3], 0x0073), 0x5410);
-            S[m] = T[m];
-        }
+            for (int i = 0; i < WIN / 2; ++i) u[i] = 0;
+            if (k < ch.ncol[j]) {
+                const uint16_t* src = ws.carry + ((size_t)band * W + ch.x[j] + k) * WIN;
+                if (WIN == 4) {
+                    const uint2 a = __ldg(reinterpret_cast<const uint2*>(src));
+                    u[0] = a.x;
+                    u[1 % (WIN / 2)] = a.y;
+                } else {
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                const uint32_t t = __shfl_up_sync(0xffffffffu, S[m], d);
-                if (lane >= d) S[m] += t;  // a warp's row count per bin is at most 128
+                    for (int q = 0; q < WIN / 8; ++q) {
+                        const uint4 a = __ldg(reinterpret_cast<const uint4*>(src) + q);
+                        u[4 * q] = a.x;
+                        u[(4 * q + 1) % (WIN / 2)] = a.y;
+                        u[(4 * q + 2) % (WIN / 2)] = a.z;
+                        u[(4 * q + 3) % (WIN / 2)] = a.w;
+                    }
+                }
             }
-        }
-        if (lane == 31) {
-#pragma unroll
-            for (int m = 0; m < NM; ++m) wtot[buf][warp][m] = S[m];
-        }
-        __syncthreads();
-        // exclusive offset of this thread's first column, 16-bit fields
-        uint32_t E[NE];
-#pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            const uint32_t x = S[m] - T[m];
-            E[2 * m] = rl_s[y - y0][2 * m] + even16(x);
-            E[2 * m + 1] = rl_s[y - y0][2 * m + 1] + odd16(x);
-        }
-        for (int w2 = 0; w2 < warp; ++w2) {
-#pragma unroll
-            for (int m = 0; m < NM; ++m) {
-                const uint32_t t = wtot[buf][w2][m];
-                E[2 * m] += even16(t);
-                E[2 * m + 1] += odd16(t);
-            }
-        }
-        buf ^= 1;
-#pragma unroll
-        for (int b = 0; b < WIN; ++b) {
-            const uint32_t base = (E[e_word(b)] >> (16 * e_half(b))) & 0xFFFFu;
-#pragma unroll
-            for (int c = 0; c < kQ; ++c) acc[c][b] += (int)(base + ((pre4[b] >> (8 * c)) & 0xFFu));
-        }
-        if (ncol > 0) {
 #pragma unroll
             for (int b = 0; b < WIN; ++b) {
-                if (b < wins) {
-                    int vals[kQ];
+                const int v = (int)((u[b >> 1] >> (16 * (b & 1))) & 0xFFFFu);
+                acc[b][4 * j + k] = k == 0 ? v : acc[b][4 * j + k - 1] + v;
+            }
+        }
+    }
 #pragma unroll
-                    for (int c = 0; c < kQ; ++c) vals[c] = acc[c][b];
-                    store4<OutT>(out_row + (size_t)b * plane, vals, ncol, vec);
+    for (int b = 0; b < WIN; ++b) {
+        int off = (int)__shfl_sync(0xffffffffu, corner, b);
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const int tot = acc[b][4 * j + 3];
+            const int incl = (int)warp_incl_scan((uint32_t)tot, lane);
+            const int o = off + incl - tot;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[b][4 * j + k] += o;
+            off += __shfl_sync(0xffffffffu, incl, 31);  // all of this slice precedes the next
+        }
+    }
+    __syncwarp();
+
+    // rows of the band: ii(x, y) = ii(x, y-1) + RL(y) + (count in the row's
+    // group columns up to x) = acc + base + in-chunk prefix
+    const size_t plane = (size_t)H * W;
+    OutT* out_row = ii + (size_t)lo * plane + (size_t)y0 * W + ch.x[0];
+    for (int r = 0; r < nrows; ++r, out_row += W) {
+        // P[j][k][m] byte e = count of bin lo+4m+e in columns 0..k of chunk j
+        uint32_t P[NCH][4][NM];
+#pragma unroll
+        for (int j = 0; j < NCH; ++j) {
+            const uint32_t w = st[r][lane][j];
+            uint32_t run[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) run[m] = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int b = (int)byte_at(w, k);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    run[m] += bit_or_zero((uint32_t)(8 * (b - lo - 4 * m)));
+                    P[j][k][m] = run[m];
                 }
             }
         }
+        // E[j][m]: count in the group columns before chunk j of this lane, 8-bit
+        // fields: slice 0's total is at most 128, and an exclusive prefix over
+        // the lanes of a slice at most 124
+        uint32_t E[NCH][NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            uint32_t before = 0;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+                const uint32_t incl = warp_incl_scan(P[j][3][m], lane);
+                E[j][m] = before + incl - P[j][3][m];
+                if (j + 1 < NCH) before += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        }
+        uint4 rl4[WIN / 4];
+#pragma unroll
+        for (int k = 0; k < WIN / 4; ++k) rl4[k] = reinterpret_cast<const uint4*>(rl_s[r])[k];
+#pragma unroll
+        for (int b = 0; b < WIN; ++b) {
+            const int m = b >> 2, e = b & 3;
+            const uint32_t rlv = e == 0 ? rl4[m].x : (e == 1 ? rl4[m].y : (e == 2 ? rl4[m].z : rl4[m].w));
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+                const int base = (int)(rlv + byte_at(E[j][m], e));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) acc[b][4 * j + k] += base + (int)byte_at(P[j][k][m], e);
+            }
+        }
+        OutT* p = out_row;
+#pragma unroll
+        for (int b = 0; b < WIN; ++b, p += plane)
+            if (b < wins)
+#pragma unroll
+                for (int j = 0; j < NCH; ++j)
+                    if (ch.ncol[j] > 0) store_chunk<OutT>(p + kSlice * j, &acc[b][4 * j], ch.ncol[j], vec);
     }
 }
 
 template <int WIN, typename OutT>
-hog_status run_window(const Plan& p, const uint8_t* bins, int n_bins, int bin_base, OutT* ii, const Ws& ws,
-                      bool vec, cudaStream_t st) {
-    dim3 grid_tiles(p.n_bands, p.n_groups);
-    hog_status s = launch_pdl(ii_tile_reduce_kernel<WIN>, grid_tiles, dim3(kThreads), 0, st, bins, p.W, p.H, p.h,
-                              p.n_bands, p.n_groups, bin_base, vec, ws);
+hog_status run_window(const Plan& p, const uint8_t* bins, int n_bins, int lo, OutT* ii, const Ws& ws, bool vec,
+                      cudaStream_t st) {
+    const int tiles = p.n_bands * p.n_groups;
+    hog_status s = launch_pdl(ii_tile_reduce_kernel<WIN>, dim3(tiles), dim3(32), 0, st, bins, p.W, p.H, p.h,
+                              p.n_bands, p.n_groups, lo, vec, ws);
     if (s != HOG_OK) return s;
-    const int nb_a = ceil_div(p.W, 32) * (WIN / 4);
-    const int nb_b = ceil_div(p.n_groups * WIN, kSegments);
-    s = launch_pdl(ii_carry_kernel<WIN>, dim3(nb_a + nb_b), dim3(32, kSegments), 0, st, p.W, p.n_bands, p.n_groups,
-                   nb_a, ws);
+    const int na = ceil_div(p.W, 32);
+    const int nbb = ceil_div((long)p.n_groups * WIN, 32);
+    const int nc = ceil_div(p.H, kCarryThreads / 32);
+    s = launch_pdl(ii_carry_kernel<WIN>, dim3(na + nbb + nc), dim3(kCarryThreads), 0, st, p.W, p.H, p.n_bands,
+                   p.n_groups, na, nbb, ws);
     if (s != HOG_OK) return s;
-    return launch_pdl(ii_tile_scan_kernel<WIN, OutT>, grid_tiles, dim3(kThreads), 0, st, bins, p.W, p.H, p.h,
-                      p.n_groups, bin_base, n_bins, vec, ws, ii);
+    return launch_pdl(ii_tile_scan_kernel<WIN, OutT>, dim3(tiles), dim3(32), 0, st, bins, p.W, p.H, p.h,
+                      p.n_groups, lo, n_bins, vec, ws, ii);
 }
 
 template <typename OutT>
 hog_status run_all(const Plan& p, const uint8_t* bins, int n_bins, OutT* ii, const Ws& ws, bool vec,
                    cudaStream_t st) {
     for (int wi = 0; wi < p.n_windows; ++wi) {
-        const int base = wi * p.win;
-        hog_status s = p.win == 4   ? run_window<4, OutT>(p, bins, n_bins, base, ii, ws, vec, st)
-                       : p.win == 8 ? run_window<8, OutT>(p, bins, n_bins, base, ii, ws, vec, st)
-                                    : run_window<16, OutT>(p, bins, n_bins, base, ii, ws, vec, st);
+        const int lo = wi * p.win;
+        hog_status s = p.win == 4   ? run_window<4, OutT>(p, bins, n_bins, lo, ii, ws, vec, st)
+                       : p.win == 8 ? run_window<8, OutT>(p, bins, n_bins, lo, ii, ws, vec, st)
+                                    : run_window<16, OutT>(p, bins, n_bins, lo, ii, ws, vec, st);
         if (s != HOG_OK) return s;
     }
     return HOG_OK;
@@ -550,7 +692,7 @@ size_t integral_workspace_bytes(int W, int H, int n_bins) {
     size_t most = 0;
     for (int h : {4, 8, 16, 32}) {
         const Plan p = make_plan(W, H, n_bins, h);
-        const size_t b = p.colcnt_bytes + p.rowcnt_bytes + p.bt_bytes + p.carry_bytes + p.gv_bytes;
+        const size_t b = p.colcnt_bytes + p.rowcnt_bytes + p.bt_bytes + p.carry_bytes;
         most = b > most ? b : most;
     }
     return most;
@@ -560,10 +702,10 @@ hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii
                            cudaStream_t st) {
     const Plan p = make_plan(W, H, n_bins);
     const Ws w = carve(p, ws);
-    const size_t elem = ii_dtype == HOG_U16 ? 2 : 4;
-    // vector path: 4-byte bin loads and 4-element stores stay aligned
-    const bool vec = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) &&
-                     (reinterpret_cast<uintptr_t>(ii) % (4 * elem) == 0) && (W % 4 == 0);
+    // vector path: a chunk's 4 bins load as one word, its 4 outputs store as
+    // one 16-byte (int32) or 8-byte (uint16) vector, and every row starts aligned
+    const bool vec = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (reinterpret_cast<uintptr_t>(ii) % 16 == 0) &&
+                     (W % 4 == 0);
     if (ii_dtype == HOG_U16) return run_all<uint16_t>(p, bins, n_bins, static_cast<uint16_t*>(ii), w, vec, st);
     return run_all<int32_t>(p, bins, n_bins, static_cast<int32_t*>(ii), w, vec, st);
 }
