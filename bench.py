@@ -640,7 +640,7 @@ def main():
     # launch shapes picked by the autotuner on this workload (results do not depend on them)
     from paper_1703_06256_gb300 import autotune
 
-    tuned = None if args.no_tune else autotune.tune_pipeline(pipe, autotune.Autotuner(), reps=10)
+    tuned = None if args.no_tune else autotune.tune_pipeline(pipe, autotune.Autotuner(), reps=30)
     step, read_total, timing_mode = graph_step(torch, fns, between=False)
     step_st, read_stages, _ = graph_step(torch, fns, between=True)
     for _ in range(max(args.warmup, 3)):
@@ -692,7 +692,7 @@ def main():
     fused = None
     if "fused" in extras:
         pipe.fused = True
-        ftuned = None if args.no_tune else autotune.tune_pipeline(pipe, autotune.Autotuner(), reps=10)
+        ftuned = None if args.no_tune else autotune.tune_pipeline(pipe, autotune.Autotuner(), reps=30)
         fstep, fread, _ = graph_step(torch, [pipe.stage_cells_fused, pipe.stage_score, pipe.stage_detect],
                                      between=False)
         fused_ms = time_steps(torch, fstep, fread, flush, args.steps, args.warmup)

@@ -129,8 +129,10 @@ def _device_name() -> str:
 
 def pipeline_measure(pipe, reps: int = 20, flush_bytes: int = 256 << 20):
     """A `measure` for `search`: apply the knobs, recapture `pipe`'s graph
-    (launch shapes are fixed at capture), and return the median device time
-    (ms) of `reps` replays, each after an L2 flush."""
+    (launch shapes are fixed at capture), and return the mean device time
+    (ms) of `reps` replays, each after an L2 flush, without the fastest and
+    slowest tenth (event times come in steps of about a microsecond, so a
+    mean separates launch shapes that a median would tie)."""
     import torch
 
     flush = torch.empty(flush_bytes // 4, dtype=torch.int32, device=pipe.device)
@@ -149,7 +151,9 @@ def pipeline_measure(pipe, reps: int = 20, flush_bytes: int = 256 << 20):
             torch.cuda.synchronize(pipe.device)
             if k >= 3:
                 times.append(ev[0].elapsed_time(ev[1]))
-        return statistics.median(times)
+        times.sort()
+        cut = len(times) // 10
+        return statistics.fmean(times[cut: len(times) - cut])
 
     return measure
 

@@ -19,10 +19,11 @@ __device__ __forceinline__ uint32_t row_word(const uint8_t* __restrict__ row, lo
     return w;
 }
 
-// Byte i of a little-endian word array, i a compile-time constant.
+// Byte i of a little-endian word array, i a compile-time constant (one byte
+// permute: byte i & 3 of the word, zero-extended).
 template <int N>
 __device__ __forceinline__ int byte_of(const uint32_t (&w)[N], int i) {
-    return (int)((w[i >> 2] >> (8 * (i & 3))) & 0xFFu);
+    return (int)__byte_perm(w[i >> 2], 0u, 0x4440u | (uint32_t)(i & 3));
 }
 
 template <int CH>
@@ -90,32 +91,36 @@ __device__ __forceinline__ void quad_gradient(const QuadWords<CH>& q, int p, int
 }
 
 // Eq. 1 and the table lookup for the 4 pixels of quad x (row loaded in q).
+// Branch-free: neighbouring pixels fall in different quadrants, so the
+// quadrant turn is a pair of selects rather than a branch per case.
 template <int CH, bool QUAD>
 __device__ __forceinline__ uint32_t bins_of_quad(const QuadWords<CH>& q, int x, int W, const uint8_t* __restrict__ lutq,
                                                  const uint8_t* __restrict__ lut, int nb, int nb4) {
     uint32_t packed = 0;
 #pragma unroll
     for (int p = 0; p < 4; ++p) {
-        uint32_t bin = kNoBin;
+        int dx, dy;
+        quad_gradient<CH>(q, p, dx, dy);
         const int xp = x + p;
-        if (xp > 0 && xp < W - 1) {
-            int dx, dy;
-            quad_gradient<CH>(q, p, dx, dy);
-            if (dx != 0 || dy != 0) {
-                if (QUAD) {
-                    int qd, u, v;  // quadrant and quadrant-0 coordinates
-                    if (dx > 0 && dy >= 0) { qd = 0; u = dx; v = dy; }
-                    else if (dx <= 0 && dy > 0) { qd = 1; u = dy; v = -dx; }
-                    else if (dx < 0 && dy <= 0) { qd = 2; u = -dx; v = -dy; }
-                    else { qd = 3; u = -dy; v = dx; }
-                    const int t = lutq[v * 256 + u - 1] + qd * nb4;
-                    bin = t >= nb ? t - nb : t;
-                } else {
-                    bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
-                }
-            }
+        const bool binned = xp > 0 && xp < W - 1 && (dx != 0 || dy != 0);
+        uint32_t bin;
+        if (QUAD) {
+            // Half-turn the lower half-plane (dy < 0, or dy = 0 and dx < 0) to
+            // the upper one, then quarter-turn its left part (ex <= 0) to the
+            // first quadrant: (u, v) has u in 1..255 and v in 0..255, and the
+            // turns add 2 and 1 quarter(s), each worth N_b/4 bins.
+            const bool upper = dy > 0 || (dy == 0 && dx > 0);
+            const int ex = upper ? dx : -dx, ey = upper ? dy : -dy;
+            const bool right = ex > 0;
+            const int u = right ? ex : ey, v = right ? ey : -ex;
+            const int turns = (upper ? 0 : 2) + (right ? 0 : 1);
+            const int idx = max(v * 256 + u - 1, 0);  // (0, 0) has no entry; its lookup is discarded
+            const int t = (int)lutq[idx] + turns * nb4;
+            bin = (uint32_t)(t >= nb ? t - nb : t);
+        } else {
+            bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
         }
-        packed |= bin << (8 * p);
+        packed |= (binned ? bin : (uint32_t)kNoBin) << (8 * p);
     }
     return packed;
 }

@@ -11,8 +11,9 @@
 // Every byte position inside the loaded words is a compile-time constant, so
 // Eq. 1 for the 4 x C channel values is register arithmetic: byte
 // extraction, differences, dx^2 + dy^2 per channel and the strongest
-// channel (ties to the lowest index).  A thread takes two quads per
-// iteration and issues both quads' loads before using either.
+// channel (ties to the lowest index).  A thread takes two quads per step
+// and issues the next step's loads before computing the current pair, so
+// four quads of loads are in flight per thread.
 //
 // The table lives in shared memory.  The full 511 x 511 table (255.5 KiB)
 // does not fit, so when 4 divides N_b the CTA holds one quadrant only:
@@ -52,7 +53,7 @@ __device__ __forceinline__ void store_quad(uint8_t* __restrict__ bins, int W, in
 }
 
 template <int CH, bool QUAD>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 3)
     bin_map_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                    const uint8_t* __restrict__ lut, int nb, uint8_t* __restrict__ bins, bool word_stores,
                    unsigned int* status) {
@@ -78,19 +79,39 @@ __global__ void __launch_bounds__(kThreads)
     pdl_wait();  // the table copy above reads only the table, built before the path runs
 
     const int qpr = (W + 3) >> 2;  // quads per row
-    const long n_quads = (long)qpr * H;
     const long row_bytes = (long)W * CH;
+    // grid-stride over quads in row-major order; the (row, quad) position
+    // advances by the stride without dividing
     const long step = (long)gridDim.x * kThreads;
-    // two quads per iteration (q and q + step): both loads are in flight together
-    for (long q0 = (long)blockIdx.x * kThreads + tid; q0 < n_quads; q0 += 2 * step) {
-        const long q1 = q0 + step;
-        const int y0 = (int)(q0 / qpr), x0 = (int)(q0 - (long)y0 * qpr) * 4;
-        const bool has1 = q1 < n_quads;
-        const int y1 = has1 ? (int)(q1 / qpr) : 0, x1 = has1 ? (int)(q1 - (long)y1 * qpr) * 4 : 0;
-        const bool in0 = y0 > 0 && y0 < H - 1, in1 = has1 && y1 > 0 && y1 < H - 1;
-        QuadWords<CH> a, b;
-        if (in0) load_quad<CH>(img, pitch, row_bytes, aligned, x0, y0, a);
-        if (in1) load_quad<CH>(img, pitch, row_bytes, aligned, x1, y1, b);
+    const int sy = (int)(step / qpr), sxq = (int)(step - (long)sy * qpr);
+    auto advance = [&](int& y, int& xq) {
+        y += sy;
+        xq += sxq;
+        if (xq >= qpr) {
+            xq -= qpr;
+            ++y;
+        }
+    };
+    auto interior = [&](int y) { return y > 0 && y < H - 1; };
+    // Two quads per step (a, and b one stride later), software-pipelined:
+    // the loads of the next step's pair are issued before this pair is
+    // computed, so every thread keeps four quads of loads in flight.
+    const long qs = (long)blockIdx.x * kThreads + tid;
+    int ya = (int)(qs / qpr), xqa = (int)(qs - (long)ya * qpr);
+    int yb = ya, xqb = xqa;
+    advance(yb, xqb);
+    QuadWords<CH> a, b;
+    if (ya < H && interior(ya)) load_quad<CH>(img, pitch, row_bytes, aligned, 4 * xqa, ya, a);
+    if (yb < H && interior(yb)) load_quad<CH>(img, pitch, row_bytes, aligned, 4 * xqb, yb, b);
+    while (ya < H) {
+        int yc = yb, xqc = xqb;
+        advance(yc, xqc);
+        int yd = yc, xqd = xqc;
+        advance(yd, xqd);
+        QuadWords<CH> c, d;
+        if (yc < H && interior(yc)) load_quad<CH>(img, pitch, row_bytes, aligned, 4 * xqc, yc, c);
+        if (yd < H && interior(yd)) load_quad<CH>(img, pitch, row_bytes, aligned, 4 * xqd, yd, d);
+        const bool in0 = interior(ya), has1 = yb < H, in1 = has1 && interior(yb);
         if (!lut_ready && (in0 || in1)) {
             if (!ptx::mbar_wait_bounded(&lut_bar, 0, kWaitLimitNs)) {
                 atomicOr(status, kStatusTimeout);
@@ -99,11 +120,18 @@ __global__ void __launch_bounds__(kThreads)
             lut_ready = true;
         }
         // border rows hold no bins
-        store_quad(bins, W, x0, y0, in0 ? bins_of_quad<CH, QUAD>(a, x0, W, lutq, lut, nb, nb4) : 0xFFFFFFFFu,
+        const int x0 = 4 * xqa, x1 = 4 * xqb;
+        store_quad(bins, W, x0, ya, in0 ? bins_of_quad<CH, QUAD>(a, x0, W, lutq, lut, nb, nb4) : 0xFFFFFFFFu,
                    word_stores);
         if (has1)
-            store_quad(bins, W, x1, y1, in1 ? bins_of_quad<CH, QUAD>(b, x1, W, lutq, lut, nb, nb4) : 0xFFFFFFFFu,
+            store_quad(bins, W, x1, yb, in1 ? bins_of_quad<CH, QUAD>(b, x1, W, lutq, lut, nb, nb4) : 0xFFFFFFFFu,
                        word_stores);
+        a = c;
+        b = d;
+        ya = yc;
+        xqa = xqc;
+        yb = yd;
+        xqb = xqd;
     }
     if (QUAD && !lut_ready) {
         // This thread never needed the table: still let the copy land before
@@ -125,7 +153,8 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     // at least 4 quads per thread, so each staged table copy serves a fair share of pixels
     const long need = (n_quads + 4 * kThreads - 1) / (4 * kThreads);
     const int per_sm = tune_get(HOG_TUNE_BINMAP_CTAS_PER_SM);
-    const long cap = (long)sm_count() * (per_sm > 0 ? per_sm : (QUAD ? 3 : 8));
+    // three CTAs per SM are resident (registers; with the quadrant, shared memory too)
+    const long cap = (long)sm_count() * (per_sm > 0 ? per_sm : 3);
     const int grid = (int)(need < cap ? need : cap);
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
     const bool word_stores = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (W % 4 == 0);

@@ -185,12 +185,12 @@ __device__ __forceinline__ void stage_rows(const uint8_t* __restrict__ bins, int
 
 // ---------------------------------------------------------------- phase A
 template <int WIN>
-__global__ void __launch_bounds__(32)
+__global__ void __launch_bounds__(32, 16)
     ii_tile_reduce_kernel(const uint8_t* __restrict__ bins, int W, int H, int h, int n_bands, int n_groups, int lo,
                           bool vec, Ws ws) {
     using C = Cfg<WIN>;
     constexpr int NCH = C::NCH, NM = C::NM;
-    __shared__ uint32_t st[kMaxBand][32][NCH];
+    static_assert(4 * NCH * 32 < 256, "a group row's count of a bin must fit a byte");
     const int tile = blockIdx.x;
     const int band = tile / n_groups, g = tile - band * n_groups;
     const int lane = threadIdx.x;
@@ -199,8 +199,6 @@ __global__ void __launch_bounds__(32)
 
     pdl_trigger();
     pdl_wait();
-    stage_rows<NCH>(bins, W, y0, nrows, ch, vec, st);
-    __syncwarp();
 
     // col[j][k][m]: counts over the band of bins lo+4m .. lo+4m+3 in column k
     // of chunk j (8-bit fields: a band has at most 32 rows)
@@ -211,37 +209,45 @@ __global__ void __launch_bounds__(32)
         for (int k = 0; k < 4; ++k)
 #pragma unroll
             for (int m = 0; m < NM; ++m) col[j][k][m] = 0;
-    // rc: lane r keeps row r's counts over the group, 16-bit fields, word i = bins lo+2i, lo+2i+1
-    uint32_t rc[2 * NM];
+    // rc: lane r keeps row r's counts over the group, 8-bit fields, word m = bins lo+4m .. lo+4m+3
+    uint32_t rc[NM];
 #pragma unroll
-    for (int i = 0; i < 2 * NM; ++i) rc[i] = 0;
+    for (int m = 0; m < NM; ++m) rc[m] = 0;
 
-    for (int r = 0; r < nrows; ++r) {
-        uint32_t rowt[NM];
+    for (int r0 = 0; r0 < nrows; r0 += 16) {
+        // the loads of 16 rows are in flight together
+        uint32_t v[16][NCH];
 #pragma unroll
-        for (int m = 0; m < NM; ++m) rowt[m] = 0;
+        for (int k = 0; k < 16; ++k) {
+            const uint8_t* row = bins + (size_t)(y0 + r0 + k) * W;
 #pragma unroll
-        for (int j = 0; j < NCH; ++j) {
-            const uint32_t w = st[r][lane][j];
+            for (int j = 0; j < NCH; ++j)
+                v[k][j] = r0 + k < nrows ? load_chunk(row + ch.x[j], ch.ncol[j], vec) : 0xFFFFFFFFu;
+        }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int b = (int)byte_at(w, k);
+        for (int k = 0; k < 16; ++k) {
+            if (r0 + k >= nrows) break;
+            uint32_t rowt[NM];
 #pragma unroll
-                for (int m = 0; m < NM; ++m) {
-                    const uint32_t oh = bit_or_zero((uint32_t)(8 * (b - lo - 4 * m)));
-                    col[j][k][m] += oh;
-                    rowt[m] += oh;
+            for (int m = 0; m < NM; ++m) rowt[m] = 0;
+#pragma unroll
+            for (int j = 0; j < NCH; ++j) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int t = 8 * ((int)byte_at(v[k][j], c) - lo);
+#pragma unroll
+                    for (int m = 0; m < NM; ++m) {
+                        const uint32_t oh = bit_or_zero((uint32_t)(t - 32 * m));
+                        col[j][c][m] += oh;
+                        rowt[m] += oh;
+                    }
                 }
             }
-        }
-        // sum over the warp in 16-bit fields (a group row holds at most 256 of a bin)
+            // sum over the warp (a group row holds at most 4 * NCH * 32 < 256 of a bin)
 #pragma unroll
-        for (int m = 0; m < NM; ++m) {
-            const uint32_t s0 = __reduce_add_sync(0xffffffffu, __byte_perm(rowt[m], 0u, 0x4140u));
-            const uint32_t s1 = __reduce_add_sync(0xffffffffu, __byte_perm(rowt[m], 0u, 0x4342u));
-            if (lane == r) {
-                rc[2 * m] = s0;
-                rc[2 * m + 1] = s1;
+            for (int m = 0; m < NM; ++m) {
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, rowt[m]);
+                if (lane == r0 + k) rc[m] = sum;
             }
         }
     }
@@ -261,22 +267,28 @@ __global__ void __launch_bounds__(32)
             }
         }
     }
-    // per-row counts of the group: WIN consecutive uint16 per row
+    // per-row counts of the group: WIN consecutive uint16 per row; rcw word i = bins lo+2i, lo+2i+1
+    uint32_t rcw[2 * NM];
+#pragma unroll
+    for (int m = 0; m < NM; ++m) {
+        rcw[2 * m] = __byte_perm(rc[m], 0u, 0x4140u);
+        rcw[2 * m + 1] = __byte_perm(rc[m], 0u, 0x4342u);
+    }
     if (lane < nrows) {
         uint16_t* dst = ws.rowcnt + ((size_t)(y0 + lane) * n_groups + g) * WIN;
         if (NM == 1) {
-            *reinterpret_cast<uint2*>(dst) = make_uint2(rc[0], rc[1 % (2 * NM)]);
+            *reinterpret_cast<uint2*>(dst) = make_uint2(rcw[0], rcw[1 % (2 * NM)]);
         } else {
 #pragma unroll
             for (int k = 0; k < NM / 2; ++k)
-                reinterpret_cast<uint4*>(dst)[k] = make_uint4(rc[4 * k], rc[(4 * k + 1) % (2 * NM)],
-                                                              rc[(4 * k + 2) % (2 * NM)], rc[(4 * k + 3) % (2 * NM)]);
+                reinterpret_cast<uint4*>(dst)[k] = make_uint4(rcw[4 * k], rcw[(4 * k + 1) % (2 * NM)],
+                                                              rcw[(4 * k + 2) % (2 * NM)], rcw[(4 * k + 3) % (2 * NM)]);
         }
     }
     // tile totals (at most 32 * 256 per bin)
     uint32_t tot[2 * NM];
 #pragma unroll
-    for (int i = 0; i < 2 * NM; ++i) tot[i] = __reduce_add_sync(0xffffffffu, lane < nrows ? rc[i] : 0u);
+    for (int i = 0; i < 2 * NM; ++i) tot[i] = __reduce_add_sync(0xffffffffu, lane < nrows ? rcw[i] : 0u);
     if (lane < WIN) {
         uint32_t v = 0;
 #pragma unroll
