@@ -382,9 +382,9 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 the gradient table: 1 = a quadrant staged in
  *                                 shared memory (N_b a multiple of 4), 2 = the
  *                                 whole table through the read-only cache; the
- *                                 library's choice is 1 for the bin map and 2
- *                                 for the fused kernel (measured on natural-image
- *                                 gradients, which cluster in the table)
+ *                                 library's choice is 2 for both (measured on
+ *                                 natural-image gradients, which cluster in the
+ *                                 table)
  *
  * hog_tune_set returns HOG_ERR_ARG for an unknown knob or a value outside its
  * range (nothing changes); hog_tune_get returns the current value (0 = the

@@ -90,37 +90,55 @@ __device__ __forceinline__ void quad_gradient(const QuadWords<CH>& q, int p, int
     }
 }
 
+// The bin of one gradient (dx, dy), not (0, 0), from the quadrant table
+// (QUAD) or the whole table.  Branch-free: neighbouring pixels fall in
+// different quadrants, so the quadrant turn is a pair of selects.
+template <bool QUAD>
+__device__ __forceinline__ uint32_t bin_of(int dx, int dy, const uint8_t* __restrict__ lutq,
+                                           const uint8_t* __restrict__ lut, int nb, int nb4) {
+    if (QUAD) {
+        // Half-turn the lower half-plane (dy < 0, or dy = 0 and dx < 0) to the
+        // upper one, then quarter-turn its left part (ex <= 0) to the first
+        // quadrant: (u, v) has u in 1..255 and v in 0..255, and the turns add
+        // 2 and 1 quarter(s), each worth N_b/4 bins.
+        const bool upper = dy > 0 || (dy == 0 && dx > 0);
+        const int ex = upper ? dx : -dx, ey = upper ? dy : -dy;
+        const bool right = ex > 0;
+        const int u = right ? ex : ey, v = right ? ey : -ex;
+        const int turns = (upper ? 0 : 2) + (right ? 0 : 1);
+        const int idx = max(v * 256 + u - 1, 0);  // (0, 0) has no entry; the caller discards it
+        const int t = (int)lutq[idx] + turns * nb4;
+        return (uint32_t)(t >= nb ? t - nb : t);
+    }
+    return __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));  // (0, 0) holds no bin
+}
+
 // Eq. 1 and the table lookup for the 4 pixels of quad x (row loaded in q).
-// Branch-free: neighbouring pixels fall in different quadrants, so the
-// quadrant turn is a pair of selects rather than a branch per case.
+// A quad whose pixels all have both horizontal neighbours skips the
+// per-pixel border test.
 template <int CH, bool QUAD>
 __device__ __forceinline__ uint32_t bins_of_quad(const QuadWords<CH>& q, int x, int W, const uint8_t* __restrict__ lutq,
                                                  const uint8_t* __restrict__ lut, int nb, int nb4) {
     uint32_t packed = 0;
+    if (x >= 1 && x + 4 <= W - 1) {
 #pragma unroll
-    for (int p = 0; p < 4; ++p) {
-        int dx, dy;
-        quad_gradient<CH>(q, p, dx, dy);
-        const int xp = x + p;
-        const bool binned = xp > 0 && xp < W - 1 && (dx != 0 || dy != 0);
-        uint32_t bin;
-        if (QUAD) {
-            // Half-turn the lower half-plane (dy < 0, or dy = 0 and dx < 0) to
-            // the upper one, then quarter-turn its left part (ex <= 0) to the
-            // first quadrant: (u, v) has u in 1..255 and v in 0..255, and the
-            // turns add 2 and 1 quarter(s), each worth N_b/4 bins.
-            const bool upper = dy > 0 || (dy == 0 && dx > 0);
-            const int ex = upper ? dx : -dx, ey = upper ? dy : -dy;
-            const bool right = ex > 0;
-            const int u = right ? ex : ey, v = right ? ey : -ex;
-            const int turns = (upper ? 0 : 2) + (right ? 0 : 1);
-            const int idx = max(v * 256 + u - 1, 0);  // (0, 0) has no entry; its lookup is discarded
-            const int t = (int)lutq[idx] + turns * nb4;
-            bin = (uint32_t)(t >= nb ? t - nb : t);
-        } else {
-            bin = __ldg(lut + (size_t)(dy + kDMax) * kLutPitch + (dx + kDMax));
+        for (int p = 0; p < 4; ++p) {
+            int dx, dy;
+            quad_gradient<CH>(q, p, dx, dy);
+            uint32_t bin = bin_of<QUAD>(dx, dy, lutq, lut, nb, nb4);
+            if (QUAD) bin = (dx != 0 || dy != 0) ? bin : (uint32_t)kNoBin;
+            packed |= bin << (8 * p);
         }
-        packed |= (binned ? bin : (uint32_t)kNoBin) << (8 * p);
+    } else {
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+            int dx, dy;
+            quad_gradient<CH>(q, p, dx, dy);
+            const int xp = x + p;
+            const bool binned = xp > 0 && xp < W - 1 && (dx != 0 || dy != 0);
+            const uint32_t bin = bin_of<QUAD>(dx, dy, lutq, lut, nb, nb4);
+            packed |= (binned ? bin : (uint32_t)kNoBin) << (8 * p);
+        }
     }
     return packed;
 }

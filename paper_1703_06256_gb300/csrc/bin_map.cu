@@ -15,8 +15,11 @@
 // and issues the next step's loads before computing the current pair, so
 // four quads of loads are in flight per thread.
 //
-// The table lives in shared memory.  The full 511 x 511 table (255.5 KiB)
-// does not fit, so when 4 divides N_b the CTA holds one quadrant only:
+// The table is read through the read-only cache by default: gradients of
+// natural images cluster near (0, 0), so the lines they touch stay in L1,
+// and one lookup is a multiply-add and a load.  On request (and when 4
+// divides N_b) the CTA instead stages one quadrant in shared memory -- the
+// full 511 x 511 table (255.5 KiB) does not fit:
 // (dx, dy) with dx in 1..255, dy in 0..255, 255 x 256 entries, 64 KiB.  A
 // quarter turn (dx, dy) -> (-dy, dx) adds pi/2 to the angle and, because
 // the sectors are half-open and N_b/4 of them span pi/2, adds exactly N_b/4
@@ -24,8 +27,8 @@
 // turns and its bin is (quadrant entry + q * N_b/4) mod N_b.  The quadrant
 // (stored contiguously after the table by hog_build_lut) arrives by one
 // 64 KiB bulk async copy that completes on an mbarrier, while the first
-// quads' pixels are loaded.  For other N_b the kernel reads the table
-// through the read-only cache.
+// quads' pixels are loaded.  That costs a dozen more instructions per pixel
+// (the turn and the wrap-around) than the direct lookup.
 //
 // The grid is persistent (a few CTAs per SM, grid-stride over quads) so
 // that each CTA stages the table once.
@@ -166,8 +169,9 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
 
 hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t pitch, const uint8_t* lut,
                           int n_bins, uint8_t* bins, unsigned int* status, cudaStream_t st) {
-    // the shared-memory quadrant needs 4 | N_b; it is the default here
-    const bool quad = (n_bins % 4 == 0) && tune_get(HOG_TUNE_TABLE) != 2;
+    // the shared-memory quadrant needs 4 | N_b and is taken on request; the
+    // whole table through the read-only cache is the default
+    const bool quad = (n_bins % 4 == 0) && tune_get(HOG_TUNE_TABLE) == 1;
     if (channels == 1)
         return quad ? launch_t<1, true>(img, W, H, pitch, lut, n_bins, bins, status, st)
                     : launch_t<1, false>(img, W, H, pitch, lut, n_bins, bins, status, st);
