@@ -78,8 +78,8 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
     }
     bool lut_ready = !QUAD;
-    pdl_trigger();
     pdl_wait();  // the table copy above reads only the table, built before the path runs
+    pdl_trigger();
 
     const int qpr = (W + 3) >> 2;  // quads per row
     const long row_bytes = (long)W * CH;

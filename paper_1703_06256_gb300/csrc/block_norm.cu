@@ -35,8 +35,8 @@ template <typename CellT>
 __global__ void __launch_bounds__(kWarps * 32)
     block_norm_kernel(const CellT* __restrict__ cells, int ncx, int nb, int r, int nbx, long n_blocks, float eps2,
                       float* __restrict__ blocks) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const long blk = (long)blockIdx.x * kWarps + (threadIdx.x >> 5);
     if (blk >= n_blocks) return;
     const int lane = threadIdx.x & 31;

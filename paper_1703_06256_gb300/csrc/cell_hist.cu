@@ -38,8 +38,8 @@ template <typename InT, typename OutT, int NB>
 __global__ void __launch_bounds__(128)
     cell_hist_kernel(const InT* __restrict__ ii, int W, int H, int nb_rt, int cell, int stride, int ncx, int ncy,
                      OutT* __restrict__ cells) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y;
     if (i >= ncx || j >= ncy) return;
@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     cell_hist_stream_kernel(const InT* __restrict__ ii, int W, int H, int s, int r, int ncx, int ncy, int TJ,
                             OutT* __restrict__ cells) {
     extern __shared__ uint32_t S[];  // [TJ + r][kTI + r][NB + 1]
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int i0 = blockIdx.x * kTI, j0 = blockIdx.y * TJ;
     const int rows = TJ + r, cols = kTI + r;
     const int kmax = ncy - 1 + r, mmax = ncx - 1 + r;  // last sample rows / columns any cell reads

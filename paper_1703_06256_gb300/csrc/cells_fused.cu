@@ -92,8 +92,8 @@ __device__ __forceinline__ bool stage_lut(uint8_t* lutq, const uint8_t* __restri
         ptx::mbar_arrive_expect_tx(bar, kQuadBytes);
         ptx::bulk_g2s(lutq, lut + kLutQuadOffset, kQuadBytes, bar);
     }
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const bool ok = ptx::mbar_wait_bounded(bar, 0, kWaitLimitNs);
     if (!ok && tid == 0) atomicOr(status, kStatusTimeout);
     return ok;
@@ -232,8 +232,8 @@ __device__ __forceinline__ FusedSmem<NB, S>* fused_prologue(uint8_t* smem, const
         if (!stage_lut(smem, lut, bar, status)) return nullptr;
         return reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
     } else {
-        pdl_trigger();
         pdl_wait();
+        pdl_trigger();
         return reinterpret_cast<FusedSmem<NB, S>*>(smem);
     }
 }

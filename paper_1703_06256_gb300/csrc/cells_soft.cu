@@ -32,8 +32,8 @@ constexpr int kMaxNb = 16;
 constexpr int kSoftPitch = HOG_LUT_PITCH;  // entries per table row (511 + 1 pad)
 
 __global__ void __launch_bounds__(256) build_soft_lut_kernel(int nb, int q, uint16_t* __restrict__ lut) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int idx = blockIdx.x * 256 + threadIdx.x;
     if (idx >= kLutSide * kSoftPitch) return;
     const int row = idx / kSoftPitch, col = idx - row * kSoftPitch;
@@ -81,8 +81,8 @@ __global__ void __launch_bounds__(kThreads, 2)
     uint32_t* bh = smem_u;                              // [BYB][BXB][nb] block votes
     uint32_t* g = smem_u + T::BYB * T::BXB * kMaxNb;    // [BYB + 1][BXB + 1][nb] corner integral image
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int tiles_x = (ncx + T::BX - 1) / T::BX, tiles_y = (ncy + T::BY - 1) / T::BY;
     const int bxn = T::BX + r - 1, byn = T::BY + r - 1;
     const long row_bytes = (long)W * CH;

@@ -197,8 +197,8 @@ __global__ void __launch_bounds__(32, 16)
     const Chunks<NCH> ch(g, C::G, W);
     const int y0 = band * h, nrows = min(h, H - y0);
 
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
 
     // col[j][k][m]: counts over the band of bins lo+4m .. lo+4m+3 in column k
     // of chunk j (8-bit fields: a band has at most 32 rows)
@@ -314,8 +314,8 @@ __global__ void __launch_bounds__(kCarryThreads)
     static_assert(kSegments == 16, "the segment scans take half a warp per column");
     __shared__ uint32_t seg_sum[4][32][kSegments + 1];  // [bin of 4][column][segment]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
 
     if ((int)blockIdx.x >= na + nbb) {
         // (c) RL(y) = exclusive prefix over groups of the row counts, in place;
@@ -519,8 +519,8 @@ __global__ void __launch_bounds__(32)
     const int y0 = band * h, nrows = min(h, H - y0);
     const int wins = min(WIN, n_bins - lo);
 
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     stage_rows<NCH>(bins, W, y0, nrows, ch, vec, st);
     // RL of the band's rows: lane r fetches row r
     if (lane < nrows) {

@@ -86,11 +86,14 @@ hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, in
 // ---- programmatic dependent launch
 // Kernels of the detection path launch with programmatic stream
 // serialisation: a kernel may start while its stream predecessor is still
-// finishing.  Every such kernel calls pdl_trigger() first (its own
-// successor may then be scheduled once all of its CTAs are running) and
-// pdl_wait() before it reads its predecessor's results or writes memory an
-// earlier kernel reads; only independent set-up (tables, weights, barriers)
-// runs before the wait.  Under stream capture the dependency becomes a
+// finishing.  Every such kernel calls pdl_wait() before it reads its
+// predecessor's results or writes memory an earlier kernel reads (only
+// independent set-up -- tables, weights, barriers -- runs before it), and
+// pdl_trigger() right after: its successor is then scheduled while it runs,
+// but no further ahead.  Triggering before the wait would let the whole
+// chain of later kernels become resident and wait on the SMs at once, where
+// their shared-memory reservations shrink the L1 cache of the kernel that is
+// actually running.  Under stream capture the dependency becomes a
 // programmatic graph edge.
 template <typename... KArgs, typename... Args>
 hog_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,

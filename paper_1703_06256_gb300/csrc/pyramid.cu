@@ -19,8 +19,8 @@ struct LevelTable {
 template <int CH>
 __global__ void __launch_bounds__(256)
     pyramid_kernel(const uint8_t* __restrict__ img, size_t pitch, int levels, LevelTable t, uint8_t* __restrict__ out) {
-    pdl_trigger();
     pdl_wait();
+    pdl_trigger();
     const int x = blockIdx.x * 32 + (threadIdx.x & 31);
     const int y = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (x >= t.W[1] || y >= t.H[1]) return;
