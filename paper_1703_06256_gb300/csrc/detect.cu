@@ -33,8 +33,8 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
     detect_count_kernel(const T* __restrict__ scores, long n, float thr_f, int thr_i, int* __restrict__ tile_count) {
     __shared__ int red[kThreads / 32];
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
     const int c = detect::tile_count<T>(scores, n, blockIdx.x, thr_f, thr_i, red);
     if (threadIdx.x == 0) tile_count[blockIdx.x] = c;
 }
@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(kThreads)
     __shared__ int red[kThreads / 32];
     __shared__ int wsum[kThreads / 32];
     __shared__ uint32_t stage[kTile * kDetWords];
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
     // detections in the tiles before this one: scanned offsets, or the sum of the counts before
     int before = 0;
     if (tile_off != nullptr) {
@@ -74,8 +74,8 @@ constexpr int kScanAbove = 2048;  // tiles
 __global__ void __launch_bounds__(kScanThreads)
     detect_scan_kernel(const int* __restrict__ tile_count, int n_tiles, int* __restrict__ tile_off) {
     __shared__ int wsum[kScanThreads / 32];
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
     const int t0 = min(tid * per, n_tiles), t1 = min(t0 + per, n_tiles);

@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(kThreads)
     detect_count_batch_kernel(const PlanItem* __restrict__ items, int n_items, float thr_f, int thr_i,
                               int* __restrict__ tile_count) {
     __shared__ int red[kThreads / 32];
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
     const int t = blockIdx.x;
     const PlanItem* it = items + find_item<Stage::kDetect>(items, n_items, t);
     const long n = (long)it->nx * it->ny;
@@ -48,8 +48,8 @@ __global__ void __launch_bounds__(kScanThreads)
                              int* __restrict__ item_counts) {
     __shared__ int wsum[kScanThreads / 32];
     __shared__ int total_s;
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int per = (n_tiles + kScanThreads - 1) / kScanThreads;
     const int t0 = min(tid * per, n_tiles), t1 = min(t0 + per, n_tiles);
@@ -100,8 +100,8 @@ __global__ void __launch_bounds__(kThreads)
                                 const int* __restrict__ tile_off, hog_det* __restrict__ out, int max_out) {
     __shared__ int wsum[kThreads / 32];
     __shared__ uint32_t stage[kTile * kDetWords];
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
     const int t = blockIdx.x;
     const PlanItem* it = items + find_item<Stage::kDetect>(items, n_items, t);
     const int nx = it->nx;

@@ -93,8 +93,10 @@ hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, in
 // but no further ahead.  Triggering before the wait would let the whole
 // chain of later kernels become resident and wait on the SMs at once, where
 // their shared-memory reservations shrink the L1 cache of the kernel that is
-// actually running.  Under stream capture the dependency becomes a
-// programmatic graph edge.
+// actually running.  The score and detection kernels at the tail of the
+// path trigger before they wait: what follows them is small, and launching
+// it early hides its launch latency.  Under stream capture the dependency
+// becomes a programmatic graph edge.
 template <typename... KArgs, typename... Args>
 hog_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                       Args&&... args) {

@@ -86,8 +86,8 @@ __global__ void __launch_bounds__(kTX* TY)
     float4* c_s = smem4 + K4;     // [rh][nb4][rw]
     const int tid = threadIdx.y * kTX + threadIdx.x;
     const int px0 = blockIdx.x * kTX, py0 = blockIdx.y * TY;
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();
-    pdl_trigger();
 
     // weights, padded per cell to nb4 float4s
     for (int i = tid; i < K4 * 4; i += kTX * TY) {

@@ -108,8 +108,8 @@ __global__ void __launch_bounds__(kThreads, 3)
     for (int i = 0; i < kCX; ++i)
 #pragma unroll
         for (int b = 0; b < kNB; ++b) wr[i][b] = wval<WT>(w, (j * kCX + i) * kNB + b);
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();  // the weights above are inputs of the call, not of a predecessor
-    pdl_trigger();
 
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int s = item % S, rblk = item / S;

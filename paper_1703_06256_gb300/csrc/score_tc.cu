@@ -331,8 +331,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();  // set-up above read only the weights; the cell rows come from the predecessor
-    pdl_trigger();
 
     const int n_stage_loads = (G.rows + kRowsPerStage - 1) / kRowsPerStage;
     const int valid_cells = min(G.row_cells, ncx - px0);  // > 0: px0 < nx <= ncx
