@@ -151,6 +151,104 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     }
 }
 
+// Persistent, double-buffered form of the streaming kernel, for tiles whose
+// (TJ + r) x N_b sample lines fit one batch of loads per warp (kWarps x
+// kLines): a CTA walks tiles with the grid's stride, and while it forms the
+// cells of one tile from shared memory, the loads of its next tile are
+// already in flight into registers; they are parked in the other buffer
+// after the cells are written.  One barrier per tile.
+constexpr int kPipeLines = 8;  // lines per warp and tile
+
+template <typename InT, typename OutT, int NB>
+__global__ void __launch_bounds__(kStreamThreads, 4)
+    cell_hist_pipe_kernel(const InT* __restrict__ ii, int W, int H, int s, int r, int ncx, int ncy, int TJ, int n_tx,
+                          int n_tiles, OutT* __restrict__ cells) {
+    extern __shared__ uint32_t S[];  // 2 x [TJ + r][kTI + r][NB + 1]
+    pdl_wait();
+    pdl_trigger();
+    constexpr int kWarps = kStreamThreads / 32, kPerLane = 3;
+    const int rows = TJ + r, cols = kTI + r, nlines = rows * NB;
+    const size_t bufw = (size_t)rows * cols * (NB + 1);
+    const int kmax = ncy - 1 + r, mmax = ncx - 1 + r;  // last sample rows / columns any cell reads
+    const size_t plane = (size_t)W * H;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t v[kPipeLines][kPerLane];
+    // each thread forms the cells of bin b_out in kParts columns, kStreamThreads / NB apart
+    constexpr int kColStep = kStreamThreads / NB, kParts = kTI / kColStep;
+    static_assert((NB & (NB - 1)) == 0 && kParts * kColStep == kTI, "the column split must cover the tile");
+    // loads of tile t's samples: warp w takes lines w * kPipeLines .. + kPipeLines - 1,
+    // lane l the samples l, l + 32, l + 64 of each line
+    auto issue = [&](int t) {
+        const int i0 = (t % n_tx) * kTI, j0 = (t / n_tx) * TJ;
+        int off[kPerLane];
+        bool colok[kPerLane];
+#pragma unroll
+        for (int u = 0; u < kPerLane; ++u) {
+            const int mm = lane + 32 * u, m = i0 + mm;
+            colok[u] = mm < cols && m > 0 && m <= mmax;
+            off[u] = s * m - 1;
+        }
+#pragma unroll
+        for (int q = 0; q < kPipeLines; ++q) {
+            const int line = warp * kPipeLines + q;
+            const int kk = line / NB, b = line & (NB - 1);
+            const int k = j0 + kk;
+            const bool row_ok = line < nlines && k > 0 && k <= kmax;
+            const InT* row = ii + (size_t)b * plane + (size_t)(s * k - 1) * W;
+#pragma unroll
+            for (int u = 0; u < kPerLane; ++u) v[q][u] = (row_ok && colok[u]) ? (uint32_t)__ldg(row + off[u]) : 0u;
+        }
+    };
+    auto park = [&](uint32_t* buf) {
+#pragma unroll
+        for (int q = 0; q < kPipeLines; ++q) {
+            const int line = warp * kPipeLines + q;
+            if (line >= nlines) break;
+            const int kk = line / NB, b = line & (NB - 1);
+            uint32_t* dst = buf + (size_t)kk * cols * (NB + 1) + b;
+#pragma unroll
+            for (int u = 0; u < kPerLane; ++u) {
+                const int mm = lane + 32 * u;
+                if (mm < cols) dst[mm * (NB + 1)] = v[q][u];
+            }
+        }
+    };
+    // this thread's cells: bin b_out, columns ci_out + h * kColStep of every cell row
+    const int b_out = threadIdx.x & (NB - 1), ci_out = threadIdx.x / NB;
+    int t = blockIdx.x;
+    if (t >= n_tiles) return;
+    issue(t);
+    park(S);
+    __syncthreads();
+    int cur = 0;
+    for (; t < n_tiles; t += gridDim.x) {
+        const int tn = t + gridDim.x;
+        if (tn < n_tiles) issue(tn);
+        const uint32_t* B = S + cur * bufw;
+        const int i0 = (t % n_tx) * kTI, j0 = (t / n_tx) * TJ;
+#pragma unroll
+        for (int h = 0; h < kParts; ++h) {
+            const int ci = ci_out + h * kColStep, i = i0 + ci;
+            if (i >= ncx) continue;
+            // samples (cj, ci), (cj, ci + r), (cj + r, ci), (cj + r, ci + r) of bin b_out
+            const uint32_t* top = B + (size_t)ci * (NB + 1) + b_out;
+            const int rstep = cols * (NB + 1);
+            OutT* out = cells + ((size_t)j0 * ncx + i) * NB + b_out;
+            for (int cj = 0; cj < TJ && j0 + cj < ncy; ++cj, top += rstep, out += (size_t)ncx * NB) {
+                const uint32_t d = top[0], bb = top[r * (NB + 1)];
+                const uint32_t c = top[r * rstep], a = top[r * rstep + r * (NB + 1)];
+                uint32_t val = (a + d) - (bb + c);
+                if (sizeof(InT) == 2) val &= 0xFFFFu;
+                *out = count_as<OutT>(val);
+            }
+        }
+        // the other buffer was last read before the previous barrier
+        if (tn < n_tiles) park(S + (cur ^ 1) * bufw);
+        __syncthreads();
+        cur ^= 1;
+    }
+}
+
 // Rows of cells per streaming CTA: the tuned value (1 = the per-cell kernel),
 // else 4 (measured best or tied among 4, 8 and 16 from 800x600 to 3840x2160).
 int stream_rows(int ncx, int ncy) {
@@ -163,6 +261,17 @@ int stream_rows(int ncx, int ncy) {
 template <typename InT, typename OutT, int NB>
 hog_status launch_stream(const void* ii, int W, int H, int stride, int r, int ncx, int ncy, int TJ, void* cells,
                          cudaStream_t st) {
+    if ((TJ + r) * NB <= (kStreamThreads / 32) * kPipeLines) {
+        const size_t smem = 2 * sizeof(uint32_t) * (size_t)(TJ + r) * (kTI + r) * (NB + 1);
+        auto kern = cell_hist_pipe_kernel<InT, OutT, NB>;
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const int n_tx = ceil_div(ncx, kTI);
+        const int n_tiles = n_tx * ceil_div(ncy, TJ);
+        const int grid = n_tiles < 4 * sm_count() ? n_tiles : 4 * sm_count();
+        return launch_pdl(kern, dim3(grid), dim3(kStreamThreads), smem, st, static_cast<const InT*>(ii), W, H, stride,
+                          r, ncx, ncy, TJ, n_tx, n_tiles, static_cast<OutT*>(cells));
+    }
     const size_t smem = sizeof(uint32_t) * (size_t)(TJ + r) * (kTI + r) * (NB + 1);
     auto kern = cell_hist_stream_kernel<InT, OutT, NB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
