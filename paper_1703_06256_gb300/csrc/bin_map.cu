@@ -153,8 +153,10 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
         if (e != cudaSuccess) return cuda_fail(e);
     }
     const long n_quads = (long)((W + 3) / 4) * H;
-    // at least 4 quads per thread, so each staged table copy serves a fair share of pixels
-    const long need = (n_quads + 4 * kThreads - 1) / (4 * kThreads);
+    // at least one step (2 quads) per thread; with a staged table copy, 4 quads,
+    // so that each copy serves a fair share of pixels
+    const int qpt = QUAD ? 4 : 2;
+    const long need = (n_quads + qpt * kThreads - 1) / (qpt * kThreads);
     const int per_sm = tune_get(HOG_TUNE_BINMAP_CTAS_PER_SM);
     // three CTAs per SM are resident (registers; with the quadrant, shared memory too)
     const long cap = (long)sm_count() * (per_sm > 0 ? per_sm : 3);
