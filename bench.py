@@ -746,6 +746,10 @@ def main():
     launches_per_step = 1 + 3 * ((nb + 15) // 16) + 1 + 1 + (2 if windows > 2048 else 1)
     status = fh.hog_device_status()
     autotune.reset()  # the extras below run with the library's own launch shapes
+    # the serving comparison runs right after the main measurement, before the heavier extras,
+    # so that both of its paths see the GPU in the state the main step saw
+    serving_res = (serving(torch, wl, args) if "serving" in extras and world == 1 and args.serve_requests > 0
+                   else None)
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
@@ -779,8 +783,7 @@ def main():
                          else None),
         "blocks": blocks_variant(torch, fh, wl, flush, args) if "blocks" in extras else None,
         "soft": soft_variant(torch, fh, wl, flush, args) if "soft" in extras else None,
-        "serving": (serving(torch, wl, args) if "serving" in extras and world == 1 and args.serve_requests > 0
-                    else None),
+        "serving": serving_res,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(img, c, args.cpu_seconds)
