@@ -64,8 +64,6 @@ int tune_get(int knob) {
     return knob >= 0 && knob < HOG_TUNE_KNOBS ? g_tune[knob].load(std::memory_order_relaxed) : 0;
 }
 
-static int n_pos(int extent, int box, int stride) { return extent < box ? 0 : (extent - box) / stride + 1; }
-
 static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 65535 && H <= 65535 && (long)W * H < (1L << 31); }
 
 }  // namespace fasthog

@@ -10,8 +10,6 @@ using namespace fasthog;
 
 namespace {
 
-int n_pos(int extent, int box, int stride) { return extent < box ? 0 : (extent - box) / stride + 1; }
-
 // The host copy of a plan, if it is one.
 const PlanHeader* checked_plan(const void* plan) {
     if (plan == nullptr || reinterpret_cast<uintptr_t>(plan) % 8 != 0) return nullptr;

@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     extern __shared__ uint32_t S[];  // 2 x [TJ + r][kTI + r][NB + 1]
     pdl_wait();
     pdl_trigger();
-    constexpr int kWarps = kStreamThreads / 32, kPerLane = 3;
+    constexpr int kPerLane = 3;
     const int rows = TJ + r, cols = kTI + r, nlines = rows * NB;
     const size_t bufw = (size_t)rows * cols * (NB + 1);
     const int kmax = ncy - 1 + r, mmax = ncx - 1 + r;  // last sample rows / columns any cell reads

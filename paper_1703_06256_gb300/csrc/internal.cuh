@@ -127,5 +127,7 @@ __device__ __forceinline__ float bf16_to_f32(uint16_t h) {
 }
 
 inline int ceil_div(long a, long b) { return static_cast<int>((a + b - 1) / b); }
+// Positions of a box of `box` pixels stepped by `stride` along `extent` pixels.
+inline int n_pos(int extent, int box, int stride) { return extent < box ? 0 : (extent - box) / stride + 1; }
 
 }  // namespace fasthog
