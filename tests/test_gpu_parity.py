@@ -141,6 +141,23 @@ def test_integral_uint16_modular(fh, g, nb):
         assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16), (ref & 0xFFFF).astype(np.uint16)), (H, W)
 
 
+@pytest.mark.parametrize("h", [4, 8, 16, 32])
+def test_integral_band_heights(fh, g, h):
+    """Every band height of the tiled scan (HOG_TUNE_INTEGRAL_BAND_ROWS), int32
+    and uint16, one window of bins and several (N_b = 20, 64): the tiles, the
+    carries between bands and groups, and partial bands at the bottom."""
+    fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_BAND_ROWS, h)
+    try:
+        for i, (H, W, nb) in enumerate([(600, 800, 8), (301, 6, 8), (70, 300, 20), (33, 1025, 64), (97, 130, 3),
+                                        (1000, 257, 16)]):
+            bins = oracle_bins(H, W, nb, 1000 * h + i)
+            ref = oracle.integral(bins, nb)
+            assert np.array_equal(g.gpu_integral(bins, nb), ref), (h, H, W, nb)
+            assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16), (ref & 0xFFFF).astype(np.uint16)), (h, H, W, nb)
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_BAND_ROWS, 0)
+
+
 def test_integral_workload_bins(fh, g):
     img = wl.config1()["images"][0]
     bins = oracle.bin_map(img, 8)
