@@ -15,15 +15,16 @@
 //
 // Per tile of BX x BY cells (origins), a CTA of 512 threads
 //   1. computes the bins of the tile's (BX + r - 1) x (BY + r - 1) blocks with
-//      the same quad code and shared-memory table quadrant as the bin-map
-//      kernel, one quad (4 pixels of a row) per task, and adds them into
+//      the same quad code and table lookup as the bin-map kernel (the whole
+//      table through the read-only cache, or on request a quadrant staged in
+//      shared memory), one quad (4 pixels of a row) per task, and adds them into
 //      per-block counters (8-bit fields, s^2 <= 64 for s = 4, 8) with
 //      shared-memory atomics;
 //   2. forms G over those blocks in shared memory (16-bit fields): warp
 //      scans along block rows, then running sums down the columns;
 //   3. writes each cell's histogram from four corners of G (16-byte stores).
 // Tiles overlap by r - 1 blocks, whose bins are computed twice.  The grid is
-// persistent so that each CTA stages the table quadrant once.
+// persistent, so a staged table quadrant is copied once per CTA.
 #include <type_traits>
 
 #include "batch_plan.cuh"
