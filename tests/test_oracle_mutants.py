@@ -46,6 +46,12 @@ MUTANTS = [
     ("soft_votes_swapped", "v[k0] += q - a;", "v[k0] += a;"),
     ("soft_centre_shift", "double t = phi * (double)nb / ORACLE_TWO_PI - 0.5;",
      "double t = phi * (double)nb / ORACLE_TWO_PI;"),
+    ("channel_by_l1_norm", "long mag = (long)dx * dx + (long)dy * dy;",
+     "long mag = (long)(dx < 0 ? -dx : dx) + (dy < 0 ? -dy : dy);"),
+    ("block_cells_transposed", "int ci = i + (q & 1) * r, cj = j + (q >> 1) * r;",
+     "int ci = i + (q >> 1) * r, cj = j + (q & 1) * r;"),
+    ("detect_drops_stride", "xs[n] = px * stride;", "xs[n] = px;"),
+    ("soft_vote_truncated", "int a = (int)floor(x + 0.5);", "int a = (int)floor(x);"),
 ]
 
 

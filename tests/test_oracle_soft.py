@@ -2,6 +2,7 @@
 forms on the axes and diagonals, agreement of the larger vote with the exact
 hard bin over the whole table, quarter-turn symmetry, a certified distance
 from rounding ties (so any correctly rounded atan2 gives the same table),
+the vote as the rounded linear interpolation weight over the whole table,
 unit mass per pixel, and cells through weighted integral images (Eq. 5,
 Eq. 6) equal to direct sums."""
 
@@ -47,6 +48,33 @@ def test_larger_vote_is_the_hard_bin(oracle_mod, nb):
     tie = a * 2 == q
     assert np.all(hard[ok & ~tie] == big[ok & ~tie])
     assert np.all((hard[ok & tie] == k0[ok & tie]) | (hard[ok & tie] == (k0[ok & tie] + 1) % nb))
+
+
+@pytest.mark.parametrize("nb", [8, 9, 16])
+def test_vote_is_the_rounded_interpolation_weight(oracle_mod, nb):
+    """The vote for the upper of the two flanking bins is the linear
+    interpolation weight between their centres, in units of 1/q, rounded to
+    the nearest unit: within 1/2 of q times the weight, for every gradient of
+    the table.  The angle here comes from numpy's arctan2, independently of the
+    oracle's libm call; the certified tie margin keeps the two from rounding
+    differently."""
+    soft, _ = oracle_mod.soft_lut(nb)
+    q = oracle_mod.SOFT_Q
+    dy, dx = np.mgrid[-255:256, -255:256]
+    ok = (dx != 0) | (dy != 0)
+    phi = np.mod(np.arctan2(dy, dx), 2 * np.pi)
+    t = phi * nb / (2 * np.pi) - 0.5
+    fl = np.floor(t)
+    w = q * (t - fl)  # q times the weight of the upper bin
+    k0 = (soft & 0xFF).astype(np.int64)
+    a = (soft >> 8).astype(np.int64)
+    lower = np.mod(fl, nb).astype(np.int64)
+    # a vote of q for the upper bin is written as 0 for the next pair of bins
+    wraps = ok & (np.abs(w - q) <= 0.5)
+    plain = ok & ~wraps
+    assert np.all(np.abs(a[plain] - w[plain]) <= 0.5)
+    assert np.all(k0[plain] == lower[plain])
+    assert np.all((a[wraps] == 0) & (k0[wraps] == (lower[wraps] + 1) % nb))
 
 
 @pytest.mark.parametrize("nb", [4, 8, 16])
