@@ -52,6 +52,16 @@ MUTANTS = [
      "int ci = i + (q >> 1) * r, cj = j + (q & 1) * r;"),
     ("detect_drops_stride", "xs[n] = px * stride;", "xs[n] = px;"),
     ("soft_vote_truncated", "int a = (int)floor(x + 0.5);", "int a = (int)floor(x);"),
+    ("plus_x_ray_in_lower_half", "static int in_upper_half(int dx, int dy) { return dy > 0 || (dy == 0 && dx > 0); }",
+     "static int in_upper_half(int dx, int dy) { return dy > 0; }"),
+    ("boundary_cross_sign_flipped", "long cr = c * dy - s * dx;", "long cr = s * dx - c * dy;"),
+    ("integral_row_sum_not_reset", "for (int y = 0; y < H; ++y) {\n            int32_t row = 0;",
+     "int32_t row = 0;\n        for (int y = 0; y < H; ++y) {"),
+    ("corner3_off_by_one", "long v3 = ii_at(ii, W, H, b, x0 - 1, y1);", "long v3 = ii_at(ii, W, H, b, x0, y1);"),
+    ("window_cells_unit_step_x", "(double)cells[((long)(py + j * r) * ncx + (px + i * r)) * nb + b];",
+     "(double)cells[((long)(py + j * r) * ncx + (px + i)) * nb + b];"),
+    ("window_cells_unit_step_y", "(double)cells[((long)(py + j * r) * ncx + (px + i * r)) * nb + b];",
+     "(double)cells[((long)(py + j) * ncx + (px + i * r)) * nb + b];"),
 ]
 
 
