@@ -161,25 +161,64 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_images(img, c, threads: int, per_thread: int):
+    """`threads` host threads each run the C oracle on `per_thread` whole
+    images (ctypes releases the GIL for the duration of each C call, so the
+    threads run on separate cores); returns the wall time."""
+    import concurrent.futures as cf
+
+    import oracle
+
+    def work(_):
+        for _ in range(per_thread):
+            oracle.pipeline(img, c["n_bins"], c["w"], c["bias"], c["stride"], c["thr"])
+
+    t0 = time.perf_counter()
+    if threads == 1:
+        work(0)
+    else:
+        with cf.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(work, range(threads)))
+    return time.perf_counter() - t0
+
+
 def cpu_baseline(img, c, seconds):
-    """The oracle as it stands, single-threaded C, on whole 800x600 images."""
+    """The oracle as it stands (plain FP64 C) on whole 800x600 images: one
+    host thread, then one thread per host core (images spread over the
+    threads).  Each leg runs for about `seconds` / 2."""
     import oracle
 
     oracle.build()
     px = img.shape[0] * img.shape[1]
-    n, t0 = 0, time.perf_counter()
-    while True:
-        oracle.pipeline(img, c["n_bins"], c["w"], c["bias"], c["stride"], c["thr"])
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
-            break
-    return {"value": round(px * n / el / 1e6, 3), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full 800x600 images through the FP64 oracle (bins, ii, Eq. 6 histograms, "
-                      f"scores, list) in {el:.1f} s"}
+    legs = {}
+    cores = host_cores()
+    for threads in (1, cores):
+        oracle_images(img, c, threads, 1)  # warm-up: every thread's first image
+        # size the sample from one timed round, then time the sample
+        t1 = oracle_images(img, c, threads, 1)
+        per = max(1, int(seconds / 2 / max(t1, 1e-3)))
+        el = oracle_images(img, c, threads, per)
+        n = per * threads
+        legs[threads] = {"value": round(px * n / el / 1e6, 3), "unit": "Mpixel/s", "cores": threads,
+                         "images": n, "seconds": round(el, 2)}
+    top = legs[cores]
+    return {"value": top["value"], "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{top['images']} full 800x600 images through the FP64 C oracle (bins, ii, Eq. 6 "
+                       f"histograms, scores, list), one image per thread at a time on {cores} host threads, "
+                       f"in {top['seconds']} s"),
+            "single_thread": dict(legs[1], sample=f"{legs[1]['images']} images on one thread")}
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle, the only other implementation of
+    this method, on every host core (one 800x600 image per thread per step)."""
     if rank != 0:
         return
     import workloads as wl
@@ -189,23 +228,38 @@ def run_reference(args, rank, world):
     import oracle
 
     oracle.build()
+    cores = host_cores()
     for _ in range(args.warmup):
-        oracle.pipeline(img, c["n_bins"], c["w"], c["bias"], c["stride"], c["thr"])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.pipeline(img, c["n_bins"], c["w"], c["bias"], c["stride"], c["thr"])
-    el = time.perf_counter() - t0
-    px = img.shape[0] * img.shape[1]
+        oracle_images(img, c, cores, 1)
+    el = sum(oracle_images(img, c, cores, 1) for _ in range(args.steps))
+    px = img.shape[0] * img.shape[1] * cores
     value = px * args.steps / el / 1e6
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD},
-        "cpu_baseline": {"value": round(value, 3), "unit": "Mpixel/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full 800x600 images, one per step, single-threaded C oracle"},
+        "cpu_baseline": {"value": round(value, 3), "unit": "Mpixel/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps of {cores} full 800x600 images, one per host thread, "
+                                   "FP64 C oracle"},
         "e2e": {"value": round(value, 3), "unit": "Mpixel/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
+
+
+def algorithmic_bytes(W, H, nb, ncx, ncy, windows):
+    """Bytes each stage must move (RGB image, int32 integral images, int32
+    cells, f32 scores): the figures the rooflines divide by."""
+    px = W * H
+    return {
+        "bin_map": px * (3 + 1),              # RGB in, bins out
+        "integral": px * (1 + 4 * nb),        # bins in, int32 planes out
+        # Eq. 6 per cell position and bin: one integral-image sample in (each
+        # sample of the stride grid is a corner of up to four cells, read once)
+        # and one int32 count out
+        "cell_hist": ncx * ncy * nb * (4 + 4),
+        "score": ncx * ncy * nb * 4 + windows * 4,  # cell map in, score out
+        "detect": windows * 4,
+    }
 
 
 def graph_step(torch, fns, between: bool):
@@ -519,14 +573,15 @@ def stage_rooflines(torch, fh, wl, flush, args, hbm):
     ms = [m / steps for m in ms]
     px, nb = W * H, 8
     windows = p.nx * p.ny
-    alg = {"bin_map": px * (3 + 1), "integral": px * (1 + 4 * nb),
-           "cell_hist": p.ncx * p.ncy * nb * (4 * 4 + 4), "score": p.ncx * p.ncy * nb * 4 + windows * 4,
-           "detect": windows * 4}
+    alg = algorithmic_bytes(W, H, nb, p.ncx, p.ncy, windows)
     out = {"workload": "3840x2160 RGB, N_b=8, stride 4, int32 integral images, int32 cells, f32 weights",
            "peak_gbs": hbm}
     for n, t in zip(names, ms):
         gbs = alg[n] / (t * 1e-3) / 1e9
-        out[n] = {"ms": round(t, 5), "algorithmic_bytes": alg[n], "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4)}
+        traffic = profiled_traffic(n, f"{W}x{H}")
+        out[n] = {"ms": round(t, 5), "algorithmic_bytes": alg[n], "gbs": round(gbs, 1), "frac": round(gbs / hbm, 4),
+                  "dram_bytes": traffic,
+                  "dram_over_algorithmic": round(traffic / alg[n], 3) if traffic else None}
     del p
     torch.cuda.empty_cache()
     return out
@@ -733,13 +788,7 @@ def main():
     stage_avg = {k: v / args.steps for k, v in stage_ms.items()}
     dom = max(stage_avg, key=stage_avg.get)
     nb = c["n_bins"]
-    alg_bytes = {
-        "bin_map": px * (3 + 1),                       # RGB in, bins out
-        "integral": px * (1 + 4 * nb),                 # bins in, int32 planes out
-        "cell_hist": pipe.ncx * pipe.ncy * nb * (4 * 4 + 4),  # 4 corners in, int32 count out, per bin
-        "score": pipe.ncx * pipe.ncy * nb * 4 + windows * 4,  # cell map in, score out
-        "detect": windows * 4,
-    }
+    alg_bytes = algorithmic_bytes(W, H, nb, pipe.ncx, pipe.ncy, windows)
     hbm, src = peaks()
     achieved = alg_bytes[dom] / (stage_avg[dom] * 1e-3) / 1e9
     # bin map 1, integral 3 per 16-bin window, cell hist 1, score 1, detect 1 (+1 past one 2048-score tile)

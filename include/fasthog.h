@@ -96,6 +96,24 @@ int hog_version(void);
 hog_status hog_device_status(uint32_t* flags, int clear);
 
 /*
+ * hog_selftest_wait_timeout -- makes one of the library's bounded device-side
+ * waits run out, so that the timeout path can be tested without faulting or
+ * hanging the GPU.  The paper has no counterpart.
+ *
+ * One CTA of 32 threads waits, for at most limit_us microseconds
+ * (1 .. 1,000,000), on something that nothing will ever provide:
+ *   mode 0: phase 0 of a shared-memory mbarrier that no thread arrives at (the
+ *           wait of the bin-map, fused-cells and tensor-core kernels), with no
+ *           bulk copy or MMA in flight;
+ *   mode 1: a flag in device memory that no CTA raises (the wait of the
+ *           single-pass integral and detection kernels).
+ * The wait gives up, the kernel sets HOG_STATUS_TIMEOUT in the device status
+ * word (read it with hog_device_status) and returns; the context stays usable.
+ * Other arguments: HOG_ERR_ARG.
+ */
+hog_status hog_selftest_wait_timeout(int mode, int limit_us, hog_stream_t stream);
+
+/*
  * hog_build_lut -- the 511 x 511 gradient lookup table (paper Section 2).
  *
  * For every (dx, dy) in [-255, 255]^2 (the paper's "-225" is read as -255,
@@ -148,7 +166,13 @@ hog_status hog_bin_map(const uint8_t* img, int W, int H, int channels, size_t pi
  *              Section 4), whatever the image size.
  *   ii         out: n_bins planes of H * W entries, [n][y][x]
  *   workspace  scratch of at least hog_integral_workspace_bytes(W, H, n_bins)
- *              bytes; contents on entry are ignored, on exit undefined.
+ *              bytes, 256-byte aligned, ZERO-FILLED before its first use with
+ *              an image size W x H (e.g. cudaMemsetAsync at allocation).  Calls
+ *              with that size (any n_bins, ii_dtype or schedule) then reuse it
+ *              without clearing: every call leaves it ready for the next.
+ *              Zero-fill it again before a call with another W or H (the
+ *              single-pass schedule keeps a tag word and one flag per tile at
+ *              its start, and where the flags end depends on the size).
  *              Calls that overlap on the device must not share a workspace.
  */
 size_t hog_integral_workspace_bytes(int W, int H, int n_bins);
@@ -218,7 +242,13 @@ hog_status hog_cell_hist_fused(const uint8_t* img, int W, int H, int channels, s
  *                      HOG_F32  -> FP32 arithmetic on CUDA cores, scores f32
  *                      HOG_BF16 -> bf16 x bf16 -> f32, scores f32
  *                      HOG_I8   -> exact; scores int32 (the bias is rounded to
- *                                  the nearest integer)
+ *                                  the nearest integer).  Exactness needs every
+ *                                  partial sum below 2^24, which holds for cells of
+ *                                  hard-vote counts (at most cell^2 per cell over
+ *                                  its bins) when 127 * cells_x * cells_y * cell^2
+ *                                  + |round(bias)| < 2^24; otherwise the call
+ *                                  returns HOG_ERR_UNSUPPORTED (e.g. cell = 64
+ *                                  with an 8 x 16-cell window)
  *                      All three run on the tensor cores (tcgen05) for
  *                      16-byte-aligned HOG_BF16 cells, n_bins 8 or 16, an
  *                      8 x 16-cell window and r = 1, 2 or 4 (f32 weights as
@@ -314,7 +344,13 @@ hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, in
  *                        the device's address space (the list is written with
  *                        plain coalesced stores, no atomics); out 4-byte aligned
  *   workspace            at least hog_detect_workspace_bytes(nx, ny) bytes of
- *                        scratch; contents ignored on entry
+ *                        scratch, 8-byte aligned, ZERO-FILLED before its first
+ *                        use (e.g. cudaMemsetAsync once at allocation); every
+ *                        call leaves it ready for the next, so it is never
+ *                        cleared again.  The single launch's tiles publish
+ *                        their counts in it (a tag word of the last call and one
+ *                        status word per 2048 scores).  Calls that overlap on
+ *                        the device must not share a workspace.
  */
 size_t hog_detect_workspace_bytes(int nx, int ny);
 hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
@@ -331,8 +367,10 @@ hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int s
  * cudaMalloc.  It computes exactly what hog_detect computes (same arguments
  * minus the workspace) and allocates nothing.
  *
- * Its scratch is a fixed 64 KiB array inside the library's device memory,
- * which every GPU that loads the library holds until the process exits.
+ * Its scratch is a fixed array of 128 KiB + 64 bytes inside the library's
+ * device memory, which every GPU that loads the library holds until the
+ * process exits.  It is zero-filled when the library is loaded and every
+ * call leaves it ready for the next: nothing has to be cleared.
  * Limits and rules:
  *  - nx * ny <= HOG_DETECT_NOALLOC_MAX_SCORES, otherwise HOG_ERR_ARG and
  *    nothing is enqueued;
@@ -361,7 +399,14 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *
  *   HOG_TUNE_INTEGRAL_BAND_ROWS   rows per tile of the integral-image scan:
  *                                 4, 8, 16 or 32 (hog_integral_workspace_bytes
- *                                 covers every choice)
+ *                                 covers every choice); on the single pass 32
+ *                                 picks tiles of 32 rows, any other value 16
+ *   HOG_TUNE_INTEGRAL_PATH        the integral images' schedule: 1 = three
+ *                                 launches (tile reduce, carries, tile scan),
+ *                                 2 = one single-pass launch (each tile sums the
+ *                                 aggregates of the tiles above and to its left);
+ *                                 the library's choice is the single pass up to
+ *                                 about 2048 x 1152 pixels
  *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
  *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 16 or 32
@@ -399,7 +444,8 @@ typedef enum {
     HOG_TUNE_CELL_ROWS = 5,
     HOG_TUNE_SCORE_PATH = 6,
     HOG_TUNE_SLIDE_WINDOWS = 7,
-    HOG_TUNE_KNOBS = 8
+    HOG_TUNE_INTEGRAL_PATH = 8,
+    HOG_TUNE_KNOBS = 9
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

@@ -182,9 +182,9 @@ def cell_hist_ii(ii: np.ndarray, n_bins: int, cell: int = 8, stride: int = 8) ->
 
 def window_score_multi(cells: np.ndarray, w: np.ndarray, biases, cells_x: int = 8, cells_y: int = 16,
                        cell: int = 8, stride: int = 8) -> np.ndarray:
-    """Several linear filters over the same windows (the scope table's
-    multiple-filter variant): `w` is [F][cells_y * cells_x * nb], `biases`
-    [F]; returns [F][ny][nx], filter f being window_score with w[f], bias f."""
+    """Several independent linear filters scored over the same windows (the
+    paper scores one): `w` is [F][cells_y * cells_x * nb], `biases` [F];
+    returns [F][ny][nx], filter f being window_score with w[f], bias f."""
     w = np.asarray(w)
     return np.stack([window_score(cells, w[f], float(biases[f]), cells_x, cells_y, cell, stride)
                      for f in range(w.shape[0])])

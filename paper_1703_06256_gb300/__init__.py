@@ -31,7 +31,8 @@ HOG_STATUS_TIMEOUT = 1
 HOG_SOFT_Q = 64
 HOG_SOFT_LUT_BYTES = HOG_LUT_SIDE * HOG_LUT_PITCH * 2
 (HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_FUSED_CTAS_PER_SM,
- HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_TABLE, HOG_TUNE_CELL_ROWS, HOG_TUNE_SCORE_PATH, HOG_TUNE_SLIDE_WINDOWS) = range(8)
+ HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_TABLE, HOG_TUNE_CELL_ROWS, HOG_TUNE_SCORE_PATH, HOG_TUNE_SLIDE_WINDOWS,
+ HOG_TUNE_INTEGRAL_PATH) = range(9)
 
 TORCH_DTYPE = {HOG_U8: torch.uint8, HOG_I32: torch.int32, HOG_BF16: torch.bfloat16, HOG_F32: torch.float32,
                HOG_I8: torch.int8, HOG_U16: torch.uint16 if hasattr(torch, "uint16") else torch.int16}
@@ -89,6 +90,7 @@ def _load() -> ctypes.CDLL:
         "hog_last_cuda_error": (I, []),
         "hog_version": (I, []),
         "hog_device_status": (I, [P, I]),
+        "hog_selftest_wait_timeout": (I, [I, I, P]),
         "hog_build_lut": (I, [I, P, P]),
         "hog_bin_map": (I, [P, I, I, I, Z, P, I, P, P]),
         "hog_integral_workspace_bytes": (Z, [I, I, I]),
@@ -129,7 +131,8 @@ def _load() -> ctypes.CDLL:
 
 
 _lib = _load()
-EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status", "hog_build_lut",
+EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status",
+            "hog_selftest_wait_timeout", "hog_build_lut",
             "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
             "hog_build_soft_lut", "hog_cell_hist_soft", "hog_block_norm", "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
@@ -186,6 +189,12 @@ def hog_device_status(clear: bool = False) -> int:
     v = ctypes.c_uint32(0)
     _check("hog_device_status", _lib.hog_device_status(ctypes.addressof(v), int(clear)))
     return v.value
+
+
+def hog_selftest_wait_timeout(mode: int, limit_us: int, stream=None) -> None:
+    """Run one bounded device-side wait that runs out (mode 0: an mbarrier,
+    mode 1: a device-memory flag); the kernel sets HOG_STATUS_TIMEOUT."""
+    _check("hog_selftest_wait_timeout", _lib.hog_selftest_wait_timeout(mode, limit_us, _stream(stream)))
 
 
 def hog_build_lut(n_bins: int, lut, stream=None) -> None:

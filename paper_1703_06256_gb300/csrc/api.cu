@@ -64,6 +64,15 @@ int tune_get(int knob) {
     return knob >= 0 && knob < HOG_TUNE_KNOBS ? g_tune[knob].load(std::memory_order_relaxed) : 0;
 }
 
+// int8 weights promise exact int32 scores.  Every kernel accumulates in f32,
+// which is exact while every partial sum is an integer below 2^24 in
+// magnitude.  A cell of hard votes holds at most cell^2 counts over all its
+// bins, so |partial sum| <= 127 * cells_x * cells_y * cell^2 + |round(bias)|.
+static bool i8_exact(int cells_x, int cells_y, int cell, double bias_rounded) {
+    const double bound = 127.0 * cells_x * cells_y * (double)cell * cell + std::fabs(bias_rounded);
+    return bound < 16777216.0;
+}
+
 static bool size_ok(int W, int H) { return W >= 1 && H >= 1 && W <= 65535 && H <= 65535 && (long)W * H < (1L << 31); }
 
 }  // namespace fasthog
@@ -83,6 +92,7 @@ hog_status hog_tune_set(int knob, int value) {
         case HOG_TUNE_CELL_ROWS: ok = ok || value == 1 || value == 4 || value == 8 || value == 16; break;
         case HOG_TUNE_SCORE_PATH: ok = ok || value == 1 || value == 2; break;
         case HOG_TUNE_SLIDE_WINDOWS: ok = ok || value == 8 || value == 16; break;
+        case HOG_TUNE_INTEGRAL_PATH: ok = ok || value == 1 || value == 2; break;
         default: return HOG_ERR_ARG;
     }
     if (!ok) return HOG_ERR_ARG;
@@ -219,6 +229,8 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
     if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
     if (w_dtype != HOG_F32 && w_dtype != HOG_BF16 && w_dtype != HOG_I8) return HOG_ERR_ARG;
     if (!std::isfinite(bias)) return HOG_ERR_ARG;
+    if (w_dtype == HOG_I8 && !i8_exact(cells_x, cells_y, cell, (double)std::llround((double)bias)))
+        return HOG_ERR_UNSUPPORTED;
     const int r = cell / stride;
     const float b = w_dtype == HOG_I8 ? (float)std::llround((double)bias) : bias;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -280,8 +292,11 @@ hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, in
     if (cell < 1 || stride < 1 || cell % stride != 0) return HOG_ERR_ARG;
     if (cell_dtype != HOG_I32 && cell_dtype != HOG_BF16 && cell_dtype != HOG_F32) return HOG_ERR_ARG;
     if (w_dtype != HOG_F32 && w_dtype != HOG_BF16 && w_dtype != HOG_I8) return HOG_ERR_ARG;
-    for (int f = 0; f < n_filters; ++f)
+    for (int f = 0; f < n_filters; ++f) {
         if (!std::isfinite(biases[f])) return HOG_ERR_ARG;
+        if (w_dtype == HOG_I8 && !i8_exact(cells_x, cells_y, cell, (double)std::llround((double)biases[f])))
+            return HOG_ERR_UNSUPPORTED;
+    }
     const int r = cell / stride;
     const long nx = (long)ncx - (long)(cells_x - 1) * r, ny = (long)ncy - (long)(cells_y - 1) * r;
     if (nx <= 0 || ny <= 0) return HOG_OK;
@@ -317,8 +332,9 @@ hog_status hog_detect(const void* scores, int score_dtype, int nx, int ny, int s
     if (score_dtype != HOG_F32 && score_dtype != HOG_I32) return HOG_ERR_ARG;
     if (std::isnan(thr)) return HOG_ERR_ARG;
     if (workspace_bytes < detect_workspace_bytes(nx, ny)) return HOG_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(workspace) % 8 != 0) return HOG_ERR_ARG;
     return launch_detect(scores, score_dtype, nx, ny, stride, thr, image, level, out, max_out, d_count, workspace,
-                         workspace_bytes, reinterpret_cast<cudaStream_t>(stream));
+                         reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -116,7 +116,7 @@ hog_status launch_t(const PlanHeader& h, const void* plan_dev, float thr, hog_de
     int thr_i = 0;
     if (std::is_same<T, int32_t>::value) {
         const double c = ceil((double)thr);
-        thr_i = c > 2147483647.0 ? 2147483647 : (c < -2147483647.0 ? -2147483647 : (int)c);
+        thr_i = c > 2147483647.0 ? 2147483647 : (c < -2147483648.0 ? (int)(-2147483647 - 1) : (int)c);
     }
     const PlanItem* items = plan_items(plan_dev);
     const int T_ = h.detect_tiles;

@@ -20,9 +20,11 @@ template <>
 __device__ __forceinline__ bool pass<float>(float v, float thr_f, int) {
     return v >= thr_f;
 }
+// Integer scores: v >= thr  <=>  v >= ceil(thr).  The caller clamps ceil(thr)
+// into the int32 range; a threshold of 2^31 or more (thr_f) passes nothing.
 template <>
-__device__ __forceinline__ bool pass<int32_t>(int32_t v, float, int thr_i) {
-    return v >= thr_i;
+__device__ __forceinline__ bool pass<int32_t>(int32_t v, float thr_f, int thr_i) {
+    return v >= thr_i && thr_f < 2147483648.0f;
 }
 
 __device__ __forceinline__ int block_sum(int v, int* red) {
@@ -52,17 +54,12 @@ __device__ __forceinline__ int tile_count(const T* __restrict__ scores, long n, 
     return block_sum(c, red);
 }
 
-// Write the detections of tile `tile` at list positions before, before + 1,
-// ... (those below max_out); returns the tile's number of detections.  The
-// tile's run of the list is built in shared memory (stage: kTile * kDetWords
-// words) and written with coalesced word stores.
+// The scores of this thread in tile `tile` (kPer consecutive ones) and the
+// bit mask of those that pass.
 template <typename T>
-__device__ __forceinline__ int tile_scatter(const T* __restrict__ scores, int nx, long n, int tile, int stride,
-                                            float thr_f, int thr_i, int image, int level, int before,
-                                            hog_det* __restrict__ out, int max_out, uint32_t* stage, int* wsum) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+__device__ __forceinline__ unsigned tile_load(const T* __restrict__ scores, long n, int tile, float thr_f, int thr_i,
+                                              T (&v)[kPer]) {
     const long base = (long)tile * kTile + (long)threadIdx.x * kPer;
-    T v[kPer];
     unsigned flags = 0;
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
@@ -70,6 +67,14 @@ __device__ __forceinline__ int tile_scatter(const T* __restrict__ scores, int nx
         v[e] = i < n ? __ldg(scores + i) : T(0);
         if (i < n && pass<T>(v[e], thr_f, thr_i)) flags |= 1u << e;
     }
+    return flags;
+}
+
+// Position of this thread's first detection in the tile's run of the list
+// (exclusive scan of the per-thread counts over the CTA); `total` gets the
+// tile's count.  Contains one barrier.
+__device__ __forceinline__ int tile_rank(unsigned flags, int* wsum, int& total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int mine = __popc(flags);
     int incl = mine;
 #pragma unroll
@@ -79,16 +84,22 @@ __device__ __forceinline__ int tile_scatter(const T* __restrict__ scores, int nx
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    int loc = incl - mine;  // this thread's first slot in the tile's list
-    int tile_total = 0;
+    int loc = incl - mine;
+    total = 0;
 #pragma unroll
     for (int w = 0; w < kThreads / 32; ++w) {
         if (w < warp) loc += wsum[w];
-        tile_total += wsum[w];
+        total += wsum[w];
     }
-    // The tile's detections are contiguous in the output: build them in
-    // shared memory, then write the whole run with coalesced word stores
-    // (full 128-byte lines, whether `out` is device or mapped host memory).
+    return loc;
+}
+
+// Build this thread's records of the tile's run of the list in shared
+// memory (stage: kTile * kDetWords words), from run position loc on.
+template <typename T>
+__device__ __forceinline__ void tile_stage(const T (&v)[kPer], unsigned flags, int loc, int nx, int tile, int stride,
+                                           int image, int level, uint32_t* stage) {
+    const long base = (long)tile * kTile + (long)threadIdx.x * kPer;
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
         if (flags & (1u << e)) {
@@ -103,11 +114,33 @@ __device__ __forceinline__ int tile_scatter(const T* __restrict__ scores, int nx
             ++loc;
         }
     }
-    __syncthreads();
+}
+
+// Copy the tile's staged run (tile_total records) to list positions
+// before, before + 1, ... (those below max_out) with coalesced word stores
+// (full 128-byte lines, whether `out` is device or mapped host memory).
+// The stage must be complete (a barrier after tile_stage).
+__device__ __forceinline__ void tile_write(const uint32_t* stage, int tile_total, int before,
+                                           hog_det* __restrict__ out, int max_out) {
     const int room = max_out - before;
     const int keep = tile_total < room ? tile_total : (room > 0 ? room : 0);
     uint32_t* dst = reinterpret_cast<uint32_t*>(out + (room > 0 ? before : 0));
     for (int j = threadIdx.x; j < keep * kDetWords; j += kThreads) dst[j] = stage[j];
+}
+
+// Write the detections of tile `tile` at list positions before, before + 1,
+// ... (those below max_out); returns the tile's number of detections.
+template <typename T>
+__device__ __forceinline__ int tile_scatter(const T* __restrict__ scores, int nx, long n, int tile, int stride,
+                                            float thr_f, int thr_i, int image, int level, int before,
+                                            hog_det* __restrict__ out, int max_out, uint32_t* stage, int* wsum) {
+    T v[kPer];
+    const unsigned flags = tile_load<T>(scores, n, tile, thr_f, thr_i, v);
+    int tile_total = 0;
+    const int loc = tile_rank(flags, wsum, tile_total);
+    tile_stage<T>(v, flags, loc, nx, tile, stride, image, level, stage);
+    __syncthreads();
+    tile_write(stage, tile_total, before, out, max_out);
     return tile_total;
 }
 

@@ -42,7 +42,24 @@
 //
 // Bins are handled in windows of at most 16; larger N_b runs the phases once
 // per window.  Limits: W, H < 65536 (16-bit row counts and carries).
+//
+// Single pass (images of moderate size, where three launches cost more in
+// latency than the planes take to write).  One CTA per tile of R = 16 or 32
+// rows by 128 columns, tiles numbered row-major; warp w owns 4 rows of the
+// tile.  A CTA loads its rows, publishes the tile's aggregates -- its
+// per-column counts over the R rows, its per-row counts over the 128
+// columns and its totals -- and raises its flag (onepass.cuh).  It then
+// waits for the flags of the tiles above and to the left (all of lower
+// number, each raised right after its own loads: no chain of waits), and
+// forms its carries directly from their aggregates:
+//   V(x, tile top - 1) = sum over the tiles above of their column counts;
+//   RL(y)              = sum over the tiles to the left of their row counts;
+//   corner             = sum over the tiles above-left of their totals.
+// Inside the tile the warps' carries come from shared memory (the column
+// counts of the warps above, the RL of the rows above), and each warp runs
+// the scan of phase C on its rows.
 #include "internal.cuh"
+#include "onepass.cuh"
 
 namespace fasthog {
 
@@ -667,6 +684,240 @@ __global__ void __launch_bounds__(32)
     }
 }
 
+// ---------------------------------------------------------------- single pass
+constexpr int kOpRowsPerWarp = 4;
+
+// Shared-memory slot of column x (0..127) of a group: lane x / 4 owns
+// columns 4L..4L+3, so slot (x % 4) * 32 + x / 4 makes a warp's accesses to
+// "column 4L + k" consecutive (no bank conflicts).
+__device__ __forceinline__ int cslot(int x) { return (x & 3) * 32 + (x >> 2); }
+
+struct OpWs {
+    void* header;      // tag of the last launch (onepass.cuh)
+    uint32_t* flags;   // [tile]            tag of the launch that published the tile's aggregates
+    uint32_t* colagg;  // [band][NM][W]     column counts over the tile's rows, 8-bit fields
+    uint16_t* rowagg;  // [y][group][WIN]   row counts over the tile's columns
+    uint32_t* totagg;  // [band][group][WIN] tile totals
+};
+
+template <int WIN, int NW, typename OutT>
+__global__ void __launch_bounds__(32 * NW)
+    ii_onepass_kernel(const uint8_t* __restrict__ bins, int W, int H, int n_groups, int lo, int n_bins, bool vec,
+                      OpWs ws, OutT* __restrict__ ii, unsigned int* status) {
+    constexpr int NM = (WIN + 3) / 4, HW = kOpRowsPerWarp, R = HW * NW, NT = 32 * NW;
+    static_assert(R <= 32, "a tile's column counts must fit 8-bit fields");
+    static_assert(NT % WIN == 0, "every thread sums one bin of the corner");
+    __shared__ uint32_t st[R][32];             // the tile's bins, 4 per lane and row
+    __shared__ uint32_t colw[NW][NM][kSlice];  // per-warp column counts, 8-bit fields, by cslot
+    __shared__ uint32_t vtop[2 * NM][kSlice];  // V at the tile top, 16-bit fields, by cslot:
+                                               // word 2m bins 4m, 4m+2; word 2m+1 bins 4m+1, 4m+3
+    __shared__ int rl_s[R][WIN];               // the tile rows' counts over the group, then RL
+    __shared__ int corner_s[WIN];
+    __shared__ uint32_t tag_s;
+
+    const int t = blockIdx.x;
+    const int I = t / n_groups, g = t - I * n_groups;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int y_tile = I * R;
+    const int y0 = y_tile + warp * HW;
+    const int nrows = max(0, min(HW, H - y0));
+    const int x0 = g * kSlice + 4 * lane;
+    const int ncol = max(0, min(4, W - x0));
+    const int wins = min(WIN, n_bins - lo);
+
+    pdl_wait();
+    if (tid == 0) tag_s = onepass::launch_tag(ws.header);
+    if (tid < WIN) corner_s[tid] = 0;
+
+    // ---- this warp's rows: stage the bins, count per column and per row
+    {
+        uint32_t v[HW];
+#pragma unroll
+        for (int k = 0; k < HW; ++k)
+            v[k] = k < nrows ? load_chunk(bins + (size_t)(y0 + k) * W + x0, ncol, vec) : 0xFFFFFFFFu;
+        uint32_t col[4][NM];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+            for (int m = 0; m < NM; ++m) col[c][m] = 0;
+#pragma unroll
+        for (int k = 0; k < HW; ++k) {
+            uint32_t rowt[NM];
+#pragma unroll
+            for (int m = 0; m < NM; ++m) rowt[m] = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int sh = 8 * ((int)byte_at(v[k], c) - lo);
+#pragma unroll
+                for (int m = 0; m < NM; ++m) {
+                    const uint32_t oh = bit_or_zero((uint32_t)(sh - 32 * m));
+                    col[c][m] += oh;
+                    rowt[m] += oh;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                const uint32_t sum = __reduce_add_sync(0xffffffffu, rowt[m]);  // at most 128 per bin
+                if (lane < 4 && 4 * m + lane < WIN) rl_s[warp * HW + k][4 * m + lane] = (int)byte_at(sum, lane);
+            }
+            st[warp * HW + k][lane] = v[k];
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) colw[warp][m][c * 32 + lane] = col[c][m];
+    }
+    __syncthreads();
+
+    // ---- publish the tile's aggregates, then its flag
+    const uint32_t tag = tag_s;
+    for (int p = tid; p < NM * kSlice; p += NT) {
+        const int m = p / kSlice, x = p - m * kSlice;
+        uint32_t a = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) a += colw[w2][m][cslot(x)];  // at most R <= 32 per field
+        if (g * kSlice + x < W) ws.colagg[((size_t)I * NM + m) * W + g * kSlice + x] = a;
+    }
+    for (int e = tid; e < R * WIN; e += NT) {
+        const int r = e / WIN, b = e - r * WIN;
+        if (y_tile + r < H) ws.rowagg[((size_t)(y_tile + r) * n_groups + g) * WIN + b] = (uint16_t)rl_s[r][b];
+    }
+    if (tid < WIN) {
+        int tot = 0;
+#pragma unroll 8
+        for (int r = 0; r < R; ++r) tot += rl_s[r][tid];
+        ws.totagg[((size_t)I * n_groups + g) * WIN + tid] = (uint32_t)tot;
+    }
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) onepass::st_release(ws.flags + t, tag);
+
+    // ---- wait for the tiles above and to the left (all of lower number)
+    {
+        bool ok = true;
+        const int nd = (I + 1) * (g + 1) - 1;
+        for (int e = tid; e < nd; e += NT) {
+            const int Ip = e / (g + 1), gp = e - Ip * (g + 1);
+            if (!onepass::wait_flag(ws.flags + (size_t)Ip * n_groups + gp, tag)) ok = false;
+        }
+        if (!ok) atomicOr(status, kStatusTimeout);
+    }
+    __syncthreads();
+    // the last tile has seen every tile's flag, so every tile has read the old tag
+    if (tid == 0 && t == (int)gridDim.x - 1) onepass::end_launch(ws.header, tag);
+    pdl_trigger();
+
+    // ---- carries from the aggregates
+    // V at the tile top: the column counts of the tiles above, 8-bit fields widened to 16
+    for (int p = tid; p < NM * kSlice; p += NT) {
+        const int m = p / kSlice, x = p - m * kSlice;
+        const int xg = g * kSlice + x;
+        uint32_t even = 0, odd = 0;
+        if (xg < W) {
+            const uint32_t* src = ws.colagg + (size_t)m * W + xg;
+#pragma unroll 4
+            for (int Ip = 0; Ip < I; ++Ip) {
+                const uint32_t a = __ldcg(src + (size_t)Ip * NM * W);
+                even += a & 0x00FF00FFu;
+                odd += (a >> 8) & 0x00FF00FFu;
+            }
+        }
+        vtop[2 * m][cslot(x)] = even;
+        vtop[2 * m + 1][cslot(x)] = odd;
+    }
+    // RL of the tile's rows: the row counts of the tiles to the left
+    for (int e = tid; e < R * WIN; e += NT) {
+        const int r = e / WIN, b = e - r * WIN;
+        const int y = y_tile + r;
+        int sum = 0;
+        if (y < H) {
+            const uint16_t* src = ws.rowagg + (size_t)y * n_groups * WIN + b;
+#pragma unroll 4
+            for (int gp = 0; gp < g; ++gp) sum += (int)__ldcg(src + (size_t)gp * WIN);
+        }
+        rl_s[r][b] = sum;
+    }
+    // corner: the totals of the tiles above-left (thread tid always takes bin tid % WIN)
+    {
+        int sum = 0;
+        const int gw = g * WIN, n = I * gw;
+        for (int e = tid; e < n; e += NT) {
+            const int Ip = e / gw;
+            sum += (int)__ldcg(ws.totagg + (size_t)Ip * n_groups * WIN + (e - Ip * gw));
+        }
+        if (sum != 0) atomicAdd(&corner_s[tid % WIN], sum);
+    }
+    __syncthreads();
+
+    // ---- this warp's rows: ii(x, y0 - 1) = corner of the rows above + prefix of V over the columns
+    int acc[WIN][4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int sl = k * 32 + lane;  // cslot(4 * lane + k)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            uint32_t even = vtop[2 * m][sl], odd = vtop[2 * m + 1][sl];
+            for (int w2 = 0; w2 < warp; ++w2) {
+                const uint32_t a = colw[w2][m][sl];
+                even += a & 0x00FF00FFu;
+                odd += (a >> 8) & 0x00FF00FFu;
+            }
+            const int vb[4] = {(int)(even & 0xFFFFu), (int)(odd & 0xFFFFu), (int)(even >> 16), (int)(odd >> 16)};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int b = 4 * m + e;
+                if (b < WIN) acc[b][k] = k == 0 ? vb[e] : acc[b][k - 1] + vb[e];
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < WIN; ++b) {
+        int corner = corner_s[b];
+        for (int r = 0; r < warp * HW; ++r) corner += rl_s[r][b];
+        const int tot = acc[b][3];
+        const int incl = (int)warp_incl_scan((uint32_t)tot, lane);
+        const int o = corner + incl - tot;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) acc[b][k] += o;
+    }
+
+    const size_t plane = (size_t)H * W;
+    OutT* out_row = ii + (size_t)lo * plane + (size_t)y0 * W + x0;
+    for (int r = 0; r < nrows; ++r, out_row += W) {
+        // P[k][m] byte e = count of bin lo+4m+e in columns 0..k of this lane's chunk
+        const uint32_t w = st[warp * HW + r][lane];
+        uint32_t P[4][NM], run[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) run[m] = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int b = (int)byte_at(w, k);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                run[m] += bit_or_zero((uint32_t)(8 * (b - lo - 4 * m)));
+                P[k][m] = run[m];
+            }
+        }
+        // E[m]: count in the group's columns left of this lane (8-bit fields: at most 124)
+        uint32_t E[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) E[m] = warp_incl_scan(P[3][m], lane) - P[3][m];
+#pragma unroll
+        for (int b = 0; b < WIN; ++b) {
+            const int m = b >> 2, e = b & 3;
+            const int base = rl_s[warp * HW + r][b] + (int)byte_at(E[m], e);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) acc[b][k] += base + (int)byte_at(P[k][m], e);
+        }
+        if (ncol > 0) {
+            OutT* p = out_row;
+#pragma unroll
+            for (int b = 0; b < WIN; ++b, p += plane)
+                if (b < wins) store_chunk<OutT>(p, acc[b], ncol, vec);
+        }
+    }
+}
+
 template <int WIN, typename OutT>
 hog_status run_window(const Plan& p, const uint8_t* bins, int n_bins, int lo, OutT* ii, const Ws& ws, bool vec,
                       cudaStream_t st) {
@@ -697,27 +948,120 @@ hog_status run_all(const Plan& p, const uint8_t* bins, int n_bins, OutT* ii, con
     return HOG_OK;
 }
 
+// ---- workspace: [sync region: tag word, one flag per single-pass tile]
+//                 [either the three-phase arrays or the single-pass aggregates]
+// The sync region is the only part that must start zero-filled; nothing else
+// writes into it, so the two paths can share one workspace.
+constexpr int kOpMinRows = kOpRowsPerWarp * 4;  // the shorter single-pass tile (4 warps)
+
+struct OpPlan {
+    int R, n_bands, n_groups, n_tiles, win, n_windows;
+};
+
+OpPlan op_plan(int W, int H, int n_bins, int R) {
+    OpPlan o{};
+    o.R = R;
+    o.n_bands = ceil_div(H, R);
+    o.n_groups = ceil_div(W, kSlice);
+    o.n_tiles = o.n_bands * o.n_groups;
+    o.win = n_bins <= 4 ? 4 : (n_bins <= 8 ? 8 : 16);
+    o.n_windows = ceil_div(n_bins, o.win);
+    return o;
+}
+
+size_t sync_bytes(int W, int H) {
+    const OpPlan o = op_plan(W, H, 1, kOpMinRows);  // the most tiles
+    return align256((size_t)onepass::kHeaderBytes + (size_t)o.n_tiles * 4);
+}
+
+size_t op_agg_bytes(int W, int H, int n_bins) {
+    const OpPlan o = op_plan(W, H, n_bins, kOpMinRows);
+    const int nm = (o.win + 3) / 4;
+    return align256((size_t)o.n_bands * nm * W * 4) + align256((size_t)H * o.n_groups * o.win * 2) +
+           align256((size_t)o.n_bands * o.n_groups * o.win * 4);
+}
+
+OpWs op_carve(const OpPlan& o, int W, int H, void* base) {
+    uint8_t* b = static_cast<uint8_t*>(base);
+    OpWs w;
+    w.header = b;
+    w.flags = reinterpret_cast<uint32_t*>(b + onepass::kHeaderBytes);
+    b += sync_bytes(W, H);
+    const int nm = (o.win + 3) / 4;
+    w.colagg = reinterpret_cast<uint32_t*>(b);
+    b += align256((size_t)o.n_bands * nm * W * 4);
+    w.rowagg = reinterpret_cast<uint16_t*>(b);
+    b += align256((size_t)H * o.n_groups * o.win * 2);
+    w.totagg = reinterpret_cast<uint32_t*>(b);
+    return w;
+}
+
+template <int WIN, typename OutT>
+hog_status op_window(const OpPlan& o, const uint8_t* bins, int W, int H, int n_bins, int lo, OutT* ii,
+                     const OpWs& ws, bool vec, unsigned int* status, cudaStream_t st) {
+    if (o.R == 32)
+        return launch_pdl(ii_onepass_kernel<WIN, 8, OutT>, dim3(o.n_tiles), dim3(256), 0, st, bins, W, H,
+                          o.n_groups, lo, n_bins, vec, ws, ii, status);
+    return launch_pdl(ii_onepass_kernel<WIN, 4, OutT>, dim3(o.n_tiles), dim3(128), 0, st, bins, W, H, o.n_groups,
+                      lo, n_bins, vec, ws, ii, status);
+}
+
+template <typename OutT>
+hog_status op_all(const OpPlan& o, const uint8_t* bins, int W, int H, int n_bins, OutT* ii, const OpWs& ws,
+                  bool vec, unsigned int* status, cudaStream_t st) {
+    for (int wi = 0; wi < o.n_windows; ++wi) {
+        const int lo = wi * o.win;
+        hog_status s = o.win == 4   ? op_window<4, OutT>(o, bins, W, H, n_bins, lo, ii, ws, vec, status, st)
+                       : o.win == 8 ? op_window<8, OutT>(o, bins, W, H, n_bins, lo, ii, ws, vec, status, st)
+                                    : op_window<16, OutT>(o, bins, W, H, n_bins, lo, ii, ws, vec, status, st);
+        if (s != HOG_OK) return s;
+    }
+    return HOG_OK;
+}
+
+// Whether the single pass is the library's choice: each tile sums the
+// aggregates of every tile above it and above-left of it, which stays small
+// next to the planes it writes while the image has a few hundred tiles.
+bool onepass_default(int W, int H) {
+    const OpPlan o = op_plan(W, H, 1, kOpMinRows);
+    return o.n_bands <= 72 && o.n_groups <= 16;
+}
+
 }  // namespace
 
+size_t integral_sync_bytes(int W, int H) { return sync_bytes(W, H); }
+
 size_t integral_workspace_bytes(int W, int H, int n_bins) {
-    // enough for every band height, so a workspace stays valid whatever the tuning
-    size_t most = 0;
+    // enough for every band height and both paths, so a workspace stays valid whatever the tuning
+    size_t most = op_agg_bytes(W, H, n_bins);
     for (int h : {4, 8, 16, 32}) {
         const Plan p = make_plan(W, H, n_bins, h);
         const size_t b = p.colcnt_bytes + p.rowcnt_bytes + p.bt_bytes + p.carry_bytes;
         most = b > most ? b : most;
     }
-    return most;
+    return sync_bytes(W, H) + most;
 }
 
 hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii, void* ws,
                            cudaStream_t st) {
-    const Plan p = make_plan(W, H, n_bins);
-    const Ws w = carve(p, ws);
     // vector path: a chunk's 4 bins load as one word, its 4 outputs store as
     // one 16-byte (int32) or 8-byte (uint16) vector, and every row starts aligned
     const bool vec = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (reinterpret_cast<uintptr_t>(ii) % 16 == 0) &&
                      (W % 4 == 0);
+    const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);
+    if (path == 2 || (path == 0 && onepass_default(W, H))) {
+        unsigned int* status = nullptr;
+        hog_status s = device_status_word(&status);
+        if (s != HOG_OK) return s;
+        const int rows = tune_get(HOG_TUNE_INTEGRAL_BAND_ROWS);
+        const OpPlan o = op_plan(W, H, n_bins, rows == 32 ? 32 : 16);
+        const OpWs w = op_carve(o, W, H, ws);
+        if (ii_dtype == HOG_U16)
+            return op_all<uint16_t>(o, bins, W, H, n_bins, static_cast<uint16_t*>(ii), w, vec, status, st);
+        return op_all<int32_t>(o, bins, W, H, n_bins, static_cast<int32_t*>(ii), w, vec, status, st);
+    }
+    const Plan p = make_plan(W, H, n_bins);
+    const Ws w = carve(p, static_cast<uint8_t*>(ws) + sync_bytes(W, H));
     if (ii_dtype == HOG_U16) return run_all<uint16_t>(p, bins, n_bins, static_cast<uint16_t*>(ii), w, vec, st);
     return run_all<int32_t>(p, bins, n_bins, static_cast<int32_t*>(ii), w, vec, st);
 }

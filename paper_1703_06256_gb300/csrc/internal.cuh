@@ -45,6 +45,8 @@ hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t
                           cudaStream_t st);
 
 size_t integral_workspace_bytes(int W, int H, int n_bins);
+// Leading bytes of an integral workspace that must be zero-filled before its first use.
+size_t integral_sync_bytes(int W, int H);
 hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
                            void* ws, cudaStream_t st);
 
@@ -81,7 +83,7 @@ size_t detect_workspace_bytes(int nx, int ny);
 int detect_tiles(long n_scores);  // 2048-score tiles of a map (0 for an empty map)
 hog_status launch_detect(const void* scores, int score_dtype, int nx, int ny, int stride, float thr,
                          int image, int level, hog_det* out, int max_out, int32_t* d_count, void* ws,
-                         size_t ws_bytes, cudaStream_t st);
+                         cudaStream_t st);
 
 // ---- programmatic dependent launch
 // Kernels of the detection path launch with programmatic stream

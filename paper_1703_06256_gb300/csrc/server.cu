@@ -172,6 +172,15 @@ struct hog_server {
         uint8_t* base = arena_base + sl.off;
         hog_stream_t st = reinterpret_cast<hog_stream_t>(sl.stream);
         const int windows = L.nx * L.ny;
+        {
+            // The request's workspaces come from reused arena memory: zero-fill them first, as the
+            // single-pass kernels need before a workspace's first use (ahead of the kernels, so the
+            // kernels still follow one another directly).
+            cudaError_t e = cudaMemsetAsync(base + L.ws_det, 0, L.ws_det_bytes, sl.stream);
+            if (e == cudaSuccess && !fused)
+                e = cudaMemsetAsync(base + L.ws_ii, 0, fasthog::integral_sync_bytes(W, H), sl.stream);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
         if (windows > 0) {
             const cudaError_t e = cudaMemcpyAsync(base + L.img, img, (size_t)W * H * channels,
                                                   cudaMemcpyHostToDevice, sl.stream);

@@ -38,14 +38,15 @@ class HogPipeline:
         self.bins = torch.empty(H * W, dtype=torch.uint8, device=dev)
         self.ii = torch.empty(n_bins * H * W, dtype=TORCH_DTYPE[ii_dtype], device=dev)
         self.ws_ii_bytes = hog_integral_workspace_bytes(W, H, n_bins)
-        self.ws_ii = torch.empty(max(self.ws_ii_bytes, 256), dtype=torch.uint8, device=dev)
+        # workspaces start zero-filled (the single-pass kernels' contract) and are never cleared again
+        self.ws_ii = torch.zeros(max(self.ws_ii_bytes, 256), dtype=torch.uint8, device=dev)
         self.cells = torch.empty(max(self.ncx * self.ncy * n_bins, 1), dtype=TORCH_DTYPE[cell_dtype], device=dev)
         self.score_dtype = HOG_I32 if w_dtype == HOG_I8 else HOG_F32
         self.scores = torch.empty(max(self.nx * self.ny, 1), dtype=TORCH_DTYPE[self.score_dtype], device=dev)
         self.det = torch.empty(self.max_out * DET_BYTES, dtype=torch.uint8, device=dev)
         self.count = torch.zeros(1, dtype=torch.int32, device=dev)
         self.ws_det_bytes = hog_detect_workspace_bytes(self.nx, self.ny)
-        self.ws_det = torch.empty(max(self.ws_det_bytes, 256), dtype=torch.uint8, device=dev)
+        self.ws_det = torch.zeros(max(self.ws_det_bytes, 256), dtype=torch.uint8, device=dev)
         self.w = torch.zeros(cells_x * cells_y * n_bins, dtype=_W_DTYPE[w_dtype], device=dev)
         self.bias = 0.0
         self.thr = 0.0

@@ -33,11 +33,17 @@ def gpu_bins(img: np.ndarray, nb: int, lut=None, pitch_pad: int = 0, offset: int
     return bins.cpu().numpy().reshape(H, W)
 
 
-def gpu_integral(bins: np.ndarray, nb: int, ii_dtype=fh.HOG_I32) -> np.ndarray:
+def gpu_integral(bins: np.ndarray, nb: int, ii_dtype=fh.HOG_I32, ws=None) -> np.ndarray:
+    """`ws`: a zero-filled workspace to reuse (at least
+    hog_integral_workspace_bytes), else a fresh one."""
     H, W = bins.shape
     b = dev(bins.reshape(-1))
     ws_bytes = fh.hog_integral_workspace_bytes(W, H, nb)
-    ws = torch.empty(ws_bytes, dtype=torch.uint8, device="cuda")
+    if ws is None:
+        ws = torch.zeros(ws_bytes, dtype=torch.uint8, device="cuda")  # zero-filled before its first use
+    else:
+        assert ws.numel() >= ws_bytes
+        ws_bytes = ws.numel()
     # canaries around the output catch writes past either end
     pad = 64
     t = torch.int32 if ii_dtype == fh.HOG_I32 else torch.int16
@@ -93,7 +99,7 @@ def gpu_detect(scores: np.ndarray, stride: int, thr: float, max_out: int | None 
     out = torch.zeros(max(cap, 1) * fh.DET_BYTES, dtype=torch.uint8, device="cuda")
     cnt = torch.full((1,), -7, dtype=torch.int32, device="cuda")
     ws_b = fh.hog_detect_workspace_bytes(nx, ny)
-    ws = torch.empty(ws_b, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(ws_b, dtype=torch.uint8, device="cuda")  # zero-filled before its first use
     fh.hog_detect(s, dtype, nx, ny, stride, thr, image, level, out, cap, cnt, ws, ws_b)
     n = int(cnt.item())
     return fh.dets_to_numpy(out.cpu(), min(n, cap)), n

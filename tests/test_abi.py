@@ -83,6 +83,24 @@ def test_argument_errors_need_no_gpu(fh):
     assert L.hog_detect(4096, fh.HOG_BF16, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 256, None) == ARG
     assert L.hog_detect(None, fh.HOG_F32, 10, 10, 4, 0.5, 0, 0, 4096, 10, 4096, 4096, 256, None) == ARG
     assert L.hog_device_status(None, 0) == ARG
+    assert L.hog_selftest_wait_timeout(2, 1000, None) == ARG
+    assert L.hog_selftest_wait_timeout(0, 0, None) == ARG
+
+
+def test_int8_scores_outside_the_exact_range_are_refused(fh):
+    # int8 weights promise exact int32 scores; f32 accumulation keeps that only
+    # while 127 * cells_x * cells_y * cell^2 + |round(bias)| < 2^24
+    L = fh.lib()
+    UNS = fh.HOG_ERR_UNSUPPORTED
+    # cell 64, 8 x 16 cells: 127 * 128 * 4096 = 66,584,576 >= 2^24
+    assert L.hog_window_score(4096, fh.HOG_I32, 200, 200, 8, 8, 16, 64, 64, 4096, fh.HOG_I8, 0.0, 4096,
+                              None) == UNS
+    # cell 32: 127 * 128 * 1024 = 16,646,144 < 2^24, but a bias of 2^17 pushes it over
+    assert L.hog_window_score(4096, fh.HOG_I32, 200, 200, 8, 8, 16, 32, 32, 4096, fh.HOG_I8, 131072.0, 4096,
+                              None) == UNS
+    biases = (ctypes.c_float * 2)(0.0, 131072.0)
+    assert L.hog_window_score_multi(4096, fh.HOG_I32, 200, 200, 8, 8, 16, 32, 32, 4096, fh.HOG_I8, 2, biases,
+                                    4096, None) == UNS
 
 
 def test_server_argument_errors_need_no_gpu(fh):

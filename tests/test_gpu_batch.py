@@ -129,6 +129,38 @@ def test_batch_int8_exact(fh):
     check_batch(fh, b, imgs, w.astype(np.float64), 3.0, 40.0, exact=True)
 
 
+def test_batch_nb16_tensor_cores_bf16(fh):
+    """N_b = 16 with bf16 weights: the batched tensor-core score with two
+    16-byte halves per cell (the kernel the pyramid benchmark times at
+    N_b = 16), three pyramid levels, against the oracle on the bf16 weights."""
+    from paper_1703_06256_gb300.batch import HogPlanBatch
+
+    imgs = images(3, 12)
+    w = wl.weights_f32(16, wl.rng_for(12))
+    w_bf = torch.from_numpy(w).to(torch.bfloat16).double().numpy()  # the weights the tensor cores see
+    b = HogPlanBatch(SIZES, channels=3, levels=3, n_bins=16, stride=4, w_dtype=fh.HOG_BF16)
+    assert b.cell_dtype == fh.HOG_BF16
+    b.set_images(imgs)
+    b.set_weights(w, 0.125, 0.5)
+    b.capture()
+    b.run()
+    check_batch(fh, b, imgs, w_bf, 0.125, 0.5, exact=False)
+
+
+def test_batch_nb16_tensor_cores_int8_exact(fh):
+    """N_b = 16 with int8 weights on the batched tensor-core score: int32
+    scores bit-exact against the oracle, and the list exact."""
+    from paper_1703_06256_gb300.batch import HogPlanBatch
+
+    imgs = images(3, 13)
+    w = wl.weights_i8(16, wl.rng_for(13))
+    b = HogPlanBatch(SIZES, channels=3, levels=3, n_bins=16, stride=4, w_dtype=fh.HOG_I8)
+    b.set_images(imgs)
+    b.set_weights(w, -2.0, 25.0)
+    b.run()
+    check_batch(fh, b, imgs, w.astype(np.float64), -2.0, 25.0, exact=True)
+
+
 @pytest.mark.parametrize("nb,stride", [(16, 4), (8, 8)])
 def test_batch_f32_weights(fh, nb, stride):
     """f32 weights: the score runs per item (CUDA cores); N_b 16 and stride 8."""

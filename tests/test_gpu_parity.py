@@ -141,12 +141,14 @@ def test_integral_uint16_modular(fh, g, nb):
         assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16), (ref & 0xFFFF).astype(np.uint16)), (H, W)
 
 
-@pytest.mark.parametrize("h", [4, 8, 16, 32])
-def test_integral_band_heights(fh, g, h):
-    """Every band height of the tiled scan (HOG_TUNE_INTEGRAL_BAND_ROWS), int32
-    and uint16, one window of bins and several (N_b = 20, 64): the tiles, the
-    carries between bands and groups, and partial bands at the bottom."""
+@pytest.mark.parametrize("path,h", [(1, 4), (1, 8), (1, 16), (1, 32), (2, 16), (2, 32)])
+def test_integral_band_heights(fh, g, path, h):
+    """Both schedules (HOG_TUNE_INTEGRAL_PATH: three launches, single pass) at
+    every tile height (HOG_TUNE_INTEGRAL_BAND_ROWS), int32 and uint16, one
+    window of bins and several (N_b = 20, 64): the tiles, the carries between
+    bands and groups, and partial bands at the bottom."""
     fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_BAND_ROWS, h)
+    fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, path)
     try:
         for i, (H, W, nb) in enumerate([(600, 800, 8), (301, 6, 8), (70, 300, 20), (33, 1025, 64), (97, 130, 3),
                                         (1000, 257, 16)]):
@@ -156,6 +158,45 @@ def test_integral_band_heights(fh, g, h):
             assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16), (ref & 0xFFFF).astype(np.uint16)), (h, H, W, nb)
     finally:
         fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_BAND_ROWS, 0)
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
+
+
+def test_integral_single_pass_many_tiles(fh, g):
+    """The single pass forced onto large maps, where a tile sums the
+    aggregates of up to 134 tiles above it and 29 to its left: 1920x1080 and
+    3840x2160 (8 bins), against the oracle."""
+    fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 2)
+    try:
+        for i, (H, W) in enumerate([(1080, 1920), (2160, 3840)]):
+            bins = oracle_bins(H, W, 8, 500 + i, p_none=0.2)
+            assert np.array_equal(g.gpu_integral(bins, 8), oracle.integral(bins, 8)), (H, W)
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
+
+
+def test_integral_one_workspace_many_calls(fh, g):
+    """One workspace, zero-filled once per image size, serves calls of that
+    size with different bin counts, dtypes and schedules in a row (each
+    single-pass launch accepts only the flags of its own launch and leaves
+    the tag for the next)."""
+    ws = torch.zeros(fh.hog_integral_workspace_bytes(1100, 600, 64), dtype=torch.uint8, device="cuda")
+    sizes = {(600, 1100): [(8, 0), (8, 0), (20, 1), (20, 2), (64, 2), (8, 2), (3, 1), (16, 2)],
+             (37, 259): [(16, 2), (8, 0), (8, 1), (8, 2)],
+             (1, 5): [(8, 2), (8, 2)]}
+    try:
+        for (H, W), calls in sizes.items():
+            ws.zero_()  # a new image size
+            for i, (nb, path) in enumerate(calls):
+                fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, path)
+                bins = oracle_bins(H, W, nb, 900 + i)
+                ref = oracle.integral(bins, nb)
+                dt = fh.HOG_U16 if i % 3 == 2 else fh.HOG_I32
+                got = g.gpu_integral(bins, nb, dt, ws=ws)
+                want = (ref & 0xFFFF).astype(np.uint16) if dt == fh.HOG_U16 else ref
+                assert np.array_equal(got, want), (H, W, i, nb, path)
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
+    assert fh.hog_device_status() == 0
 
 
 def test_integral_workload_bins(fh, g):
@@ -292,9 +333,10 @@ def test_detect_float_and_overflow(fh, g):
 
 
 def test_detect_many_tiles(fh, g):
-    """A map of more than 2048 tiles takes the scanned-offset form (count,
-    one-CTA scan, scatter): the list equals the oracle's, in order, also
-    truncated mid-list; a workspace below hog_detect_workspace_bytes is refused."""
+    """A map of 2154 tiles (look-back over many windows of 32 predecessors):
+    the list equals the oracle's, in order, also truncated mid-list, call
+    after call on the same workspace; a workspace below
+    hog_detect_workspace_bytes is refused."""
     rng = np.random.default_rng(14)
     ny, nx = 2100, 2100  # 4.41M scores, 2154 tiles
     S = rng.normal(0, 1, size=(ny, nx)).astype(np.float32)
@@ -310,7 +352,7 @@ def test_detect_many_tiles(fh, g):
     s_d = torch.from_numpy(S.reshape(-1)).cuda()
     out = torch.empty(16 * fh.DET_BYTES, dtype=torch.uint8, device="cuda")
     cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
-    ws = torch.empty(ws_b, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(ws_b, dtype=torch.uint8, device="cuda")
     with pytest.raises(fh.HogError):
         fh.hog_detect(s_d, fh.HOG_F32, nx, ny, 4, 1.5, 0, 0, out, 16, cnt, ws, ws_b - 256)
 
@@ -324,7 +366,7 @@ def test_detect_truncation_and_offsets(fh, g):
     n_ref = len(xs)
     s = torch.from_numpy(S.reshape(-1)).cuda()
     ws_b = fh.hog_detect_workspace_bytes(211, 97)
-    ws = torch.empty(ws_b, dtype=torch.uint8, device="cuda")
+    ws = torch.zeros(ws_b, dtype=torch.uint8, device="cuda")  # one workspace for every call below
     for max_out in (0, 1, 1023, 1024, 1025, 5000, n_ref - 1, n_ref, n_ref + 7):
         for shift in (0, 4, 8, 12):
             total = (n_ref + 16) * fh.DET_BYTES + 64

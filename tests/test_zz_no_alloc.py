@@ -40,7 +40,7 @@ def run_both(fh, S, stride, thr, max_out):
                                       out.data_ptr(), max_out, cnt.data_ptr(), stream)
         else:
             ws_b = L.hog_detect_workspace_bytes(nx, ny)
-            ws = torch.empty(max(ws_b, 256), dtype=torch.uint8, device="cuda")
+            ws = torch.zeros(max(ws_b, 256), dtype=torch.uint8, device="cuda")
             rc = L.hog_detect(s.data_ptr(), dtype, nx, ny, stride, ctypes.c_float(thr), 5, 1, out.data_ptr(),
                               max_out, cnt.data_ptr(), ws.data_ptr(), ws_b, stream)
         assert rc == fh.HOG_OK
@@ -65,6 +65,30 @@ def test_noalloc_matches_workspace_entry_point_twice(fh):
     for _ in range(2):
         (ref, got), (n_ref, n_got) = run_both(fh, S, 8, 10.0, 500)
         assert n_ref == n_got and len(got) == 500 and np.array_equal(ref, got)
+
+
+def test_noalloc_many_tiles_and_at_its_limit(fh):
+    import oracle
+
+    rng = np.random.default_rng(2025)
+    # 2100 x 2100 scores: 2154 tiles, against hog_detect and the oracle's list
+    S = rng.normal(0.0, 1.0, size=(2100, 2100)).astype(np.float32)
+    (ref, got), (n_ref, n_got) = run_both(fh, S, 4, 2.5, 2100 * 2100)
+    xs, ys, sc = oracle.detect(S.astype(np.float64), 4, 2.5)
+    assert n_ref == n_got == len(xs)
+    assert np.array_equal(ref, got)
+    assert np.array_equal(got["x"], xs) and np.array_equal(got["y"], ys)
+    assert np.array_equal(got["score"], sc.astype(np.float32))
+    # exactly HOG_DETECT_NOALLOC_MAX_SCORES scores (every status word of the
+    # scratch in use), twice in a row, with a list capped mid-way
+    ny, nx = 8192, fh.HOG_DETECT_NOALLOC_MAX_SCORES // 8192
+    S = torch.randn(ny * nx, generator=torch.Generator().manual_seed(7)).numpy().reshape(ny, nx)
+    for _ in range(2):
+        (ref, got), (n_ref, n_got) = run_both(fh, S, 4, 3.5, 5000)
+        ys, xs = np.nonzero(S >= np.float32(3.5))
+        assert n_ref == n_got == len(xs) and len(got) == 5000
+        assert np.array_equal(ref, got)
+        assert np.array_equal(got["x"], xs[:5000] * 4) and np.array_equal(got["y"], ys[:5000] * 4)
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(fh):

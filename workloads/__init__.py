@@ -59,15 +59,15 @@ def _value_noise_octave(W: int, H: int, cell: float, rng: np.random.Generator, c
     fy = ys - y0
     fx = fx * fx * (3 - 2 * fx)
     fy = fy * fy * (3 - 2 * fy)
-    a = lat[y0][:, x0]
-    b = lat[y0][:, x0 + 1]
-    c = lat[y0 + 1][:, x0]
-    d = lat[y0 + 1][:, x0 + 1]
-    fx = fx[None, :, None]
-    fy = fy[:, None, None]
-    top = a + (b - a) * fx
-    bot = c + (d - c) * fx
-    return top + (bot - top) * fy
+    # interpolate along x once per lattice row, then pick and blend rows per
+    # pixel row (the same float32 operations per pixel as blending the four
+    # corners of every pixel directly)
+    left = lat[:, x0]
+    right = lat[:, x0 + 1]
+    along_x = left + (right - left) * fx[None, :, None]
+    top = along_x[y0]
+    bot = along_x[y0 + 1]
+    return top + (bot - top) * fy[:, None, None]
 
 
 def rgb_smooth_shapes(W: int, H: int, rng: np.random.Generator, octaves: int = 4,
@@ -91,8 +91,11 @@ def rgb_smooth_shapes(W: int, H: int, rng: np.random.Generator, octaves: int = 4
         if rng.random() < 0.5:
             img[max(cy - ry, 0):cy + ry, max(cx - rx, 0):cx + rx] = color
         else:
-            m = ((xx - cx) / rx) ** 2 + ((yy - cy) / ry) ** 2 <= 1.0
-            img[m] = color
+            # the ellipse lies inside its bounding box; test only the pixels there
+            ya, yb = max(cy - ry, 0), min(cy + ry + 1, H)
+            xa, xb = max(cx - rx, 0), min(cx + rx + 1, W)
+            m = ((xx[ya:yb, xa:xb] - cx) / rx) ** 2 + ((yy[ya:yb, xa:xb] - cy) / ry) ** 2 <= 1.0
+            img[ya:yb, xa:xb][m] = color
     return img
 
 
