@@ -246,18 +246,18 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def algorithmic_bytes(W, H, nb, ncx, ncy, windows):
-    """Bytes each stage must move (RGB image, int32 integral images, int32
-    cells, f32 scores): the figures the rooflines divide by."""
+def algorithmic_bytes(W, H, nb, ncx, ncy, windows, cell_bytes=2):
+    """Bytes each stage must move (RGB image, int32 integral images, cells of
+    `cell_bytes` per count, f32 scores): the figures the rooflines divide by."""
     px = W * H
     return {
         "bin_map": px * (3 + 1),              # RGB in, bins out
         "integral": px * (1 + 4 * nb),        # bins in, int32 planes out
         # Eq. 6 per cell position and bin: one integral-image sample in (each
         # sample of the stride grid is a corner of up to four cells, read once)
-        # and one int32 count out
-        "cell_hist": ncx * ncy * nb * (4 + 4),
-        "score": ncx * ncy * nb * 4 + windows * 4,  # cell map in, score out
+        # and one count out
+        "cell_hist": ncx * ncy * nb * (4 + cell_bytes),
+        "score": ncx * ncy * nb * cell_bytes + windows * 4,  # cell map in, score out
         "detect": windows * 4,
     }
 
@@ -550,7 +550,7 @@ def stage_rooflines(torch, fh, wl, flush, args, hbm):
     mean time (events between the stages inside one graph), against the
     measured HBM peak.  N_b = 8, stride 4, int32 integral images and cells."""
     W, H = 3840, 2160
-    p = fh.HogPipeline(W, H, 3, 8, 4)
+    p = fh.HogPipeline(W, H, 3, 8, 4, cell_dtype=fh.HOG_BF16)
     p.set_weights(wl.weights_f32(8, wl.rng_for(1)), 0.0, 0.5)
     p.set_image(base_4k(wl))
     fns = [p.stage_bin_map, p.stage_integral, p.stage_cell_hist, p.stage_score, p.stage_detect]
@@ -574,7 +574,8 @@ def stage_rooflines(torch, fh, wl, flush, args, hbm):
     px, nb = W * H, 8
     windows = p.nx * p.ny
     alg = algorithmic_bytes(W, H, nb, p.ncx, p.ncy, windows)
-    out = {"workload": "3840x2160 RGB, N_b=8, stride 4, int32 integral images, int32 cells, f32 weights",
+    out = {"workload": "3840x2160 RGB, N_b=8, stride 4, int32 integral images, bf16 cells (exact counts), "
+                       "f32 weights",
            "peak_gbs": hbm}
     for n, t in zip(names, ms):
         gbs = alg[n] / (t * 1e-3) / 1e9
@@ -654,10 +655,48 @@ def blocks_variant(torch, fh, wl, flush, args):
             "windows": nx * ny, "windows_per_s": round(nx * ny / (sum(ms) * 1e-3), 1)}
 
 
+def free_port() -> int:
+    import socket
+
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(n: int, argv: list[str]) -> int:
+    """`--gpus N` outside a torchrun launch: run this same command as N ranks
+    of one node (one process per GPU; torch.distributed.run sets RANK,
+    LOCAL_RANK, WORLD_SIZE and the rendezvous on 127.0.0.1).  Rank 0 prints
+    the JSON line; returns the launcher's exit code."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr=127.0.0.1", f"--master-port={free_port()}", os.path.abspath(__file__), *argv]
+    return subprocess.run(cmd).returncode
+
+
+def timed_region(run_step, read_ms, steps: int, barrier, sync) -> float:
+    """The timed region of every rank: a barrier and a device synchronise on
+    both sides, `steps` steps (each read back by `read_ms` after its own
+    synchronise), then the mean ms per step of this rank."""
+    if barrier is not None:
+        barrier()
+    sync()
+    total = 0.0
+    for k in range(steps):
+        run_step(k)
+        sync()
+        total += read_ms()
+    sync()
+    if barrier is not None:
+        barrier()
+    return total / steps
+
+
 def main():
     args = parse()
     extras = set() if args.no_extras else {e.strip() for e in args.extras.split(",") if e.strip()}
     rank, world, local = dist_env()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        return launch_ranks(args.gpus, sys.argv[1:])
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -679,7 +718,8 @@ def main():
         c["images"] = [wl.rgb_smooth_shapes(iw, ih, wl.rng_for(1, wl.BASE_SEED + 1 + rank))]
     img = c["images"][0]
     H, W = img.shape[:2]
-    pipe = fh.HogPipeline(W, H, 3, c["n_bins"], c["stride"])
+    # bf16 cells: counts <= 64 are exact in bf16, and the score's tensor-core kernel reads them as they lie
+    pipe = fh.HogPipeline(W, H, 3, c["n_bins"], c["stride"], cell_dtype=fh.HOG_BF16)
     pipe.set_weights(c["w"], c["bias"], c["thr"])
     pipe.set_image(img)
     pipe.img_host.copy_(torch.from_numpy(img.reshape(-1)))
@@ -714,21 +754,15 @@ def main():
 
     # timed region: each step is replayed from its graph after an L2 flush;
     # the events are recorded by the GPU at the two ends of the step
-    total_ms = 0.0
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    for k in range(args.steps):
+    def run_step(k):
         flush.fill_(k)
         step()
-        torch.cuda.synchronize()
-        total_ms += read_total()[1]
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
+
+    mine_ms = timed_region(run_step, lambda: read_total()[1], args.steps,
+                           dist.barrier if dist is not None else None, torch.cuda.synchronize)
     clocks = sampler.stop()
     # the slowest replica sets the time; the rate counts every rank's pixels
-    ms_per_step = replicas.max_over_ranks(total_ms / args.steps, device="cuda")
+    ms_per_step = replicas.max_over_ranks(mine_ms, device="cuda")
 
     # per-stage breakdown (same steps, events between the stages)
     stage_ms = {n: 0.0 for n in names}
@@ -843,4 +877,4 @@ def main():
 
 
 if __name__ == "__main__":
-    main()
+    sys.exit(main() or 0)

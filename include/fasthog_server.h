@@ -21,10 +21,12 @@
  * (first fit, 256-byte aligned) and returned to it when the request
  * completes.
  *
- * Threads.  A server is used by one host thread at a time; calls on one
- * server from several threads must be serialised by the caller.  All calls
- * run on the device that was current at hog_server_create (they switch to
- * it and back if another device is current).
+ * Threads.  Without the dispatcher thread (below) a server is used by one
+ * host thread at a time; calls on one server from several threads must be
+ * serialised by the caller.  With it, enqueue, collect and release may come
+ * from any thread.  All calls run on the device that was current at
+ * hog_server_create (they switch to it and back if another device is
+ * current).
  *
  * Errors follow fasthog.h: HOG_ERR_ARG for bad arguments (nothing is
  * enqueued), HOG_ERR_CUDA with hog_last_cuda_error() for a failed CUDA call.
@@ -106,8 +108,43 @@ hog_status hog_server_poll(hog_server* s, hog_server_result* out, int max_out, i
 hog_status hog_server_release(hog_server* s, int32_t token);
 
 /* Requests on the GPU, arena bytes they hold, and slots that are neither on
- * the GPU nor awaiting release.  Any pointer may be NULL. */
+ * the GPU nor awaiting release.  Any pointer may be NULL.  HOG_ERR_UNSUPPORTED
+ * while the dispatcher thread runs (it owns these counts then). */
 hog_status hog_server_stats(const hog_server* s, int* in_flight, size_t* bytes_in_use, int* free_slots);
+
+/*
+ * The server's own dispatcher thread (optional).  hog_server_start launches a
+ * host thread that admits queued requests in arrival order (first in, first
+ * out) as soon as a slot is free and their buffers fit, and watches the
+ * requests on the GPU; so admission and completion never wait for a call
+ * from the caller, and a stall of the caller's thread delays neither.
+ * While it runs, use hog_server_enqueue, hog_server_collect and
+ * hog_server_release (from any thread) instead of hog_server_submit and
+ * hog_server_poll.  hog_server_stop waits until every queued request has
+ * completed, then joins the thread; the results it left stay collectable.
+ * hog_server_destroy stops a running dispatcher first.
+ *
+ * Timestamps are nanoseconds of the steady clock that hog_server_clock_ns
+ * reads (CLOCK_MONOTONIC).
+ */
+typedef struct {
+    hog_server_result r;   /* as hog_server_poll returns it; release r.token when done with r.dets */
+    int64_t t_enqueue_ns;  /* when hog_server_enqueue queued the request (its arrival) */
+    int64_t t_admit_ns;    /* when the dispatcher put its work on the GPU */
+    int64_t t_done_ns;     /* when the dispatcher saw its work complete (detections in host memory) */
+} hog_server_timed_result;
+
+hog_status hog_server_start(hog_server* s);
+hog_status hog_server_stop(hog_server* s);
+/* Queue one request (arguments as hog_server_submit; the image must stay
+ * unchanged until its result is collected).  Never waits for the GPU.
+ * HOG_ERR_ARG for a request that can never be admitted (nothing is queued);
+ * HOG_ERR_UNSUPPORTED when the dispatcher is not running. */
+hog_status hog_server_enqueue(hog_server* s, int32_t rid, const uint8_t* img, int W, int H, int channels);
+/* Completed requests, oldest first: up to max_out of them to `out` (host
+ * memory), their number to *n_out.  Never blocks on the GPU. */
+hog_status hog_server_collect(hog_server* s, hog_server_timed_result* out, int max_out, int* n_out);
+int64_t hog_server_clock_ns(void);
 
 #ifdef __cplusplus
 }

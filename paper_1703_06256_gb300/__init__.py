@@ -69,6 +69,12 @@ class HogServerResult(ctypes.Structure):
                 ("dets", ctypes.c_void_p)]
 
 
+class HogServerTimedResult(ctypes.Structure):
+    """hog_server_timed_result of include/fasthog_server.h."""
+    _fields_ = [("r", HogServerResult), ("t_enqueue_ns", ctypes.c_int64), ("t_admit_ns", ctypes.c_int64),
+                ("t_done_ns", ctypes.c_int64)]
+
+
 class HogError(RuntimeError):
     def __init__(self, fn: str, status: int, cuda_error: int = 0):
         self.status = status
@@ -122,6 +128,11 @@ def _load() -> ctypes.CDLL:
         "hog_server_poll": (I, [P, P, I, P]),
         "hog_server_release": (I, [P, ctypes.c_int32]),
         "hog_server_stats": (I, [P, P, P, P]),
+        "hog_server_start": (I, [P]),
+        "hog_server_stop": (I, [P]),
+        "hog_server_enqueue": (I, [P, ctypes.c_int32, P, I, I, I]),
+        "hog_server_collect": (I, [P, P, I, P]),
+        "hog_server_clock_ns": (ctypes.c_int64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -138,7 +149,8 @@ EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_devi
             "hog_build_soft_lut", "hog_cell_hist_soft", "hog_block_norm", "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
-            "hog_server_poll", "hog_server_release", "hog_server_stats")
+            "hog_server_poll", "hog_server_release", "hog_server_stats", "hog_server_start", "hog_server_stop",
+            "hog_server_enqueue", "hog_server_collect", "hog_server_clock_ns")
 
 
 def lib() -> ctypes.CDLL:
@@ -384,6 +396,31 @@ def hog_server_poll(handle, out, max_out: int) -> int:
 
 def hog_server_release(handle, token: int) -> None:
     _check("hog_server_release", _lib.hog_server_release(handle, token))
+
+
+def hog_server_start(handle) -> None:
+    _check("hog_server_start", _lib.hog_server_start(handle))
+
+
+def hog_server_stop(handle) -> None:
+    _check("hog_server_stop", _lib.hog_server_stop(handle))
+
+
+def hog_server_enqueue(handle, rid: int, img_host, W: int, H: int, channels: int) -> None:
+    """Queue a request for the dispatcher thread; `img_host` must stay alive
+    and unchanged until its result has been collected."""
+    _check("hog_server_enqueue", _lib.hog_server_enqueue(handle, rid, _host_ptr(img_host), W, H, channels))
+
+
+def hog_server_collect(handle, out, max_out: int) -> int:
+    """Fill `out` (a ctypes array of HogServerTimedResult) and return how many."""
+    n = ctypes.c_int(0)
+    _check("hog_server_collect", _lib.hog_server_collect(handle, out, max_out, ctypes.byref(n)))
+    return n.value
+
+
+def hog_server_clock_ns() -> int:
+    return _lib.hog_server_clock_ns()
 
 
 def hog_server_stats(handle) -> tuple[int, int, int]:

@@ -96,8 +96,9 @@ class HogPlanBatch:
         self.channels, self.levels, self.n_bins = channels, levels, n_bins
         self.stride, self.cell, self.cells_x, self.cells_y = stride, cell, cells_x, cells_y
         self.w_dtype = HOG_BF16 if w_dtype is None else w_dtype
-        self.cell_dtype = (HOG_BF16 if self.w_dtype != HOG_F32 and cell <= 16 else HOG_F32) \
-            if cell_dtype is None else cell_dtype
+        # counts of cells up to 16 x 16 are exact in bf16, and the tensor-core scores read bf16 cells
+        # (with any weight type)
+        self.cell_dtype = (HOG_BF16 if cell <= 16 else HOG_F32) if cell_dtype is None else cell_dtype
         self.score_dtype = HOG_I32 if self.w_dtype == HOG_I8 else HOG_F32
         dev = self.device
         self.lut = torch.empty(HOG_LUT_BYTES, dtype=torch.uint8, device=dev)
@@ -188,10 +189,10 @@ class HogPlanBatch:
     def launches(self) -> int:
         """Kernels one pass launches: pyramids, fused cells, score, and the
         detection count, scan and scatter."""
-        from . import HOG_BF16, HOG_F32
+        from . import HOG_BF16
 
         n_pyr = len(self.sizes) if self.levels > 1 else 0
-        tc = (self.w_dtype != HOG_F32 and self.cell_dtype == HOG_BF16 and self.n_bins in (8, 16)
+        tc = (self.cell_dtype == HOG_BF16 and self.n_bins in (8, 16)
               and (self.cells_x, self.cells_y) == (8, 16) and self.cell // self.stride in (1, 2, 4))
         score = 1 if tc else sum(1 for m in self.item_meta if m["nx"] * m["ny"] > 0)
         return n_pyr + 1 + score + (3 if self.windows > 0 else 1)

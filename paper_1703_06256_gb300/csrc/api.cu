@@ -234,11 +234,15 @@ hog_status hog_window_score(const void* cells, int cell_dtype, int ncx, int ncy,
     const int r = cell / stride;
     const float b = w_dtype == HOG_I8 ? (float)std::llround((double)bias) : bias;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const bool rows = score_rows_supported(cells, cell_dtype, n_bins, cells_x, cells_y, r);
     const bool tc = score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx);
     const bool slide = score_slide_supported(cells, n_bins, cells_x, cells_y, r);
     const int path = tune_get(HOG_TUNE_SCORE_PATH);
-    // automatic: bf16 and int8 weights on the tensor cores; f32 weights (three MMAs per step) there only
-    // when the map alone fills the GPU, else on the CUDA cores
+    // automatic: bf16 cells of 8 bins on the row-GEMM tensor-core kernel (any weights); other bf16 cells
+    // on the banded tensor-core kernel for bf16 and int8 weights, and for f32 weights (three MMAs per
+    // step) when the map alone fills the GPU, else on the CUDA cores
+    if (rows && path != 1)
+        return launch_score_rows(static_cast<const uint16_t*>(cells), ncx, ncy, r, w, w_dtype, 1, &b, scores, st);
     const bool auto_tc = w_dtype != HOG_F32 || !slide || score_tc_fills_gpu(ncx, ncy, n_bins, r);
     const bool use_tc = tc && (path == 2 || (path == 0 && auto_tc));
     if (use_tc)
@@ -301,6 +305,11 @@ hog_status hog_window_score_multi(const void* cells, int cell_dtype, int ncx, in
     const long nx = (long)ncx - (long)(cells_x - 1) * r, ny = (long)ncy - (long)(cells_y - 1) * r;
     if (nx <= 0 || ny <= 0) return HOG_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    // 8 bins: the row-GEMM kernel, several filters per pass, each scored exactly as alone
+    if (score_rows_supported(cells, cell_dtype, n_bins, cells_x, cells_y, r) &&
+        tune_get(HOG_TUNE_SCORE_PATH) != 1)
+        return launch_score_rows(static_cast<const uint16_t*>(cells), ncx, ncy, r, w, w_dtype, n_filters, biases,
+                                 scores, st);
     if (score_tc_supported(cell_dtype, n_bins, cells_x, cells_y, r, ncx) &&
         reinterpret_cast<uintptr_t>(cells) % 16 == 0)
         return launch_score_tc_multi(static_cast<const uint16_t*>(cells), ncx, ncy, n_bins, r, w, w_dtype, n_filters,

@@ -40,9 +40,12 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
     if (cell < 1 || stride < 1 || cell % stride != 0) return HOG_ERR_ARG;
     if (!cells_fused_supported(n_bins, cell, stride)) return HOG_ERR_UNSUPPORTED;
     const int r = cell / stride;
-    const int wpc = score_tc_windows(n_bins);
+    // 8 bins, 8 x 16 cells: the row-GEMM score (strips of 128 windows by ranges of rows); otherwise the
+    // banded tensor-core score (score_tc_windows() windows by Tc rows of one residue class)
+    const bool rows = n_bins == 8 && cells_x == 8 && cells_y == 16 && (r == 1 || r == 2 || r == 4);
+    const int wpc = rows ? 128 : score_tc_windows(n_bins);
     // first pass: sizes, and the tensor-core row count the whole batch supports
-    long ctas32 = 0;
+    long ctas32 = 0, strip_rows = 0;
     for (int i = 0; i < n_items; ++i) {
         const hog_batch_item& it = items[i];
         if (it.img == nullptr || it.cells == nullptr) return HOG_ERR_ARG;
@@ -54,9 +57,12 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
         if (nx > 0 && ny > 0) {
             if (it.scores == nullptr) return HOG_ERR_ARG;
             ctas32 += (long)((nx + wpc - 1) / wpc) * ((ny + 32 * r - 1) / (32 * r)) * r;
+            strip_rows += (long)((nx + wpc - 1) / wpc) * ny;
         }
     }
-    const int Tc = score_tc_rows_for(ctas32);
+    const int Tc = rows ? score_rows_batch_rows(strip_rows) : score_tc_rows_for(ctas32);
+    const int band_rows = rows ? Tc : Tc * r;  // output rows of one CTA's range (all residues, or one class)
+    const int classes = rows ? 1 : r;
     PlanHeader* h = static_cast<PlanHeader*>(plan);
     std::memset(h, 0, sizeof(PlanHeader));
     PlanItem* out = const_cast<PlanItem*>(plan_items(plan));
@@ -76,8 +82,8 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
         cells_t += p.ncx > 0 && p.ncy > 0 ? cells_fused_tiles(p.ncx, p.ncy, stride) : 0;
         p.score_c0 = (int)score_c;
         p.score_tx = (p.nx + wpc - 1) / wpc;
-        p.score_bands = (p.ny + Tc * r - 1) / (Tc * r);
-        score_c += (long)p.score_tx * p.score_bands * r;
+        p.score_bands = (p.ny + band_rows - 1) / band_rows;
+        score_c += (long)p.score_tx * p.score_bands * classes;
         p.detect_t0 = (int)detect_t;
         detect_t += detect_tiles((long)p.nx * p.ny);
         if (cells_t > 0x7FFFFFFFL || score_c > 0x7FFFFFFFL || detect_t > 0x7FFFFFFFL) return HOG_ERR_ARG;
@@ -94,6 +100,7 @@ hog_status hog_batch_plan(const hog_batch_item* items, int n_items, int channels
     h->cells_tiles = (int)cells_t;
     h->score_tc = Tc;
     h->score_ctas = (int)score_c;
+    h->score_rows = rows ? 1 : 0;
     h->detect_tiles = (int)detect_t;
     return HOG_OK;
 }
@@ -123,12 +130,16 @@ hog_status hog_window_score_batch(const void* plan, const void* plan_dev, int ce
     if (w_dtype != HOG_F32 && w_dtype != HOG_BF16 && w_dtype != HOG_I8) return HOG_ERR_ARG;
     if (!std::isfinite(bias)) return HOG_ERR_ARG;
     const PlanItem* items = plan_items(plan);
+    if (w_dtype == HOG_I8 && 127.0 * h->cells_x * h->cells_y * (double)h->cell * h->cell +
+                                     std::fabs((double)std::llround((double)bias)) >= 16777216.0)
+        return HOG_ERR_UNSUPPORTED;  // int8 scores are exact only below 2^24 (as hog_window_score)
     bool tc = score_tc_supported(cell_dtype, h->n_bins, h->cells_x, h->cells_y, h->r, 0);
     for (int i = 0; i < h->n_items && tc; ++i)
         if (items[i].nx > 0 && reinterpret_cast<uintptr_t>(items[i].it.cells) % 16 != 0) tc = false;
     const cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (tc) {
         const float b = w_dtype == HOG_I8 ? (float)std::llround((double)bias) : bias;
+        if (h->score_rows) return launch_score_rows_batch(*h, plan_dev, w, w_dtype, b, st);
         return launch_score_tc_batch(*h, plan_dev, w, w_dtype, b, st);
     }
     // other combinations: the per-image call on each item, in plan order

@@ -18,14 +18,15 @@ struct PlanHeader {
     int score_tc;      // output rows per tensor-core CTA
     int score_ctas;    // tensor-core CTAs over the whole batch
     int detect_tiles;  // detection tiles over the whole batch
-    int pad[3];
+    int score_rows;    // 1: the row-GEMM tensor-core score (score_tc = output rows per CTA), 0: banded
+    int pad[2];
 };
 
 struct PlanItem {
     hog_batch_item it;
     int ncx, ncy, nx, ny;
     int cells_t0, cells_tx;               // first fused tile of the item, fused tiles per tile row
-    int score_c0, score_tx, score_bands;  // first tensor-core CTA, 128-window columns, row bands
+    int score_c0, score_tx, score_bands;  // first tensor-core CTA, 128-window columns, row bands (ranges)
     int detect_t0;                        // first detection tile
     int pad[2];
 };
@@ -76,6 +77,11 @@ hog_status launch_detect_batch(const PlanHeader& h, const void* plan_dev, int sc
                                int max_out, int32_t* d_count, int32_t* item_counts, void* ws, cudaStream_t st);
 size_t pyramid_bytes(int W, int H, int channels, int levels);
 int score_tc_rows_for(long ctas32);
+// The row-GEMM score over a batch: output rows per CTA for strip_rows
+// (128-window strips x output rows, summed over the items), and the launch.
+int score_rows_batch_rows(long strip_rows);
+hog_status launch_score_rows_batch(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
+                                   cudaStream_t st);
 hog_status launch_pyramid(const uint8_t* img, int W, int H, int channels, size_t pitch, int levels, uint8_t* out,
                           cudaStream_t st);
 

@@ -711,7 +711,8 @@ __global__ void __launch_bounds__(32 * NW)
     __shared__ uint32_t colw[NW][NM][kSlice];  // per-warp column counts, 8-bit fields, by cslot
     __shared__ uint32_t vtop[2 * NM][kSlice];  // V at the tile top, 16-bit fields, by cslot:
                                                // word 2m bins 4m, 4m+2; word 2m+1 bins 4m+1, 4m+3
-    __shared__ int rl_s[R][WIN];               // the tile rows' counts over the group, then RL
+    __shared__ int rl_s[R][WIN];               // the tile rows' counts over the group
+    __shared__ uint32_t rl16_s[R][WIN / 2];    // RL of the tile's rows, 16-bit fields (bins 2i, 2i + 1)
     __shared__ int corner_s[WIN];
     __shared__ uint32_t tag_s;
 
@@ -728,6 +729,8 @@ __global__ void __launch_bounds__(32 * NW)
     pdl_wait();
     if (tid == 0) tag_s = onepass::launch_tag(ws.header);
     if (tid < WIN) corner_s[tid] = 0;
+    for (int e = tid; e < 2 * NM * kSlice; e += NT) (&vtop[0][0])[e] = 0;
+    for (int e = tid; e < R * (WIN / 2); e += NT) (&rl16_s[0][0])[e] = 0;
 
     // ---- this warp's rows: stage the bins, count per column and per row
     {
@@ -792,14 +795,31 @@ __global__ void __launch_bounds__(32 * NW)
     __syncthreads();
     if (tid == 0) onepass::st_release(ws.flags + t, tag);
 
-    // ---- wait for the tiles above and to the left (all of lower number)
+    // ---- wait for the tiles above and to the left (all of lower number): every thread
+    // checks its share of their flags with independent loads, then acquires
     {
-        bool ok = true;
         const int nd = (I + 1) * (g + 1) - 1;
-        for (int e = tid; e < nd; e += NT) {
-            const int Ip = e / (g + 1), gp = e - Ip * (g + 1);
-            if (!onepass::wait_flag(ws.flags + (size_t)Ip * n_groups + gp, tag)) ok = false;
+        bool ok = true;
+        for (int e0 = 0; e0 < nd; e0 += 8 * NT) {
+            const uint64_t t0 = ptx::globaltimer_ns();
+            while (true) {
+                bool all = true;
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const int e = e0 + k * NT + tid;
+                    if (e < nd) {
+                        const int Ip = e / (g + 1), gp = e - Ip * (g + 1);
+                        all &= onepass::ld_relaxed(ws.flags + (size_t)Ip * n_groups + gp) == tag;
+                    }
+                }
+                if (all) break;
+                if (ptx::globaltimer_ns() - t0 > kWaitLimitNs) {
+                    ok = false;
+                    break;
+                }
+            }
         }
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
         if (!ok) atomicOr(status, kStatusTimeout);
     }
     __syncthreads();
@@ -807,45 +827,110 @@ __global__ void __launch_bounds__(32 * NW)
     if (tid == 0 && t == (int)gridDim.x - 1) onepass::end_launch(ws.header, tag);
     pdl_trigger();
 
-    // ---- carries from the aggregates
-    // V at the tile top: the column counts of the tiles above, 8-bit fields widened to 16
-    for (int p = tid; p < NM * kSlice; p += NT) {
-        const int m = p / kSlice, x = p - m * kSlice;
-        const int xg = g * kSlice + x;
-        uint32_t even = 0, odd = 0;
-        if (xg < W) {
-            const uint32_t* src = ws.colagg + (size_t)m * W + xg;
-#pragma unroll 4
-            for (int Ip = 0; Ip < I; ++Ip) {
-                const uint32_t a = __ldcg(src + (size_t)Ip * NM * W);
-                even += a & 0x00FF00FFu;
-                odd += (a >> 8) & 0x00FF00FFu;
+    // ---- carries from the aggregates (loads from L2, many in flight per thread)
+    // V at the tile top: task (m, column quad q), the bands above split over NT / (32 NM)
+    // slices; 8-bit fields widened to 16 (V <= H < 65536), slices added in shared memory
+    {
+        constexpr int NTASK = 32 * NM, NSL = NT / NTASK;
+        static_assert(NT % NTASK == 0, "every thread takes one task and one slice of the bands");
+        {
+            const int task = tid % NTASK, s0 = tid / NTASK;
+            const int m = task >> 5, q = task & 31;
+            const int xg = g * kSlice + 4 * q;
+            uint32_t even[4] = {0, 0, 0, 0}, odd[4] = {0, 0, 0, 0};
+            for (int sl = s0; xg < W && sl < I; sl += NSL * 4) {
+                uint32_t a[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int Ip = sl + u * NSL;
+                    const uint32_t* src = ws.colagg + ((size_t)Ip * NM + m) * W + xg;
+                    if (Ip >= I) {
+                        a[u][0] = a[u][1] = a[u][2] = a[u][3] = 0;
+                    } else if (vec) {
+                        const uint4 v4 = __ldcg(reinterpret_cast<const uint4*>(src));
+                        a[u][0] = v4.x;
+                        a[u][1] = v4.y;
+                        a[u][2] = v4.z;
+                        a[u][3] = v4.w;
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) a[u][k] = xg + k < W ? __ldcg(src + k) : 0u;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        even[k] += a[u][k] & 0x00FF00FFu;
+                        odd[k] += (a[u][k] >> 8) & 0x00FF00FFu;
+                    }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // packed 16-bit adds: no field passes H < 65536
+                if (even[k]) atomicAdd(&vtop[2 * m][cslot(4 * q + k)], even[k]);
+                if (odd[k]) atomicAdd(&vtop[2 * m + 1][cslot(4 * q + k)], odd[k]);
             }
         }
-        vtop[2 * m][cslot(x)] = even;
-        vtop[2 * m + 1][cslot(x)] = odd;
     }
-    // RL of the tile's rows: the row counts of the tiles to the left
-    for (int e = tid; e < R * WIN; e += NT) {
-        const int r = e / WIN, b = e - r * WIN;
-        const int y = y_tile + r;
-        int sum = 0;
-        if (y < H) {
-            const uint16_t* src = ws.rowagg + (size_t)y * n_groups * WIN + b;
-#pragma unroll 4
-            for (int gp = 0; gp < g; ++gp) sum += (int)__ldcg(src + (size_t)gp * WIN);
-        }
-        rl_s[r][b] = sum;
-    }
-    // corner: the totals of the tiles above-left (thread tid always takes bin tid % WIN)
+    // RL of the tile's rows: task (row r, group slice), the groups to the left split over
+    // NT / R slices; WIN 16-bit counts per (row, group) load as one vector
     {
-        int sum = 0;
-        const int gw = g * WIN, n = I * gw;
-        for (int e = tid; e < n; e += NT) {
-            const int Ip = e / gw;
-            sum += (int)__ldcg(ws.totagg + (size_t)Ip * n_groups * WIN + (e - Ip * gw));
+        constexpr int NSL = NT / R;
+        const int r = tid % R, sl0 = tid / R;
+        const int y = y_tile + r;
+        uint32_t acc[WIN / 2];
+#pragma unroll
+        for (int i = 0; i < WIN / 2; ++i) acc[i] = 0;
+        if (y < H) {
+            const uint16_t* row = ws.rowagg + (size_t)y * n_groups * WIN;
+#pragma unroll 2
+            for (int gp = sl0; gp < g; gp += NSL) {
+                const uint32_t* src = reinterpret_cast<const uint32_t*>(row + (size_t)gp * WIN);
+                if (WIN == 4) {
+                    const uint2 v2 = __ldcg(reinterpret_cast<const uint2*>(src));
+                    acc[0] += v2.x;
+                    acc[1 % (WIN / 2)] += v2.y;
+                } else {
+#pragma unroll
+                    for (int q = 0; q < WIN / 8; ++q) {
+                        const uint4 v4 = __ldcg(reinterpret_cast<const uint4*>(src) + q);
+                        acc[4 * q] += v4.x;
+                        acc[(4 * q + 1) % (WIN / 2)] += v4.y;
+                        acc[(4 * q + 2) % (WIN / 2)] += v4.z;
+                        acc[(4 * q + 3) % (WIN / 2)] += v4.w;
+                    }
+                }
+            }
         }
-        if (sum != 0) atomicAdd(&corner_s[tid % WIN], sum);
+#pragma unroll
+        for (int i = 0; i < WIN / 2; ++i)  // a row holds at most W < 65536 of a bin
+            if (acc[i]) atomicAdd(&rl16_s[r][i], acc[i]);
+    }
+    // corner: the totals of the tiles above-left, task (band, group), warp sums per bin
+    {
+        int acc[WIN];
+#pragma unroll
+        for (int b = 0; b < WIN; ++b) acc[b] = 0;
+        const int n = I * g;
+        for (int task = tid; task < n; task += NT) {
+            const int Ip = task / g, gp = task - Ip * g;
+            const uint4* src = reinterpret_cast<const uint4*>(ws.totagg + ((size_t)Ip * n_groups + gp) * WIN);
+#pragma unroll
+            for (int q = 0; q < WIN / 4; ++q) {
+                const uint4 v4 = __ldcg(src + q);
+                acc[4 * q] += (int)v4.x;
+                acc[4 * q + 1] += (int)v4.y;
+                acc[4 * q + 2] += (int)v4.z;
+                acc[4 * q + 3] += (int)v4.w;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < WIN; ++b) {
+            int v = acc[b];
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+            if (lane == 0 && v != 0) atomicAdd(&corner_s[b], v);
+        }
     }
     __syncthreads();
 
@@ -873,7 +958,7 @@ __global__ void __launch_bounds__(32 * NW)
 #pragma unroll
     for (int b = 0; b < WIN; ++b) {
         int corner = corner_s[b];
-        for (int r = 0; r < warp * HW; ++r) corner += rl_s[r][b];
+        for (int r = 0; r < warp * HW; ++r) corner += (int)((rl16_s[r][b >> 1] >> (16 * (b & 1))) & 0xFFFFu);
         const int tot = acc[b][3];
         const int incl = (int)warp_incl_scan((uint32_t)tot, lane);
         const int o = corner + incl - tot;
@@ -905,7 +990,8 @@ __global__ void __launch_bounds__(32 * NW)
 #pragma unroll
         for (int b = 0; b < WIN; ++b) {
             const int m = b >> 2, e = b & 3;
-            const int base = rl_s[warp * HW + r][b] + (int)byte_at(E[m], e);
+            const int base = (int)((rl16_s[warp * HW + r][b >> 1] >> (16 * (b & 1))) & 0xFFFFu) +
+                             (int)byte_at(E[m], e);
 #pragma unroll
             for (int k = 0; k < 4; ++k) acc[b][k] += base + (int)byte_at(P[k][m], e);
         }

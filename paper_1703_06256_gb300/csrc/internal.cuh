@@ -65,6 +65,11 @@ bool score_tc_fills_gpu(int ncx, int ncy, int n_bins, int r);
 hog_status launch_score_tc(const uint16_t* cells_bf16, int ncx, int ncy, int n_bins, int cells_x,
                            int cells_y, int r, const void* w, int w_dtype, float bias,
                            void* scores, cudaStream_t st);
+// The row-GEMM tensor-core score (score_rows.cu): bf16 cells of 8 bins, 8 x 16-cell windows.
+bool score_rows_supported(const void* cells, int cell_dtype, int n_bins, int cells_x, int cells_y, int r);
+// n_filters filters of 1024 weights each, host biases (rounded for int8 weights by the launcher).
+hog_status launch_score_rows(const uint16_t* cells_bf16, int ncx, int ncy, int r, const void* w, int w_dtype,
+                             int n_filters, const float* biases, void* scores, cudaStream_t st);
 bool cells_soft_supported(int n_bins, int cell, int stride);
 hog_status launch_build_soft_lut(int n_bins, uint16_t* lut, cudaStream_t st);
 hog_status launch_cells_soft(const uint8_t* img, int W, int H, int channels, size_t pitch, const uint16_t* lut,

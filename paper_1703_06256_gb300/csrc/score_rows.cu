@@ -1,0 +1,419 @@
+// score_rows.cu -- window score on the tensor cores, one GEMM per cell row
+// (the paper's linear score, Sections 1 and 4: the inner product of the
+// window feature with a weight vector at every scan position), for windows
+// of 8 x 16 cells of 8 bins.
+//
+//   P[c][px][j] = sum_{i<8, b<8} w[j][i][b] * C[c][px + i r][b]
+//   S[py][px]   = bias + sum_{j<16} P[py + j r][px][j]
+//
+// P of one cell row c is a dense GEMM: M = 128 windows px, N = the 16 filter
+// rows j, K = 8 cells x 8 bins.  A is the cell row in shared memory as it
+// lies in HBM ([px][8 bins] bf16, 16 bytes per cell): the 8 x 16-byte core
+// matrix (windows px0 + 8g .. +7, cell i) starts at byte (8g + i r) * 16, so
+// an MMA over cells i, i + 1 takes a descriptor at cell i r with a K-direction
+// stride (LBO) of r * 16 bytes and an M-direction stride (SBO) of 128 bytes:
+// the descriptor does the im2col.  B holds, per cell i, the N rows of its
+// weights (one row per filter row j and weight part; 8 bins each).  f32
+// weights become three exact bf16 parts (each the bf16 rounding of what the
+// parts before it leave), which sit side by side as N = 48 accumulator
+// columns; bf16 and int8 weights (exact in bf16) are one part, N = 16.
+// Counts are exact in bf16 and a count times a bf16 part is exact in f32, so
+// every product is exact; only the f32 sums round.
+//
+// Several filters (hog_window_score_multi) widen the GEMM: filter f's rows
+// follow filter f - 1's in B, N = 16 x parts x filters (up to 256), each
+// filter keeps its own ring of running sums, and one pass over the cell rows
+// scores all of them; a filter's sums are formed in the same order as when it
+// is scored alone, so its scores are the same bit for bit.
+//
+// Every MMA row is useful: a CTA streams the cell rows py0 .. py1 - 1 + 15 r
+// of one strip of 128 windows through a ring of shared-memory stages (bulk
+// copies, mbarriers), one thread issues 4 MMAs per row (K = 64) into one of
+// two TMEM accumulators, and four epilogue warps (one per 32 TMEM lanes: lane
+// m is window px0 + m) read P of the row back, add the parts ((lo + mid) +
+// hi), and add P_j into a running sum per window py = c - j r kept in
+// shared memory (a ring of 16 r rows per window column).  After row c the
+// window py = c - 15 r has all 16 of its rows: it is written (with the bias)
+// and its ring slot cleared.  Rows of windows above py0 fall in the ring
+// too and are cleared unwritten.
+//
+// Every wait is bounded: on a timeout the kernel sets the device status bit,
+// lets its copies and MMAs drain (again bounded), frees TMEM and returns.
+#include <cmath>
+#include <type_traits>
+
+#include "batch_plan.cuh"
+#include "internal.cuh"
+#include "ptx.cuh"
+#include "tcgen05.cuh"
+
+namespace fasthog {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kM = 128;        // windows per CTA (TMEM lanes)
+constexpr int kEpiWarps = 4;   // one per 32 TMEM lanes
+constexpr int kThreads = 32 * (kEpiWarps + 2);
+constexpr int kStages = 8;     // cell rows in flight
+constexpr int kBufs = 2;       // TMEM accumulators
+
+constexpr int kMaxFilters = 16;  // filters per launch at most (N <= 256 with one part)
+
+// Per-filter biases, passed by value (captured with the launch).
+struct RowsBias {
+    float b[kMaxFilters];
+};
+
+// Shared-memory and TMEM layout for nf filters of `parts` weight parts at r.
+struct RowsGeom {
+    int N, BUF, COLS, RS, ROW_BYTES, PLANE_BYTES;
+    size_t planes, stages, ring, bars;
+    __host__ __device__ RowsGeom(int r, int parts, int nf) {
+        N = 16 * parts * nf;                                  // accumulator columns of one row
+        BUF = 16;
+        while (BUF < N) BUF *= 2;                             // column stride of the two accumulators
+        COLS = kBufs * BUF < 32 ? 32 : kBufs * BUF;           // TMEM columns allocated
+        RS = 16 * r;                                          // ring rows per window column and filter
+        ROW_BYTES = (kM + 7 * r) * 16;
+        PLANE_BYTES = N * 16;                                 // one cell's weights: N rows of 8 bf16
+        planes = (size_t)8 * PLANE_BYTES;
+        stages = (size_t)kStages * ROW_BYTES;
+        ring = (size_t)nf * RS * kM * 4;
+        bars = (2 * kStages + 2 * kBufs + 2) * 8;
+    }
+    __host__ __device__ size_t smem_bytes() const { return 1024 + planes + stages + ring + bars; }
+};
+
+// BATCH = false: one image, CTA (blockIdx.x, .y) = (strip of 128 windows,
+// range of rows_per_cta output rows).  BATCH = true: the CTAs of every item
+// of a batch plan in one 1-D grid; each CTA finds its item and its (strip,
+// range) from the plan and overrides the image arguments.
+template <int R, typename WT, typename OutT, bool BATCH>
+__global__ void __launch_bounds__(kThreads, 1)
+    score_rows_kernel(const uint16_t* __restrict__ cells, int ncx, int ncy, const WT* __restrict__ w, int nf,
+                      const __grid_constant__ RowsBias fbias, int nx, int ny, int rows_per_cta,
+                      OutT* __restrict__ scores, const PlanItem* __restrict__ items, int n_items,
+                      unsigned int* status) {
+    constexpr int PARTS = weight_parts<WT>();
+    const RowsGeom G(R, PARTS, nf);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint8_t* planes = base;
+    uint8_t* stages = planes + G.planes;
+    float* ring = reinterpret_cast<float*>(stages + G.stages);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(ring) + G.ring);
+    uint64_t* full = bars;                 // [kStages] a cell row has landed
+    uint64_t* empty = bars + kStages;      // [kStages] its MMAs have read it
+    uint64_t* dfull = bars + 2 * kStages;  // [kBufs]   an accumulator holds P of a row
+    uint64_t* dempty = dfull + kBufs;      // [kBufs]   the epilogue has read it
+    uint64_t* done = dempty + kBufs;       // every MMA issued has completed
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    __shared__ int aborted;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int xt = blockIdx.x, yr = blockIdx.y;
+    if constexpr (BATCH) {
+        const PlanItem* it = items + find_item<Stage::kScore>(items, n_items, (int)blockIdx.x);
+        const int local = (int)blockIdx.x - it->score_c0;
+        xt = local % it->score_tx;
+        yr = local / it->score_tx;
+        cells = static_cast<const uint16_t*>(it->it.cells);
+        scores = static_cast<OutT*>(it->it.scores);
+        ncx = it->ncx;
+        ncy = it->ncy;
+        nx = it->nx;
+        ny = it->ny;
+    }
+    const int px0 = xt * kM;
+    const int py0 = yr * rows_per_cta;
+    const int py1 = min(ny, py0 + rows_per_cta);
+    const int nrows = (py1 - py0) + 15 * R;  // cell rows py0 .. py1 - 1 + 15 r (all < ncy)
+
+    // weights: plane i, row n = (f * PARTS + part) * 16 + j holds bins 0..7 of filter f's
+    // w[j][i][.], part `part`
+    for (int e = tid; e < 8 * G.N; e += kThreads) {
+        const int i = e / G.N, n = e - i * G.N, fp = n >> 4, j = n & 15;
+        const int f = fp / PARTS, part = fp - f * PARTS;
+        *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) =
+            load_weight8_part<WT>(w, f * 1024 + (j * 8 + i) * 8, part);
+    }
+    for (int e = tid; e < nf * G.RS * kM; e += kThreads) ring[e] = 0.f;
+    if (tid == 0) {
+        aborted = 0;
+        for (int s = 0; s < kStages; ++s) {
+            ptx::mbar_init(&full[s], 1);
+            ptx::mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < kBufs; ++b) {
+            ptx::mbar_init(&dfull[b], 1);
+            ptx::mbar_init(&dempty[b], kEpiWarps);
+        }
+        ptx::mbar_init(done, 1);
+        ptx::fence_mbar_init();
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         ptx::smem_addr(tmem_slot)),
+                     "r"(G.COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // the planes were written by ordinary stores; the MMAs read them through the async proxy
+    ptx::fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    pdl_trigger();  // tail of the path: the successor is small, launch it early
+    pdl_wait();     // set-up above read only the weights; the cell rows come from the predecessor
+
+    if (warp == kEpiWarps) {
+        if (lane == 0) {
+            // producer: cell rows py0 + q into the stage ring
+            const int valid = min(kM + 7 * R, ncx - px0);  // > 0: px0 < nx <= ncx
+            const uint32_t bytes = (uint32_t)valid * 16;
+            int armed = 0;
+            for (int q = 0; q < nrows; ++q) {
+                const int s = q % kStages;
+                if (!ptx::mbar_wait_bounded(&empty[s], ((q / kStages) & 1) ^ 1, kWaitLimitNs) ||
+                    *reinterpret_cast<volatile int*>(&aborted)) {
+                    atomicOr(status, kStatusTimeout);
+                    atomicExch(&aborted, 1);
+                    break;
+                }
+                ptx::mbar_arrive_expect_tx(&full[s], bytes);
+                ptx::bulk_g2s(stages + (size_t)s * G.ROW_BYTES, cells + ((size_t)(py0 + q) * ncx + px0) * 8, bytes,
+                              &full[s]);
+                armed = q + 1;
+            }
+            if (*reinterpret_cast<volatile int*>(&aborted)) {
+                // let the copies already issued land before the CTA can exit (bounded)
+                for (int k = armed > kStages ? armed - kStages : 0; k < armed; ++k)
+                    ptx::mbar_wait_bounded(&full[k % kStages], (k / kStages) & 1, kWaitLimitNs);
+            }
+        }
+    } else if (warp == kEpiWarps + 1) {
+        if (lane == 0) {
+            // MMA issuer: P of row q into accumulator q % kBufs
+            const uint32_t idesc = instr_desc(kM, G.N);
+            const uint32_t planes_addr = ptx::smem_addr(planes);
+            for (int q = 0; q < nrows; ++q) {
+                const int s = q % kStages, b = q % kBufs;
+                if (!ptx::mbar_wait_bounded(&full[s], (q / kStages) & 1, kWaitLimitNs) ||
+                    !ptx::mbar_wait_bounded(&dempty[b], ((q / kBufs) & 1) ^ 1, kWaitLimitNs) ||
+                    *reinterpret_cast<volatile int*>(&aborted)) {
+                    atomicOr(status, kStatusTimeout);
+                    atomicExch(&aborted, 1);
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_addr = ptx::smem_addr(stages + (size_t)s * G.ROW_BYTES);
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {  // cells 2ks, 2ks + 1
+                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * R * 16), (uint32_t)(R * 16), 128);
+                    const uint64_t bd = smem_desc(planes_addr + (uint32_t)(2 * ks * G.PLANE_BYTES),
+                                                  (uint32_t)G.PLANE_BYTES, 128);
+                    mma_bf16(tmem + (uint32_t)(b * G.BUF), ad, bd, idesc, ks > 0 ? 1u : 0u);
+                }
+                mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
+                mma_commit(&dfull[b]);  // the accumulator holds P of row q
+            }
+            mma_commit(done);
+            if (!ptx::mbar_wait_bounded(done, 0, kWaitLimitNs)) atomicOr(status, kStatusTimeout);
+        }
+    } else {
+        // epilogue: thread tid is TMEM lane tid, window column px0 + tid
+        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
+        const int px = px0 + tid;
+        const size_t plane = (size_t)nx * ny;
+        for (int q = 0; q < nrows; ++q) {
+            const int b = q % kBufs;
+            if (!ptx::mbar_wait_bounded(&dfull[b], (q / kBufs) & 1, kWaitLimitNs) ||
+                *reinterpret_cast<volatile int*>(&aborted)) {
+                atomicOr(status, kStatusTimeout);
+                atomicExch(&aborted, 1);
+                break;
+            }
+            tc_fence_after();
+            const int c = py0 + q;       // cell row
+            const int py = c - 15 * R;   // the window that has all of its rows after this one
+            for (int f = 0; f < nf; ++f) {
+                uint32_t v[PARTS][16];
+#pragma unroll
+                for (int p = 0; p < PARTS; ++p)
+                    tmem_load16_async(lane_base + (uint32_t)(b * G.BUF + (f * PARTS + p) * 16), v[p]);
+                tmem_wait_ld();
+                if (f == nf - 1) {  // the accumulator is read: the next row's MMAs may overwrite it
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) ptx::mbar_arrive(&dempty[b]);
+                }
+                float* col = ring + (size_t)f * G.RS * kM + tid;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float pj;
+                    if constexpr (PARTS == 3) {
+                        pj = (__uint_as_float(v[2][j]) + __uint_as_float(v[1][j])) + __uint_as_float(v[0][j]);
+                    } else {
+                        pj = __uint_as_float(v[0][j]);
+                    }
+                    col[((c - j * R) & (G.RS - 1)) * kM] += pj;
+                }
+                float* slot = col + (py & (G.RS - 1)) * kM;
+                const float sum = *slot;
+                *slot = 0.f;
+                if (py >= py0 && px < nx) {
+                    const float sc = sum + fbias.b[f];
+                    if constexpr (std::is_same<OutT, int32_t>::value) {
+                        scores[f * plane + (size_t)py * nx + px] = __float2int_rn(sc);  // exact: an integer < 2^24
+                    } else {
+                        scores[f * plane + (size_t)py * nx + px] = sc;
+                    }
+                }
+            }
+        }
+    }
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.COLS) : "memory");
+    }
+}
+
+// Output rows per CTA: the tuned value, else the fewest that keep the grid to
+// one CTA per SM (a CTA streams 15 r rows beyond its own, so fewer, longer
+// CTAs do less redundant work once every SM has one).
+int rows_per_cta(int nx, int ny) {
+    const int tuned = tune_get(HOG_TUNE_SCORE_TC_ROWS);
+    if (tuned > 0) return tuned;
+    const long strips = (nx + kM - 1) / kM;
+    const long per = (ny * strips + sm_count() - 1) / sm_count();
+    return (int)(per < 1 ? 1 : per);
+}
+
+constexpr size_t kMaxSmem = 226 * 1024;  // dynamic shared memory per CTA, below the 227 KiB opt-in limit
+
+// Filters per launch: as many as N <= 256 and the shared memory allow.
+int filters_per_launch(int r, int parts, int n_filters) {
+    int g = n_filters < kMaxFilters ? n_filters : kMaxFilters;
+    while (g > 1 && (16 * parts * g > 256 || RowsGeom(r, parts, g).smem_bytes() > kMaxSmem)) --g;
+    return g;
+}
+
+// nf filters (w: nf consecutive filters of 1024 weights; scores: nf planes of nx * ny).
+template <int R, typename WT, typename OutT>
+hog_status launch_t(const uint16_t* cells, int ncx, int ncy, const WT* w, int nf, const RowsBias& bias,
+                    OutT* scores, cudaStream_t st) {
+    const int nx = ncx - 7 * R, ny = ncy - 15 * R;
+    if (nx <= 0 || ny <= 0) return HOG_OK;
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    const size_t smem = RowsGeom(R, weight_parts<WT>(), nf).smem_bytes();
+    if (smem > kMaxSmem) return HOG_ERR_UNSUPPORTED;
+    auto kern = score_rows_kernel<R, WT, OutT, false>;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int rpc = rows_per_cta(nx, ny);
+    const dim3 grid((nx + kM - 1) / kM, (ny + rpc - 1) / rpc);
+    return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, w, nf, bias, nx, ny, rpc, scores,
+                      static_cast<const PlanItem*>(nullptr), 0, status);
+}
+
+// Any number of filters: groups of filters_per_launch() per launch.
+template <int R, typename WT, typename OutT>
+hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, const void* w, int n_filters,
+                          const float* biases, void* scores, cudaStream_t st) {
+    const int nx = ncx - 7 * R, ny = ncy - 15 * R;
+    if (nx <= 0 || ny <= 0) return HOG_OK;
+    const int group = filters_per_launch(R, weight_parts<WT>(), n_filters);
+    for (int f0 = 0; f0 < n_filters; f0 += group) {
+        const int g = n_filters - f0 < group ? n_filters - f0 : group;
+        RowsBias rb{};
+        for (int k = 0; k < g; ++k) {
+            const float b = biases[f0 + k];
+            rb.b[k] = std::is_same<OutT, int32_t>::value ? (float)std::llround((double)b) : b;
+        }
+        const hog_status s = launch_t<R, WT, OutT>(cells, ncx, ncy, static_cast<const WT*>(w) + (size_t)f0 * 1024,
+                                                   g, rb, static_cast<OutT*>(scores) + (size_t)f0 * nx * ny, st);
+        if (s != HOG_OK) return s;
+    }
+    return HOG_OK;
+}
+
+template <int R, typename WT, typename OutT>
+hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void* w, float bias, cudaStream_t st) {
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    const size_t smem = RowsGeom(R, weight_parts<WT>(), 1).smem_bytes();
+    auto kern = score_rows_kernel<R, WT, OutT, true>;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    RowsBias rb{};
+    rb.b[0] = bias;
+    return launch_pdl(kern, dim3(h.score_ctas), dim3(kThreads), smem, st, static_cast<const uint16_t*>(nullptr), 0,
+                      0, static_cast<const WT*>(w), 1, rb, 0, 0, h.score_tc, static_cast<OutT*>(nullptr),
+                      plan_items(plan_dev), h.n_items, status);
+}
+
+template <int R>
+hog_status by_w(const uint16_t* cells, int ncx, int ncy, const void* w, int w_dtype, int n_filters,
+                const float* biases, void* scores, cudaStream_t st) {
+    if (w_dtype == HOG_F32)
+        return launch_multi_t<R, float, float>(cells, ncx, ncy, w, n_filters, biases, scores, st);
+    if (w_dtype == HOG_BF16)
+        return launch_multi_t<R, uint16_t, float>(cells, ncx, ncy, w, n_filters, biases, scores, st);
+    if (w_dtype == HOG_I8)
+        return launch_multi_t<R, int8_t, int32_t>(cells, ncx, ncy, w, n_filters, biases, scores, st);
+    return HOG_ERR_UNSUPPORTED;
+}
+
+template <int R>
+hog_status batch_by_w(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
+                      cudaStream_t st) {
+    if (w_dtype == HOG_F32) return launch_batch_t<R, float, float>(h, plan_dev, w, bias, st);
+    if (w_dtype == HOG_BF16) return launch_batch_t<R, uint16_t, float>(h, plan_dev, w, bias, st);
+    if (w_dtype == HOG_I8) return launch_batch_t<R, int8_t, int32_t>(h, plan_dev, w, bias, st);
+    return HOG_ERR_UNSUPPORTED;
+}
+
+}  // namespace
+
+bool score_rows_supported(const void* cells, int cell_dtype, int n_bins, int cells_x, int cells_y, int r) {
+    return cell_dtype == HOG_BF16 && n_bins == 8 && cells_x == 8 && cells_y == 16 &&
+           reinterpret_cast<uintptr_t>(cells) % 16 == 0 && (r == 1 || r == 2 || r == 4);
+}
+
+int score_rows_batch_rows(long strip_rows) {
+    const int tuned = tune_get(HOG_TUNE_SCORE_TC_ROWS);
+    if (tuned > 0) return tuned;
+    const long per = (strip_rows + 2L * sm_count() - 1) / (2L * sm_count());  // about two CTAs per SM
+    return (int)(per < 16 ? 16 : per);
+}
+
+hog_status launch_score_rows_batch(const PlanHeader& h, const void* plan_dev, const void* w, int w_dtype, float bias,
+                                   cudaStream_t st) {
+    if (h.score_ctas == 0) return HOG_OK;
+    switch (h.r) {
+        case 1: return batch_by_w<1>(h, plan_dev, w, w_dtype, bias, st);
+        case 2: return batch_by_w<2>(h, plan_dev, w, w_dtype, bias, st);
+        case 4: return batch_by_w<4>(h, plan_dev, w, w_dtype, bias, st);
+        default: return HOG_ERR_UNSUPPORTED;
+    }
+}
+
+hog_status launch_score_rows(const uint16_t* cells_bf16, int ncx, int ncy, int r, const void* w, int w_dtype,
+                             int n_filters, const float* biases, void* scores, cudaStream_t st) {
+    switch (r) {
+        case 1: return by_w<1>(cells_bf16, ncx, ncy, w, w_dtype, n_filters, biases, scores, st);
+        case 2: return by_w<2>(cells_bf16, ncx, ncy, w, w_dtype, n_filters, biases, scores, st);
+        case 4: return by_w<4>(cells_bf16, ncx, ncy, w, w_dtype, n_filters, biases, scores, st);
+        default: return HOG_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace fasthog

@@ -12,10 +12,14 @@
 // requests on the GPU; a finished request gives its arena block back at once
 // and hands its host buffer to the caller until release.
 #include <atomic>
+#include <chrono>
 #include <cmath>
+#include <deque>
 #include <iterator>
 #include <map>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/fasthog_server.h"
@@ -102,7 +106,21 @@ struct Layout {
 
 enum class SlotState { kFree, kBusy, kHeld };
 
+int64_t clock_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// A request waiting for the dispatcher thread.
+struct Pending {
+    int32_t rid;
+    const uint8_t* img;
+    int W, H, channels;
+    int64_t t_enqueue;
+};
+
 struct Slot {
+    int64_t t_enqueue = 0, t_admit = 0;  // the dispatcher's stamps of the request on the slot
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     hog_det* dets_host = nullptr;  // page-locked, mapped
@@ -130,6 +148,16 @@ struct hog_server {
     std::vector<Slot> slots;
     std::vector<int> free_slots;  // stack of free slot indices
     std::vector<int> busy;        // slots on the GPU, in submission order
+
+    // dispatcher thread (hog_server_start): the queue, finished results and
+    // slots to free are shared with the callers' threads under `mu`; every
+    // other member belongs to the dispatcher while it runs
+    std::thread worker;
+    std::atomic<bool> running{false}, stopping{false};
+    std::mutex mu;
+    std::deque<Pending> queue;
+    std::deque<hog_server_timed_result> finished;
+    std::vector<int> to_release;
 
     Layout plan(int W, int H, int channels) const {
         Layout L{};
@@ -209,7 +237,146 @@ struct hog_server {
                           windows, count_dev, base + L.ws_det, L.ws_det_bytes, st);
     }
 
+    // Admit one request if a slot is free and its buffers fit (*admitted).
+    hog_status submit_one(int32_t rid, const uint8_t* img, int W, int H, int channels, int* admitted) {
+        *admitted = 0;
+        if (!size_ok(W, H) || (channels != 1 && channels != 3)) return HOG_ERR_ARG;
+        if (W > cfg.max_W || H > cfg.max_H) return HOG_ERR_ARG;
+        const Layout L = plan(W, H, channels);
+        if (L.total > cfg.budget_bytes) return HOG_ERR_ARG;
+        if (free_slots.empty()) return HOG_OK;
+        size_t off = 0;
+        if (!arena.take(L.total, &off)) return HOG_OK;
+        DeviceGuard g(device);
+        if (g.error() != cudaSuccess) {
+            arena.give(off, L.total);
+            return cuda_fail(g.error());
+        }
+        const int i = free_slots.back();
+        Slot& sl = slots[i];
+        sl.off = off;
+        sl.bytes = L.total;
+        sl.rid = rid;
+        sl.W = W;
+        sl.H = H;
+        counts_host[i * kCountStride] = -1;
+        hog_status st = enqueue(sl, L, img, W, H, channels, counts_dev + i * kCountStride);
+        if (st == HOG_OK) {
+            const cudaError_t e = cudaEventRecord(sl.done, sl.stream);
+            if (e != cudaSuccess) st = cuda_fail(e);
+        }
+        if (st != HOG_OK) {
+            // Part of the work may be enqueued: let it finish before the block is reused.
+            cudaStreamSynchronize(sl.stream);
+            arena.give(off, L.total);
+            return st;
+        }
+        free_slots.pop_back();
+        sl.state = SlotState::kBusy;
+        busy.push_back(i);
+        *admitted = 1;
+        return HOG_OK;
+    }
+
+    // Collect up to max_out finished requests (their arena blocks are free at once).
+    hog_status poll_some(hog_server_result* out, int max_out, int* n_out, int64_t* t_done = nullptr) {
+        *n_out = 0;
+        DeviceGuard g(device);
+        if (g.error() != cudaSuccess) return cuda_fail(g.error());
+        int n = 0;
+        size_t keep = 0;
+        for (size_t k = 0; k < busy.size(); ++k) {
+            const int i = busy[k];
+            Slot& sl = slots[i];
+            cudaError_t e = n < max_out ? cudaEventQuery(sl.done) : cudaErrorNotReady;
+            if (e == cudaErrorNotReady) {
+                busy[keep++] = i;
+                continue;
+            }
+            std::atomic_thread_fence(std::memory_order_acquire);
+            if (t_done) t_done[n] = clock_ns();
+            hog_server_result& r = out[n++];
+            r.rid = sl.rid;
+            r.status = e == cudaSuccess ? HOG_OK : cuda_fail(e);
+            r.count = e == cudaSuccess ? *static_cast<volatile int32_t*>(counts_host + i * kCountStride) : 0;
+            r.token = i;
+            r.W = sl.W;
+            r.H = sl.H;
+            r.dets = sl.dets_host;
+            arena.give(sl.off, sl.bytes);
+            sl.state = SlotState::kHeld;
+        }
+        busy.resize(keep);
+        *n_out = n;
+        return HOG_OK;
+    }
+
+    // The dispatcher thread: free released slots, collect finished requests,
+    // admit queued ones in order; yield when nothing moved.
+    void dispatch() {
+        cudaSetDevice(device);
+        std::vector<hog_server_result> got(slots.size());
+        std::vector<int64_t> t_done(slots.size());
+        while (true) {
+            bool moved = false;
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                for (int tok : to_release) {
+                    slots[tok].state = SlotState::kFree;
+                    free_slots.push_back(tok);
+                }
+                moved = moved || !to_release.empty();
+                to_release.clear();
+            }
+            int n = 0;
+            if (!busy.empty() && poll_some(got.data(), (int)got.size(), &n, t_done.data()) == HOG_OK && n > 0) {
+                std::lock_guard<std::mutex> lock(mu);
+                for (int k = 0; k < n; ++k) {
+                    const Slot& sl = slots[got[k].token];
+                    finished.push_back(hog_server_timed_result{got[k], sl.t_enqueue, sl.t_admit, t_done[k]});
+                }
+                moved = true;
+            }
+            while (true) {
+                Pending p;
+                {
+                    std::lock_guard<std::mutex> lock(mu);
+                    if (queue.empty()) break;
+                    p = queue.front();
+                }
+                int admitted = 0;
+                const hog_status st = submit_one(p.rid, p.img, p.W, p.H, p.channels, &admitted);
+                if (st == HOG_OK && !admitted) break;  // wait for a slot or for memory: first in, first out
+                std::lock_guard<std::mutex> lock(mu);
+                queue.pop_front();
+                if (st != HOG_OK) {  // failed to enqueue on the GPU: report it as the request's result
+                    hog_server_result r{p.rid, st, 0, -1, p.W, p.H, nullptr};
+                    finished.push_back(hog_server_timed_result{r, p.t_enqueue, clock_ns(), clock_ns()});
+                } else {
+                    Slot& sl = slots[busy.back()];
+                    sl.t_enqueue = p.t_enqueue;
+                    sl.t_admit = clock_ns();
+                }
+                moved = true;
+            }
+            if (stopping.load(std::memory_order_acquire) && busy.empty()) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (queue.empty()) break;
+            }
+            if (!moved) std::this_thread::yield();
+        }
+    }
+
+    void stop_worker() {
+        if (!running.load()) return;
+        stopping.store(true, std::memory_order_release);
+        worker.join();
+        running.store(false);
+        stopping.store(false);
+    }
+
     void release_all() {
+        stop_worker();
         for (Slot& sl : slots) {
             if (sl.state == SlotState::kBusy && sl.done) cudaEventSynchronize(sl.done);
             if (sl.done) cudaEventDestroy(sl.done);
@@ -257,8 +424,9 @@ hog_status hog_server_create(const hog_server_config* cfg, const void* w, hog_se
     if (s == nullptr) return HOG_ERR_ARG;
     s->cfg = *cfg;
     const hog_server_config& c = s->cfg;
-    // Histogram counts of cells up to 16 x 16 are exact in bf16; the tensor-core score takes bf16 cells.
-    s->cell_dtype = (c.w_dtype != HOG_F32 && c.cell <= 16) ? HOG_BF16 : HOG_F32;
+    // Histogram counts of cells up to 16 x 16 are exact in bf16; the tensor-core scores take bf16 cells
+    // (with any weight type).
+    s->cell_dtype = c.cell <= 16 ? HOG_BF16 : HOG_F32;
     s->score_dtype = c.w_dtype == HOG_I8 ? HOG_I32 : HOG_F32;
     s->fused = c.fused == 1 || (c.fused == -1 && fasthog::cells_fused_supported(c.n_bins, c.cell, c.stride));
     const int r = c.cell / c.stride;
@@ -326,78 +494,27 @@ hog_status hog_server_submit(hog_server* s, int32_t rid, const uint8_t* img, int
                              int* admitted) {
     if (s == nullptr || img == nullptr || admitted == nullptr) return HOG_ERR_ARG;
     *admitted = 0;
-    if (!size_ok(W, H) || (channels != 1 && channels != 3)) return HOG_ERR_ARG;
-    if (W > s->cfg.max_W || H > s->cfg.max_H) return HOG_ERR_ARG;
-    const Layout L = s->plan(W, H, channels);
-    if (L.total > s->cfg.budget_bytes) return HOG_ERR_ARG;
-    if (s->free_slots.empty()) return HOG_OK;
-    size_t off = 0;
-    if (!s->arena.take(L.total, &off)) return HOG_OK;
-    DeviceGuard g(s->device);
-    if (g.error() != cudaSuccess) {
-        s->arena.give(off, L.total);
-        return cuda_fail(g.error());
-    }
-    const int i = s->free_slots.back();
-    Slot& sl = s->slots[i];
-    sl.off = off;
-    sl.bytes = L.total;
-    sl.rid = rid;
-    sl.W = W;
-    sl.H = H;
-    s->counts_host[i * kCountStride] = -1;
-    hog_status st = s->enqueue(sl, L, img, W, H, channels, s->counts_dev + i * kCountStride);
-    if (st == HOG_OK) {
-        const cudaError_t e = cudaEventRecord(sl.done, sl.stream);
-        if (e != cudaSuccess) st = cuda_fail(e);
-    }
-    if (st != HOG_OK) {
-        // Part of the work may be enqueued: let it finish before the block is reused.
-        cudaStreamSynchronize(sl.stream);
-        s->arena.give(off, L.total);
-        return st;
-    }
-    s->free_slots.pop_back();
-    sl.state = SlotState::kBusy;
-    s->busy.push_back(i);
-    *admitted = 1;
-    return HOG_OK;
+    if (s->running.load()) return HOG_ERR_UNSUPPORTED;  // the dispatcher thread owns admission
+    return s->submit_one(rid, img, W, H, channels, admitted);
 }
 
 hog_status hog_server_poll(hog_server* s, hog_server_result* out, int max_out, int* n_out) {
     if (s == nullptr || n_out == nullptr || max_out < 0 || (out == nullptr && max_out > 0)) return HOG_ERR_ARG;
     *n_out = 0;
-    DeviceGuard g(s->device);
-    if (g.error() != cudaSuccess) return cuda_fail(g.error());
-    int n = 0;
-    size_t keep = 0;
-    for (size_t k = 0; k < s->busy.size(); ++k) {
-        const int i = s->busy[k];
-        Slot& sl = s->slots[i];
-        cudaError_t e = n < max_out ? cudaEventQuery(sl.done) : cudaErrorNotReady;
-        if (e == cudaErrorNotReady) {
-            s->busy[keep++] = i;
-            continue;
-        }
-        std::atomic_thread_fence(std::memory_order_acquire);
-        hog_server_result& r = out[n++];
-        r.rid = sl.rid;
-        r.status = e == cudaSuccess ? HOG_OK : cuda_fail(e);
-        r.count = e == cudaSuccess ? *static_cast<volatile int32_t*>(s->counts_host + i * kCountStride) : 0;
-        r.token = i;
-        r.W = sl.W;
-        r.H = sl.H;
-        r.dets = sl.dets_host;
-        s->arena.give(sl.off, sl.bytes);
-        sl.state = SlotState::kHeld;
-    }
-    s->busy.resize(keep);
-    *n_out = n;
-    return HOG_OK;
+    if (s->running.load()) return HOG_ERR_UNSUPPORTED;
+    return s->poll_some(out, max_out, n_out);
 }
 
 hog_status hog_server_release(hog_server* s, int32_t token) {
     if (s == nullptr || token < 0 || token >= (int32_t)s->slots.size()) return HOG_ERR_ARG;
+    if (s->running.load()) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        if (s->slots[token].state != SlotState::kHeld) return HOG_ERR_ARG;
+        for (int t : s->to_release)
+            if (t == token) return HOG_ERR_ARG;
+        s->to_release.push_back(token);
+        return HOG_OK;
+    }
     Slot& sl = s->slots[token];
     if (sl.state != SlotState::kHeld) return HOG_ERR_ARG;
     sl.state = SlotState::kFree;
@@ -405,8 +522,54 @@ hog_status hog_server_release(hog_server* s, int32_t token) {
     return HOG_OK;
 }
 
+hog_status hog_server_start(hog_server* s) {
+    if (s == nullptr) return HOG_ERR_ARG;
+    if (s->running.load()) return HOG_ERR_ARG;
+    s->stopping.store(false);
+    s->running.store(true);
+    try {
+        s->worker = std::thread([s] { s->dispatch(); });
+    } catch (...) {
+        s->running.store(false);
+        return HOG_ERR_UNSUPPORTED;
+    }
+    return HOG_OK;
+}
+
+hog_status hog_server_stop(hog_server* s) {
+    if (s == nullptr) return HOG_ERR_ARG;
+    s->stop_worker();
+    return HOG_OK;
+}
+
+hog_status hog_server_enqueue(hog_server* s, int32_t rid, const uint8_t* img, int W, int H, int channels) {
+    if (s == nullptr || img == nullptr) return HOG_ERR_ARG;
+    if (!size_ok(W, H) || (channels != 1 && channels != 3)) return HOG_ERR_ARG;
+    if (W > s->cfg.max_W || H > s->cfg.max_H) return HOG_ERR_ARG;
+    if (s->plan(W, H, channels).total > s->cfg.budget_bytes) return HOG_ERR_ARG;
+    if (!s->running.load() || s->stopping.load()) return HOG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->queue.push_back(Pending{rid, img, W, H, channels, clock_ns()});
+    return HOG_OK;
+}
+
+hog_status hog_server_collect(hog_server* s, hog_server_timed_result* out, int max_out, int* n_out) {
+    if (s == nullptr || n_out == nullptr || max_out < 0 || (out == nullptr && max_out > 0)) return HOG_ERR_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    int n = 0;
+    while (n < max_out && !s->finished.empty()) {
+        out[n++] = s->finished.front();
+        s->finished.pop_front();
+    }
+    *n_out = n;
+    return HOG_OK;
+}
+
+int64_t hog_server_clock_ns(void) { return clock_ns(); }
+
 hog_status hog_server_stats(const hog_server* s, int* in_flight, size_t* bytes_in_use, int* free_slots) {
     if (s == nullptr) return HOG_ERR_ARG;
+    if (s->running.load()) return HOG_ERR_UNSUPPORTED;  // the dispatcher thread owns these counts
     if (in_flight) *in_flight = (int)s->busy.size();
     if (bytes_in_use) *bytes_in_use = s->arena.used();
     if (free_slots) *free_slots = (int)s->free_slots.size();

@@ -23,9 +23,10 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import (DET_BYTES, HOG_BF16, HOG_F32, HOG_I8, HOG_I32, HogServerConfig, HogServerResult, dets_to_numpy,
-               hog_server_create, hog_server_destroy, hog_server_poll, hog_server_release, hog_server_request_bytes,
-               hog_server_stats, hog_server_submit)
+from . import (DET_BYTES, HOG_BF16, HOG_F32, HOG_I8, HOG_I32, HogServerConfig, HogServerResult,
+               HogServerTimedResult, dets_to_numpy, hog_server_clock_ns, hog_server_collect, hog_server_create,
+               hog_server_destroy, hog_server_enqueue, hog_server_poll, hog_server_release, hog_server_request_bytes,
+               hog_server_start, hog_server_stats, hog_server_stop, hog_server_submit)
 
 _MAX_POLL = 64
 
@@ -153,6 +154,57 @@ class HogServer:
             if gc_was_on:
                 gc.enable()
         return results
+
+    def serve_native(self, requests: list[Request], keep: bool = True) -> tuple[list[Result], dict]:
+        """Replay `requests` at their arrival times through the server's own
+        dispatcher thread (hog_server_start): this thread only queues each
+        request when it arrives and collects results; admission and
+        completion run natively.  Latency is the native enqueue-to-done
+        time.  Returns the results in completion order and the replay's own
+        lateness (how far behind its arrival time a request was queued)."""
+        queue = sorted(requests, key=lambda r: r.arrival)
+        out = (HogServerTimedResult * _MAX_POLL)()
+        results: list[Result] = []
+        held: dict[int, tuple] = {}
+        late = []
+        gc_was_on = gc.isenabled()
+        gc.disable()
+        hog_server_start(self._h)
+        try:
+            t0 = hog_server_clock_ns()
+            i = 0
+            while i < len(queue) or held:
+                now = (hog_server_clock_ns() - t0) * 1e-9
+                while i < len(queue) and queue[i].arrival <= now:
+                    req = queue[i]
+                    img = req.image
+                    img = (img if img.is_contiguous() else img.contiguous()) if isinstance(img, torch.Tensor) \
+                        else np.ascontiguousarray(img, dtype=np.uint8)
+                    H, W = img.shape[:2]
+                    hog_server_enqueue(self._h, req.rid, img, W, H, 1 if img.ndim == 2 else 3)
+                    held[req.rid] = (req, img)  # the image must outlive the request
+                    late.append(now - req.arrival)
+                    i += 1
+                n = hog_server_collect(self._h, out, _MAX_POLL)
+                for k in range(n):
+                    t = out[k]
+                    r = t.r
+                    if r.status != 0:
+                        raise RuntimeError(f"request {r.rid} failed on the GPU (status {r.status})")
+                    dets = None
+                    if keep:
+                        raw = ctypes.string_at(r.dets, r.count * DET_BYTES) if r.count else b""
+                        dets = dets_to_numpy(raw, r.count)
+                    hog_server_release(self._h, r.token)
+                    held.pop(r.rid)
+                    results.append(Result(r.rid, dets, r.count, (t.t_done_ns - t.t_enqueue_ns) * 1e-9, (r.H, r.W)))
+        finally:
+            hog_server_stop(self._h)
+            if gc_was_on:
+                gc.enable()
+        lat = np.array(late) * 1e3 if late else np.zeros(1)
+        return results, {"replay_late_p50_ms": round(float(np.percentile(lat, 50)), 3),
+                         "replay_late_p99_ms": round(float(np.percentile(lat, 99)), 3)}
 
     def run_one(self, image, rid: int = 0) -> Result:
         """The plain per-image path: submit one request and wait for it."""

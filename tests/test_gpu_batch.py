@@ -163,7 +163,8 @@ def test_batch_nb16_tensor_cores_int8_exact(fh):
 
 @pytest.mark.parametrize("nb,stride", [(16, 4), (8, 8)])
 def test_batch_f32_weights(fh, nb, stride):
-    """f32 weights: the score runs per item (CUDA cores); N_b 16 and stride 8."""
+    """f32 weights (three exact bf16 parts on the tensor cores, bf16 cells);
+    N_b 16 and stride 8."""
     from paper_1703_06256_gb300.batch import HogPlanBatch
 
     imgs = images(3, 3)

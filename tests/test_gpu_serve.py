@@ -65,6 +65,45 @@ def test_same_alone_and_in_the_mix(fused, budget, streams):
     srv.close()
 
 
+@pytest.mark.parametrize("fused", [True, False])
+def test_native_dispatcher_same_as_alone(fused):
+    """The server's own dispatcher thread (hog_server_start / enqueue /
+    collect): requests queued at staggered arrival times, under a budget that
+    holds only some of them at once, give the same lists as each alone; the
+    native stamps are ordered (enqueue <= admit <= done); the synchronous
+    calls are refused while the thread runs."""
+    import paper_1703_06256_gb300 as fh
+    from paper_1703_06256_gb300.serve import HogServer, Request
+
+    rng = wl.rng_for(4)
+    w = wl.weights_f32(8, rng)
+    images = _images(rng)
+    budget = 8 << 20 if fused else 96 << 20
+    srv = HogServer(w, 0.0, 0.5, w_dtype=fh.HOG_F32, budget_bytes=budget, n_streams=4, fused=fused,
+                    max_wh=(1280, 1000))
+    alone = {i: srv.run_one(img, i) for i, img in enumerate(images)}
+    reqs = [Request(i, img, 0.0005 * (i % 4)) for i, img in enumerate(images * 3)]
+    mix, replay = srv.serve_native(reqs)
+    assert sorted(r.rid for r in mix) == list(range(len(reqs)))
+    assert replay["replay_late_p99_ms"] >= 0
+    for r in mix:
+        a = alone[r.rid % len(images)]
+        assert r.count == a.count == len(r.detections)
+        assert np.array_equal(r.detections["x"], a.detections["x"])
+        assert np.array_equal(r.detections["score"], a.detections["score"])
+        assert np.all(r.detections["image"] == r.rid)
+        assert r.latency > 0
+    assert srv.idle() and srv.used == 0
+    # while the dispatcher runs, the caller-driven calls are refused
+    fh.hog_server_start(srv._h)
+    try:
+        with pytest.raises(fh.HogError):
+            srv.try_submit(Request(0, images[0]))
+    finally:
+        fh.hog_server_stop(srv._h)
+    srv.close()
+
+
 def test_int8_weights_exact_in_the_mix():
     """Integer weights: scores are exact, so the lists equal the oracle's exactly."""
     import paper_1703_06256_gb300 as fh
