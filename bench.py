@@ -391,27 +391,29 @@ def serving(torch, wl, args):
 
     def run(srv, reqs):
         t0 = time.perf_counter()
-        res = srv.serve(reqs, keep=False)
-        return res, time.perf_counter() - t0
+        res, replay = srv.serve_native(reqs, keep=False)
+        return res, time.perf_counter() - t0, replay
 
     burst = [Request(i, pool[i % len(pool)], 0.0) for i in range(min(1000, n_req))]
     for srv in (served, plain):  # warm-up: every kernel loaded, allocator pools filled
         run(srv, burst[: len(pool)])
     torch.cuda.synchronize()
-    _, t_plain = run(plain, burst)
-    _, t_served = run(served, burst)
+    _, t_plain, _ = run(plain, burst)
+    _, t_served, _ = run(served, burst)
     cap_plain, cap_served = len(burst) / t_plain, len(burst) / t_served
     rate = 0.8 * cap_plain
     reqs = [Request(i, pool[i % len(pool)], stream[i]["t"] / rate) for i in range(n_req)]
     out = {"workload": ("Poisson arrivals at 0.8 x the plain path's capacity; RGB images, W, H uniform over multiples "
                         "of 8 in 320..3840 x 240..2160 (128 distinct pinned host images, cycled); N_b=8, stride 4, "
-                        "bf16 cells x bf16 weights; 8 GB device budget; latency = arrival to detections on the host"),
+                        "bf16 cells x bf16 weights; 8 GB device budget; admission and completion on the server's "
+                        "native dispatcher thread; latency = enqueue to detections in host memory (native clock); "
+                        "replay_late = how far behind its arrival time the replaying thread queued a request"),
            "requests": n_req, "rate_per_s": round(rate, 1),
            "mean_mpixel_per_request": round(sum(int(t.numel()) for t in pool) / 3 / len(pool) / 1e6, 3),
            "capacity_images_per_s": {"plain": round(cap_plain, 1), "served": round(cap_served, 1)}}
     for label, srv, streams in (("served", served, 16), ("plain", plain, 1)):
-        res, wall = run(srv, reqs)
-        out[label] = dict(latency_summary(res, wall), streams=streams, fused=srv.fused)
+        res, wall, replay = run(srv, reqs)
+        out[label] = dict(latency_summary(res, wall), streams=streams, fused=srv.fused, **replay)
     del served, plain, pool
     torch.cuda.empty_cache()
     return out
@@ -791,8 +793,9 @@ def main():
                  "unit": "Mpixel/s", "ms_per_step": round(fused_ms, 5),
                  "calls": "hog_cell_hist_fused + hog_window_score + hog_detect", "tuned": ftuned}
 
-    # end to end through the public API, from pinned host memory (graph replay)
-    pipe.capture()
+    # end to end through the public API, from pinned host memory (graph replay: image copy, five calls,
+    # detections and count written by the GPU into pinned host memory, one synchronisation)
+    pipe.capture_host()
     for _ in range(3):
         pipe.detect_host()
     d2h = []
@@ -810,10 +813,10 @@ def main():
     srv = HogServer(c["w"], c["bias"], c["thr"], n_bins=c["n_bins"], stride=c["stride"], w_dtype=fh.HOG_F32,
                     budget_bytes=2 << 30, n_streams=16, fused=False, max_wh=(W, H))
     img_pinned = torch.from_numpy(np.ascontiguousarray(img)).pin_memory()
-    srv.serve([Request(k, img_pinned, 0.0) for k in range(64)], keep=False)  # warm-up
+    srv.serve_native([Request(k, img_pinned, 0.0) for k in range(64)], keep=False)  # warm-up
     n_req = max(args.steps * 5, 500)
     t0 = time.perf_counter()
-    res = srv.serve([Request(k, img_pinned, 0.0) for k in range(n_req)], keep=False)
+    res, _ = srv.serve_native([Request(k, img_pinned, 0.0) for k in range(n_req)], keep=False)
     served_s = replicas.max_over_ranks((time.perf_counter() - t0) / n_req, device="cuda")
     served_d2h = 4 + int(statistics.mean(r.count for r in res)) * fh.DET_BYTES
     srv.close()
@@ -825,8 +828,11 @@ def main():
     alg_bytes = algorithmic_bytes(W, H, nb, pipe.ncx, pipe.ncy, windows)
     hbm, src = peaks()
     achieved = alg_bytes[dom] / (stage_avg[dom] * 1e-3) / 1e9
-    # bin map 1, integral 3 per 16-bin window, cell hist 1, score 1, detect 1 (+1 past one 2048-score tile)
-    launches_per_step = 1 + 3 * ((nb + 15) // 16) + 1 + 1 + (2 if windows > 2048 else 1)
+    # bin map 1; integral 1 (single pass) or 3 per window of bins, under the knobs the step was captured
+    # with; cell histograms 1; score 1; detection 1 (single pass)
+    if tuned:
+        autotune.apply(tuned["config"])
+    launches_per_step = 1 + fh.hog_integral_launches(W, H, nb) + 1 + 1 + 1
     status = fh.hog_device_status()
     autotune.reset()  # the extras below run with the library's own launch shapes
     # the serving comparison runs right after the main measurement, before the heavier extras,
@@ -849,10 +855,13 @@ def main():
                      "traffic_source": "profiles/traffic.txt (ncu, summed over the stage's kernels)"},
         "e2e": {"value": round(replicas.aggregate_rate(px, served_s, world) / 1e6, 2), "unit": "Mpixel/s",
                 "h2d_bytes_per_step": pipe.h2d_bytes(), "d2h_bytes_per_step": served_d2h,
-                "api": "HogServer (hog_server_submit / hog_server_poll), five calls per request, 16 in flight",
+                "api": "HogServer (native dispatcher: hog_server_enqueue / hog_server_collect), five calls per "
+                       "request, 16 in flight",
                 "requests": n_req,
                 "one_at_a_time": {"value": round(replicas.aggregate_rate(px, e2e_s, world) / 1e6, 2),
-                                  "unit": "Mpixel/s", "api": "HogPipeline.detect_host (graph, synchronous)",
+                                  "unit": "Mpixel/s",
+                                  "api": "HogPipeline.detect_host (one graph: image copy, five calls, list into pinned "
+                                         "host memory; one synchronisation per image)",
                                   "d2h_bytes_per_step": int(statistics.mean(d2h))}},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,

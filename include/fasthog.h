@@ -176,6 +176,10 @@ hog_status hog_bin_map(const uint8_t* img, int W, int H, int channels, size_t pi
  *              Calls that overlap on the device must not share a workspace.
  */
 size_t hog_integral_workspace_bytes(int W, int H, int n_bins);
+/* Kernel launches one hog_integral call of this size enqueues under the
+ * current launch-shape knobs (1 or 3 per window of up to 16 bins); 0 for an
+ * invalid size. */
+int hog_integral_launches(int W, int H, int n_bins);
 hog_status hog_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
                         void* workspace, size_t workspace_bytes, hog_stream_t stream);
 
@@ -409,7 +413,10 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 about 2048 x 1152 pixels
  *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
- *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 16 or 32
+ *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 1, 2, 4, 8, 16,
+ *                                 32 or 64 for the row-GEMM kernel (8 bins); the
+ *                                 banded kernel (16 bins) takes 16 or 32 and its
+ *                                 own choice for the other values
  *   HOG_TUNE_CELL_ROWS            cell rows per CTA of the cell-histogram kernel
  *                                 that stages the integral-image samples in
  *                                 shared memory: 4, 8 or 16; 1 = one thread per

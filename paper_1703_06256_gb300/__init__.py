@@ -100,6 +100,7 @@ def _load() -> ctypes.CDLL:
         "hog_build_lut": (I, [I, P, P]),
         "hog_bin_map": (I, [P, I, I, I, Z, P, I, P, P]),
         "hog_integral_workspace_bytes": (Z, [I, I, I]),
+        "hog_integral_launches": (I, [I, I, I]),
         "hog_integral": (I, [P, I, I, I, I, P, P, Z, P]),
         "hog_cell_hist": (I, [P, I, I, I, I, I, I, I, P, P]),
         "hog_window_score": (I, [P, I, I, I, I, I, I, I, I, P, I, F, P, P]),
@@ -144,7 +145,7 @@ def _load() -> ctypes.CDLL:
 _lib = _load()
 EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_device_status",
             "hog_selftest_wait_timeout", "hog_build_lut",
-            "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral", "hog_cell_hist", "hog_window_score",
+            "hog_bin_map", "hog_integral_workspace_bytes", "hog_integral_launches", "hog_integral", "hog_cell_hist", "hog_window_score",
             "hog_detect_workspace_bytes", "hog_detect", "hog_detect_noalloc", "hog_cell_hist_fused",
             "hog_build_soft_lut", "hog_cell_hist_soft", "hog_block_norm", "hog_window_score_multi", "hog_tune_set", "hog_tune_get", "hog_batch_plan_bytes", "hog_batch_plan", "hog_cell_hist_fused_batch", "hog_window_score_batch",
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
@@ -161,8 +162,9 @@ def _ptr(x) -> int | None:
     if x is None:
         return None
     if isinstance(x, torch.Tensor):
-        if x.device.type != "cuda":
-            raise ValueError("libfasthog takes CUDA tensors (device memory); got a CPU tensor")
+        if x.device.type != "cuda" and not x.is_pinned():
+            # page-locked host memory is mapped into the device's address space (same address)
+            raise ValueError("libfasthog takes CUDA tensors or page-locked CPU tensors; got pageable host memory")
         return x.data_ptr()
     return int(x)
 
@@ -217,6 +219,10 @@ def hog_bin_map(img, W: int, H: int, channels: int, pitch_bytes: int, lut, n_bin
                 stream=None) -> None:
     _check("hog_bin_map", _lib.hog_bin_map(_ptr(img), W, H, channels, pitch_bytes, _ptr(lut), n_bins,
                                            _ptr(bins), _stream(stream)))
+
+
+def hog_integral_launches(W: int, H: int, n_bins: int) -> int:
+    return _lib.hog_integral_launches(W, H, n_bins)
 
 
 def hog_integral_workspace_bytes(W: int, H: int, n_bins: int) -> int:

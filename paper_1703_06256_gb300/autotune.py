@@ -31,7 +31,7 @@ KNOBS = {
     "integral_band_rows": (HOG_TUNE_INTEGRAL_BAND_ROWS, (0, 4, 8, 16, 32)),
     "binmap_ctas_per_sm": (HOG_TUNE_BINMAP_CTAS_PER_SM, (0, 1, 2, 4)),
     "fused_ctas_per_sm": (HOG_TUNE_FUSED_CTAS_PER_SM, (0, 1)),
-    "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 16, 32)),
+    "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 2, 4, 8, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
     "score_path": (HOG_TUNE_SCORE_PATH, (0, 1, 2)),

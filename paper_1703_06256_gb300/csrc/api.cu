@@ -87,7 +87,10 @@ hog_status hog_tune_set(int knob, int value) {
         case HOG_TUNE_INTEGRAL_BAND_ROWS: ok = ok || value == 4 || value == 8 || value == 16 || value == 32; break;
         case HOG_TUNE_BINMAP_CTAS_PER_SM: ok = ok || (value >= 1 && value <= 8); break;
         case HOG_TUNE_FUSED_CTAS_PER_SM: ok = ok || value == 1 || value == 2; break;
-        case HOG_TUNE_SCORE_TC_ROWS: ok = ok || value == 16 || value == 32; break;
+        case HOG_TUNE_SCORE_TC_ROWS:
+            ok = ok || value == 1 || value == 2 || value == 4 || value == 8 || value == 16 || value == 32 ||
+                 value == 64;
+            break;
         case HOG_TUNE_TABLE: ok = ok || value == 1 || value == 2; break;
         case HOG_TUNE_CELL_ROWS: ok = ok || value == 1 || value == 4 || value == 8 || value == 16; break;
         case HOG_TUNE_SCORE_PATH: ok = ok || value == 1 || value == 2; break;
@@ -177,6 +180,11 @@ hog_status hog_bin_map(const uint8_t* img, int W, int H, int channels, size_t pi
 size_t hog_integral_workspace_bytes(int W, int H, int n_bins) {
     if (!size_ok(W, H) || n_bins < 1 || n_bins > kMaxBins) return 0;
     return integral_workspace_bytes(W, H, n_bins);
+}
+
+int hog_integral_launches(int W, int H, int n_bins) {
+    if (!size_ok(W, H) || n_bins < 1 || n_bins > kMaxBins) return 0;
+    return integral_launches(W, H, n_bins);
 }
 
 hog_status hog_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii, void* workspace,

@@ -45,7 +45,7 @@
 //
 // Single pass (images of moderate size, where three launches cost more in
 // latency than the planes take to write).  One CTA per tile of R = 16 or 32
-// rows by 128 columns, tiles numbered row-major; warp w owns 4 rows of the
+// rows by 128 columns, tiles numbered row-major; warp w owns 2 rows of the
 // tile.  A CTA loads its rows, publishes the tile's aggregates -- its
 // per-column counts over the R rows, its per-row counts over the 128
 // columns and its totals -- and raises its flag (onepass.cuh).  It then
@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(32)
 }
 
 // ---------------------------------------------------------------- single pass
-constexpr int kOpRowsPerWarp = 4;
+constexpr int kOpRowsPerWarp = 2;
 
 // Shared-memory slot of column x (0..127) of a group: lane x / 4 owns
 // columns 4L..4L+3, so slot (x % 4) * 32 + x / 4 makes a warp's accesses to
@@ -713,6 +713,7 @@ __global__ void __launch_bounds__(32 * NW)
                                                // word 2m bins 4m, 4m+2; word 2m+1 bins 4m+1, 4m+3
     __shared__ int rl_s[R][WIN];               // the tile rows' counts over the group
     __shared__ uint32_t rl16_s[R][WIN / 2];    // RL of the tile's rows, 16-bit fields (bins 2i, 2i + 1)
+    __shared__ int rlpre_s[R][WIN];            // RL summed over the tile's rows above each row
     __shared__ int corner_s[WIN];
     __shared__ uint32_t tag_s;
 
@@ -791,28 +792,30 @@ __global__ void __launch_bounds__(32 * NW)
         for (int r = 0; r < R; ++r) tot += rl_s[r][tid];
         ws.totagg[((size_t)I * n_groups + g) * WIN + tid] = (uint32_t)tot;
     }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) onepass::st_release(ws.flags + t, tag);
+    __syncthreads();  // every thread's aggregates are stored
+    if (tid == 0) {
+        __threadfence();  // ... and visible to the GPU before the flag
+        onepass::st_release(ws.flags + t, tag);
+    }
 
-    // ---- wait for the tiles above and to the left (all of lower number): every thread
-    // checks its share of their flags with independent loads, then acquires
-    {
+    // ---- wait for the tiles above and to the left (all of lower number): the first warp
+    // checks their flags (a lane per flag, independent loads), then acquires
+    if (warp == 0) {
         const int nd = (I + 1) * (g + 1) - 1;
         bool ok = true;
-        for (int e0 = 0; e0 < nd; e0 += 8 * NT) {
+        for (int e0 = 0; e0 < nd; e0 += 8 * 32) {
             const uint64_t t0 = ptx::globaltimer_ns();
             while (true) {
                 bool all = true;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const int e = e0 + k * NT + tid;
+                    const int e = e0 + k * 32 + lane;
                     if (e < nd) {
                         const int Ip = e / (g + 1), gp = e - Ip * (g + 1);
                         all &= onepass::ld_relaxed(ws.flags + (size_t)Ip * n_groups + gp) == tag;
                     }
                 }
-                if (all) break;
+                if (__all_sync(0xffffffffu, all)) break;
                 if (ptx::globaltimer_ns() - t0 > kWaitLimitNs) {
                     ok = false;
                     break;
@@ -838,10 +841,10 @@ __global__ void __launch_bounds__(32 * NW)
             const int m = task >> 5, q = task & 31;
             const int xg = g * kSlice + 4 * q;
             uint32_t even[4] = {0, 0, 0, 0}, odd[4] = {0, 0, 0, 0};
-            for (int sl = s0; xg < W && sl < I; sl += NSL * 4) {
-                uint32_t a[4][4];
+            for (int sl = s0; xg < W && sl < I; sl += NSL * 8) {
+                uint32_t a[8][4];  // eight bands' loads in flight
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < 8; ++u) {
                     const int Ip = sl + u * NSL;
                     const uint32_t* src = ws.colagg + ((size_t)Ip * NM + m) * W + xg;
                     if (Ip >= I) {
@@ -858,7 +861,7 @@ __global__ void __launch_bounds__(32 * NW)
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < 8; ++u)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         even[k] += a[u][k] & 0x00FF00FFu;
@@ -933,6 +936,16 @@ __global__ void __launch_bounds__(32 * NW)
         }
     }
     __syncthreads();
+    // RL summed over the rows above each row of the tile (independent loads, one task per (row, bin))
+    for (int e = tid; e < R * WIN; e += NT) {
+        const int r = e / WIN, b = e - r * WIN;
+        int sum = 0;
+#pragma unroll
+        for (int r2 = 0; r2 < R - 1; ++r2)
+            if (r2 < r) sum += (int)((rl16_s[r2][b >> 1] >> (16 * (b & 1))) & 0xFFFFu);
+        rlpre_s[r][b] = sum;
+    }
+    __syncthreads();
 
     // ---- this warp's rows: ii(x, y0 - 1) = corner of the rows above + prefix of V over the columns
     int acc[WIN][4];
@@ -942,8 +955,9 @@ __global__ void __launch_bounds__(32 * NW)
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             uint32_t even = vtop[2 * m][sl], odd = vtop[2 * m + 1][sl];
-            for (int w2 = 0; w2 < warp; ++w2) {
-                const uint32_t a = colw[w2][m][sl];
+#pragma unroll
+            for (int w2 = 0; w2 < NW - 1; ++w2) {  // the warps above: independent loads
+                const uint32_t a = w2 < warp ? colw[w2][m][sl] : 0u;
                 even += a & 0x00FF00FFu;
                 odd += (a >> 8) & 0x00FF00FFu;
             }
@@ -957,8 +971,7 @@ __global__ void __launch_bounds__(32 * NW)
     }
 #pragma unroll
     for (int b = 0; b < WIN; ++b) {
-        int corner = corner_s[b];
-        for (int r = 0; r < warp * HW; ++r) corner += (int)((rl16_s[r][b >> 1] >> (16 * (b & 1))) & 0xFFFFu);
+        const int corner = corner_s[b] + rlpre_s[warp * HW][b];
         const int tot = acc[b][3];
         const int incl = (int)warp_incl_scan((uint32_t)tot, lane);
         const int o = corner + incl - tot;
@@ -1038,7 +1051,7 @@ hog_status run_all(const Plan& p, const uint8_t* bins, int n_bins, OutT* ii, con
 //                 [either the three-phase arrays or the single-pass aggregates]
 // The sync region is the only part that must start zero-filled; nothing else
 // writes into it, so the two paths can share one workspace.
-constexpr int kOpMinRows = kOpRowsPerWarp * 4;  // the shorter single-pass tile (4 warps)
+constexpr int kOpMinRows = 16;  // the shorter single-pass tile (8 warps of 2 rows)
 
 struct OpPlan {
     int R, n_bands, n_groups, n_tiles, win, n_windows;
@@ -1086,9 +1099,9 @@ template <int WIN, typename OutT>
 hog_status op_window(const OpPlan& o, const uint8_t* bins, int W, int H, int n_bins, int lo, OutT* ii,
                      const OpWs& ws, bool vec, unsigned int* status, cudaStream_t st) {
     if (o.R == 32)
-        return launch_pdl(ii_onepass_kernel<WIN, 8, OutT>, dim3(o.n_tiles), dim3(256), 0, st, bins, W, H,
+        return launch_pdl(ii_onepass_kernel<WIN, 16, OutT>, dim3(o.n_tiles), dim3(512), 0, st, bins, W, H,
                           o.n_groups, lo, n_bins, vec, ws, ii, status);
-    return launch_pdl(ii_onepass_kernel<WIN, 4, OutT>, dim3(o.n_tiles), dim3(128), 0, st, bins, W, H, o.n_groups,
+    return launch_pdl(ii_onepass_kernel<WIN, 8, OutT>, dim3(o.n_tiles), dim3(256), 0, st, bins, W, H, o.n_groups,
                       lo, n_bins, vec, ws, ii, status);
 }
 
@@ -1116,6 +1129,13 @@ bool onepass_default(int W, int H) {
 }  // namespace
 
 size_t integral_sync_bytes(int W, int H) { return sync_bytes(W, H); }
+
+int integral_launches(int W, int H, int n_bins) {
+    const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);
+    const bool one = path == 2 || (path == 0 && onepass_default(W, H));
+    const int win = n_bins <= 4 ? 4 : (n_bins <= 8 ? 8 : 16);
+    return (one ? 1 : 3) * ceil_div(n_bins, win);
+}
 
 size_t integral_workspace_bytes(int W, int H, int n_bins) {
     // enough for every band height and both paths, so a workspace stays valid whatever the tuning

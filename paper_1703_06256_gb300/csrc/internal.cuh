@@ -47,6 +47,8 @@ hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t
 size_t integral_workspace_bytes(int W, int H, int n_bins);
 // Leading bytes of an integral workspace that must be zero-filled before its first use.
 size_t integral_sync_bytes(int W, int H);
+// Kernel launches hog_integral makes for this size under the current knobs.
+int integral_launches(int W, int H, int n_bins);
 hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
                            void* ws, cudaStream_t st);
 

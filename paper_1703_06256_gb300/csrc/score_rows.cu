@@ -27,15 +27,21 @@
 // is scored alone, so its scores are the same bit for bit.
 //
 // Every MMA row is useful: a CTA streams the cell rows py0 .. py1 - 1 + 15 r
-// of one strip of 128 windows through a ring of shared-memory stages (bulk
-// copies, mbarriers), one thread issues 4 MMAs per row (K = 64) into one of
-// two TMEM accumulators, and four epilogue warps (one per 32 TMEM lanes: lane
-// m is window px0 + m) read P of the row back, add the parts ((lo + mid) +
-// hi), and add P_j into a running sum per window py = c - j r kept in
-// shared memory (a ring of 16 r rows per window column).  After row c the
-// window py = c - 15 r has all 16 of its rows: it is written (with the bias)
-// and its ring slot cleared.  Rows of windows above py0 fall in the ring
-// too and are cleared unwritten.
+// of one strip of 128 windows through a ring of shared-memory stages of up to
+// four rows each (one bulk copy per row, one mbarrier per stage), one thread
+// issues 4 MMAs per row (K = 64) into the stage's TMEM accumulator (row t of
+// the stage at column t N; two to four accumulators in turn), and eight
+// epilogue warps (two groups of four, one warp per 32 TMEM lanes in each:
+// lane m is window px0 + m) read P back row by row, add the parts ((lo +
+// mid) + hi), and add P_j into a running sum per window py = c - j r kept
+// in shared memory (a ring of 16 r rows per window column).  With r > 1 one
+// group takes the cell rows of even index and the other those of odd index:
+// their ring rows never meet.  After row c the window py = c - 15 r has all
+// 16 of its rows: it is written (with the bias) and its ring slot cleared.
+// Rows of windows above py0 fall in the ring too and are cleared unwritten.
+// Synchronising once per stage and per accumulator rather than once per row
+// keeps the handoffs between the copy, MMA and epilogue threads off the
+// critical path.
 //
 // Every wait is bounded: on a timeout the kernel sets the device status bit,
 // lets its copies and MMAs drain (again bounded), frees TMEM and returns.
@@ -54,10 +60,10 @@ namespace {
 using namespace tc;
 
 constexpr int kM = 128;        // windows per CTA (TMEM lanes)
-constexpr int kEpiWarps = 4;   // one per 32 TMEM lanes
+constexpr int kEpiWarps = 8;   // two groups of four, one warp per 32 TMEM lanes in each
 constexpr int kThreads = 32 * (kEpiWarps + 2);
-constexpr int kStages = 8;     // cell rows in flight
-constexpr int kBufs = 2;       // TMEM accumulators
+constexpr int kStages = 4;     // stages (of STEP cell rows each) in flight
+constexpr int kMaxBufs = 4;    // TMEM accumulators at most
 
 constexpr int kMaxFilters = 16;  // filters per launch at most (N <= 256 with one part)
 
@@ -68,23 +74,100 @@ struct RowsBias {
 
 // Shared-memory and TMEM layout for nf filters of `parts` weight parts at r.
 struct RowsGeom {
-    int N, BUF, COLS, RS, ROW_BYTES, PLANE_BYTES;
+    int N, STEP, BUF, NBUF, COLS, RS, ROW_BYTES, PLANE_BYTES;
     size_t planes, stages, ring, bars;
     __host__ __device__ RowsGeom(int r, int parts, int nf) {
         N = 16 * parts * nf;                                  // accumulator columns of one row
+        STEP = N <= 64 ? 4 : (N <= 128 ? 2 : 1);              // cell rows per stage and per accumulator
         BUF = 16;
-        while (BUF < N) BUF *= 2;                             // column stride of the two accumulators
-        COLS = kBufs * BUF < 32 ? 32 : kBufs * BUF;           // TMEM columns allocated
+        while (BUF < STEP * N) BUF *= 2;                      // column stride of the accumulators
+        NBUF = BUF <= 128 ? kMaxBufs : 2;                     // at most 512 TMEM columns
+        COLS = NBUF * BUF < 32 ? 32 : NBUF * BUF;             // TMEM columns allocated
         RS = 16 * r;                                          // ring rows per window column and filter
         ROW_BYTES = (kM + 7 * r) * 16;
         PLANE_BYTES = N * 16;                                 // one cell's weights: N rows of 8 bf16
         planes = (size_t)8 * PLANE_BYTES;
-        stages = (size_t)kStages * ROW_BYTES;
+        stages = (size_t)kStages * STEP * ROW_BYTES;
         ring = (size_t)nf * RS * kM * 4;
-        bars = (2 * kStages + 2 * kBufs + 2) * 8;
+        bars = (2 * kStages + 2 * kMaxBufs + 2) * 8;
     }
     __host__ __device__ size_t smem_bytes() const { return 1024 + planes + stages + ring + bars; }
 };
+
+// The epilogue of one filter: the running sums of the windows in flight stay
+// in registers.  A group's cell rows arrive two (r > 1) or four (r = 1) per
+// stage of four; counting the group's rows with u, row u adds P_j to the
+// window u - j H (H = r / 2, or 1 for r = 1) and completes the window
+// u - 15 H.  The windows in flight fit a ring of 16 H registers, indexed at
+// compile time: the loop over stages is unrolled by one turn of the ring.
+template <int R, int PARTS, typename OutT>
+__device__ __forceinline__ void epilogue_one_filter(uint32_t lane_base, int nsteps, int nrows, int py0, int nbuf,
+                                                    int buf_cols, int grp, int px, int nx, float bias,
+                                                    OutT* __restrict__ scores, uint64_t* dfull, uint64_t* dempty,
+                                                    int* aborted, unsigned int* status) {
+    constexpr int N = 16 * PARTS;
+    constexpr int G2 = R > 1 ? 2 : 1;   // epilogue groups that share the rows
+    constexpr int H = R > 1 ? R / 2 : 1;
+    constexpr int RG = 16 * H;          // ring registers
+    constexpr int RPS = 4 / G2;         // the group's rows per stage of four
+    constexpr int PERIOD = RG / RPS;    // stages per turn of the ring
+    const int lane = threadIdx.x & 31;
+    const int t0 = R > 1 ? ((grp - py0) & 1) : 0;  // the group's first row within a stage
+    float ring[RG];
+#pragma unroll
+    for (int i = 0; i < RG; ++i) ring[i] = 0.f;
+    for (int k0 = 0; k0 < nsteps; k0 += PERIOD) {
+#pragma unroll
+        for (int kk = 0; kk < PERIOD; ++kk) {
+            const int k = k0 + kk;
+            if (k >= nsteps) break;
+            const int b = k % nbuf, rows = min(4, nrows - 4 * k);
+            if (!ptx::mbar_wait_bounded(&dfull[b], (k / nbuf) & 1, kWaitLimitNs) ||
+                *reinterpret_cast<volatile int*>(aborted)) {
+                atomicOr(status, kStatusTimeout);
+                atomicExch(aborted, 1);
+                return;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int tp = 0; tp < RPS; ++tp) {
+                const int t = t0 + G2 * tp;
+                if (t >= rows) break;
+                uint32_t v[PARTS][16];
+#pragma unroll
+                for (int p = 0; p < PARTS; ++p)
+                    tmem_load16_async(lane_base + (uint32_t)(b * buf_cols + t * N + 16 * p), v[p]);
+                tmem_wait_ld();
+                const int u = kk * RPS + tp;  // the group's row, modulo one turn of the ring
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    float pj;
+                    if constexpr (PARTS == 3) {
+                        pj = (__uint_as_float(v[2][j]) + __uint_as_float(v[1][j])) + __uint_as_float(v[0][j]);
+                    } else {
+                        pj = __uint_as_float(v[0][j]);
+                    }
+                    ring[(u - j * H + 16 * RG) % RG] += pj;
+                }
+                const int fin = (u - 15 * H + 16 * RG) % RG;  // the window this row completes
+                const float sum = ring[fin];
+                ring[fin] = 0.f;
+                const int py = py0 + 4 * k + t - 15 * R;
+                if (py >= py0 && px < nx) {
+                    if constexpr (std::is_same<OutT, int32_t>::value) {
+                        scores[(size_t)py * nx + px] = __float2int_rn(sum + bias);  // exact integer
+                    } else {
+                        scores[(size_t)py * nx + px] = sum + bias;
+                    }
+                }
+            }
+            // this warp's reads of the accumulator are done: the MMAs of stage k + nbuf may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&dempty[b]);
+        }
+    }
+}
 
 // BATCH = false: one image, CTA (blockIdx.x, .y) = (strip of 128 windows,
 // range of rows_per_cta output rows).  BATCH = true: the CTAs of every item
@@ -104,11 +187,12 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* stages = planes + G.planes;
     float* ring = reinterpret_cast<float*>(stages + G.stages);
     uint64_t* bars = reinterpret_cast<uint64_t*>(reinterpret_cast<uint8_t*>(ring) + G.ring);
-    uint64_t* full = bars;                 // [kStages] a cell row has landed
-    uint64_t* empty = bars + kStages;      // [kStages] its MMAs have read it
-    uint64_t* dfull = bars + 2 * kStages;  // [kBufs]   an accumulator holds P of a row
-    uint64_t* dempty = dfull + kBufs;      // [kBufs]   the epilogue has read it
-    uint64_t* done = dempty + kBufs;       // every MMA issued has completed
+    uint64_t* full = bars;                 // [kStages] a stage's cell rows have landed
+    uint64_t* empty = bars + kStages;      // [kStages] their MMAs have read them
+    uint64_t* dfull = bars + 2 * kStages;  // [NBUF]    an accumulator holds P of a step's rows
+    uint64_t* dempty = dfull + kMaxBufs;   // [NBUF]    the epilogue has read it
+    uint64_t* done = dempty + kMaxBufs;    // every MMA issued has completed
+    const int nbuf = G.NBUF;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
     __shared__ int aborted;
 
@@ -130,14 +214,29 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int py0 = yr * rows_per_cta;
     const int py1 = min(ny, py0 + rows_per_cta);
     const int nrows = (py1 - py0) + 15 * R;  // cell rows py0 .. py1 - 1 + 15 r (all < ncy)
+    const int step = G.STEP, nsteps = (nrows + step - 1) / step;
 
-    // weights: plane i, row n = (f * PARTS + part) * 16 + j holds bins 0..7 of filter f's
-    // w[j][i][.], part `part`
-    for (int e = tid; e < 8 * G.N; e += kThreads) {
-        const int i = e / G.N, n = e - i * G.N, fp = n >> 4, j = n & 15;
-        const int f = fp / PARTS, part = fp - f * PARTS;
-        *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) =
-            load_weight8_part<WT>(w, f * 1024 + (j * 8 + i) * 8, part);
+    // weights: first the raw values into shared memory (the ring's space, which is cleared
+    // afterwards) with all loads in flight at once, then plane i, row n = (f * PARTS + part) *
+    // 16 + j holds bins 0..7 of filter f's w[j][i][.], part `part`
+    {
+        const int raw_bytes = nf * 1024 * (int)sizeof(WT);
+        uint8_t* raw = reinterpret_cast<uint8_t*>(ring);
+        if ((reinterpret_cast<uintptr_t>(w) & 15) == 0) {
+            for (int e = tid; e < raw_bytes / 16; e += kThreads)
+                reinterpret_cast<uint4*>(raw)[e] = __ldg(reinterpret_cast<const uint4*>(w) + e);
+        } else {
+            for (int e = tid; e < raw_bytes; e += kThreads) raw[e] = __ldg(reinterpret_cast<const uint8_t*>(w) + e);
+        }
+        __syncthreads();
+        const WT* ws = reinterpret_cast<const WT*>(raw);
+        for (int e = tid; e < 8 * G.N; e += kThreads) {
+            const int i = e / G.N, n = e - i * G.N, fp = n >> 4, j = n & 15;
+            const int f = fp / PARTS, part = fp - f * PARTS;
+            *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) =
+                weight8_part<WT>(ws + f * 1024 + (j * 8 + i) * 8, part);
+        }
+        __syncthreads();
     }
     for (int e = tid; e < nf * G.RS * kM; e += kThreads) ring[e] = 0.f;
     if (tid == 0) {
@@ -146,9 +245,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             ptx::mbar_init(&full[s], 1);
             ptx::mbar_init(&empty[s], 1);
         }
-        for (int b = 0; b < kBufs; ++b) {
+        for (int b = 0; b < nbuf; ++b) {
             ptx::mbar_init(&dfull[b], 1);
-            ptx::mbar_init(&dempty[b], kEpiWarps);
+            ptx::mbar_init(&dempty[b], R > 1 ? kEpiWarps : 4);  // every working epilogue warp, once per step
         }
         ptx::mbar_init(done, 1);
         ptx::fence_mbar_init();
@@ -175,18 +274,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int valid = min(kM + 7 * R, ncx - px0);  // > 0: px0 < nx <= ncx
             const uint32_t bytes = (uint32_t)valid * 16;
             int armed = 0;
-            for (int q = 0; q < nrows; ++q) {
-                const int s = q % kStages;
-                if (!ptx::mbar_wait_bounded(&empty[s], ((q / kStages) & 1) ^ 1, kWaitLimitNs) ||
+            for (int k = 0; k < nsteps; ++k) {
+                const int s = k % kStages, rows = min(step, nrows - k * step);
+                if (!ptx::mbar_wait_bounded(&empty[s], ((k / kStages) & 1) ^ 1, kWaitLimitNs) ||
                     *reinterpret_cast<volatile int*>(&aborted)) {
                     atomicOr(status, kStatusTimeout);
                     atomicExch(&aborted, 1);
                     break;
                 }
-                ptx::mbar_arrive_expect_tx(&full[s], bytes);
-                ptx::bulk_g2s(stages + (size_t)s * G.ROW_BYTES, cells + ((size_t)(py0 + q) * ncx + px0) * 8, bytes,
-                              &full[s]);
-                armed = q + 1;
+                ptx::mbar_arrive_expect_tx(&full[s], bytes * rows);
+                for (int t = 0; t < rows; ++t)
+                    ptx::bulk_g2s(stages + ((size_t)s * step + t) * G.ROW_BYTES,
+                                  cells + ((size_t)(py0 + k * step + t) * ncx + px0) * 8, bytes, &full[s]);
+                armed = k + 1;
             }
             if (*reinterpret_cast<volatile int*>(&aborted)) {
                 // let the copies already issued land before the CTA can exit (bounded)
@@ -196,83 +296,106 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else if (warp == kEpiWarps + 1) {
         if (lane == 0) {
-            // MMA issuer: P of row q into accumulator q % kBufs
+            // MMA issuer: P of the rows of step k into accumulator k % nbuf (row t at column t N)
             const uint32_t idesc = instr_desc(kM, G.N);
-            const uint32_t planes_addr = ptx::smem_addr(planes);
-            for (int q = 0; q < nrows; ++q) {
-                const int s = q % kStages, b = q % kBufs;
-                if (!ptx::mbar_wait_bounded(&full[s], (q / kStages) & 1, kWaitLimitNs) ||
-                    !ptx::mbar_wait_bounded(&dempty[b], ((q / kBufs) & 1) ^ 1, kWaitLimitNs) ||
+            // descriptors: B of K step ks fixed; A of a row is the stage row's descriptor plus
+            // 2 ks r cells (the start-address field counts 16-byte units and never carries: shared
+            // addresses are below 2^18)
+            uint64_t bdesc[4];
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+                bdesc[ks] = smem_desc(ptx::smem_addr(planes) + (uint32_t)(2 * ks * G.PLANE_BYTES),
+                                      (uint32_t)G.PLANE_BYTES, 128);
+            const uint64_t adesc0 = smem_desc(ptx::smem_addr(stages), (uint32_t)(R * 16), 128);
+            for (int k = 0; k < nsteps; ++k) {
+                const int s = k % kStages, b = k % nbuf, rows = min(step, nrows - k * step);
+                if (!ptx::mbar_wait_bounded(&full[s], (k / kStages) & 1, kWaitLimitNs) ||
+                    !ptx::mbar_wait_bounded(&dempty[b], ((k / nbuf) & 1) ^ 1, kWaitLimitNs) ||
                     *reinterpret_cast<volatile int*>(&aborted)) {
                     atomicOr(status, kStatusTimeout);
                     atomicExch(&aborted, 1);
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_addr = ptx::smem_addr(stages + (size_t)s * G.ROW_BYTES);
+                for (int t = 0; t < rows; ++t) {
+                    const uint64_t arow = adesc0 + (uint64_t)((((uint32_t)s * step + t) * G.ROW_BYTES) >> 4);
+                    const uint32_t d = tmem + (uint32_t)(b * G.BUF + t * G.N);
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {  // cells 2ks, 2ks + 1
-                    const uint64_t ad = smem_desc(a_addr + (uint32_t)(2 * ks * R * 16), (uint32_t)(R * 16), 128);
-                    const uint64_t bd = smem_desc(planes_addr + (uint32_t)(2 * ks * G.PLANE_BYTES),
-                                                  (uint32_t)G.PLANE_BYTES, 128);
-                    mma_bf16(tmem + (uint32_t)(b * G.BUF), ad, bd, idesc, ks > 0 ? 1u : 0u);
+                    for (int ks = 0; ks < 4; ++ks)  // cells 2ks, 2ks + 1
+                        mma_bf16(d, arow + (uint64_t)(2 * ks * R), bdesc[ks], idesc, ks > 0 ? 1u : 0u);
                 }
                 mma_commit(&empty[s]);  // the stage is free once these MMAs have read it
-                mma_commit(&dfull[b]);  // the accumulator holds P of row q
+                mma_commit(&dfull[b]);  // the accumulator holds P of the step's rows
             }
             mma_commit(done);
             if (!ptx::mbar_wait_bounded(done, 0, kWaitLimitNs)) atomicOr(status, kStatusTimeout);
         }
     } else {
-        // epilogue: thread tid is TMEM lane tid, window column px0 + tid
-        const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
-        const int px = px0 + tid;
+        // epilogue: lane m = tid % 128 of TMEM, window column px0 + m.  With r > 1 the two groups
+        // of four warps take the cell rows of even and of odd index: a row c only touches the ring
+        // rows (c - j r) mod 16 r, which keep the parity of c, so the groups share nothing.
+        const int m = tid & (kM - 1), grp = R > 1 ? tid / kM : 0;
+        const uint32_t lane_base = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        const int px = px0 + m;
         const size_t plane = (size_t)nx * ny;
-        for (int q = 0; q < nrows; ++q) {
-            const int b = q % kBufs;
-            if (!ptx::mbar_wait_bounded(&dfull[b], (q / kBufs) & 1, kWaitLimitNs) ||
+        const bool works = R > 1 || tid < kM;  // with r = 1 the second group has no rows
+        if (works && nf == 1 && step == 4)
+            epilogue_one_filter<R, PARTS, OutT>(lane_base, nsteps, nrows, py0, nbuf, G.BUF, grp, px, nx,
+                                                fbias.b[0], scores, dfull, dempty, &aborted, status);
+        else if (works)
+        for (int k = 0; k < nsteps; ++k) {
+            const int b = k % nbuf, rows = min(step, nrows - k * step);
+            if (!ptx::mbar_wait_bounded(&dfull[b], (k / nbuf) & 1, kWaitLimitNs) ||
                 *reinterpret_cast<volatile int*>(&aborted)) {
                 atomicOr(status, kStatusTimeout);
                 atomicExch(&aborted, 1);
                 break;
             }
             tc_fence_after();
-            const int c = py0 + q;       // cell row
-            const int py = c - 15 * R;   // the window that has all of its rows after this one
-            for (int f = 0; f < nf; ++f) {
-                uint32_t v[PARTS][16];
+            for (int t = 0; t < rows; ++t) {
+                const int c = py0 + k * step + t;  // cell row
+                const int py = c - 15 * R;         // the window that has all of its rows after this one
+                if (R > 1 && (c & 1) != grp) continue;  // the other group's row
+                for (int f = 0; f < nf; ++f) {
+                    uint32_t v[PARTS][16];
 #pragma unroll
-                for (int p = 0; p < PARTS; ++p)
-                    tmem_load16_async(lane_base + (uint32_t)(b * G.BUF + (f * PARTS + p) * 16), v[p]);
-                tmem_wait_ld();
-                if (f == nf - 1) {  // the accumulator is read: the next row's MMAs may overwrite it
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) ptx::mbar_arrive(&dempty[b]);
-                }
-                float* col = ring + (size_t)f * G.RS * kM + tid;
+                    for (int p = 0; p < PARTS; ++p)
+                        tmem_load16_async(lane_base + (uint32_t)(b * G.BUF + t * G.N + (f * PARTS + p) * 16),
+                                          v[p]);
+                    tmem_wait_ld();
+                    float* col = ring + (size_t)f * G.RS * kM + m;
+                    // the 16 running sums this row adds to: distinct slots (16 r <= RS), so every load
+                    // goes out before any store
+                    float run[16];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    float pj;
-                    if constexpr (PARTS == 3) {
-                        pj = (__uint_as_float(v[2][j]) + __uint_as_float(v[1][j])) + __uint_as_float(v[0][j]);
-                    } else {
-                        pj = __uint_as_float(v[0][j]);
+                    for (int j = 0; j < 16; ++j) run[j] = col[((c - j * R) & (G.RS - 1)) * kM];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        float pj;
+                        if constexpr (PARTS == 3) {
+                            pj = (__uint_as_float(v[2][j]) + __uint_as_float(v[1][j])) + __uint_as_float(v[0][j]);
+                        } else {
+                            pj = __uint_as_float(v[0][j]);
+                        }
+                        col[((c - j * R) & (G.RS - 1)) * kM] = run[j] + pj;
                     }
-                    col[((c - j * R) & (G.RS - 1)) * kM] += pj;
-                }
-                float* slot = col + (py & (G.RS - 1)) * kM;
-                const float sum = *slot;
-                *slot = 0.f;
-                if (py >= py0 && px < nx) {
-                    const float sc = sum + fbias.b[f];
-                    if constexpr (std::is_same<OutT, int32_t>::value) {
-                        scores[f * plane + (size_t)py * nx + px] = __float2int_rn(sc);  // exact: an integer < 2^24
-                    } else {
-                        scores[f * plane + (size_t)py * nx + px] = sc;
+                    float* slot = col + (py & (G.RS - 1)) * kM;
+                    const float sum = *slot;
+                    *slot = 0.f;
+                    if (py >= py0 && px < nx) {
+                        const float sc = sum + fbias.b[f];
+                        if constexpr (std::is_same<OutT, int32_t>::value) {
+                            scores[f * plane + (size_t)py * nx + px] = __float2int_rn(sc);  // exact integer
+                        } else {
+                            scores[f * plane + (size_t)py * nx + px] = sc;
+                        }
                     }
                 }
             }
+            // this warp's reads of the accumulator are done: the MMAs of step k + nbuf may overwrite it
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&dempty[b]);
         }
     }
     __syncwarp();

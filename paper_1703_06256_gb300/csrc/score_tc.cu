@@ -354,7 +354,7 @@ int choose_tc(int nx, int ny, int r, int wpc) {
     // 32 output rows per CTA when that still gives every SM a CTA, else 16
     const long tiles_x = (nx + wpc - 1) / wpc;
     const int tuned = tune_get(HOG_TUNE_SCORE_TC_ROWS);
-    if (tuned > 0) return tuned;
+    if (tuned == 16 || tuned == 32) return tuned;  // the banded kernel's two heights; other values: its own choice
     const long ctas32 = tiles_x * ((ny + 32 * r - 1) / (32 * r)) * r;
     return ctas32 >= sm_count() ? 32 : 16;
 }
@@ -487,7 +487,7 @@ hog_status launch_score_tc_batch(const PlanHeader& h, const void* plan_dev, cons
 
 int score_tc_rows_for(long ctas32) {
     const int tuned = tune_get(HOG_TUNE_SCORE_TC_ROWS);
-    return tuned > 0 ? tuned : (ctas32 >= kNumSMs ? 32 : 16);
+    return (tuned == 16 || tuned == 32) ? tuned : (ctas32 >= kNumSMs ? 32 : 16);
 }
 
 int score_tc_windows(int n_bins) { return kM / (n_bins == 16 ? 2 : 1); }

@@ -122,6 +122,34 @@ __device__ __forceinline__ uint4 load_weight8_part<float>(const float* w, int of
     return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
+// Part `part` of the 8 weights at w (any address space, read with plain
+// loads) as 8 bf16 values.
+template <typename WT>
+__device__ __forceinline__ uint4 weight8_part(const WT* w, int part);
+template <>
+__device__ __forceinline__ uint4 weight8_part<float>(const float* w, int part) {
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = bf16_part(w[2 * k], part) | (bf16_part(w[2 * k + 1], part) << 16);
+    return make_uint4(h[0], h[1], h[2], h[3]);
+}
+template <>
+__device__ __forceinline__ uint4 weight8_part<uint16_t>(const uint16_t* w, int) {
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) h[k] = (uint32_t)w[2 * k] | ((uint32_t)w[2 * k + 1] << 16);
+    return make_uint4(h[0], h[1], h[2], h[3]);
+}
+template <>
+__device__ __forceinline__ uint4 weight8_part<int8_t>(const int8_t* w, int) {
+    uint32_t h[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)  // |w| <= 127: exact in bf16
+        h[k] = (uint32_t)f32_to_bf16_exact_int((float)w[2 * k]) |
+               ((uint32_t)f32_to_bf16_exact_int((float)w[2 * k + 1]) << 16);
+    return make_uint4(h[0], h[1], h[2], h[3]);
+}
+
 template <typename WT>
 __host__ __device__ constexpr int weight_parts() {
     return std::is_same<WT, float>::value ? 3 : 1;

@@ -140,23 +140,55 @@ class HogPipeline:
         else:
             self.run_eager(stream)
 
-    def detect_host(self, img_host: torch.Tensor | None = None, stream=None):
-        """End to end from pinned host memory: H2D copy, the path, D2H of the
-        count and of the detections.  Returns the detections as a numpy
-        record array.  Synchronises the stream."""
-        s = torch.cuda.current_stream(self.device) if stream is None else stream
-        src = self.img_host if img_host is None else img_host
-        with torch.cuda.stream(s):
-            self.img.copy_(src, non_blocking=True)
-            self.run(s)
-            self.count_host.copy_(self.count, non_blocking=True)
-        s.synchronize()
-        n = min(int(self.count_host[0]), self.max_out)
-        if n:
+    def _enqueue_host(self) -> None:
+        """The whole path from the page-locked image to page-locked results:
+        the image's host-to-device copy, the calls, and the detection list
+        and its count written by hog_detect straight into page-locked host
+        memory (mapped into the device's address space)."""
+        self.img.copy_(self.img_host, non_blocking=True)
+        if self.fused:
+            self.stage_cells_fused()
+        else:
+            self.stage_bin_map()
+            self.stage_integral()
+            self.stage_cell_hist()
+        self.stage_score()
+        hog_detect(self.scores, self.score_dtype, self.nx, self.ny, self.stride, self.thr, 0, 0, self.det_host,
+                   self.max_out, self.count_host, self.ws_det, self.ws_det_bytes)
+
+    host_graph = None
+
+    def capture_host(self) -> None:
+        """Record _enqueue_host as one CUDA graph (copy node + kernels); after
+        it, detect_host is one replay and one synchronisation."""
+        with torch.cuda.device(self.device):
+            s = torch.cuda.Stream(self.device)
+            s.wait_stream(torch.cuda.current_stream(self.device))
             with torch.cuda.stream(s):
-                self.det_host[: n * DET_BYTES].copy_(self.det[: n * DET_BYTES], non_blocking=True)
+                self._enqueue_host()  # first launches load the kernels outside the capture
             s.synchronize()
-        return dets_to_numpy(self.det_host, n), int(self.count_host[0])
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                self._enqueue_host()
+            self.host_graph = g
+
+    def detect_host(self, img_host: torch.Tensor | None = None, stream=None):
+        """End to end from pinned host memory: the image is copied in, the
+        path runs, and the GPU writes the count and the detections straight
+        into pinned host memory; one synchronisation.  Returns the
+        detections as a numpy record array and the count."""
+        s = torch.cuda.current_stream(self.device) if stream is None else stream
+        if img_host is not None:
+            self.img_host.copy_(img_host.reshape(-1))
+        with torch.cuda.stream(s):
+            if self.host_graph is not None:
+                self.host_graph.replay()
+            else:
+                self._enqueue_host()
+        s.synchronize()
+        n_all = int(self.count_host[0])
+        n = min(n_all, self.max_out)
+        return dets_to_numpy(self.det_host, n), n_all
 
     def h2d_bytes(self) -> int:
         return self.img.numel()
