@@ -421,12 +421,18 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 that stages the integral-image samples in
  *                                 shared memory: 4, 8 or 16; 1 = one thread per
  *                                 cell reading its corners directly
- *   HOG_TUNE_SCORE_PATH           the single-image score's engine where both apply:
- *                                 1 = CUDA cores, 2 = tensor cores; the
- *                                 library's choice is the tensor cores for bf16
- *                                 and int8 weights, and for f32 weights (three
- *                                 MMAs per step) only when the tensor-core grid
- *                                 alone gives every SM a CTA
+ *   HOG_TUNE_SCORE_PATH           the single-image score's engine where more than
+ *                                 one applies: 1 = CUDA cores, 2 = tensor cores
+ *                                 (8 bins: the row-GEMM kernel, one CTA per block
+ *                                 of windows), 3 = tensor cores with each filter's
+ *                                 16 rows split over a cluster of 4 CTAs (8 bins;
+ *                                 the partial sums meet in shared memory); the
+ *                                 library's choice for bf16 cells of 8 bins is 3
+ *                                 for maps of at most about 8 x 128 x (number of
+ *                                 SMs) window rows x columns, else 2; for other
+ *                                 cells the banded tensor-core kernel for bf16
+ *                                 and int8 weights, and for f32 weights only
+ *                                 when its grid alone gives every SM a CTA
  *   HOG_TUNE_SLIDE_WINDOWS        windows per sequence of the CUDA-core score
  *                                 (8 or 16): fewer gives more CTAs, more shares
  *                                 each staged cell row among more windows

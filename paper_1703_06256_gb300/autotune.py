@@ -34,7 +34,7 @@ KNOBS = {
     "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 2, 4, 8, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
-    "score_path": (HOG_TUNE_SCORE_PATH, (0, 1, 2)),
+    "score_path": (HOG_TUNE_SCORE_PATH, (0, 1, 2, 3)),
     "slide_windows": (HOG_TUNE_SLIDE_WINDOWS, (0, 8, 16)),
     "integral_path": (HOG_TUNE_INTEGRAL_PATH, (0, 1, 2)),
 }

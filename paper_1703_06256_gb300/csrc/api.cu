@@ -93,7 +93,7 @@ hog_status hog_tune_set(int knob, int value) {
             break;
         case HOG_TUNE_TABLE: ok = ok || value == 1 || value == 2; break;
         case HOG_TUNE_CELL_ROWS: ok = ok || value == 1 || value == 4 || value == 8 || value == 16; break;
-        case HOG_TUNE_SCORE_PATH: ok = ok || value == 1 || value == 2; break;
+        case HOG_TUNE_SCORE_PATH: ok = ok || value == 1 || value == 2 || value == 3; break;
         case HOG_TUNE_SLIDE_WINDOWS: ok = ok || value == 8 || value == 16; break;
         case HOG_TUNE_INTEGRAL_PATH: ok = ok || value == 1 || value == 2; break;
         default: return HOG_ERR_ARG;

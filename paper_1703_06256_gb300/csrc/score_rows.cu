@@ -73,11 +73,15 @@ struct RowsBias {
 };
 
 // Shared-memory and TMEM layout for nf filters of `parts` weight parts at r.
+constexpr int kSplit = 4;       // CTAs of a cluster that share a window block by filter rows (4 each)
+constexpr int kSplitRows = 16;  // output rows per CTA at most when split (their partial sums meet in shared memory)
+
 struct RowsGeom {
     int N, STEP, BUF, NBUF, COLS, RS, ROW_BYTES, PLANE_BYTES;
     size_t planes, stages, ring, bars;
-    __host__ __device__ RowsGeom(int r, int parts, int nf) {
-        N = 16 * parts * nf;                                  // accumulator columns of one row
+    // split: one filter, 4 of its 16 rows per CTA (N = 16 with the parts of the 4 rows, zero-padded)
+    __host__ __device__ RowsGeom(int r, int parts, int nf, bool split = false) {
+        N = split ? 16 : 16 * parts * nf;                     // accumulator columns of one row
         STEP = N <= 64 ? 4 : (N <= 128 ? 2 : 1);              // cell rows per stage and per accumulator
         BUF = 16;
         while (BUF < STEP * N) BUF *= 2;                      // column stride of the accumulators
@@ -88,7 +92,8 @@ struct RowsGeom {
         PLANE_BYTES = N * 16;                                 // one cell's weights: N rows of 8 bf16
         planes = (size_t)8 * PLANE_BYTES;
         stages = (size_t)kStages * STEP * ROW_BYTES;
-        ring = (size_t)nf * RS * kM * 4;
+        ring = split ? (size_t)kSplit * kSplitRows * kM * 4     // the partial sums of the cluster's CTAs
+                     : (size_t)nf * RS * kM * 4;
         bars = (2 * kStages + 2 * kMaxBufs + 2) * 8;
     }
     __host__ __device__ size_t smem_bytes() const { return 1024 + planes + stages + ring + bars; }
@@ -169,18 +174,95 @@ __device__ __forceinline__ void epilogue_one_filter(uint32_t lane_base, int nste
     }
 }
 
+__device__ __forceinline__ uint32_t mapa_shared(uint32_t addr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_f32(uint32_t addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// The epilogue of CTA q of a split cluster (filter rows 4q .. 4q + 3 of one
+// filter): as epilogue_one_filter with 4 filter rows, a ring of 4 H
+// registers; a window's partial sum over the CTA's rows goes into shared
+// memory of the cluster's first CTA, slot [q][py - py0][m].
+template <int R, int PARTS>
+__device__ __forceinline__ void epilogue_split(uint32_t lane_base, int nsteps, int nrows, int c0, int py0, int py1,
+                                               int q, int nbuf, int buf_cols, int grp, int m, uint32_t partial0,
+                                               uint64_t* dfull, uint64_t* dempty, int* aborted,
+                                               unsigned int* status) {
+    constexpr int G2 = R > 1 ? 2 : 1;
+    constexpr int H = R > 1 ? R / 2 : 1;
+    constexpr int RG = 4 * H;          // ring registers
+    constexpr int RPS = 4 / G2;        // the group's rows per stage of four
+    constexpr int PERIOD = RG / RPS > 0 ? RG / RPS : 1;
+    const int lane = threadIdx.x & 31;
+    const int t0 = R > 1 ? ((grp - c0) & 1) : 0;
+    const uint32_t leader = mapa_shared(partial0, 0);
+    float ring[RG];
+#pragma unroll
+    for (int i = 0; i < RG; ++i) ring[i] = 0.f;
+    for (int k0 = 0; k0 < nsteps; k0 += PERIOD) {
+#pragma unroll
+        for (int kk = 0; kk < PERIOD; ++kk) {
+            const int k = k0 + kk;
+            if (k >= nsteps) break;
+            const int b = k % nbuf, rows = min(4, nrows - 4 * k);
+            if (!ptx::mbar_wait_bounded(&dfull[b], (k / nbuf) & 1, kWaitLimitNs) ||
+                *reinterpret_cast<volatile int*>(aborted)) {
+                atomicOr(status, kStatusTimeout);
+                atomicExch(aborted, 1);
+                return;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int tp = 0; tp < RPS; ++tp) {
+                const int t = t0 + G2 * tp;
+                if (t >= rows) break;
+                uint32_t v[16];  // column part * 4 + jj: part `part` of filter row 4q + jj
+                tmem_load16_async(lane_base + (uint32_t)(b * buf_cols + t * 16), v);
+                tmem_wait_ld();
+                const int u = kk * RPS + tp;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    float pj;
+                    if constexpr (PARTS == 3) {
+                        pj = (__uint_as_float(v[8 + jj]) + __uint_as_float(v[4 + jj])) + __uint_as_float(v[jj]);
+                    } else {
+                        pj = __uint_as_float(v[jj]);
+                    }
+                    ring[(u - jj * H + 4 * RG) % RG] += pj;
+                }
+                const int fin = (u - 3 * H + 4 * RG) % RG;  // the window whose 4 rows this row completes
+                const float sum = ring[fin];
+                ring[fin] = 0.f;
+                const int py = c0 + 4 * k + t - (4 * q + 3) * R;  // the window whose last row of 4q..4q+3 this is
+                if (py >= py0 && py < py1)
+                    st_cluster_f32(leader + (uint32_t)(((q * kSplitRows + (py - py0)) * kM + m) * 4), sum);
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&dempty[b]);
+        }
+    }
+}
+
 // BATCH = false: one image, CTA (blockIdx.x, .y) = (strip of 128 windows,
 // range of rows_per_cta output rows).  BATCH = true: the CTAs of every item
 // of a batch plan in one 1-D grid; each CTA finds its item and its (strip,
 // range) from the plan and overrides the image arguments.
-template <int R, typename WT, typename OutT, bool BATCH>
+template <int R, typename WT, typename OutT, bool BATCH, bool SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
     score_rows_kernel(const uint16_t* __restrict__ cells, int ncx, int ncy, const WT* __restrict__ w, int nf,
                       const __grid_constant__ RowsBias fbias, int nx, int ny, int rows_per_cta,
                       OutT* __restrict__ scores, const PlanItem* __restrict__ items, int n_items,
                       unsigned int* status) {
     constexpr int PARTS = weight_parts<WT>();
-    const RowsGeom G(R, PARTS, nf);
+    const RowsGeom G(R, PARTS, nf, SPLIT);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint8_t* planes = base;
@@ -213,14 +295,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int px0 = xt * kM;
     const int py0 = yr * rows_per_cta;
     const int py1 = min(ny, py0 + rows_per_cta);
-    const int nrows = (py1 - py0) + 15 * R;  // cell rows py0 .. py1 - 1 + 15 r (all < ncy)
+    // split: CTA q of the cluster takes filter rows 4q .. 4q + 3, i.e. cell rows py0 + 4 q r ..
+    // py1 - 1 + (4 q + 3) r; otherwise cell rows py0 .. py1 - 1 + 15 r (all < ncy)
+    const int q = SPLIT ? (int)blockIdx.z : 0;
+    const int c0 = py0 + 4 * q * R;
+    const int nrows = (py1 - py0) + (SPLIT ? 3 : 15) * R;
     const int step = G.STEP, nsteps = (nrows + step - 1) / step;
 
     // weights: first the raw values into shared memory (the ring's space, which is cleared
     // afterwards) with all loads in flight at once, then plane i, row n = (f * PARTS + part) *
     // 16 + j holds bins 0..7 of filter f's w[j][i][.], part `part`
     {
-        const int raw_bytes = nf * 1024 * (int)sizeof(WT);
+        const int raw_bytes = nf * 1024 * (int)sizeof(WT);  // <= the ring's (or partial sums') space
         uint8_t* raw = reinterpret_cast<uint8_t*>(ring);
         if ((reinterpret_cast<uintptr_t>(w) & 15) == 0) {
             for (int e = tid; e < raw_bytes / 16; e += kThreads)
@@ -231,14 +317,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncthreads();
         const WT* ws = reinterpret_cast<const WT*>(raw);
         for (int e = tid; e < 8 * G.N; e += kThreads) {
-            const int i = e / G.N, n = e - i * G.N, fp = n >> 4, j = n & 15;
-            const int f = fp / PARTS, part = fp - f * PARTS;
-            *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) =
-                weight8_part<WT>(ws + f * 1024 + (j * 8 + i) * 8, part);
+            const int i = e / G.N, n = e - i * G.N;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (SPLIT) {  // row n = part * 4 + jj: filter row 4 q + jj; rows past 4 parts are zero
+                if (n < 4 * PARTS) v = weight8_part<WT>(ws + ((4 * q + (n & 3)) * 8 + i) * 8, n >> 2);
+            } else {
+                const int fp = n >> 4, j = n & 15, f = fp / PARTS, part = fp - f * PARTS;
+                v = weight8_part<WT>(ws + f * 1024 + (j * 8 + i) * 8, part);
+            }
+            *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) = v;
         }
         __syncthreads();
     }
-    for (int e = tid; e < nf * G.RS * kM; e += kThreads) ring[e] = 0.f;
+    if (!SPLIT)
+        for (int e = tid; e < nf * G.RS * kM; e += kThreads) ring[e] = 0.f;
     if (tid == 0) {
         aborted = 0;
         for (int s = 0; s < kStages; ++s) {
@@ -265,6 +357,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if constexpr (SPLIT) cluster_sync_all();  // every CTA of the cluster runs before any writes to another
     pdl_trigger();  // tail of the path: the successor is small, launch it early
     pdl_wait();     // set-up above read only the weights; the cell rows come from the predecessor
 
@@ -285,7 +378,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ptx::mbar_arrive_expect_tx(&full[s], bytes * rows);
                 for (int t = 0; t < rows; ++t)
                     ptx::bulk_g2s(stages + ((size_t)s * step + t) * G.ROW_BYTES,
-                                  cells + ((size_t)(py0 + k * step + t) * ncx + px0) * 8, bytes, &full[s]);
+                                  cells + ((size_t)(c0 + k * step + t) * ncx + px0) * 8, bytes, &full[s]);
                 armed = k + 1;
             }
             if (*reinterpret_cast<volatile int*>(&aborted)) {
@@ -339,7 +432,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int px = px0 + m;
         const size_t plane = (size_t)nx * ny;
         const bool works = R > 1 || tid < kM;  // with r = 1 the second group has no rows
-        if (works && nf == 1 && step == 4)
+        if (SPLIT) {
+            if (works)
+                epilogue_split<R, PARTS>(lane_base, nsteps, nrows, c0, py0, py1, q, nbuf, G.BUF, grp, m,
+                                         ptx::smem_addr(ring), dfull, dempty, &aborted, status);
+        } else if (works && nf == 1 && step == 4)
             epilogue_one_filter<R, PARTS, OutT>(lane_base, nsteps, nrows, py0, nbuf, G.BUF, grp, px, nx,
                                                 fbias.b[0], scores, dfull, dempty, &aborted, status);
         else if (works)
@@ -404,6 +501,27 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == 0) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.COLS) : "memory");
     }
+    if constexpr (SPLIT) {
+        // every CTA's partial sums are in the first CTA's shared memory; it adds the four in order
+        cluster_sync_all();
+        if (q == 0 && !*reinterpret_cast<volatile int*>(&aborted)) {
+            const float* part = ring;
+            for (int e = tid; e < (py1 - py0) * kM; e += kThreads) {
+                const int row = e / kM, mm = e - row * kM;
+                const int px = px0 + mm;
+                if (px >= nx) continue;
+                float sum = part[(0 * kSplitRows + row) * kM + mm];
+#pragma unroll
+                for (int qq = 1; qq < kSplit; ++qq) sum += part[(qq * kSplitRows + row) * kM + mm];
+                const float sc = sum + fbias.b[0];
+                if constexpr (std::is_same<OutT, int32_t>::value) {
+                    scores[(size_t)(py0 + row) * nx + px] = __float2int_rn(sc);  // exact integer
+                } else {
+                    scores[(size_t)(py0 + row) * nx + px] = sc;
+                }
+            }
+        }
+    }
 }
 
 // Output rows per CTA: the tuned value, else the fewest that keep the grid to
@@ -437,7 +555,7 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, const WT* w, int nf
     if (s != HOG_OK) return s;
     const size_t smem = RowsGeom(R, weight_parts<WT>(), nf).smem_bytes();
     if (smem > kMaxSmem) return HOG_ERR_UNSUPPORTED;
-    auto kern = score_rows_kernel<R, WT, OutT, false>;
+    auto kern = score_rows_kernel<R, WT, OutT, false, false>;
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     const int rpc = rows_per_cta(nx, ny);
@@ -446,12 +564,69 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, const WT* w, int nf
                       static_cast<const PlanItem*>(nullptr), 0, status);
 }
 
+// One filter split over clusters of kSplit CTAs (4 filter rows each).
+template <int R, typename WT, typename OutT>
+hog_status launch_split_t(const uint16_t* cells, int ncx, int ncy, const WT* w, float bias, OutT* scores, int rpc,
+                          cudaStream_t st) {
+    const int nx = ncx - 7 * R, ny = ncy - 15 * R;
+    unsigned int* status = nullptr;
+    hog_status s = device_status_word(&status);
+    if (s != HOG_OK) return s;
+    // at least 80 KiB of shared memory, so that at most two of these CTAs share an SM: their TMEM
+    // (256 columns each) then always fits, and no CTA waits in tcgen05.alloc while a CTA of its
+    // cluster waits for it at the cluster barrier
+    const size_t need = RowsGeom(R, weight_parts<WT>(), 1, true).smem_bytes();
+    const size_t smem = need > 80 * 1024 ? need : 80 * 1024;
+    static_assert(kSplit * kSplitRows * kM * 4 + 8 * 16 * 16 + kStages * 4 * (kM + 28) * 16 + 2048 < 113 * 1024,
+                  "two split CTAs fit one SM");
+    auto kern = score_rows_kernel<R, WT, OutT, false, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_fail(e);
+    RowsBias rb{};
+    rb.b[0] = bias;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((nx + kM - 1) / kM, (ny + rpc - 1) / rpc, kSplit);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 1;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = kSplit;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    e = cudaLaunchKernelEx(&cfg, kern, cells, ncx, ncy, w, 1, rb, nx, ny, rpc, scores,
+                           static_cast<const PlanItem*>(nullptr), 0, status);
+    return e == cudaSuccess ? HOG_OK : cuda_fail(e);
+}
+
 // Any number of filters: groups of filters_per_launch() per launch.
 template <int R, typename WT, typename OutT>
 hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, const void* w, int n_filters,
                           const float* biases, void* scores, cudaStream_t st) {
     const int nx = ncx - 7 * R, ny = ncy - 15 * R;
     if (nx <= 0 || ny <= 0) return HOG_OK;
+    const int path = tune_get(HOG_TUNE_SCORE_PATH);
+    const long strips = (nx + kM - 1) / kM;
+    if (path == 3 || (path != 2 && (long)ny * strips <= 8L * sm_count())) {
+        // small maps: split each filter's 16 rows over clusters of 4 CTAs, so a CTA streams its output
+        // rows plus 3 r rows instead of 15 r; one filter per launch, so that a filter's scores are the
+        // same whether it is scored alone or with others
+        const int tuned = tune_get(HOG_TUNE_SCORE_TC_ROWS);
+        int rpc = tuned > 0 ? tuned : (int)(((long)ny * strips * kSplit + sm_count() - 1) / sm_count());
+        rpc = rpc < 1 ? 1 : (rpc > kSplitRows ? kSplitRows : rpc);
+        for (int f = 0; f < n_filters; ++f) {
+            const float b = std::is_same<OutT, int32_t>::value ? (float)std::llround((double)biases[f]) : biases[f];
+            const hog_status s = launch_split_t<R, WT, OutT>(
+                cells, ncx, ncy, static_cast<const WT*>(w) + (size_t)f * 1024, b,
+                static_cast<OutT*>(scores) + (size_t)f * nx * ny, rpc, st);
+            if (s != HOG_OK) return s;
+        }
+        return HOG_OK;
+    }
     const int group = filters_per_launch(R, weight_parts<WT>(), n_filters);
     for (int f0 = 0; f0 < n_filters; f0 += group) {
         const int g = n_filters - f0 < group ? n_filters - f0 : group;
@@ -473,7 +648,7 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void*
     hog_status s = device_status_word(&status);
     if (s != HOG_OK) return s;
     const size_t smem = RowsGeom(R, weight_parts<WT>(), 1).smem_bytes();
-    auto kern = score_rows_kernel<R, WT, OutT, true>;
+    auto kern = score_rows_kernel<R, WT, OutT, true, false>;
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e);
     RowsBias rb{};
