@@ -831,6 +831,45 @@ __global__ void __launch_bounds__(32 * NW)
     pdl_trigger();
 
     // ---- carries from the aggregates (loads from L2, many in flight per thread)
+    // The first RL and corner loads of this thread go out first, so that their latency
+    // overlaps that of the V loads.
+    constexpr int RL_NSL = NT / R;
+    const int rl_r = tid % R, rl_sl0 = tid / R, rl_y = y_tile + rl_r;
+    uint32_t rl_pf[WIN / 2];
+#pragma unroll
+    for (int i = 0; i < WIN / 2; ++i) rl_pf[i] = 0;
+    if (rl_y < H && rl_sl0 < g) {
+        const uint32_t* src =
+            reinterpret_cast<const uint32_t*>(ws.rowagg + ((size_t)rl_y * n_groups + rl_sl0) * WIN);
+        if (WIN == 4) {
+            const uint2 v2 = __ldcg(reinterpret_cast<const uint2*>(src));
+            rl_pf[0] = v2.x;
+            rl_pf[1 % (WIN / 2)] = v2.y;
+        } else {
+#pragma unroll
+            for (int q = 0; q < WIN / 8; ++q) {
+                const uint4 v4 = __ldcg(reinterpret_cast<const uint4*>(src) + q);
+                rl_pf[4 * q] = v4.x;
+                rl_pf[(4 * q + 1) % (WIN / 2)] = v4.y;
+                rl_pf[(4 * q + 2) % (WIN / 2)] = v4.z;
+                rl_pf[(4 * q + 3) % (WIN / 2)] = v4.w;
+            }
+        }
+    }
+    const int n_corner = I * g;
+    uint4 c_pf[2][WIN / 4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const int task = tid + u * NT;
+#pragma unroll
+        for (int qd = 0; qd < WIN / 4; ++qd) c_pf[u][qd] = make_uint4(0, 0, 0, 0);
+        if (task < n_corner) {
+            const int Ip = task / g, gp = task - Ip * g;
+            const uint4* src = reinterpret_cast<const uint4*>(ws.totagg + ((size_t)Ip * n_groups + gp) * WIN);
+#pragma unroll
+            for (int qd = 0; qd < WIN / 4; ++qd) c_pf[u][qd] = __ldcg(src + qd);
+        }
+    }
     // V at the tile top: task (m, column quad q), the bands above split over NT / (32 NM)
     // slices; 8-bit fields widened to 16 (V <= H < 65536), slices added in shared memory
     {
@@ -878,16 +917,16 @@ __global__ void __launch_bounds__(32 * NW)
     // RL of the tile's rows: task (row r, group slice), the groups to the left split over
     // NT / R slices; WIN 16-bit counts per (row, group) load as one vector
     {
-        constexpr int NSL = NT / R;
-        const int r = tid % R, sl0 = tid / R;
-        const int y = y_tile + r;
+        constexpr int NSL = RL_NSL;
+        const int r = rl_r, sl0 = rl_sl0;
+        const int y = rl_y;
         uint32_t acc[WIN / 2];
 #pragma unroll
-        for (int i = 0; i < WIN / 2; ++i) acc[i] = 0;
+        for (int i = 0; i < WIN / 2; ++i) acc[i] = rl_pf[i];  // group sl0, loaded above
         if (y < H) {
             const uint16_t* row = ws.rowagg + (size_t)y * n_groups * WIN;
 #pragma unroll 2
-            for (int gp = sl0; gp < g; gp += NSL) {
+            for (int gp = sl0 + NSL; gp < g; gp += NSL) {
                 const uint32_t* src = reinterpret_cast<const uint32_t*>(row + (size_t)gp * WIN);
                 if (WIN == 4) {
                     const uint2 v2 = __ldcg(reinterpret_cast<const uint2*>(src));
@@ -914,8 +953,17 @@ __global__ void __launch_bounds__(32 * NW)
         int acc[WIN];
 #pragma unroll
         for (int b = 0; b < WIN; ++b) acc[b] = 0;
-        const int n = I * g;
-        for (int task = tid; task < n; task += NT) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u)  // the two tasks loaded above
+#pragma unroll
+            for (int qd = 0; qd < WIN / 4; ++qd) {
+                acc[4 * qd] += (int)c_pf[u][qd].x;
+                acc[4 * qd + 1] += (int)c_pf[u][qd].y;
+                acc[4 * qd + 2] += (int)c_pf[u][qd].z;
+                acc[4 * qd + 3] += (int)c_pf[u][qd].w;
+            }
+        const int n = n_corner;
+        for (int task = tid + 2 * NT; task < n; task += NT) {
             const int Ip = task / g, gp = task - Ip * g;
             const uint4* src = reinterpret_cast<const uint4*>(ws.totagg + ((size_t)Ip * n_groups + gp) * WIN);
 #pragma unroll

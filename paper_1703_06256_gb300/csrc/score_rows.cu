@@ -315,18 +315,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int e = tid; e < raw_bytes; e += kThreads) raw[e] = __ldg(reinterpret_cast<const uint8_t*>(w) + e);
         }
         __syncthreads();
+        // task (f, j, i): the 8 bins of filter f's w[j][i][.] (consecutive in the raw copy: neighbouring
+        // tasks read neighbouring 8-value groups), split once into its parts, one plane row per part
         const WT* ws = reinterpret_cast<const WT*>(raw);
-        for (int e = tid; e < 8 * G.N; e += kThreads) {
-            const int i = e / G.N, n = e - i * G.N;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (SPLIT) {  // row n = part * 4 + jj: filter row 4 q + jj; rows past 4 parts are zero
-                if (n < 4 * PARTS) v = weight8_part<WT>(ws + ((4 * q + (n & 3)) * 8 + i) * 8, n >> 2);
-            } else {
-                const int fp = n >> 4, j = n & 15, f = fp / PARTS, part = fp - f * PARTS;
-                v = weight8_part<WT>(ws + f * 1024 + (j * 8 + i) * 8, part);
+        const int nrow = SPLIT ? 4 : 16;  // filter rows this CTA keeps
+        for (int e = tid; e < nf * nrow * 8; e += kThreads) {
+            const int f = e / (nrow * 8), ji = e - f * nrow * 8, jl = ji >> 3, i = ji & 7;
+            const int j = SPLIT ? 4 * q + jl : jl;
+            uint4 parts[PARTS];
+            weight8_parts<WT, PARTS>(ws + f * 1024 + (j * 8 + i) * 8, parts);
+#pragma unroll
+            for (int part = 0; part < PARTS; ++part) {
+                // row n: split, part * 4 + jj (rows past 4 parts stay zero); else (f * PARTS + part) * 16 + j
+                const int n = SPLIT ? part * 4 + jl : (f * PARTS + part) * 16 + j;
+                *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) = parts[part];
             }
-            *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) = v;
         }
+        if (SPLIT)  // the zero rows past the parts (N = 16)
+            for (int e = tid; e < 8 * (16 - 4 * PARTS); e += kThreads) {
+                const int i = e / (16 - 4 * PARTS), n = 4 * PARTS + e % (16 - 4 * PARTS);
+                *reinterpret_cast<uint4*>(planes + (size_t)i * G.PLANE_BYTES + (size_t)n * 16) = make_uint4(0, 0, 0, 0);
+            }
         __syncthreads();
     }
     if (!SPLIT)

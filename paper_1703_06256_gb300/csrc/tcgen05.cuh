@@ -150,6 +150,31 @@ __device__ __forceinline__ uint4 weight8_part<int8_t>(const int8_t* w, int) {
     return make_uint4(h[0], h[1], h[2], h[3]);
 }
 
+// All PARTS parts of the 8 weights at w (any address space): part p is the
+// bf16 rounding of what parts 0 .. p - 1 leave of each weight.
+template <typename WT, int PARTS>
+__device__ __forceinline__ void weight8_parts(const WT* w, uint4 (&out)[PARTS]) {
+    if constexpr (std::is_same<WT, float>::value) {
+        float x[8];
+        const float4 a = reinterpret_cast<const float4*>(w)[0], b = reinterpret_cast<const float4*>(w)[1];
+        x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+        x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+#pragma unroll
+        for (int p = 0; p < PARTS; ++p) {
+            uint32_t h[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const __nv_bfloat16 r = __float2bfloat16_rn(x[k]);
+                h[k] = (uint32_t)__bfloat16_as_ushort(r);
+                x[k] -= __bfloat162float(r);  // exact: the residual keeps the low bits of x
+            }
+            out[p] = make_uint4(h[0] | (h[1] << 16), h[2] | (h[3] << 16), h[4] | (h[5] << 16), h[6] | (h[7] << 16));
+        }
+    } else {
+        out[0] = weight8_part<WT>(w, 0);
+    }
+}
+
 template <typename WT>
 __host__ __device__ constexpr int weight_parts() {
     return std::is_same<WT, float>::value ? 3 : 1;
