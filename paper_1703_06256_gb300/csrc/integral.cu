@@ -993,6 +993,18 @@ __global__ void __launch_bounds__(32 * NW)
             if (r2 < r) sum += (int)((rl16_s[r2][b >> 1] >> (16 * (b & 1))) & 0xFFFFu);
         rlpre_s[r][b] = sum;
     }
+    // the column counts of the warps above each warp, in place (8-bit fields: at most 2 (NW - 1)
+    // rows): one task per (word, column), a running sum down the warps
+    for (int e = tid; e < NM * kSlice; e += NT) {
+        const int m = e / kSlice, sl = e - m * kSlice;
+        uint32_t run = 0;
+#pragma unroll
+        for (int w2 = 0; w2 < NW; ++w2) {
+            const uint32_t a = colw[w2][m][sl];
+            colw[w2][m][sl] = run;
+            run += a;
+        }
+    }
     __syncthreads();
 
     // ---- this warp's rows: ii(x, y0 - 1) = corner of the rows above + prefix of V over the columns
@@ -1003,12 +1015,9 @@ __global__ void __launch_bounds__(32 * NW)
 #pragma unroll
         for (int m = 0; m < NM; ++m) {
             uint32_t even = vtop[2 * m][sl], odd = vtop[2 * m + 1][sl];
-#pragma unroll
-            for (int w2 = 0; w2 < NW - 1; ++w2) {  // the warps above: independent loads
-                const uint32_t a = w2 < warp ? colw[w2][m][sl] : 0u;
-                even += a & 0x00FF00FFu;
-                odd += (a >> 8) & 0x00FF00FFu;
-            }
+            const uint32_t a = colw[warp][m][sl];  // the counts of the warps above this one
+            even += a & 0x00FF00FFu;
+            odd += (a >> 8) & 0x00FF00FFu;
             const int vb[4] = {(int)(even & 0xFFFFu), (int)(odd & 0xFFFFu), (int)(even >> 16), (int)(odd >> 16)};
 #pragma unroll
             for (int e = 0; e < 4; ++e) {
