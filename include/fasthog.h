@@ -174,11 +174,13 @@ hog_status hog_bin_map(const uint8_t* img, int W, int H, int channels, size_t pi
  *              single-pass schedule keeps a tag word and one flag per tile at
  *              its start, and where the flags end depends on the size).
  *              Calls that overlap on the device must not share a workspace.
+ *              (The cluster schedule, the library's choice for images up to
+ *              640 rows and 8 bins, does not touch it.)
  */
 size_t hog_integral_workspace_bytes(int W, int H, int n_bins);
 /* Kernel launches one hog_integral call of this size enqueues under the
- * current launch-shape knobs (1 or 3 per window of up to 16 bins); 0 for an
- * invalid size. */
+ * current launch-shape knobs (1 or 3 per window of up to 16 bins, 1 per
+ * window of up to 8 bins on the cluster schedule); 0 for an invalid size. */
 int hog_integral_launches(int W, int H, int n_bins);
 hog_status hog_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
                         void* workspace, size_t workspace_bytes, hog_stream_t stream);
@@ -408,9 +410,19 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *   HOG_TUNE_INTEGRAL_PATH        the integral images' schedule: 1 = three
  *                                 launches (tile reduce, carries, tile scan),
  *                                 2 = one single-pass launch (each tile sums the
- *                                 aggregates of the tiles above and to its left);
- *                                 the library's choice is the single pass up to
- *                                 about 2048 x 1152 pixels
+ *                                 aggregates of the tiles above and to its left),
+ *                                 3 = one launch of thread-block clusters, one
+ *                                 cluster of up to 16 CTAs per 128 columns
+ *                                 (images up to 1280 rows and 8192 columns;
+ *                                 taller or wider ones take three launches).
+ *                                 The library's choice: 3 for images up to 640
+ *                                 rows with at most 8 bins whose clusters all
+ *                                 fit the GPU at once, else 2 up to 250,000
+ *                                 pixels, else 1
+ *   HOG_TUNE_INTEGRAL_WARP_ROWS   rows per warp of the cluster schedule: 2, 4
+ *                                 or 8 (2 and 4 cover up to 640 rows, 8 up to
+ *                                 1280; the library's choice is 2 where every
+ *                                 cluster fits the GPU at once, else 4)
  *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
  *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 1, 2, 4, 8, 16,
@@ -458,7 +470,8 @@ typedef enum {
     HOG_TUNE_SCORE_PATH = 6,
     HOG_TUNE_SLIDE_WINDOWS = 7,
     HOG_TUNE_INTEGRAL_PATH = 8,
-    HOG_TUNE_KNOBS = 9
+    HOG_TUNE_INTEGRAL_WARP_ROWS = 9,
+    HOG_TUNE_KNOBS = 10
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

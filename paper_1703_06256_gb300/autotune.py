@@ -23,7 +23,8 @@ import os
 import statistics
 
 from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_CELL_ROWS, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
-               HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_INTEGRAL_PATH, HOG_TUNE_SCORE_PATH, HOG_TUNE_SCORE_TC_ROWS,
+               HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_INTEGRAL_PATH, HOG_TUNE_INTEGRAL_WARP_ROWS, HOG_TUNE_SCORE_PATH,
+               HOG_TUNE_SCORE_TC_ROWS,
                HOG_TUNE_SLIDE_WINDOWS, hog_tune_get, hog_tune_set)
 
 # knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
@@ -36,11 +37,12 @@ KNOBS = {
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
     "score_path": (HOG_TUNE_SCORE_PATH, (0, 1, 2, 3)),
     "slide_windows": (HOG_TUNE_SLIDE_WINDOWS, (0, 8, 16)),
-    "integral_path": (HOG_TUNE_INTEGRAL_PATH, (0, 1, 2)),
+    "integral_path": (HOG_TUNE_INTEGRAL_PATH, (0, 1, 2, 3)),
+    "integral_warp_rows": (HOG_TUNE_INTEGRAL_WARP_ROWS, (0, 2, 4, 8)),
 }
 # the knobs each path's launches read
 PATH_KNOBS = {
-    "separate": ("integral_path", "integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_path",
+    "separate": ("integral_path", "integral_warp_rows", "integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_path",
                  "score_tc_rows", "slide_windows", "table"),
     "fused": ("fused_ctas_per_sm", "score_path", "score_tc_rows", "slide_windows", "table"),
 }

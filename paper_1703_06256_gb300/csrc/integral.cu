@@ -43,8 +43,12 @@
 // Bins are handled in windows of at most 16; larger N_b runs the phases once
 // per window.  Limits: W, H < 65536 (16-bit row counts and carries).
 //
-// Single pass (images of moderate size, where three launches cost more in
-// latency than the planes take to write).  One CTA per tile of R = 16 or 32
+// Three schedules compute the same planes: the three launches above (large
+// images), a single pass (small images, where three launches cost more in
+// latency than the planes take to write) and a cluster pass (images up to
+// 640 rows; see "cluster pass" below).
+//
+// Single pass.  One CTA per tile of R = 16 or 32
 // rows by 128 columns, tiles numbered row-major; warp w owns 2 rows of the
 // tile.  A CTA loads its rows, publishes the tile's aggregates -- its
 // per-column counts over the R rows, its per-row counts over the 128
@@ -58,6 +62,10 @@
 // Inside the tile the warps' carries come from shared memory (the column
 // counts of the warps above, the RL of the rows above), and each warp runs
 // the scan of phase C on its rows.
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "internal.cuh"
 #include "onepass.cuh"
 
@@ -1074,6 +1082,290 @@ __global__ void __launch_bounds__(32 * NW)
     }
 }
 
+// ---------------------------------------------------------------- cluster pass
+// One thread-block cluster per 128-column group, its CTAs stacked down the
+// image (rank k owns rows k R .. k R + R - 1, R = HW rows per warp x NW
+// warps, at most 16 CTAs per cluster, so images up to 16 R rows).  Nothing
+// is published to global memory and no CTA waits on a flag:
+//   V(x, tile top - 1)  the column counts of the CTAs above in the cluster,
+//                       read from their shared memory (distributed shared
+//                       memory) after one cluster barrier;
+//   RL(y)               counted by the CTA itself from the bins left of the
+//                       group in its own rows (the bin map is one byte per
+//                       pixel, so this is a short read);
+//   corner              the sums of RL over the rows of the CTAs above,
+//                       read the same way as V.
+// A second cluster barrier, arrived at after the reads and waited on at the
+// very end, keeps every CTA's shared memory alive until its peers are done
+// reading it.  Inside a CTA, warp w owns HW rows and the scan of each row is
+// that of the single pass.
+
+__device__ __forceinline__ uint32_t cl_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cl_ld(const void* local, uint32_t rank) {
+    uint32_t a, v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(ptx::smem_addr(local)), "r"(rank));
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ void cl_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cl_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+
+constexpr int kClMaxCtas = 16;   // CTAs per cluster at most (non-portable size)
+constexpr int kClMaxGroups = 63; // groups left of a tile: 4 per lane and row in 8-bit fields
+// Warps per CTA at most: 20 of 2 rows (one CTA per SM), else 10 (two CTAs per SM,
+// so that a cluster packs into fewer SMs).
+__host__ __device__ constexpr int cl_max_warps(int HW) { return HW == 2 ? 20 : 10; }
+
+// One-hot counts of the 4 bins in w in 4-bit fields (bin lo + k in bits 4k .. 4k + 3;
+// bins outside lo .. lo + 7, and 0xFF, shift out of the word).
+__device__ __forceinline__ uint32_t onehot4(uint32_t w, int lo) {
+    uint32_t n = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) n += bit_or_zero(4u * (byte_at(w, c) - (uint32_t)lo));
+    return n;
+}
+
+// 4 nibbles (bits 16h .. 16h + 15 of x) spread to the 4 bytes of a word.
+__device__ __forceinline__ uint32_t nibbles_to_bytes(uint32_t x, int h) {
+    uint32_t a = (x >> (16 * h)) & 0xFFFFu;
+    a = (a | (a << 8)) & 0x00FF00FFu;
+    return (a | (a << 4)) & 0x0F0F0F0Fu;
+}
+
+// Shared-memory layout of the cluster kernel (32-bit words), for NW warps of HW rows.
+struct ClSmem {
+    int st, colw, colcnt, vtop, rl, rlpre, rltile, corner, words;
+    __host__ __device__ ClSmem(int HW, int NW, int WIN) {
+        const int NM = (WIN + 3) / 4, R = HW * NW;
+        st = 0;                         // [R][32]        the tile's bins, 4 per lane and row
+        colw = st + R * 32;             // [NW][NM][128]  per-warp column counts, then their prefix over warps
+        colcnt = colw + NW * NM * 128;  // [NM][128]      the CTA's column counts (read by the CTAs below)
+        vtop = colcnt + NM * 128;       // [2 NM][128]    V at the tile top, 16-bit fields
+        rl = vtop + 2 * NM * 128;       // [R][WIN]       RL of each row
+        rlpre = rl + R * WIN;           // [R][WIN]       RL summed over the tile's rows above
+        rltile = rlpre + R * WIN;       // [WIN]          RL summed over the tile (read by the CTAs below)
+        corner = rltile + WIN;          // [WIN]
+        words = corner + WIN;
+    }
+};
+
+template <int WIN, int HW, typename OutT>
+__global__ void __launch_bounds__(32 * cl_max_warps(HW), HW == 2 ? 1 : 2)
+    ii_cluster_kernel(const uint8_t* __restrict__ bins, int W, int H, int lo, int n_bins, bool vec,
+                      OutT* __restrict__ ii) {
+    static_assert(WIN <= 8, "the 4-bit one-hot counts hold 8 bins");
+    constexpr int NM = (WIN + 3) / 4, MAXW = cl_max_warps(HW);
+    extern __shared__ __align__(16) uint32_t sm[];
+    const int NW = (int)blockDim.x >> 5, NT = (int)blockDim.x, R = HW * NW;
+    const ClSmem L(HW, NW, WIN);
+    uint32_t* st = sm + L.st;
+    uint32_t* colw = sm + L.colw;
+    uint32_t* colcnt = sm + L.colcnt;
+    uint32_t* vtop = sm + L.vtop;
+    int* rl = reinterpret_cast<int*>(sm + L.rl);
+    int* rlpre = reinterpret_cast<int*>(sm + L.rlpre);
+    int* rltile = reinterpret_cast<int*>(sm + L.rltile);
+    int* corner = reinterpret_cast<int*>(sm + L.corner);
+
+    const int g = blockIdx.x;
+    const int k = (int)cl_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int y_tile = k * R;
+    const int y0 = y_tile + warp * HW;
+    const int nrows = max(0, min(HW, H - y0));
+    const int x0 = g * kSlice + 4 * lane;
+    const int ncol = max(0, min(4, W - x0));
+    const int wins = min(WIN, n_bins - lo);
+
+    pdl_wait();
+    // ---- this warp's rows: the bins of the group, then RL from the bins left of it
+    uint32_t v[HW];
+#pragma unroll
+    for (int r = 0; r < HW; ++r)
+        v[r] = r < nrows ? load_chunk(bins + (size_t)(y0 + r) * W + x0, ncol, vec) : 0xFFFFFFFFu;
+    {
+        // per row, 8-bit fields: ae byte i = bin lo + 2i, ao byte i = bin lo + 2i + 1 (at most
+        // 4 g <= 252 per lane); 4-bit sums of 3 words (at most 12) are folded in
+        uint32_t ae[HW], ao[HW];
+#pragma unroll
+        for (int r = 0; r < HW; ++r) ae[r] = ao[r] = 0;
+        for (int j0 = 0; j0 < g; j0 += 3) {  // 3 x HW loads in flight; every column left of the group exists
+            uint32_t wv[HW][3];
+#pragma unroll
+            for (int r = 0; r < HW; ++r)
+#pragma unroll
+                for (int u = 0; u < 3; ++u)
+                    wv[r][u] = r < nrows && j0 + u < g
+                                   ? load_chunk(bins + (size_t)(y0 + r) * W + kSlice * (j0 + u) + 4 * lane, 4, vec)
+                                   : 0xFFFFFFFFu;
+#pragma unroll
+            for (int r = 0; r < HW; ++r) {
+                const uint32_t n4 = onehot4(wv[r][0], lo) + onehot4(wv[r][1], lo) + onehot4(wv[r][2], lo);
+                ae[r] += n4 & 0x0F0F0F0Fu;
+                ao[r] += (n4 >> 4) & 0x0F0F0F0Fu;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < HW; ++r) {  // 16-bit fields for the warp sums: a row holds at most W < 65536
+            // bins lo + {0, 4}, {2, 6}, {1, 5}, {3, 7}
+            const uint32_t s0 = __reduce_add_sync(0xffffffffu, ae[r] & 0x00FF00FFu);
+            const uint32_t s2 = __reduce_add_sync(0xffffffffu, (ae[r] >> 8) & 0x00FF00FFu);
+            const uint32_t s1 = __reduce_add_sync(0xffffffffu, ao[r] & 0x00FF00FFu);
+            const uint32_t s3 = __reduce_add_sync(0xffffffffu, (ao[r] >> 8) & 0x00FF00FFu);
+            if (lane < WIN) {
+                const int q = lane & 3;
+                const uint32_t f = q == 0 ? s0 : (q == 1 ? s1 : (q == 2 ? s2 : s3));
+                rl[(warp * HW + r) * WIN + lane] = (int)((f >> (16 * (lane >> 2))) & 0xFFFFu);
+            }
+        }
+    }
+    {
+        uint32_t col4[4] = {0, 0, 0, 0};  // 4-bit fields: at most HW <= 8 per column
+#pragma unroll
+        for (int r = 0; r < HW; ++r) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) col4[c] += bit_or_zero(4u * (byte_at(v[r], c) - (uint32_t)lo));
+            st[(warp * HW + r) * 32 + lane] = v[r];
+        }
+#pragma unroll
+        for (int m = 0; m < NM; ++m)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) colw[(warp * NM + m) * kSlice + c * 32 + lane] = nibbles_to_bytes(col4[c], m);
+    }
+    __syncthreads();
+
+    // ---- the CTA's aggregates: column counts (and each warp's prefix over the warps above),
+    // RL summed over the rows above each row and over the tile
+    for (int e = tid; e < NM * kSlice; e += NT) {
+        uint32_t a[MAXW];
+#pragma unroll
+        for (int w2 = 0; w2 < MAXW; ++w2) a[w2] = w2 < NW ? colw[w2 * NM * kSlice + e] : 0u;
+        uint32_t run = 0;  // at most R <= 80 per 8-bit field
+#pragma unroll
+        for (int w2 = 0; w2 < MAXW; ++w2)
+            if (w2 < NW) {
+                colw[w2 * NM * kSlice + e] = run;
+                run += a[w2];
+            }
+        colcnt[e] = run;
+    }
+    for (int b = warp; b < WIN; b += NW) {  // lane L: rows 4L .. 4L + 3 (R <= 80)
+        int rv[4], tot = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = 4 * lane + q;
+            rv[q] = r < R ? rl[r * WIN + b] : 0;
+            tot += rv[q];
+        }
+        const int incl = (int)warp_incl_scan((uint32_t)tot, lane);
+        int ex = incl - tot;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int r = 4 * lane + q;
+            if (r < R) rlpre[r * WIN + b] = ex;
+            ex += rv[q];
+        }
+        if (lane == 31) rltile[b] = incl;
+    }
+    cl_arrive();  // this CTA's aggregates are ready (release) ...
+    cl_wait();    // ... and so are those of every CTA of the cluster (acquire)
+
+    // ---- carries from the CTAs above: V (per column, widened to 16-bit fields) and the corner
+    for (int e = tid; e < NM * kSlice; e += NT) {
+        uint32_t a[kClMaxCtas - 1];
+#pragma unroll
+        for (int q = 0; q < kClMaxCtas - 1; ++q) a[q] = q < k ? cl_ld(colcnt + e, (uint32_t)q) : 0u;
+        uint32_t even = 0, odd = 0;  // packed 16-bit adds: no field passes H < 65536
+#pragma unroll
+        for (int q = 0; q < kClMaxCtas - 1; ++q) {
+            even += a[q] & 0x00FF00FFu;
+            odd += (a[q] >> 8) & 0x00FF00FFu;
+        }
+        const int m = e / kSlice, sl = e - m * kSlice;
+        vtop[(2 * m) * kSlice + sl] = even;
+        vtop[(2 * m + 1) * kSlice + sl] = odd;
+    }
+    if (tid >= NT - WIN) {
+        const int b = tid - (NT - WIN);
+        int c = 0;
+        for (int q = 0; q < k; ++q) c += (int)cl_ld(rltile + b, (uint32_t)q);
+        corner[b] = c;
+    }
+    cl_arrive();  // done reading the other CTAs' shared memory (waited on before exit)
+    __syncthreads();
+    pdl_trigger();
+
+    // ---- this warp's rows: ii(x, y0 - 1) = corner + RL above + prefix of V over the columns
+    int acc[WIN][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const int sl = c * 32 + lane;  // cslot(4 * lane + c)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) {
+            uint32_t even = vtop[(2 * m) * kSlice + sl], odd = vtop[(2 * m + 1) * kSlice + sl];
+            const uint32_t a = colw[(warp * NM + m) * kSlice + sl];  // the counts of the warps above this one
+            even += a & 0x00FF00FFu;
+            odd += (a >> 8) & 0x00FF00FFu;
+            const int vb[4] = {(int)(even & 0xFFFFu), (int)(odd & 0xFFFFu), (int)(even >> 16), (int)(odd >> 16)};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int b = 4 * m + e;
+                if (b < WIN) acc[b][c] = c == 0 ? vb[e] : acc[b][c - 1] + vb[e];
+            }
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < WIN; ++b) {
+        const int cb = corner[b] + rlpre[(warp * HW) * WIN + b];
+        const int tot = acc[b][3];
+        const int incl = (int)warp_incl_scan((uint32_t)tot, lane);
+        const int o = cb + incl - tot;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[b][c] += o;
+    }
+
+    const size_t plane = (size_t)H * W;
+    OutT* out_row = ii + (size_t)lo * plane + (size_t)y0 * W + x0;
+#pragma unroll
+    for (int r = 0; r < HW; ++r, out_row += W) {
+        if (r >= nrows) break;
+        const uint32_t w = st[(warp * HW + r) * 32 + lane];
+        uint32_t P[4][NM], run[NM];
+#pragma unroll
+        for (int m = 0; m < NM; ++m) run[m] = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const uint32_t sh = 8u * (byte_at(w, c) - (uint32_t)lo);
+#pragma unroll
+            for (int m = 0; m < NM; ++m) {
+                run[m] += bit_or_zero(sh - 32u * m);
+                P[c][m] = run[m];
+            }
+        }
+        uint32_t E[NM];  // count in the group's columns left of this lane (8-bit fields: at most 124)
+#pragma unroll
+        for (int m = 0; m < NM; ++m) E[m] = warp_incl_scan(P[3][m], lane) - P[3][m];
+#pragma unroll
+        for (int b = 0; b < WIN; ++b) {
+            const int m = b >> 2, e = b & 3;
+            const int base = rl[(warp * HW + r) * WIN + b] + (int)byte_at(E[m], e);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[b][c] += base + (int)byte_at(P[c][m], e);
+        }
+        if (ncol > 0) {
+            OutT* p = out_row;
+#pragma unroll
+            for (int b = 0; b < WIN; ++b, p += plane)
+                if (b < wins) store_chunk<OutT>(p, acc[b], ncol, vec);
+        }
+    }
+    cl_wait();  // every CTA of the cluster has read what it needed from this one
+}
+
 template <int WIN, typename OutT>
 hog_status run_window(const Plan& p, const uint8_t* bins, int n_bins, int lo, OutT* ii, const Ws& ws, bool vec,
                       cudaStream_t st) {
@@ -1175,13 +1467,154 @@ hog_status op_all(const OpPlan& o, const uint8_t* bins, int W, int H, int n_bins
     return HOG_OK;
 }
 
-// Whether the single pass is the library's choice: each tile sums the
-// aggregates of every tile above it and above-left of it, which stays small
-// next to the planes it writes while the image has a few hundred tiles.
-bool onepass_default(int W, int H) {
-    const OpPlan o = op_plan(W, H, 1, kOpMinRows);
-    return o.n_bands <= 72 && o.n_groups <= 16;
+// ---- cluster pass: geometry, co-scheduling check, launch
+// Bins per launch: at most 8 (16 would keep 64 accumulators per thread and spill).
+inline int cl_win(int n_bins) { return n_bins <= 4 ? 4 : 8; }
+
+struct ClPlan {
+    int HW, NW, CL, n_groups;
+    size_t smem;
+};
+
+// Rows per warp: `want` (2, 4 or 8) if given, else the fewest that cover H
+// with at most 16 CTAs; false if no shape does or the group is too far right.
+bool cl_plan(int W, int H, int win, int want, ClPlan* p) {
+    const int n_groups = ceil_div(W, kSlice);
+    if (n_groups - 1 > kClMaxGroups) return false;
+    for (int hw : {2, 4, 8}) {
+        if (want != 0 && hw != want) continue;
+        int nw = ceil_div(H, hw * kClMaxCtas);
+        nw = nw < 1 ? 1 : nw;
+        if (nw > cl_max_warps(hw)) continue;
+        p->HW = hw;
+        p->NW = nw;
+        p->CL = ceil_div(H, hw * nw);
+        p->n_groups = n_groups;
+        p->smem = (size_t)ClSmem(hw, nw, win).words * 4;
+        return true;
+    }
+    return false;
 }
+
+template <int WIN, int HW, typename OutT>
+cudaLaunchConfig_t cl_config(const ClPlan& c, cudaStream_t st, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c.n_groups, c.CL);
+    cfg.blockDim = dim3(32 * c.NW);
+    cfg.dynamicSmemBytes = c.smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = 1;
+    attr[1].val.clusterDim.y = c.CL;
+    attr[1].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cfg;
+}
+
+template <int WIN, int HW, typename OutT>
+cudaError_t cl_attributes(const ClPlan& c) {
+    auto kern = ii_cluster_kernel<WIN, HW, OutT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+// How many clusters of this shape can be resident on the current device at
+// once (a cluster's CTAs must all fit the SMs of one GPC); 0 if none can.
+// Remembered per device and shape.
+template <int WIN, int HW, typename OutT>
+int cl_active_t(const ClPlan& c) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int>, int> seen;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    const auto key = std::make_tuple(dev, c.NW, c.CL);
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = seen.find(key);
+    if (it != seen.end()) return it->second;
+    int n = 0;
+    if (cl_attributes<WIN, HW, OutT>(c) == cudaSuccess) {
+        cudaLaunchAttribute attr[2];
+        cudaLaunchConfig_t cfg = cl_config<WIN, HW, OutT>(c, nullptr, attr);
+        if (cudaOccupancyMaxActiveClusters(&n, ii_cluster_kernel<WIN, HW, OutT>, &cfg) != cudaSuccess) n = 0;
+    }
+    cudaGetLastError();  // a refused query leaves no error behind
+    seen[key] = n;
+    return n;
+}
+
+template <int WIN, typename OutT>
+int cl_active_w(const ClPlan& c) {
+    return c.HW == 2 ? cl_active_t<WIN, 2, OutT>(c)
+                     : (c.HW == 4 ? cl_active_t<WIN, 4, OutT>(c) : cl_active_t<WIN, 8, OutT>(c));
+}
+
+template <typename OutT>
+int cl_active(const ClPlan& c, int win) {
+    return win == 4 ? cl_active_w<4, OutT>(c) : cl_active_w<8, OutT>(c);
+}
+
+template <int WIN, int HW, typename OutT>
+hog_status cl_launch_t(const ClPlan& c, const uint8_t* bins, int W, int H, int lo, int n_bins, bool vec, OutT* ii,
+                       cudaStream_t st) {
+    cudaError_t e = cl_attributes<WIN, HW, OutT>(c);
+    if (e != cudaSuccess) return cuda_fail(e);
+    cudaLaunchAttribute attr[2];
+    cudaLaunchConfig_t cfg = cl_config<WIN, HW, OutT>(c, st, attr);
+    e = cudaLaunchKernelEx(&cfg, ii_cluster_kernel<WIN, HW, OutT>, bins, W, H, lo, n_bins, vec, ii);
+    return e == cudaSuccess ? HOG_OK : cuda_fail(e);
+}
+
+template <typename OutT>
+hog_status cl_all(const ClPlan& c, const uint8_t* bins, int W, int H, int n_bins, int win, bool vec, OutT* ii,
+                  cudaStream_t st) {
+    for (int lo = 0; lo < n_bins; lo += win) {
+        hog_status s;
+        if (c.HW == 2)
+            s = win == 4 ? cl_launch_t<4, 2, OutT>(c, bins, W, H, lo, n_bins, vec, ii, st)
+                         : cl_launch_t<8, 2, OutT>(c, bins, W, H, lo, n_bins, vec, ii, st);
+        else if (c.HW == 4)
+            s = win == 4 ? cl_launch_t<4, 4, OutT>(c, bins, W, H, lo, n_bins, vec, ii, st)
+                         : cl_launch_t<8, 4, OutT>(c, bins, W, H, lo, n_bins, vec, ii, st);
+        else
+            s = win == 4 ? cl_launch_t<4, 8, OutT>(c, bins, W, H, lo, n_bins, vec, ii, st)
+                         : cl_launch_t<8, 8, OutT>(c, bins, W, H, lo, n_bins, vec, ii, st);
+        if (s != HOG_OK) return s;
+    }
+    return HOG_OK;
+}
+
+constexpr int kClDefaultRows = 640;  // the library takes the cluster pass up to this image height
+
+// The cluster pass for this call, if it applies and a cluster of its shape
+// fits the device.  Forced by the tuning knob, it takes any image it can
+// cover.  The library's own choice (measured): images up to 640 rows and 8
+// bins, with 2 rows per warp when every cluster can be resident at once,
+// else 4 (two CTAs per SM); past that, three launches are as fast or faster.
+bool use_cluster(int W, int H, int n_bins, int ii_dtype, ClPlan* c) {
+    const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);
+    if (path != 3 && path != 0) return false;
+    const int win = cl_win(n_bins);
+    const int want = tune_get(HOG_TUNE_INTEGRAL_WARP_ROWS);
+    auto active = [&](const ClPlan& p) {
+        return ii_dtype == HOG_U16 ? cl_active<uint16_t>(p, win) : cl_active<int32_t>(p, win);
+    };
+    if (path == 3) return cl_plan(W, H, win, want, c) && active(*c) >= 1;
+    if (H > kClDefaultRows || n_bins > 8) return false;
+    for (int hw : {2, 4}) {
+        if (want != 0 && hw != want) continue;
+        if (cl_plan(W, H, win, hw, c) && active(*c) >= c->n_groups) return true;
+    }
+    return false;
+}
+
+// Whether the single pass is the library's choice where the cluster pass is
+// not: small images only (measured: up to about 640 x 360 it beats three
+// launches, from 640 x 480 up it is slower).
+bool onepass_default(int W, int H) { return (long)W * H <= 250000L; }
 
 }  // namespace
 
@@ -1189,6 +1622,8 @@ size_t integral_sync_bytes(int W, int H) { return sync_bytes(W, H); }
 
 int integral_launches(int W, int H, int n_bins) {
     const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);
+    ClPlan c{};
+    if (use_cluster(W, H, n_bins, HOG_I32, &c)) return ceil_div(n_bins, cl_win(n_bins));
     const bool one = path == 2 || (path == 0 && onepass_default(W, H));
     const int win = n_bins <= 4 ? 4 : (n_bins <= 8 ? 8 : 16);
     return (one ? 1 : 3) * ceil_div(n_bins, win);
@@ -1211,6 +1646,13 @@ hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii
     // one 16-byte (int32) or 8-byte (uint16) vector, and every row starts aligned
     const bool vec = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (reinterpret_cast<uintptr_t>(ii) % 16 == 0) &&
                      (W % 4 == 0);
+    ClPlan c{};
+    if (use_cluster(W, H, n_bins, ii_dtype, &c)) {
+        const int win = cl_win(n_bins);
+        if (ii_dtype == HOG_U16)
+            return cl_all<uint16_t>(c, bins, W, H, n_bins, win, vec, static_cast<uint16_t*>(ii), st);
+        return cl_all<int32_t>(c, bins, W, H, n_bins, win, vec, static_cast<int32_t*>(ii), st);
+    }
     const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);
     if (path == 2 || (path == 0 && onepass_default(W, H))) {
         unsigned int* status = nullptr;

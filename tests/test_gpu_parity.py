@@ -141,12 +141,12 @@ def test_integral_uint16_modular(fh, g, nb):
         assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16), (ref & 0xFFFF).astype(np.uint16)), (H, W)
 
 
-@pytest.mark.parametrize("path,h", [(1, 4), (1, 8), (1, 16), (1, 32), (2, 16), (2, 32)])
+@pytest.mark.parametrize("path,h", [(1, 4), (1, 8), (1, 16), (1, 32), (2, 16), (2, 32), (3, 0)])
 def test_integral_band_heights(fh, g, path, h):
-    """Both schedules (HOG_TUNE_INTEGRAL_PATH: three launches, single pass) at
-    every tile height (HOG_TUNE_INTEGRAL_BAND_ROWS), int32 and uint16, one
-    window of bins and several (N_b = 20, 64): the tiles, the carries between
-    bands and groups, and partial bands at the bottom."""
+    """Every schedule (HOG_TUNE_INTEGRAL_PATH: three launches, single pass,
+    cluster pass) at every tile height (HOG_TUNE_INTEGRAL_BAND_ROWS), int32 and
+    uint16, one window of bins and several (N_b = 20, 64): the tiles, the
+    carries between bands and groups, and partial bands at the bottom."""
     fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_BAND_ROWS, h)
     fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, path)
     try:
@@ -174,6 +174,36 @@ def test_integral_single_pass_many_tiles(fh, g):
         fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
 
 
+@pytest.mark.parametrize("nb,warp_rows", [(8, 0), (8, 2), (8, 4), (8, 8), (3, 0), (16, 0), (20, 0), (20, 8)])
+def test_integral_cluster_pass(fh, g, nb, warp_rows):
+    """The cluster pass (one cluster of CTAs per 128-column group, carries
+    through distributed shared memory, the row carries counted from the bins
+    to the left) at every row count per warp (HOG_TUNE_INTEGRAL_WARP_ROWS: 2
+    and 4 take images up to 640 rows, 8 up to 1280): cluster sizes from 1 to
+    16 CTAs, the tallest image each takes, ragged right and bottom edges, an
+    unaligned width (scalar loads and stores), and the widest image (63 groups
+    to the left of the last one).  The pass uses no workspace: a zero-filled
+    one stays zero, which also shows that the pass ran.  Images it does not
+    take fall back to another schedule."""
+    shapes = [(600, 800), (1, 1), (5, 129), (64, 128), (65, 130), (130, 333), (480, 640), (640, 300),
+              (641, 300), (1080, 1920), (1280, 260), (17, 8192), (9, 8191), (301, 6), (1281, 100)]
+    fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 3)
+    fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_WARP_ROWS, warp_rows)
+    tallest = 640 if warp_rows in (2, 4) else 1280
+    try:
+        for i, (H, W) in enumerate(shapes):
+            bins = oracle_bins(H, W, nb, 4000 + 37 * nb + i, p_none=0.25)
+            ref = oracle.integral(bins, nb)
+            ws = torch.zeros(fh.hog_integral_workspace_bytes(W, H, nb), dtype=torch.uint8, device="cuda")
+            assert np.array_equal(g.gpu_integral(bins, nb, ws=ws), ref), (H, W, nb)
+            assert np.array_equal(g.gpu_integral(bins, nb, fh.HOG_U16, ws=ws), (ref & 0xFFFF).astype(np.uint16)), \
+                (H, W, nb)
+            assert (int(ws.count_nonzero()) == 0) == (H <= tallest), (H, W, "cluster pass taken or not")
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_WARP_ROWS, 0)
+
+
 def test_integral_one_workspace_many_calls(fh, g):
     """One workspace, zero-filled once per image size, serves calls of that
     size with different bin counts, dtypes and schedules in a row (each
@@ -181,7 +211,7 @@ def test_integral_one_workspace_many_calls(fh, g):
     the tag for the next)."""
     ws = torch.zeros(fh.hog_integral_workspace_bytes(1100, 600, 64), dtype=torch.uint8, device="cuda")
     sizes = {(600, 1100): [(8, 0), (8, 0), (20, 1), (20, 2), (64, 2), (8, 2), (3, 1), (16, 2)],
-             (37, 259): [(16, 2), (8, 0), (8, 1), (8, 2)],
+             (37, 259): [(16, 2), (8, 0), (8, 1), (8, 3), (8, 2), (20, 3), (8, 1)],
              (1, 5): [(8, 2), (8, 2)]}
     try:
         for (H, W), calls in sizes.items():
