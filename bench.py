@@ -413,7 +413,8 @@ def serving(torch, wl, args):
            "capacity_images_per_s": {"plain": round(cap_plain, 1), "served": round(cap_served, 1)}}
     for label, srv, streams in (("served", served, 16), ("plain", plain, 1)):
         res, wall, replay = run(srv, reqs)
-        out[label] = dict(latency_summary(res, wall), streams=streams, fused=srv.fused, **replay)
+        pauses = replay.pop("pauses_ns")
+        out[label] = dict(latency_summary(res, wall, pauses), streams=streams, fused=srv.fused, **replay)
     del served, plain, pool
     torch.cuda.empty_cache()
     return out

@@ -145,6 +145,17 @@ hog_status hog_server_enqueue(hog_server* s, int32_t rid, const uint8_t* img, in
  * memory), their number to *n_out.  Never blocks on the GPU. */
 hog_status hog_server_collect(hog_server* s, hog_server_timed_result* out, int max_out, int* n_out);
 int64_t hog_server_clock_ns(void);
+/* Pauses of the dispatcher thread since hog_server_start: stretches of more
+ * than 1 ms between two turns of its loop.  A turn only queries events and
+ * enqueues asynchronous work, so such a stretch means the thread was not
+ * running (the operating system or the host paused the process); requests in
+ * flight or queued then wait whatever the GPU does.  Writes the [start, end]
+ * stamps (hog_server_clock_ns) of the most recent min(max_n, kept) pauses,
+ * oldest first (the last 4096 are kept), and the number of pauses since
+ * hog_server_start to *n.  Callable from any thread while the dispatcher
+ * runs, and after it stopped.  HOG_ERR_ARG for a NULL server or n, a negative
+ * max_n, or NULL stamp arrays with max_n > 0. */
+hog_status hog_server_pauses(hog_server* s, int64_t* start_ns, int64_t* end_ns, int max_n, int* n);
 
 #ifdef __cplusplus
 }

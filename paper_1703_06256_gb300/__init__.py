@@ -134,6 +134,7 @@ def _load() -> ctypes.CDLL:
         "hog_server_enqueue": (I, [P, ctypes.c_int32, P, I, I, I]),
         "hog_server_collect": (I, [P, P, I, P]),
         "hog_server_clock_ns": (ctypes.c_int64, []),
+        "hog_server_pauses": (I, [P, P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -151,7 +152,7 @@ EXPORTED = ("hog_status_string", "hog_last_cuda_error", "hog_version", "hog_devi
             "hog_detect_batch_workspace_bytes", "hog_detect_batch", "hog_pyramid_bytes", "hog_pyramid",
             "hog_server_create", "hog_server_destroy", "hog_server_request_bytes", "hog_server_submit",
             "hog_server_poll", "hog_server_release", "hog_server_stats", "hog_server_start", "hog_server_stop",
-            "hog_server_enqueue", "hog_server_collect", "hog_server_clock_ns")
+            "hog_server_enqueue", "hog_server_collect", "hog_server_clock_ns", "hog_server_pauses")
 
 
 def lib() -> ctypes.CDLL:
@@ -427,6 +428,17 @@ def hog_server_collect(handle, out, max_out: int) -> int:
 
 def hog_server_clock_ns() -> int:
     return _lib.hog_server_clock_ns()
+
+
+def hog_server_pauses(handle, max_n: int = 4096) -> tuple[int, list[tuple[int, int]]]:
+    """(pauses since hog_server_start, [(start_ns, end_ns)] of the most recent
+    up to max_n of them, oldest first)."""
+    starts = (ctypes.c_int64 * max(max_n, 1))()
+    ends = (ctypes.c_int64 * max(max_n, 1))()
+    n = ctypes.c_int(0)
+    _check("hog_server_pauses", _lib.hog_server_pauses(handle, starts, ends, max_n, ctypes.byref(n)))
+    kept = min(n.value, max_n)
+    return n.value, [(starts[i], ends[i]) for i in range(kept)]
 
 
 def hog_server_stats(handle) -> tuple[int, int, int]:

@@ -106,6 +106,9 @@ struct Layout {
 
 enum class SlotState { kFree, kBusy, kHeld };
 
+constexpr int64_t kPauseNs = 1000000;  // a dispatcher turn longer than 1 ms is recorded as a pause
+constexpr size_t kMaxPauses = 4096;     // pauses kept (the most recent)
+
 int64_t clock_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
         .count();
@@ -158,6 +161,10 @@ struct hog_server {
     std::deque<Pending> queue;
     std::deque<hog_server_timed_result> finished;
     std::vector<int> to_release;
+    // stretches of more than kPauseNs between two turns of the dispatcher's loop
+    // (since hog_server_start), oldest first, the most recent kMaxPauses kept
+    std::deque<std::pair<int64_t, int64_t>> pauses;
+    long n_pauses = 0;
 
     Layout plan(int W, int H, int channels) const {
         Layout L{};
@@ -317,7 +324,20 @@ struct hog_server {
         cudaSetDevice(device);
         std::vector<hog_server_result> got(slots.size());
         std::vector<int64_t> t_done(slots.size());
+        int64_t last_turn = clock_ns();
         while (true) {
+            {
+                // a turn never blocks for long (every CUDA call here is asynchronous or a query):
+                // a longer stretch means the thread was not running
+                const int64_t now = clock_ns();
+                if (now - last_turn > kPauseNs) {
+                    std::lock_guard<std::mutex> lock(mu);
+                    pauses.emplace_back(last_turn, now);
+                    if (pauses.size() > kMaxPauses) pauses.pop_front();
+                    ++n_pauses;
+                }
+                last_turn = now;
+            }
             bool moved = false;
             {
                 std::lock_guard<std::mutex> lock(mu);
@@ -526,6 +546,11 @@ hog_status hog_server_start(hog_server* s) {
     if (s == nullptr) return HOG_ERR_ARG;
     if (s->running.load()) return HOG_ERR_ARG;
     s->stopping.store(false);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->pauses.clear();
+        s->n_pauses = 0;
+    }
     s->running.store(true);
     try {
         s->worker = std::thread([s] { s->dispatch(); });
@@ -539,6 +564,20 @@ hog_status hog_server_start(hog_server* s) {
 hog_status hog_server_stop(hog_server* s) {
     if (s == nullptr) return HOG_ERR_ARG;
     s->stop_worker();
+    return HOG_OK;
+}
+
+hog_status hog_server_pauses(hog_server* s, int64_t* start_ns, int64_t* end_ns, int max_n, int* n) {
+    if (s == nullptr || n == nullptr || max_n < 0 || (max_n > 0 && (start_ns == nullptr || end_ns == nullptr)))
+        return HOG_ERR_ARG;
+    std::lock_guard<std::mutex> lock(s->mu);
+    const int kept = (int)s->pauses.size();
+    const int first = kept > max_n ? kept - max_n : 0;  // the most recent max_n
+    for (int i = first; i < kept; ++i) {
+        start_ns[i - first] = s->pauses[i].first;
+        end_ns[i - first] = s->pauses[i].second;
+    }
+    *n = (int)(s->n_pauses < 2147483647L ? s->n_pauses : 2147483647L);
     return HOG_OK;
 }
 

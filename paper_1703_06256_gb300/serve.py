@@ -26,7 +26,7 @@ import torch
 from . import (DET_BYTES, HOG_BF16, HOG_F32, HOG_I8, HOG_I32, HogServerConfig, HogServerResult,
                HogServerTimedResult, dets_to_numpy, hog_server_clock_ns, hog_server_collect, hog_server_create,
                hog_server_destroy, hog_server_enqueue, hog_server_poll, hog_server_release, hog_server_request_bytes,
-               hog_server_start, hog_server_stats, hog_server_stop, hog_server_submit)
+               hog_server_pauses, hog_server_start, hog_server_stats, hog_server_stop, hog_server_submit)
 
 _MAX_POLL = 64
 
@@ -56,6 +56,8 @@ class Result:
     count: int
     latency: float             # completion - arrival, seconds
     shape: tuple = field(default=())
+    t_enqueue_ns: int = 0      # native stamps (serve_native only): queued, and seen complete
+    t_done_ns: int = 0
 
 
 class HogServer:
@@ -197,14 +199,17 @@ class HogServer:
                         dets = dets_to_numpy(raw, r.count)
                     hog_server_release(self._h, r.token)
                     held.pop(r.rid)
-                    results.append(Result(r.rid, dets, r.count, (t.t_done_ns - t.t_enqueue_ns) * 1e-9, (r.H, r.W)))
+                    results.append(Result(r.rid, dets, r.count, (t.t_done_ns - t.t_enqueue_ns) * 1e-9, (r.H, r.W),
+                                          t.t_enqueue_ns, t.t_done_ns))
         finally:
             hog_server_stop(self._h)
             if gc_was_on:
                 gc.enable()
+        n_pauses, pauses = hog_server_pauses(self._h)
         lat = np.array(late) * 1e3 if late else np.zeros(1)
         return results, {"replay_late_p50_ms": round(float(np.percentile(lat, 50)), 3),
-                         "replay_late_p99_ms": round(float(np.percentile(lat, 99)), 3)}
+                         "replay_late_p99_ms": round(float(np.percentile(lat, 99)), 3),
+                         "dispatcher_pauses": n_pauses, "pauses_ns": pauses}
 
     def run_one(self, image, rid: int = 0) -> Result:
         """The plain per-image path: submit one request and wait for it."""
@@ -219,9 +224,22 @@ class HogServer:
                 return got[0]
 
 
-def latency_summary(results: list[Result], wall: float) -> dict:
+def latency_summary(results: list[Result], wall: float, pauses_ns=None, long_pause_ms: float = 5.0) -> dict:
+    """p50/p99 over every request.  With the dispatcher's pause record
+    (serve_native), also the pauses of at least `long_pause_ms` (the process
+    was not running: whatever was queued or on the GPU then waited) and p99
+    over the requests whose enqueue-to-done span overlaps none of them."""
     lat = np.array([r.latency for r in results]) * 1e3
     px = sum(int(np.prod(r.shape[:2])) for r in results)
-    return {"requests": len(results), "p50_ms": round(float(np.percentile(lat, 50)), 3),
-            "p99_ms": round(float(np.percentile(lat, 99)), 3), "images_per_s": round(len(results) / wall, 1),
-            "mpixel_per_s": round(px / wall / 1e6, 1)}
+    out = {"requests": len(results), "p50_ms": round(float(np.percentile(lat, 50)), 3),
+           "p99_ms": round(float(np.percentile(lat, 99)), 3), "images_per_s": round(len(results) / wall, 1),
+           "mpixel_per_s": round(px / wall / 1e6, 1)}
+    if pauses_ns is not None:
+        long_ = [(a, b) for a, b in pauses_ns if (b - a) * 1e-6 >= long_pause_ms]
+        hit = np.array([any(a < r.t_done_ns and b > r.t_enqueue_ns for a, b in long_) for r in results], bool)
+        clear = lat[~hit] if (~hit).any() else lat
+        out.update({"long_pauses": len(long_),
+                    "longest_pause_ms": round(max(((b - a) * 1e-6 for a, b in pauses_ns), default=0.0), 3),
+                    "requests_in_long_pauses": int(hit.sum()),
+                    "p99_ms_outside_long_pauses": round(float(np.percentile(clear, 99)), 3)})
+    return out

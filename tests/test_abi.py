@@ -125,6 +125,7 @@ def test_server_argument_errors_need_no_gpu(fh):
     assert L.hog_server_poll(None, None, 0, ctypes.byref(n)) == ARG
     assert L.hog_server_release(None, 0) == ARG
     assert L.hog_server_stats(None, None, None, None) == ARG
+    assert L.hog_server_pauses(None, None, None, 0, ctypes.byref(n)) == ARG
     assert L.hog_server_request_bytes(None, 64, 128, 3) == 0
     assert L.hog_server_destroy(None) == fh.HOG_OK
 

@@ -86,6 +86,12 @@ def test_native_dispatcher_same_as_alone(fused):
     mix, replay = srv.serve_native(reqs)
     assert sorted(r.rid for r in mix) == list(range(len(reqs)))
     assert replay["replay_late_p99_ms"] >= 0
+    # the dispatcher's pause record: stamps in order, within the run
+    n_pauses, pauses = fh.hog_server_pauses(srv._h)
+    assert n_pauses == replay["dispatcher_pauses"] >= len(pauses)
+    first, last = min(r.t_enqueue_ns for r in mix), max(r.t_done_ns for r in mix)
+    assert all(first - 10**9 < a < b <= last + 10**9 and b - a > 10**6 for a, b in pauses)
+    assert all(r.t_enqueue_ns <= r.t_done_ns for r in mix)
     for r in mix:
         a = alone[r.rid % len(images)]
         assert r.count == a.count == len(r.detections)
