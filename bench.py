@@ -108,6 +108,37 @@ def profiled_traffic(stage: str, workload: str):
     return None
 
 
+def measured_precision():
+    """The bf16 score's measured error on the 32 x 1920x1080 precision workload
+    (profiles/precision_1080p.txt, written from the precision test's output),
+    or None once the score kernel's source has changed since."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "precision_1080p.txt")
+    try:
+        lines = [ln for ln in open(path).read().splitlines() if ln.strip() and not ln.startswith("#")]
+    except OSError:
+        return None
+    out = {}
+    for ln in lines:
+        key, val = ln.split(None, 1)
+        if key == "source":
+            src, sha = val.split()
+            cur = hashlib.sha256(open(os.path.join(ROOT, src), "rb").read()).hexdigest()[:16]
+            if cur != sha:
+                return None
+            out["source"] = "profiles/precision_1080p.txt (python -m pytest tests/test_gpu_precision.py -s)"
+        elif key == "windows":
+            out[key] = int(val)
+        elif key.startswith("int8"):
+            out[key] = val
+        else:
+            out[key] = float(val)
+    out["workload"] = "32 RGB 1920x1080, N_b=8, stride 4, bf16 cells x bf16 weights (tensor cores), FP32 accumulation"
+    out["tolerance"] = "weight rounding <= 2^-8, FP32 accumulation <= 1e-5, of sum_k |w_k| h_k + |bias| per window"
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 200 ms."""
 
@@ -158,7 +189,7 @@ class ClockSampler:
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "sm_min_mhz": min(sm) if sm else None, "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def host_cores() -> int:
@@ -412,9 +443,13 @@ def serving(torch, wl, args):
            "mean_mpixel_per_request": round(sum(int(t.numel()) for t in pool) / 3 / len(pool) / 1e6, 3),
            "capacity_images_per_s": {"plain": round(cap_plain, 1), "served": round(cap_served, 1)}}
     for label, srv, streams in (("served", served, 16), ("plain", plain, 1)):
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
         res, wall, replay = run(srv, reqs)
+        clocks = sampler.stop()
         pauses = replay.pop("pauses_ns")
-        out[label] = dict(latency_summary(res, wall, pauses), streams=streams, fused=srv.fused, **replay)
+        out[label] = dict(latency_summary(res, wall, pauses), streams=streams, fused=srv.fused, clocks=clocks,
+                          **replay)
     del served, plain, pool
     torch.cuda.empty_cache()
     return out
@@ -870,6 +905,7 @@ def main():
         "fused": fused,
         "stages_4k": stage_rooflines(torch, fh, wl, flush, args, hbm) if "stages_4k" in extras else None,
         "batch_1080p": batch_1080p(torch, fh, wl, replicas, flush, args, world) if "batch_1080p" in extras else None,
+        "precision": measured_precision(),
         "batch_pyramid": (batch_pyramid(torch, fh, wl, replicas, flush, args, world) if "batch_pyramid" in extras
                           else None),
         "multi_filter": (multi_filter(torch, fh, wl, flush, args, bf16_peak()) if "multi_filter" in extras

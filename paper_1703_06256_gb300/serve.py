@@ -56,8 +56,9 @@ class Result:
     count: int
     latency: float             # completion - arrival, seconds
     shape: tuple = field(default=())
-    t_enqueue_ns: int = 0      # native stamps (serve_native only): queued, and seen complete
+    t_enqueue_ns: int = 0      # native stamps (serve_native only): queued, put on the GPU, seen complete
     t_done_ns: int = 0
+    t_admit_ns: int = 0
 
 
 class HogServer:
@@ -200,7 +201,7 @@ class HogServer:
                     hog_server_release(self._h, r.token)
                     held.pop(r.rid)
                     results.append(Result(r.rid, dets, r.count, (t.t_done_ns - t.t_enqueue_ns) * 1e-9, (r.H, r.W),
-                                          t.t_enqueue_ns, t.t_done_ns))
+                                          t.t_enqueue_ns, t.t_done_ns, t.t_admit_ns))
         finally:
             hog_server_stop(self._h)
             if gc_was_on:
@@ -242,4 +243,10 @@ def latency_summary(results: list[Result], wall: float, pauses_ns=None, long_pau
                     "longest_pause_ms": round(max(((b - a) * 1e-6 for a, b in pauses_ns), default=0.0), 3),
                     "requests_in_long_pauses": int(hit.sum()),
                     "p99_ms_outside_long_pauses": round(float(np.percentile(clear, 99)), 3)})
+        # where the slowest requests spent their time: waiting for a slot or memory, or on the GPU
+        t0 = min(r.t_enqueue_ns for r in results)
+        slow = sorted(results, key=lambda r: -r.latency)[:5]
+        out["slowest"] = [{"W": r.shape[1], "H": r.shape[0], "at_ms": round((r.t_enqueue_ns - t0) * 1e-6, 2),
+                           "wait_ms": round((r.t_admit_ns - r.t_enqueue_ns) * 1e-6, 3),
+                           "gpu_ms": round((r.t_done_ns - r.t_admit_ns) * 1e-6, 3)} for r in slow]
     return out
