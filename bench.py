@@ -831,15 +831,19 @@ def main():
 
     # end to end through the public API, from pinned host memory (graph replay: image copy, five calls,
     # detections and count written by the GPU into pinned host memory, one synchronisation)
-    pipe.capture_host()
-    for _ in range(3):
-        pipe.detect_host()
-    d2h = []
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        _, n = pipe.detect_host()
-        d2h.append(4 + min(n, pipe.max_out) * fh.DET_BYTES)
-    e2e_s = replicas.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda")
+    def one_at_a_time(zero_copy):
+        pipe.capture_host(zero_copy)
+        for _ in range(3):
+            pipe.detect_host()
+        d2h_ = []
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            _, n = pipe.detect_host()
+            d2h_.append(4 + min(n, pipe.max_out) * fh.DET_BYTES)
+        return replicas.max_over_ranks((time.perf_counter() - t0) / args.steps, device="cuda"), d2h_
+
+    e2e_s, d2h = one_at_a_time(False)
+    e2e_zc_s, _ = one_at_a_time(True)
 
     # end to end through the request server (the public serving API): the same five calls on the same
     # image, each step one request -- its image copied in from pinned host memory, its detections written
@@ -898,7 +902,12 @@ def main():
                                   "unit": "Mpixel/s",
                                   "api": "HogPipeline.detect_host (one graph: image copy, five calls, list into pinned "
                                          "host memory; one synchronisation per image)",
-                                  "d2h_bytes_per_step": int(statistics.mean(d2h))}},
+                                  "d2h_bytes_per_step": int(statistics.mean(d2h)),
+                                  "zero_copy": {"value": round(replicas.aggregate_rate(px, e2e_zc_s, world) / 1e6, 2),
+                                                "unit": "Mpixel/s",
+                                                "api": "HogPipeline.detect_host after capture_host(zero_copy=True): "
+                                                       "the bin map reads the pinned image in place (its bytes "
+                                                       "cross to the GPU inside that kernel), no copy node"}}},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "device_status": status,

@@ -462,14 +462,22 @@ def grid_shapes(W: int, H: int, cell: int = 8, stride: int = 8, cells_x: int = 8
     return ncx, ncy, nx, ny
 
 
+_DET_DTYPE = None
+
+
 def dets_to_numpy(raw, count: int):
-    """Unpack `count` hog_det records from a uint8 tensor (host or device) or
-    a bytes object."""
+    """Unpack `count` hog_det records from a uint8 tensor (host or device), a
+    uint8 numpy array or a bytes object (host memory is viewed, not copied)."""
     import numpy as np
 
-    dt = np.dtype([("x", "<i4"), ("y", "<i4"), ("score", "<f4"), ("image", "<i4"), ("level", "<i4")])
+    global _DET_DTYPE
+    if _DET_DTYPE is None:
+        _DET_DTYPE = np.dtype([("x", "<i4"), ("y", "<i4"), ("score", "<f4"), ("image", "<i4"), ("level", "<i4")])
+    dt = _DET_DTYPE
     if isinstance(raw, (bytes, bytearray)):
         return np.frombuffer(raw, dtype=np.uint8, count=count * DET_BYTES).view(dt)
+    if isinstance(raw, np.ndarray):
+        return raw[: count * DET_BYTES].view(dt)
     return raw[: count * DET_BYTES].cpu().numpy().view(dt)
 
 

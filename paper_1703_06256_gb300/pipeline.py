@@ -56,6 +56,9 @@ class HogPipeline:
         self.img_host = torch.empty(H * W * channels, dtype=torch.uint8, pin_memory=True)
         self.count_host = torch.zeros(1, dtype=torch.int32, pin_memory=True)
         self.det_host = torch.empty(self.max_out * DET_BYTES, dtype=torch.uint8, pin_memory=True)
+        # numpy views of the same page-locked memory: reading them costs no torch dispatch
+        self._count_np = self.count_host.numpy()
+        self._det_np = self.det_host.numpy()
 
     def set_weights(self, w, bias: float = 0.0, thr: float = 0.0) -> None:
         t = torch.as_tensor(np.asarray(w)).reshape(-1)
@@ -69,10 +72,10 @@ class HogPipeline:
         a = np.ascontiguousarray(img, dtype=np.uint8).reshape(-1)
         self.img.copy_(torch.from_numpy(a))
 
-    # -- the five per-image calls
-    def stage_bin_map(self, stream=None):
-        hog_bin_map(self.img, self.W, self.H, self.channels, self.W * self.channels, self.lut, self.n_bins,
-                    self.bins, stream)
+    # -- the five per-image calls (`img`: where the bin map reads the image, by default the device copy)
+    def stage_bin_map(self, stream=None, img=None):
+        hog_bin_map(self.img if img is None else img, self.W, self.H, self.channels, self.W * self.channels, self.lut,
+                    self.n_bins, self.bins, stream)
 
     def stage_integral(self, stream=None):
         hog_integral(self.bins, self.W, self.H, self.n_bins, self.ii_dtype, self.ii, self.ws_ii, self.ws_ii_bytes,
@@ -90,11 +93,11 @@ class HogPipeline:
         hog_detect(self.scores, self.score_dtype, self.nx, self.ny, self.stride, self.thr, 0, 0, self.det,
                    self.max_out, self.count, self.ws_det, self.ws_det_bytes, stream)
 
-    def stage_cells_fused(self, stream=None):
+    def stage_cells_fused(self, stream=None, img=None):
         """Bin map, integral images and cell histograms in one call (the bin
         map and the integral planes are not written)."""
-        hog_cell_hist_fused(self.img, self.W, self.H, self.channels, self.W * self.channels, self.lut, self.n_bins,
-                            self.cell, self.stride, self.cell_dtype, self.cells, stream)
+        hog_cell_hist_fused(self.img if img is None else img, self.W, self.H, self.channels, self.W * self.channels,
+                            self.lut, self.n_bins, self.cell, self.stride, self.cell_dtype, self.cells, stream)
 
     fused = False
 
@@ -140,16 +143,20 @@ class HogPipeline:
         else:
             self.run_eager(stream)
 
-    def _enqueue_host(self) -> None:
+    def _enqueue_host(self, zero_copy: bool = False) -> None:
         """The whole path from the page-locked image to page-locked results:
-        the image's host-to-device copy, the calls, and the detection list
-        and its count written by hog_detect straight into page-locked host
-        memory (mapped into the device's address space)."""
-        self.img.copy_(self.img_host, non_blocking=True)
+        the image's host-to-device copy (or, with zero_copy, none: the first
+        kernel reads the page-locked image in place, which is mapped into
+        the device's address space, so its bytes cross to the GPU inside that
+        kernel), the calls, and the detection list and its count written by
+        hog_detect straight into page-locked host memory."""
+        src = self.img_host if zero_copy else self.img
+        if not zero_copy:
+            self.img.copy_(self.img_host, non_blocking=True)
         if self.fused:
-            self.stage_cells_fused()
+            self.stage_cells_fused(img=src)
         else:
-            self.stage_bin_map()
+            self.stage_bin_map(img=src)
             self.stage_integral()
             self.stage_cell_hist()
         self.stage_score()
@@ -158,18 +165,19 @@ class HogPipeline:
 
     host_graph = None
 
-    def capture_host(self) -> None:
-        """Record _enqueue_host as one CUDA graph (copy node + kernels); after
-        it, detect_host is one replay and one synchronisation."""
+    def capture_host(self, zero_copy: bool = False) -> None:
+        """Record _enqueue_host as one CUDA graph (copy node + kernels, or the
+        kernels alone with zero_copy); after it, detect_host is one replay
+        and one synchronisation."""
         with torch.cuda.device(self.device):
             s = torch.cuda.Stream(self.device)
             s.wait_stream(torch.cuda.current_stream(self.device))
             with torch.cuda.stream(s):
-                self._enqueue_host()  # first launches load the kernels outside the capture
+                self._enqueue_host(zero_copy)  # first launches load the kernels outside the capture
             s.synchronize()
             g = torch.cuda.CUDAGraph()
             with torch.cuda.graph(g):
-                self._enqueue_host()
+                self._enqueue_host(zero_copy)
             self.host_graph = g
 
     def detect_host(self, img_host: torch.Tensor | None = None, stream=None):
@@ -177,18 +185,25 @@ class HogPipeline:
         path runs, and the GPU writes the count and the detections straight
         into pinned host memory; one synchronisation.  Returns the
         detections as a numpy record array and the count."""
-        s = torch.cuda.current_stream(self.device) if stream is None else stream
         if img_host is not None:
             self.img_host.copy_(img_host.reshape(-1))
-        with torch.cuda.stream(s):
+        if stream is None:
+            s = torch.cuda.current_stream(self.device)
             if self.host_graph is not None:
                 self.host_graph.replay()
             else:
                 self._enqueue_host()
+        else:
+            s = stream
+            with torch.cuda.stream(s):
+                if self.host_graph is not None:
+                    self.host_graph.replay()
+                else:
+                    self._enqueue_host()
         s.synchronize()
-        n_all = int(self.count_host[0])
+        n_all = int(self._count_np[0])
         n = min(n_all, self.max_out)
-        return dets_to_numpy(self.det_host, n), n_all
+        return dets_to_numpy(self._det_np, n), n_all
 
     def h2d_bytes(self) -> int:
         return self.img.numel()

@@ -459,15 +459,18 @@ def test_pipeline_end_to_end_host(fh, g):
     S_gpu = pipe.scores[: pipe.nx * pipe.ny].cpu().numpy().reshape(pipe.ny, pipe.nx)
     tol = g.score_tolerance(ref["cells"], c["w"], 0.0, stride=4)
     g.check_detections(det, n, S_gpu, ref["scores"], tol, c["thr"], 4)
-    # the same from one captured graph, on a second image and then the first again
-    pipe.capture_host()
+    # the same from one captured graph, on a second image and then the first again; with the
+    # image copied in, and with the bin map reading the page-locked image in place (zero copy)
     img2 = wl.rgb_smooth_shapes(800, 600, wl.rng_for(1, 99))
-    for im in (img2, img):
-        det, n = pipe.detect_host(torch.from_numpy(im.reshape(-1)))
-        ref = oracle.pipeline(im, 8, c["w"], 0.0, 4)
-        S_gpu = pipe.scores[: pipe.nx * pipe.ny].cpu().numpy().reshape(pipe.ny, pipe.nx)
-        g.check_detections(det, n, S_gpu, ref["scores"], g.score_tolerance(ref["cells"], c["w"], 0.0, stride=4),
-                           c["thr"], 4)
+    for zero_copy in (False, True):
+        pipe.capture_host(zero_copy)
+        for im in (img2, img):
+            det, n = pipe.detect_host(torch.from_numpy(im.reshape(-1)))
+            ref = oracle.pipeline(im, 8, c["w"], 0.0, 4)
+            assert np.array_equal(pipe.bins.cpu().numpy().reshape(600, 800), ref["bins"])
+            S_gpu = pipe.scores[: pipe.nx * pipe.ny].cpu().numpy().reshape(pipe.ny, pipe.nx)
+            g.check_detections(det, n, S_gpu, ref["scores"],
+                               g.score_tolerance(ref["cells"], c["w"], 0.0, stride=4), c["thr"], 4)
 
 
 # ---------------------------------------------------------------- tensor-core scores
