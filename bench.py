@@ -50,11 +50,14 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip every extra figure (the main line is unchanged)")
     ap.add_argument("--extras",
-                    default="fused,stages_4k,batch_1080p,batch_pyramid,multi_filter,blocks,soft,serving",
+                    default="ii_other,fused,stages_4k,batch_1080p,batch_pyramid,multi_filter,blocks,soft,serving",
                     help="comma-separated extra figures to run (default: all)")
     ap.add_argument("--image", default="800x600", help="WxH of the RGB image (same recipe as 800x600)")
     ap.add_argument("--serve-requests", type=int, default=10000, help="requests in the served stream (0: skip)")
     ap.add_argument("--no-tune", action="store_true", help="keep the library's default launch shapes")
+    ap.add_argument("--ii", choices=["i32", "u16"], default="i32",
+                    help="integral images of the main step: int32, or uint16 modulo 2^16 (exact box sums for "
+                         "boxes below 65536 pixels; every result of the path is the same)")
     return ap.parse_args()
 
 
@@ -277,17 +280,18 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def algorithmic_bytes(W, H, nb, ncx, ncy, windows, cell_bytes=2):
-    """Bytes each stage must move (RGB image, int32 integral images, cells of
-    `cell_bytes` per count, f32 scores): the figures the rooflines divide by."""
+def algorithmic_bytes(W, H, nb, ncx, ncy, windows, cell_bytes=2, ii_bytes=4):
+    """Bytes each stage must move (RGB image, integral images of `ii_bytes`
+    per entry, cells of `cell_bytes` per count, f32 scores): the figures the
+    rooflines divide by."""
     px = W * H
     return {
         "bin_map": px * (3 + 1),              # RGB in, bins out
-        "integral": px * (1 + 4 * nb),        # bins in, int32 planes out
+        "integral": px * (1 + ii_bytes * nb),  # bins in, planes out
         # Eq. 6 per cell position and bin: one integral-image sample in (each
         # sample of the stride grid is a corner of up to four cells, read once)
         # and one count out
-        "cell_hist": ncx * ncy * nb * (4 + cell_bytes),
+        "cell_hist": ncx * ncy * nb * (ii_bytes + cell_bytes),
         "score": ncx * ncy * nb * cell_bytes + windows * 4,  # cell map in, score out
         "detect": windows * 4,
     }
@@ -757,7 +761,9 @@ def main():
     img = c["images"][0]
     H, W = img.shape[:2]
     # bf16 cells: counts <= 64 are exact in bf16, and the score's tensor-core kernel reads them as they lie
-    pipe = fh.HogPipeline(W, H, 3, c["n_bins"], c["stride"], cell_dtype=fh.HOG_BF16)
+    ii_u16 = args.ii == "u16"
+    pipe = fh.HogPipeline(W, H, 3, c["n_bins"], c["stride"], cell_dtype=fh.HOG_BF16,
+                          ii_dtype=fh.HOG_U16 if ii_u16 else fh.HOG_I32)
     pipe.set_weights(c["w"], c["bias"], c["thr"])
     pipe.set_image(img)
     pipe.img_host.copy_(torch.from_numpy(img.reshape(-1)))
@@ -815,6 +821,25 @@ def main():
     value = replicas.aggregate_rate(px, ms_per_step * 1e-3, world) / 1e6
     windows = pipe.nx * pipe.ny
 
+    # the same five calls with the other integral-image type (uint16 modulo 2^16 beside int32, or the
+    # reverse): every result of the path is the same, the planes take half (or twice) the bytes
+    other_ii = None
+    if "ii_other" in extras:
+        op = fh.HogPipeline(W, H, 3, c["n_bins"], c["stride"], cell_dtype=fh.HOG_BF16,
+                            ii_dtype=fh.HOG_I32 if ii_u16 else fh.HOG_U16)
+        op.set_weights(c["w"], c["bias"], c["thr"])
+        op.set_image(img)
+        for _ in range(3):
+            op.run_eager()
+        ostep, oread, _ = graph_step(torch, [op.stage_bin_map, op.stage_integral, op.stage_cell_hist,
+                                             op.stage_score, op.stage_detect], between=False)
+        oms = time_steps(torch, ostep, oread, flush, args.steps, args.warmup)
+        other_ii = {"integral_images": "int32" if ii_u16 else "uint16 modulo 2^16",
+                    "value": round(replicas.aggregate_rate(W * H, replicas.max_over_ranks(oms, "cuda") * 1e-3,
+                                                           world) / 1e6, 2),
+                    "unit": "Mpixel/s", "ms_per_step": round(oms, 5), "launch_shapes": "library defaults"}
+        del op
+
     # the same step with the fused image-to-cells kernel (no bin map or integral planes in HBM)
     fused = None
     if "fused" in extras:
@@ -865,7 +890,7 @@ def main():
     stage_avg = {k: v / args.steps for k, v in stage_ms.items()}
     dom = max(stage_avg, key=stage_avg.get)
     nb = c["n_bins"]
-    alg_bytes = algorithmic_bytes(W, H, nb, pipe.ncx, pipe.ncy, windows)
+    alg_bytes = algorithmic_bytes(W, H, nb, pipe.ncx, pipe.ncy, windows, ii_bytes=2 if ii_u16 else 4)
     hbm, src = peaks()
     achieved = alg_bytes[dom] / (stage_avg[dom] * 1e-3) / 1e9
     # bin map 1; integral 1 (single pass) or 3 per window of bins, under the knobs the step was captured
@@ -882,15 +907,17 @@ def main():
     out = {
         "metric": METRIC, "value": round(value, 2), "unit": "Mpixel/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "int32+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "u16+f32" if ii_u16 else "int32+f32", "data": "synthetic",
         "config": {"workload": WORKLOAD.replace("800x600", f"{W}x{H}"), "image": f"{W}x{H}x3", "windows_per_image": windows,
+                   "integral_images": "uint16 modulo 2^16" if ii_u16 else "int32",
                    "l2": "flushed between steps (256 MB write, outside the timed events)",
                    "lut": "built once before timing", "timing": timing_mode,
                    "launch_shapes": "autotuned" if tuned else "library defaults", "tuned": tuned},
         "windows_per_s": round(world * windows / (ms_per_step * 1e-3), 1),
         "stages_ms": {k: round(v, 5) for k, v in stage_avg.items()},
         "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
-                     "frac": round(achieved / hbm, 4), "traffic": profiled_traffic(dom, f"{W}x{H}"),
+                     "frac": round(achieved / hbm, 4),
+                     "traffic": profiled_traffic(dom, f"{W}x{H}" + ("-u16" if ii_u16 else "")),
                      "peak_source": src, "algorithmic_bytes_per_launch": alg_bytes[dom],
                      "traffic_source": "profiles/traffic.txt (ncu, summed over the stage's kernels)"},
         "e2e": {"value": round(replicas.aggregate_rate(px, served_s, world) / 1e6, 2), "unit": "Mpixel/s",
@@ -912,6 +939,7 @@ def main():
         "clocks": clocks,
         "device_status": status,
         "fused": fused,
+        "ii_other": other_ii,
         "stages_4k": stage_rooflines(torch, fh, wl, flush, args, hbm) if "stages_4k" in extras else None,
         "batch_1080p": batch_1080p(torch, fh, wl, replicas, flush, args, world) if "batch_1080p" in extras else None,
         "precision": measured_precision(),
