@@ -80,6 +80,20 @@ __device__ __forceinline__ uint32_t out_bits(uint32_t v) {
     }
 }
 
+// 1 << n, or 0 when n >= 32 as an unsigned number (PTX clamps the shift amount).
+__device__ __forceinline__ uint32_t one_or_zero_shl(uint32_t n) {
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(n));
+    return r;
+}
+
+// The 4 nibbles of the 16-bit half h of x, one per byte.
+__device__ __forceinline__ uint32_t nibbles_to_bytes(uint32_t x, int h) {
+    uint32_t a = (x >> (16 * h)) & 0xFFFFu;
+    a = (a | (a << 8)) & 0x00FF00FFu;
+    return (a | (a << 4)) & 0x0F0F0F0Fu;
+}
+
 // Stage the shared-memory quadrant of the table (one bulk copy, bounded wait).
 __device__ __forceinline__ bool stage_lut(uint8_t* lutq, const uint8_t* __restrict__ lut, uint64_t* bar,
                                           unsigned int* status) {
@@ -120,27 +134,41 @@ __device__ __forceinline__ void fused_tile(FusedSmem<NB, S>& sm, const uint8_t* 
     __syncthreads();
     // 1. block histograms: one quad (4 pixels of one row) per task; the
     //    8-bit fields of a block's words collect at most s^2 <= 64 pixels.
+    //    A thread's task position (pixel row, quad) steps by kThreads tasks
+    //    without a division.
+    const int step_rows = kThreads / row_tasks, step_cols = kThreads - step_rows * row_tasks;
+    int prow = tid / row_tasks, qc = tid - prow * row_tasks;
     for (int task = tid; task < n_tasks; task += kThreads) {
-        const int prow = task / row_tasks, qc = task - prow * row_tasks;
         const int y = by0 * S + prow, x = bx0 * S + 4 * qc;
-        if (y <= 0 || y >= H - 1 || x >= W) continue;  // border rows, or outside the image: no bins
-        QuadWords<CH> q;
-        load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
-        const uint32_t packed = bins_of_quad<CH, QUAD>(q, x, W, lutq, lut, NB, NB / 4);
-        uint32_t h[F::NW8];
+        if (y > 0 && y < H - 1 && x < W) {  // else a border row, or outside the image: no bins
+            QuadWords<CH> q;
+            load_quad<CH>(img, pitch, row_bytes, aligned, x, y, q);
+            const uint32_t packed = bins_of_quad<CH, QUAD>(q, x, W, lutq, lut, NB, NB / 4);
+            // the quad's one-hot votes in 4-bit fields, bins 8k .. 8k + 7 in word k (at most 4 per
+            // field; 0xFF shifts out), then spread to the 8-bit fields of the block histogram
+            uint32_t h4[NB / 8];
 #pragma unroll
-        for (int k = 0; k < F::NW8; ++k) h[k] = 0;
+            for (int k = 0; k < NB / 8; ++k) h4[k] = 0;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) {
-            const uint32_t v = (packed >> (8 * p)) & 0xFFu;
-            const uint32_t inc = 1u << ((v & 3) << 3);
+            for (int p = 0; p < 4; ++p) {
+                const uint32_t v = __byte_perm(packed, 0u, 0x4440u | (uint32_t)p);
 #pragma unroll
-            for (int k = 0; k < F::NW8; ++k) h[k] += ((v >> 2) == (uint32_t)k) ? inc : 0u;  // 0xFF: none
+                for (int k = 0; k < NB / 8; ++k) h4[k] += one_or_zero_shl(4u * (v - 8u * (uint32_t)k));
+            }
+            uint32_t* dst = sm.bh[prow / S][qc / QPR];
+#pragma unroll
+            for (int k = 0; k < NB / 8; ++k) {
+                const uint32_t lo = nibbles_to_bytes(h4[k], 0), hi = nibbles_to_bytes(h4[k], 1);
+                if (lo) atomicAdd(dst + 2 * k, lo);
+                if (hi) atomicAdd(dst + 2 * k + 1, hi);
+            }
         }
-        uint32_t* dst = sm.bh[prow / S][qc / QPR];
-#pragma unroll
-        for (int k = 0; k < F::NW8; ++k)
-            if (h[k]) atomicAdd(dst + k, h[k]);
+        prow += step_rows;
+        qc += step_cols;
+        if (qc >= row_tasks) {
+            qc -= row_tasks;
+            ++prow;
+        }
     }
     __syncthreads();
     // 2. G: exclusive 2-D prefix of the block histograms in 16-bit fields
@@ -171,11 +199,16 @@ __device__ __forceinline__ void fused_tile(FusedSmem<NB, S>& sm, const uint8_t* 
     __syncthreads();
     for (int task = tid; task < (bxn + 1) * F::NW16; task += kThreads) {
         const int I = task / F::NW16, e = task % F::NW16;
+        uint32_t v[F::BYB];  // the column's values, all loads in flight before the running sum
+#pragma unroll
+        for (int J = 0; J < F::BYB; ++J) v[J] = J < byn ? sm.g[J + 1][I][e] : 0u;
         uint32_t run = 0;
-        for (int J = 1; J <= byn; ++J) {
-            run += sm.g[J][I][e];
-            sm.g[J][I][e] = run;
-        }
+#pragma unroll
+        for (int J = 0; J < F::BYB; ++J)
+            if (J < byn) {
+                run += v[J];
+                sm.g[J + 1][I][e] = run;
+            }
     }
     __syncthreads();
     // 3. cells: Eq. 6 on the corner-sampled integral image
