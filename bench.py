@@ -430,6 +430,10 @@ def serving(torch, wl, args):
         return res, time.perf_counter() - t0, replay
 
     burst = [Request(i, pool[i % len(pool)], 0.0) for i in range(min(1000, n_req))]
+    # clocks over the whole comparison; the sampler (an nvidia-smi process) starts before the warm-up,
+    # so that its start-up falls outside the measured streams
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
     for srv in (served, plain):  # warm-up: every kernel loaded, allocator pools filled
         run(srv, burst[: len(pool)])
     torch.cuda.synchronize()
@@ -447,13 +451,10 @@ def serving(torch, wl, args):
            "mean_mpixel_per_request": round(sum(int(t.numel()) for t in pool) / 3 / len(pool) / 1e6, 3),
            "capacity_images_per_s": {"plain": round(cap_plain, 1), "served": round(cap_served, 1)}}
     for label, srv, streams in (("served", served, 16), ("plain", plain, 1)):
-        sampler = ClockSampler(torch.cuda.current_device())
-        sampler.start()
         res, wall, replay = run(srv, reqs)
-        clocks = sampler.stop()
         pauses = replay.pop("pauses_ns")
-        out[label] = dict(latency_summary(res, wall, pauses), streams=streams, fused=srv.fused, clocks=clocks,
-                          **replay)
+        out[label] = dict(latency_summary(res, wall, pauses), streams=streams, fused=srv.fused, **replay)
+    out["clocks"] = sampler.stop()
     del served, plain, pool
     torch.cuda.empty_cache()
     return out

@@ -12,11 +12,13 @@
  * its result does not depend on what else is running.
  *
  * Memory.  hog_server_create allocates everything the server will use: one
- * device arena of `budget_bytes` (requests' image, cell map, scores and
- * detection workspace, plus bin map and integral images when the path is
- * not fused), the gradient table and the weights (resident for the server's
- * life), and per slot a stream, an event and a page-locked host buffer that
- * the GPU writes the detection list and its count into directly.  Submit and
+ * device arena of `budget_bytes` (requests' image, cell map and scores, plus
+ * bin map, integral images and their workspace when the path is not fused),
+ * the gradient table and the weights (resident for the server's life), and
+ * per slot a stream, an event, a detection workspace sized for the largest
+ * request (zero-filled once; every request leaves it ready for the next) and
+ * a page-locked host buffer that the GPU writes the detection list and its
+ * count into directly.  Submit and
  * poll allocate nothing: a request's buffers are carved out of the arena
  * (first fit, 256-byte aligned) and returned to it when the request
  * completes.

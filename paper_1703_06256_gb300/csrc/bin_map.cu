@@ -149,7 +149,7 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_
     const size_t smem = QUAD ? kQuadBytes : 0;
     auto kern = bin_map_kernel<CH, QUAD>;
     if (QUAD) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = smem_at_least<bin_map_kernel<CH, QUAD>>(smem);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     const long n_quads = (long)((W + 3) / 4) * H;

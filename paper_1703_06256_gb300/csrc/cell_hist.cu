@@ -264,7 +264,7 @@ hog_status launch_stream(const void* ii, int W, int H, int stride, int r, int nc
     if ((TJ + r) * NB <= (kStreamThreads / 32) * kPipeLines) {
         const size_t smem = 2 * sizeof(uint32_t) * (size_t)(TJ + r) * (kTI + r) * (NB + 1);
         auto kern = cell_hist_pipe_kernel<InT, OutT, NB>;
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = smem_at_least<cell_hist_pipe_kernel<InT, OutT, NB>>(smem);
         if (e != cudaSuccess) return cuda_fail(e);
         const int n_tx = ceil_div(ncx, kTI);
         const int n_tiles = n_tx * ceil_div(ncy, TJ);
@@ -274,7 +274,7 @@ hog_status launch_stream(const void* ii, int W, int H, int stride, int r, int nc
     }
     const size_t smem = sizeof(uint32_t) * (size_t)(TJ + r) * (kTI + r) * (NB + 1);
     auto kern = cell_hist_stream_kernel<InT, OutT, NB>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<cell_hist_stream_kernel<InT, OutT, NB>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     dim3 grid(ceil_div(ncx, kTI), ceil_div(ncy, TJ));
     return launch_pdl(kern, grid, dim3(kStreamThreads), smem, st, static_cast<const InT*>(ii), W, H, stride, r, ncx,

@@ -321,7 +321,7 @@ hog_status launch_q(const uint8_t* img, int W, int H, size_t pitch, const uint8_
                     void* cells, unsigned int* status, cudaStream_t st) {
     const size_t smem = (QUAD ? kQuadBytes : 0) + sizeof(FusedSmem<NB, S>);
     auto kern = cells_fused_kernel<CH, NB, S, OutT, QUAD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<cells_fused_kernel<CH, NB, S, OutT, QUAD>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
     const int tiles = ((ncx + BX - 1) / BX) * ((ncy + BY - 1) / BY);
@@ -398,7 +398,7 @@ hog_status launch_batch_q(const PlanHeader& h, const void* plan_dev, const uint8
                           cudaStream_t st) {
     const size_t smem = (QUAD ? kQuadBytes : 0) + sizeof(FusedSmem<NB, S>);
     auto kern = cells_fused_batch_kernel<CH, NB, S, OutT, QUAD>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<cells_fused_batch_kernel<CH, NB, S, OutT, QUAD>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     const int per_sm = tune_get(HOG_TUNE_FUSED_CTAS_PER_SM);
     const int cap = (per_sm > 0 ? per_sm : 2) * sm_count();

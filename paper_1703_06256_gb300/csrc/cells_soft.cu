@@ -164,7 +164,7 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint16
     using T = SoftTile<S>;
     const size_t smem = sizeof(uint32_t) * ((size_t)T::BYB * T::BXB + (size_t)(T::BYB + 1) * (T::BXB + 1)) * kMaxNb;
     auto kern = cells_soft_kernel<CH, S, OutT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<cells_soft_kernel<CH, S, OutT>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     const int tiles = ((ncx + T::BX - 1) / T::BX) * ((ncy + T::BY - 1) / T::BY);
     const int cap = 2 * sm_count();

@@ -1516,10 +1516,17 @@ cudaLaunchConfig_t cl_config(const ClPlan& c, cudaStream_t st, cudaLaunchAttribu
 
 template <int WIN, int HW, typename OutT>
 cudaError_t cl_attributes(const ClPlan& c) {
-    auto kern = ii_cluster_kernel<WIN, HW, OutT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-    return e;
+    // clusters of up to 16 CTAs: allowed once per kernel and device, before its first launch
+    static std::atomic<int> nonportable[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64 || nonportable[dev].load(std::memory_order_acquire) == 0) {
+        e = cudaFuncSetAttribute(ii_cluster_kernel<WIN, HW, OutT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        if (dev >= 0 && dev < 64) nonportable[dev].store(1, std::memory_order_release);
+    }
+    return smem_at_least<ii_cluster_kernel<WIN, HW, OutT>>(c.smem);
 }
 
 // How many clusters of this shape can be resident on the current device at
@@ -1619,6 +1626,13 @@ bool onepass_default(int W, int H) { return (long)W * H <= 250000L; }
 }  // namespace
 
 size_t integral_sync_bytes(int W, int H) { return sync_bytes(W, H); }
+
+bool integral_uses_sync(int W, int H, int n_bins, int ii_dtype) {
+    ClPlan c{};
+    if (use_cluster(W, H, n_bins, ii_dtype, &c)) return false;
+    const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);
+    return path == 2 || (path == 0 && onepass_default(W, H));
+}
 
 int integral_launches(int W, int H, int n_bins) {
     const int path = tune_get(HOG_TUNE_INTEGRAL_PATH);

@@ -2,6 +2,9 @@
 // Not installed; the public interface is include/fasthog.h.
 #pragma once
 
+#include <atomic>
+#include <mutex>
+
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -47,6 +50,10 @@ hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t
 size_t integral_workspace_bytes(int W, int H, int n_bins);
 // Leading bytes of an integral workspace that must be zero-filled before its first use.
 size_t integral_sync_bytes(int W, int H);
+// Whether hog_integral of this size, under the current knobs, takes the single
+// pass, the one schedule that reads the workspace's tag and flags (the others
+// never touch that region).
+bool integral_uses_sync(int W, int H, int n_bins, int ii_dtype);
 // Kernel launches hog_integral makes for this size under the current knobs.
 int integral_launches(int W, int H, int n_bins);
 hog_status launch_integral(const uint8_t* bins, int W, int H, int n_bins, int ii_dtype, void* ii,
@@ -122,6 +129,29 @@ hog_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sm
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
     return e == cudaSuccess ? HOG_OK : cuda_fail(e);
 }
+// Raise kernel Kern's dynamic shared-memory limit on the current device to at
+// least `bytes`.  The driver is called only when a launch needs more than the
+// limit already set there (once per kernel and device in practice), so the
+// attribute costs no host time on every launch.  Kern is the kernel itself,
+// so every kernel keeps its own record.
+template <auto Kern>
+cudaError_t smem_at_least(size_t bytes) {
+    constexpr int kDevices = 64;
+    static std::atomic<int> have[kDevices];
+    static std::mutex mu;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int want = (int)bytes;
+    if (dev < 0 || dev >= kDevices) return cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (have[dev].load(std::memory_order_acquire) >= want) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(mu);
+    if (have[dev].load(std::memory_order_relaxed) >= want) return cudaSuccess;
+    e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, want);
+    if (e == cudaSuccess) have[dev].store(want, std::memory_order_release);
+    return e;
+}
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 

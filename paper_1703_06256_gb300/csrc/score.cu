@@ -154,7 +154,7 @@ template <typename CellT, typename WT, typename OutT, bool SMEM, int TY>
 hog_status launch_ty(const void* cells, int ncx, int ncy, int nb, int cells_x, int cells_y, int r, const void* w,
                      float bias, void* scores, int nx, int ny, size_t smem, cudaStream_t st) {
     auto k = score_kernel<CellT, WT, OutT, SMEM, TY>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<score_kernel<CellT, WT, OutT, SMEM, TY>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     dim3 grid(ceil_div(nx, kTX), ceil_div(ny, TY)), block(kTX, TY);
     return launch_pdl(k, grid, block, smem, st, static_cast<const CellT*>(cells), ncx, ncy, nb, cells_x, cells_y, r,

@@ -565,7 +565,7 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, const WT* w, int nf
     const size_t smem = RowsGeom(R, weight_parts<WT>(), nf).smem_bytes();
     if (smem > kMaxSmem) return HOG_ERR_UNSUPPORTED;
     auto kern = score_rows_kernel<R, WT, OutT, false, false>;
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = smem_at_least<score_rows_kernel<R, WT, OutT, false, false>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     const int rpc = rows_per_cta(nx, ny);
     const dim3 grid((nx + kM - 1) / kM, (ny + rpc - 1) / rpc);
@@ -589,7 +589,7 @@ hog_status launch_split_t(const uint16_t* cells, int ncx, int ncy, const WT* w, 
     static_assert(kSplit * kSplitRows * kM * 4 + 8 * 16 * 16 + kStages * 4 * (kM + 28) * 16 + 2048 < 113 * 1024,
                   "two split CTAs fit one SM");
     auto kern = score_rows_kernel<R, WT, OutT, false, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<score_rows_kernel<R, WT, OutT, false, true>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     RowsBias rb{};
     rb.b[0] = bias;
@@ -658,7 +658,7 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void*
     if (s != HOG_OK) return s;
     const size_t smem = RowsGeom(R, weight_parts<WT>(), 1).smem_bytes();
     auto kern = score_rows_kernel<R, WT, OutT, true, false>;
-    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = smem_at_least<score_rows_kernel<R, WT, OutT, true, false>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     RowsBias rb{};
     rb.b[0] = bias;

@@ -186,7 +186,7 @@ hog_status launch_t(const void* cells, int ncx, int ncy, int r, const void* w, f
     const int n_items = ((ny + G.rb - 1) / G.rb) * S;
     const size_t smem = G.smem_bytes();
     auto kern = score_slide_kernel<CellT, WT, OutT>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<score_slide_kernel<CellT, WT, OutT>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     const int per_sm = smem <= 70 * 1024 ? 3 : (smem <= 110 * 1024 ? 2 : 1);
     const int cap = per_sm * sm_count();

@@ -373,7 +373,7 @@ hog_status launch_t(const uint16_t* cells, int ncx, int ncy, int r, const void* 
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
     auto kern = score_tc_kernel<NB, WT, OutT, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<score_tc_kernel<NB, WT, OutT, false>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     dim3 grid((nx + wpc - 1) / wpc, (ny + Tc * r - 1) / (Tc * r), r);
     return launch_pdl(kern, grid, dim3(kThreads), smem, st, cells, ncx, ncy, r, Tc, static_cast<const WT*>(w), bias,
@@ -390,7 +390,7 @@ hog_status launch_batch_t(const PlanHeader& h, const void* plan_dev, const void*
     if (G.cols > 512) return HOG_ERR_UNSUPPORTED;
     const size_t smem = G.smem_bytes();
     auto kern = score_tc_kernel<NB, WT, OutT, true>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = smem_at_least<score_tc_kernel<NB, WT, OutT, true>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
     return launch_pdl(kern, dim3(h.score_ctas), dim3(kThreads), smem, st, static_cast<const uint16_t*>(nullptr), 0,
                       0, h.r, h.score_tc, static_cast<const WT*>(w), bias, 1, FilterBias{}, 0, 0,
@@ -423,7 +423,7 @@ hog_status launch_multi_t(const uint16_t* cells, int ncx, int ncy, int r, const 
     if (!fits(Tc, group)) return HOG_ERR_UNSUPPORTED;
     auto kern = score_tc_kernel<NB, WT, OutT, false>;
     const size_t smem_max = TcGeom(r, Tc, NB / 8, group, weight_parts<WT>()).smem_bytes();
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+    cudaError_t e = smem_at_least<score_tc_kernel<NB, WT, OutT, false>>(smem_max);
     if (e != cudaSuccess) return cuda_fail(e);
     const dim3 grid((nx + wpc - 1) / wpc, (ny + Tc * r - 1) / (Tc * r), r);
     const size_t per_filter = (size_t)kCX * kCY * NB;

@@ -101,7 +101,7 @@ class DeviceGuard {
 // Byte offsets of one request's buffers inside its arena block.
 struct Layout {
     int ncx, ncy, nx, ny;
-    size_t img, cells, scores, ws_det, ws_det_bytes, bins, ii, ws_ii, ws_ii_bytes, total;
+    size_t img, cells, scores, bins, ii, ws_ii, ws_ii_bytes, total;
 };
 
 enum class SlotState { kFree, kBusy, kHeld };
@@ -128,6 +128,7 @@ struct Slot {
     cudaEvent_t done = nullptr;
     hog_det* dets_host = nullptr;  // page-locked, mapped
     hog_det* dets_dev = nullptr;   // the same memory, as the device addresses it
+    void* ws_det = nullptr;        // the slot's detection workspace (largest request), zero-filled once
     SlotState state = SlotState::kFree;
     size_t off = 0, bytes = 0;
     int32_t rid = 0;
@@ -142,6 +143,7 @@ struct hog_server {
     int cell_dtype = HOG_F32, score_dtype = HOG_F32;
     bool fused = false;
     size_t max_windows = 0;
+    size_t ws_det_bytes = 0;  // each slot's detection workspace
     uint8_t* arena_base = nullptr;
     uint8_t* lut = nullptr;
     void* w = nullptr;
@@ -183,9 +185,6 @@ struct hog_server {
         o += align_up((size_t)L.ncx * L.ncy * c.n_bins * cell_bytes + 1);
         L.scores = o;
         o += align_up(windows * 4 + 1);
-        L.ws_det = o;
-        L.ws_det_bytes = hog_detect_workspace_bytes(L.nx, L.ny);
-        o += align_up(L.ws_det_bytes);
         L.bins = L.ii = L.ws_ii = L.ws_ii_bytes = 0;
         if (!fused) {
             L.bins = o;
@@ -207,13 +206,12 @@ struct hog_server {
         uint8_t* base = arena_base + sl.off;
         hog_stream_t st = reinterpret_cast<hog_stream_t>(sl.stream);
         const int windows = L.nx * L.ny;
-        {
-            // The request's workspaces come from reused arena memory: zero-fill them first, as the
-            // single-pass kernels need before a workspace's first use (ahead of the kernels, so the
-            // kernels still follow one another directly).
-            cudaError_t e = cudaMemsetAsync(base + L.ws_det, 0, L.ws_det_bytes, sl.stream);
-            if (e == cudaSuccess && !fused)
-                e = cudaMemsetAsync(base + L.ws_ii, 0, fasthog::integral_sync_bytes(W, H), sl.stream);
+        if (!fused && fasthog::integral_uses_sync(W, H, c.n_bins, c.ii_dtype)) {
+            // The single pass reads a tag and flags from its workspace, which here is reused arena
+            // memory: zero-fill that region first (ahead of the kernels, so the kernels still follow
+            // one another directly).  The slot's detection workspace was zero-filled once, and every
+            // call leaves it ready for the next, whatever the size.
+            const cudaError_t e = cudaMemsetAsync(base + L.ws_ii, 0, fasthog::integral_sync_bytes(W, H), sl.stream);
             if (e != cudaSuccess) return cuda_fail(e);
         }
         if (windows > 0) {
@@ -241,7 +239,7 @@ struct hog_server {
         }
         // With no window position the list call still runs: it writes the count 0.
         return hog_detect(base + L.scores, score_dtype, L.nx, L.ny, c.stride, c.thr, sl.rid, 0, sl.dets_dev,
-                          windows, count_dev, base + L.ws_det, L.ws_det_bytes, st);
+                          windows, count_dev, sl.ws_det, ws_det_bytes, st);
     }
 
     // Admit one request if a slot is free and its buffers fit (*admitted).
@@ -402,6 +400,7 @@ struct hog_server {
             if (sl.done) cudaEventDestroy(sl.done);
             if (sl.stream) cudaStreamDestroy(sl.stream);
             if (sl.dets_host) cudaFreeHost(sl.dets_host);
+            if (sl.ws_det) cudaFree(sl.ws_det);
         }
         slots.clear();
         if (counts_host) cudaFreeHost(counts_host);
@@ -453,6 +452,7 @@ hog_status hog_server_create(const hog_server_config* cfg, const void* w, hog_se
     const long mx = n_pos(c.max_W, c.cell, c.stride) - (long)(c.cells_x - 1) * r;
     const long my = n_pos(c.max_H, c.cell, c.stride) - (long)(c.cells_y - 1) * r;
     s->max_windows = (size_t)(mx > 0 ? mx : 0) * (size_t)(my > 0 ? my : 0);
+    s->ws_det_bytes = hog_detect_workspace_bytes(mx > 0 ? (int)mx : 0, my > 0 ? (int)my : 0);
 
     cudaError_t e = cudaGetDevice(&s->device);
     const size_t w_elems = (size_t)c.cells_x * c.cells_y * c.n_bins;
@@ -473,6 +473,8 @@ hog_status hog_server_create(const hog_server_config* cfg, const void* w, hog_se
         const size_t det_bytes = (s->max_windows > 0 ? s->max_windows : 1) * sizeof(hog_det);
         if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&sl.dets_host), det_bytes, cudaHostAllocMapped);
         if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&sl.dets_dev), sl.dets_host, 0);
+        if (e == cudaSuccess) e = cudaMalloc(&sl.ws_det, s->ws_det_bytes);
+        if (e == cudaSuccess) e = cudaMemset(sl.ws_det, 0, s->ws_det_bytes);  // zero once: the tags' start
     }
     if (e != cudaSuccess) {
         st = cuda_fail(e);
