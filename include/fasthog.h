@@ -417,8 +417,7 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 taller or wider ones take three launches).
  *                                 The library's choice: 3 for images up to 640
  *                                 rows with at most 8 bins whose clusters all
- *                                 fit the GPU at once, else 2 up to 250,000
- *                                 pixels, else 1
+ *                                 fit the GPU at once, else 1
  *   HOG_TUNE_INTEGRAL_WARP_ROWS   rows per warp of the cluster schedule: 2, 4
  *                                 or 8 (2 and 4 cover up to 640 rows, 8 up to
  *                                 1280; the library's choice is 2 where every

@@ -1619,9 +1619,16 @@ bool use_cluster(int W, int H, int n_bins, int ii_dtype, ClPlan* c) {
 }
 
 // Whether the single pass is the library's choice where the cluster pass is
-// not: small images only (measured: up to about 640 x 360 it beats three
-// launches, from 640 x 480 up it is slower).
-bool onepass_default(int W, int H) { return (long)W * H <= 250000L; }
+// not: never.  Alone on the GPU it beats three launches only on small images
+// (about 1.4 us up to 640 x 360), which the cluster pass takes; with many
+// streams sharing the GPU its tiles wait on tiles that other kernels keep off
+// the SMs (a request server's throughput fell to a third in some runs), so
+// it runs only when the tuning knob asks for it.
+bool onepass_default(int W, int H) {
+    (void)W;
+    (void)H;
+    return false;
+}
 
 }  // namespace
 
