@@ -166,28 +166,33 @@ class HogServer:
         time.  Returns the results in completion order and the replay's own
         lateness (how far behind its arrival time a request was queued)."""
         queue = sorted(requests, key=lambda r: r.arrival)
+        # the images as the C ABI takes them (contiguous), kept alive until their results are in
+        imgs = []
+        for req in queue:
+            img = req.image
+            img = (img if img.is_contiguous() else img.contiguous()) if isinstance(img, torch.Tensor) \
+                else np.ascontiguousarray(img, dtype=np.uint8)
+            imgs.append(img)
+        arrivals = [req.arrival for req in queue]
         out = (HogServerTimedResult * _MAX_POLL)()
-        results: list[Result] = []
-        held: dict[int, tuple] = {}
+        raw = []  # per completed request: its stamps and, with keep, its detections
         late = []
+        n_total, n_done = len(queue), 0
         gc_was_on = gc.isenabled()
         gc.disable()
         hog_server_start(self._h)
         try:
             t0 = hog_server_clock_ns()
             i = 0
-            while i < len(queue) or held:
-                now = (hog_server_clock_ns() - t0) * 1e-9
-                while i < len(queue) and queue[i].arrival <= now:
-                    req = queue[i]
-                    img = req.image
-                    img = (img if img.is_contiguous() else img.contiguous()) if isinstance(img, torch.Tensor) \
-                        else np.ascontiguousarray(img, dtype=np.uint8)
-                    H, W = img.shape[:2]
-                    hog_server_enqueue(self._h, req.rid, img, W, H, 1 if img.ndim == 2 else 3)
-                    held[req.rid] = (req, img)  # the image must outlive the request
-                    late.append(now - req.arrival)
-                    i += 1
+            while n_done < n_total:
+                if i < n_total:
+                    now = (hog_server_clock_ns() - t0) * 1e-9
+                    while i < n_total and arrivals[i] <= now:
+                        img = imgs[i]
+                        H, W = img.shape[:2]
+                        hog_server_enqueue(self._h, queue[i].rid, img, W, H, 1 if img.ndim == 2 else 3)
+                        late.append(now - arrivals[i])
+                        i += 1
                 n = hog_server_collect(self._h, out, _MAX_POLL)
                 for k in range(n):
                     t = out[k]
@@ -196,16 +201,16 @@ class HogServer:
                         raise RuntimeError(f"request {r.rid} failed on the GPU (status {r.status})")
                     dets = None
                     if keep:
-                        raw = ctypes.string_at(r.dets, r.count * DET_BYTES) if r.count else b""
-                        dets = dets_to_numpy(raw, r.count)
-                    hog_server_release(self._h, r.token)
-                    held.pop(r.rid)
-                    results.append(Result(r.rid, dets, r.count, (t.t_done_ns - t.t_enqueue_ns) * 1e-9, (r.H, r.W),
-                                          t.t_enqueue_ns, t.t_done_ns, t.t_admit_ns))
+                        dets = ctypes.string_at(r.dets, r.count * DET_BYTES) if r.count else b""
+                    hog_server_release(self._h, r.token)  # the slot is free again before any other work
+                    raw.append((r.rid, dets, r.count, r.H, r.W, t.t_enqueue_ns, t.t_done_ns, t.t_admit_ns))
+                n_done += n
         finally:
             hog_server_stop(self._h)
             if gc_was_on:
                 gc.enable()
+        results = [Result(rid, dets_to_numpy(d, cnt) if keep else None, cnt, (td - te) * 1e-9, (h, w), te, td, ta)
+                   for rid, d, cnt, h, w, te, td, ta in raw]
         n_pauses, pauses = hog_server_pauses(self._h)
         lat = np.array(late) * 1e3 if late else np.zeros(1)
         return results, {"replay_late_p50_ms": round(float(np.percentile(lat, 50)), 3),
