@@ -60,6 +60,11 @@ typedef struct {
     int n_slots;         /* requests on the GPU at once (one stream each), 1..64 */
     size_t budget_bytes; /* device memory for the requests' buffers */
     int max_W, max_H;    /* largest image accepted; sizes each slot's host detection buffer */
+    int image_in_place;  /* 1: a request whose image is page-locked host memory mapped into the
+                            device's address space (cudaHostAlloc, cudaHostRegister, or PyTorch's
+                            pinned memory) is read in place by its first kernel, so its bytes
+                            cross to the GPU inside that kernel and no copy is enqueued; other
+                            images are copied in.  0: every image is copied in first. */
 } hog_server_config;
 
 typedef struct {

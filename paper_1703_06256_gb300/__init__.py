@@ -59,7 +59,7 @@ class HogServerConfig(ctypes.Structure):
                 ("cells_x", ctypes.c_int), ("cells_y", ctypes.c_int), ("w_dtype", ctypes.c_int),
                 ("bias", ctypes.c_float), ("thr", ctypes.c_float), ("fused", ctypes.c_int),
                 ("ii_dtype", ctypes.c_int), ("n_slots", ctypes.c_int), ("budget_bytes", ctypes.c_size_t),
-                ("max_W", ctypes.c_int), ("max_H", ctypes.c_int)]
+                ("max_W", ctypes.c_int), ("max_H", ctypes.c_int), ("image_in_place", ctypes.c_int)]
 
 
 class HogServerResult(ctypes.Structure):

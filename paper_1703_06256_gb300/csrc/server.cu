@@ -215,16 +215,27 @@ struct hog_server {
             if (e != cudaSuccess) return cuda_fail(e);
         }
         if (windows > 0) {
-            const cudaError_t e = cudaMemcpyAsync(base + L.img, img, (size_t)W * H * channels,
-                                                  cudaMemcpyHostToDevice, sl.stream);
-            if (e != cudaSuccess) return cuda_fail(e);
+            // the image the first kernel reads: in place where it is page-locked and mapped, else a copy
+            const uint8_t* src = nullptr;
+            if (c.image_in_place) {
+                cudaPointerAttributes a{};
+                if (cudaPointerGetAttributes(&a, img) == cudaSuccess && a.type == cudaMemoryTypeHost &&
+                    a.devicePointer != nullptr)
+                    src = static_cast<const uint8_t*>(a.devicePointer);
+                cudaGetLastError();  // an unknown pointer leaves no error behind
+            }
+            if (src == nullptr) {
+                const cudaError_t e = cudaMemcpyAsync(base + L.img, img, (size_t)W * H * channels,
+                                                      cudaMemcpyHostToDevice, sl.stream);
+                if (e != cudaSuccess) return cuda_fail(e);
+                src = base + L.img;
+            }
             hog_status s;
             if (fused) {
-                s = hog_cell_hist_fused(base + L.img, W, H, channels, (size_t)W * channels, lut, c.n_bins, c.cell,
+                s = hog_cell_hist_fused(src, W, H, channels, (size_t)W * channels, lut, c.n_bins, c.cell,
                                         c.stride, cell_dtype, base + L.cells, st);
             } else {
-                s = hog_bin_map(base + L.img, W, H, channels, (size_t)W * channels, lut, c.n_bins, base + L.bins,
-                                st);
+                s = hog_bin_map(src, W, H, channels, (size_t)W * channels, lut, c.n_bins, base + L.bins, st);
                 if (s == HOG_OK)
                     s = hog_integral(base + L.bins, W, H, c.n_bins, c.ii_dtype, base + L.ii, base + L.ws_ii,
                                      L.ws_ii_bytes, st);
@@ -422,6 +433,7 @@ hog_status check_config(const hog_server_config* c) {
     if (c->w_dtype != HOG_F32 && c->w_dtype != HOG_BF16 && c->w_dtype != HOG_I8) return HOG_ERR_ARG;
     if (!std::isfinite(c->bias) || std::isnan(c->thr)) return HOG_ERR_ARG;
     if (c->fused < -1 || c->fused > 1) return HOG_ERR_ARG;
+    if (c->image_in_place != 0 && c->image_in_place != 1) return HOG_ERR_ARG;
     if (c->ii_dtype != HOG_I32 && c->ii_dtype != HOG_U16) return HOG_ERR_ARG;
     if (c->n_slots < 1 || c->n_slots > kMaxSlots || c->budget_bytes == 0) return HOG_ERR_ARG;
     if (!size_ok(c->max_W, c->max_H)) return HOG_ERR_ARG;

@@ -65,12 +65,13 @@ class HogServer:
     def __init__(self, w, bias: float = 0.0, thr: float = 0.5, n_bins: int = 8, stride: int = 4, cell: int = 8,
                  cells_x: int = 8, cells_y: int = 16, w_dtype: int = HOG_BF16, budget_bytes: int = 8 << 30,
                  n_streams: int = 16, fused: bool | None = None, ii_dtype: int = HOG_I32,
-                 max_wh: tuple = (3840, 2160), device=None):
+                 max_wh: tuple = (3840, 2160), image_in_place: bool = False, device=None):
         self.device = torch.device("cuda") if device is None else torch.device(device)
         cfg = HogServerConfig(n_bins=n_bins, cell=cell, stride=stride, cells_x=cells_x, cells_y=cells_y,
                               w_dtype=w_dtype, bias=float(bias), thr=float(thr),
                               fused=-1 if fused is None else int(bool(fused)), ii_dtype=ii_dtype,
-                              n_slots=n_streams, budget_bytes=int(budget_bytes), max_W=max_wh[0], max_H=max_wh[1])
+                              n_slots=n_streams, budget_bytes=int(budget_bytes), max_W=max_wh[0], max_H=max_wh[1],
+                              image_in_place=int(bool(image_in_place)))
         self.n_streams = n_streams
         self.fused = fused  # None: fused wherever hog_cell_hist_fused supports the parameters
         self._w = _weights_host(w, w_dtype)

@@ -114,7 +114,8 @@ def test_server_argument_errors_need_no_gpu(fh):
     assert L.hog_server_create(ctypes.byref(fh.HogServerConfig(**good)), None, ctypes.byref(h)) == ARG
     for bad in (dict(n_bins=0), dict(stride=3), dict(cells_x=0), dict(w_dtype=fh.HOG_U8), dict(fused=2),
                 dict(ii_dtype=fh.HOG_F32), dict(n_slots=0), dict(n_slots=65), dict(budget_bytes=0),
-                dict(max_W=0), dict(thr=float("nan")), dict(bias=float("inf"))):
+                dict(max_W=0), dict(thr=float("nan")), dict(bias=float("inf")), dict(image_in_place=2),
+                dict(image_in_place=-1)):
         cfg = fh.HogServerConfig(**{**good, **bad})
         assert L.hog_server_create(ctypes.byref(cfg), w, ctypes.byref(h)) == ARG, bad
     cfg = fh.HogServerConfig(**{**good, "fused": 1, "n_bins": 9})  # the fused call takes N_b 8 or 16

@@ -146,3 +146,33 @@ def test_oversize_request_is_refused():
         srv.try_submit(Request(1, img))
     assert srv.idle()
     srv.close()
+
+
+@pytest.mark.parametrize("fused", [True, False])
+def test_images_read_in_place(fused):
+    """image_in_place: page-locked request images are read in place by the
+    first kernel (no copy is enqueued), pageable ones are still copied in;
+    every request's list equals the copying server's, with the dispatcher
+    thread and without it."""
+    import paper_1703_06256_gb300 as fh
+    from paper_1703_06256_gb300.serve import HogServer, Request
+
+    rng = wl.rng_for(4)
+    w = wl.weights_f32(8, rng)
+    images = _images(rng)
+    mixed = [torch.from_numpy(np.ascontiguousarray(im)).pin_memory() if i % 2 == 0 else im
+             for i, im in enumerate(images)]
+    kw = dict(w_dtype=fh.HOG_F32, budget_bytes=96 << 20, n_streams=4, fused=fused, max_wh=(1280, 1000))
+    ref = HogServer(w, 0.0, 0.5, **kw)
+    want = {r.rid: r for r in ref.serve([Request(i, im, 0.0) for i, im in enumerate(images)])}
+    ref.close()
+    srv = HogServer(w, 0.0, 0.5, image_in_place=True, **kw)
+    got_sync = srv.serve([Request(i, im, 0.0) for i, im in enumerate(mixed)])
+    got_native, _ = srv.serve_native([Request(i, im, 0.0005 * i) for i, im in enumerate(mixed)])
+    for got in (got_sync, got_native):
+        assert sorted(r.rid for r in got) == list(range(len(images)))
+        for r in got:
+            a = want[r.rid]
+            assert r.count == a.count
+            assert np.array_equal(r.detections, a.detections)
+    srv.close()
