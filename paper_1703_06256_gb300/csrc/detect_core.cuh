@@ -3,6 +3,8 @@
 // (detect.cu) and the batch kernels (detect_batch.cu).
 #pragma once
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace fasthog {
@@ -59,7 +61,27 @@ __device__ __forceinline__ int tile_count(const T* __restrict__ scores, long n, 
 template <typename T>
 __device__ __forceinline__ unsigned tile_load(const T* __restrict__ scores, long n, int tile, float thr_f, int thr_i,
                                               T (&v)[kPer]) {
+    static_assert(sizeof(T) == 4 && kPer == 8, "two 16-byte loads per thread");
     const long base = (long)tile * kTile + (long)threadIdx.x * kPer;
+    if (base + kPer <= n && (reinterpret_cast<uintptr_t>(scores + base) & 15) == 0) {
+        // the thread's 8 scores as two 16-byte loads (a warp reads 1 KB in one go)
+        const uint4 a = __ldg(reinterpret_cast<const uint4*>(scores + base));
+        const uint4 b = __ldg(reinterpret_cast<const uint4*>(scores + base) + 1);
+        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int e = 0; e < kPer; ++e) {
+            if constexpr (std::is_same<T, float>::value) {
+                v[e] = __uint_as_float(w[e]);
+            } else {
+                v[e] = (T)w[e];
+            }
+        }
+        unsigned flags = 0;
+#pragma unroll
+        for (int e = 0; e < kPer; ++e)
+            if (pass<T>(v[e], thr_f, thr_i)) flags |= 1u << e;
+        return flags;
+    }
     unsigned flags = 0;
 #pragma unroll
     for (int e = 0; e < kPer; ++e) {
@@ -104,7 +126,8 @@ __device__ __forceinline__ void tile_stage(const T (&v)[kPer], unsigned flags, i
     for (int e = 0; e < kPer; ++e) {
         if (flags & (1u << e)) {
             const long i = base + e;
-            const int py = (int)(i / nx), px = (int)(i - (long)py * nx);
+            // a map holds fewer than 2^31 scores (every caller checks the size), so 32-bit division
+            const int py = (int)((uint32_t)i / (uint32_t)nx), px = (int)i - py * nx;
             uint32_t* d = stage + loc * kDetWords;
             d[0] = (uint32_t)(px * stride);
             d[1] = (uint32_t)(py * stride);
