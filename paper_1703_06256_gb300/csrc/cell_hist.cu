@@ -151,6 +151,40 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     }
 }
 
+// One cell's NB counts as OutT at `out`: 16-byte stores when the map is 16-byte
+// aligned (a cell is 16 or 32 bytes of bf16, 32 or 64 of 4-byte counts), else
+// one store per count.
+template <typename OutT, int NB>
+__device__ __forceinline__ void write_cell(OutT* __restrict__ out, const uint32_t (&val)[NB], bool vec) {
+    if (vec) {
+        if constexpr (sizeof(OutT) == 2) {
+#pragma unroll
+            for (int k = 0; k < NB / 8; ++k) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    w[e] = (uint32_t)count_as<OutT>(val[8 * k + 2 * e]) |
+                           ((uint32_t)count_as<OutT>(val[8 * k + 2 * e + 1]) << 16);
+                reinterpret_cast<uint4*>(out)[k] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NB / 4; ++k) {
+                uint32_t w[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const OutT o = count_as<OutT>(val[4 * k + e]);
+                    w[e] = *reinterpret_cast<const uint32_t*>(&o);
+                }
+                reinterpret_cast<uint4*>(out)[k] = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int b = 0; b < NB; ++b) out[b] = count_as<OutT>(val[b]);
+    }
+}
+
 // Persistent, double-buffered form of the streaming kernel, for tiles whose
 // (TJ + r) x N_b sample lines fit one batch of loads per warp (kWarps x
 // kLines): a CTA walks tiles with the grid's stride, and while it forms the
@@ -162,7 +196,7 @@ constexpr int kPipeLines = 8;  // lines per warp and tile
 template <typename InT, typename OutT, int NB>
 __global__ void __launch_bounds__(kStreamThreads, 4)
     cell_hist_pipe_kernel(const InT* __restrict__ ii, int W, int H, int s, int r, int ncx, int ncy, int TJ, int n_tx,
-                          int n_tiles, OutT* __restrict__ cells) {
+                          int n_tiles, OutT* __restrict__ cells, bool vec_out) {
     extern __shared__ uint32_t S[];  // 2 x [TJ + r][kTI + r][NB + 1]
     pdl_wait();
     pdl_trigger();
@@ -173,9 +207,7 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
     const size_t plane = (size_t)W * H;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t v[kPipeLines][kPerLane];
-    // each thread forms the cells of bin b_out in kParts columns, kStreamThreads / NB apart
-    constexpr int kColStep = kStreamThreads / NB, kParts = kTI / kColStep;
-    static_assert((NB & (NB - 1)) == 0 && kParts * kColStep == kTI, "the column split must cover the tile");
+    static_assert((NB & (NB - 1)) == 0 && NB % 8 == 0, "8 or 16 bins: whole 16-byte stores per cell");
     // loads of tile t's samples: warp w takes lines w * kPipeLines .. + kPipeLines - 1,
     // lane l the samples l, l + 32, l + 64 of each line
     auto issue = [&](int t) {
@@ -213,8 +245,6 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
             }
         }
     };
-    // this thread's cells: bin b_out, columns ci_out + h * kColStep of every cell row
-    const int b_out = threadIdx.x & (NB - 1), ci_out = threadIdx.x / NB;
     int t = blockIdx.x;
     if (t >= n_tiles) return;
     issue(t);
@@ -226,21 +256,26 @@ __global__ void __launch_bounds__(kStreamThreads, 4)
         if (tn < n_tiles) issue(tn);
         const uint32_t* B = S + cur * bufw;
         const int i0 = (t % n_tx) * kTI, j0 = (t / n_tx) * TJ;
+        // one cell (all NB bins) per thread and step, cells of the tile in row-major order: a lane's
+        // samples are NB + 1 words from its neighbour's (no bank conflicts), and its cell's counts
+        // leave in 16-byte stores next to its neighbour's
+        const int rstep = cols * (NB + 1);
+        for (int cell = threadIdx.x; cell < TJ * kTI; cell += kStreamThreads) {
+            const int ci = cell % kTI, cj = cell / kTI;
+            const int i = i0 + ci, j = j0 + cj;
+            if (i >= ncx || j >= ncy) continue;
+            const uint32_t* top = B + (size_t)cj * rstep + (size_t)ci * (NB + 1);  // sample (cj, ci), bin 0
+            uint32_t val[NB];
 #pragma unroll
-        for (int h = 0; h < kParts; ++h) {
-            const int ci = ci_out + h * kColStep, i = i0 + ci;
-            if (i >= ncx) continue;
-            // samples (cj, ci), (cj, ci + r), (cj + r, ci), (cj + r, ci + r) of bin b_out
-            const uint32_t* top = B + (size_t)ci * (NB + 1) + b_out;
-            const int rstep = cols * (NB + 1);
-            OutT* out = cells + ((size_t)j0 * ncx + i) * NB + b_out;
-            for (int cj = 0; cj < TJ && j0 + cj < ncy; ++cj, top += rstep, out += (size_t)ncx * NB) {
-                const uint32_t d = top[0], bb = top[r * (NB + 1)];
-                const uint32_t c = top[r * rstep], a = top[r * rstep + r * (NB + 1)];
-                uint32_t val = (a + d) - (bb + c);
-                if (sizeof(InT) == 2) val &= 0xFFFFu;
-                *out = count_as<OutT>(val);
+            for (int b = 0; b < NB; ++b) {
+                // samples (cj, ci), (cj, ci + r), (cj + r, ci), (cj + r, ci + r)
+                const uint32_t d = top[b], bb = top[r * (NB + 1) + b];
+                const uint32_t c = top[r * rstep + b], a = top[r * rstep + r * (NB + 1) + b];
+                uint32_t v = (a + d) - (bb + c);
+                if (sizeof(InT) == 2) v &= 0xFFFFu;
+                val[b] = v;
             }
+            write_cell<OutT, NB>(cells + ((size_t)j * ncx + i) * NB, val, vec_out);
         }
         // the other buffer was last read before the previous barrier
         if (tn < n_tiles) park(S + (cur ^ 1) * bufw);
@@ -269,8 +304,9 @@ hog_status launch_stream(const void* ii, int W, int H, int stride, int r, int nc
         const int n_tx = ceil_div(ncx, kTI);
         const int n_tiles = n_tx * ceil_div(ncy, TJ);
         const int grid = n_tiles < 4 * sm_count() ? n_tiles : 4 * sm_count();
+        const bool vec_out = reinterpret_cast<uintptr_t>(cells) % 16 == 0;
         return launch_pdl(kern, dim3(grid), dim3(kStreamThreads), smem, st, static_cast<const InT*>(ii), W, H, stride,
-                          r, ncx, ncy, TJ, n_tx, n_tiles, static_cast<OutT*>(cells));
+                          r, ncx, ncy, TJ, n_tx, n_tiles, static_cast<OutT*>(cells), vec_out);
     }
     const size_t smem = sizeof(uint32_t) * (size_t)(TJ + r) * (kTI + r) * (NB + 1);
     auto kern = cell_hist_stream_kernel<InT, OutT, NB>;
