@@ -5,6 +5,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "ptx.cuh"
 
 namespace fasthog {
 
@@ -17,6 +18,21 @@ __device__ __forceinline__ uint32_t row_word(const uint8_t* __restrict__ row, lo
     for (int b = 0; b < 4; ++b)
         if (off + b >= 0 && off + b < row_bytes) w |= (uint32_t)__ldg(row + off + b) << (8 * b);
     return w;
+}
+
+// Fetch the whole table (511 rows of kLutPitch bytes) into L2, one slice per
+// CTA of the grid, issued by thread 0 at kernel start.  After other work has
+// evicted it, the first lookups would otherwise each wait for DRAM once the
+// gradients are known; the prefetch overlaps that with the image loads.
+// The table is 16-byte aligned and its size a multiple of 16.
+__device__ __forceinline__ void prefetch_table_l2(const uint8_t* __restrict__ lut) {
+    if (threadIdx.x != 0) return;
+    constexpr uint32_t kUnits = (uint32_t)kLutSide * kLutPitch / 16;
+    const uint32_t per = (kUnits + gridDim.x - 1) / gridDim.x;
+    const uint32_t u0 = blockIdx.x * per;
+    if (u0 >= kUnits) return;
+    const uint32_t n = min(per, kUnits - u0);
+    ptx::bulk_prefetch_l2(lut + (size_t)u0 * 16, n * 16);
 }
 
 // Byte i of a little-endian word array, i a compile-time constant (one byte

@@ -17,7 +17,9 @@
 //
 // The table is read through the read-only cache by default: gradients of
 // natural images cluster near (0, 0), so the lines they touch stay in L1,
-// and one lookup is a multiply-add and a load.  On request (and when 4
+// and one lookup is a multiply-add and a load.  Each CTA first asks L2 for
+// its slice of the table, so that a table evicted by other work arrives
+// while the image loads are in flight.  On request (and when 4
 // divides N_b) the CTA instead stages one quadrant in shared memory -- the
 // full 511 x 511 table (255.5 KiB) does not fit:
 // (dx, dy) with dx in 1..255, dy in 0..255, 255 x 256 entries, 64 KiB.  A
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(kThreads, 3)
         }
     }
     bool lut_ready = !QUAD;
-    pdl_wait();  // the table copy above reads only the table, built before the path runs
+    if (!QUAD) prefetch_table_l2(lut);
+    pdl_wait();  // the table copy or prefetch above reads only the table, built before the path runs
     pdl_trigger();
 
     const int qpr = (W + 3) >> 2;  // quads per row

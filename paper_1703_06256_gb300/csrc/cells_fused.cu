@@ -258,7 +258,8 @@ __host__ __device__ inline int cells_alignment(const void* cells) {
 
 // The table: QUAD = true stages its quadrant in shared memory (one bulk
 // copy per CTA, quarter-turn lookups); QUAD = false reads the whole table
-// through the read-only cache and leaves the shared memory to the tile.
+// through the read-only cache (after an L2 prefetch of one slice per CTA)
+// and leaves the shared memory to the tile.
 template <bool QUAD, int NB, int S>
 __device__ __forceinline__ FusedSmem<NB, S>* fused_prologue(uint8_t* smem, const uint8_t* lut, uint64_t* bar,
                                                             unsigned int* status) {
@@ -266,6 +267,7 @@ __device__ __forceinline__ FusedSmem<NB, S>* fused_prologue(uint8_t* smem, const
         if (!stage_lut(smem, lut, bar, status)) return nullptr;
         return reinterpret_cast<FusedSmem<NB, S>*>(smem + kQuadBytes);
     } else {
+        prefetch_table_l2(lut);
         pdl_wait();
         pdl_trigger();
         return reinterpret_cast<FusedSmem<NB, S>*>(smem);

@@ -72,6 +72,12 @@ __device__ __forceinline__ void bulk_g2s(void* dst_smem, const void* src_gmem, u
         : "memory");
 }
 
+// Ask L2 to fetch `bytes` bytes at `src` (16-byte aligned address, bytes a
+// multiple of 16); no completion to wait on.
+__device__ __forceinline__ void bulk_prefetch_l2(const void* src_gmem, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
+}
+
 }  // namespace ptx
 
 // One second: the bound on every device-side wait in this library.
