@@ -422,7 +422,19 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 or 8 (2 and 4 cover up to 640 rows, 8 up to
  *                                 1280; the library's choice is 2 where every
  *                                 cluster fits the GPU at once, else 4)
- *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8
+ *   HOG_TUNE_BINMAP_CTAS_PER_SM   bin-map grid cap, CTAs per SM: 1..8 (the
+ *                                 grid-stride schedule)
+ *   HOG_TUNE_BINMAP_SCHEDULE      the bin map's schedule: 1 = a persistent grid
+ *                                 striding over quads of 4 pixels, each thread
+ *                                 loading its words straight from global memory;
+ *                                 2 = one CTA per tile of 128 pixels x 16 rows,
+ *                                 the tile's rows (and one above and below)
+ *                                 staged in shared memory by 16-byte copies
+ *                                 (images whose base address and pitch are
+ *                                 multiples of 16, read through the whole table;
+ *                                 others take 1).  The library's choice: 2 where
+ *                                 it applies and every tile's CTA is resident at
+ *                                 once, else 1
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
  *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 1, 2, 4, 8, 16,
  *                                 32 or 64 for the row-GEMM kernel (8 bins); the
@@ -470,7 +482,8 @@ typedef enum {
     HOG_TUNE_SLIDE_WINDOWS = 7,
     HOG_TUNE_INTEGRAL_PATH = 8,
     HOG_TUNE_INTEGRAL_WARP_ROWS = 9,
-    HOG_TUNE_KNOBS = 10
+    HOG_TUNE_BINMAP_SCHEDULE = 10,
+    HOG_TUNE_KNOBS = 11
 } hog_tune_knob;
 hog_status hog_tune_set(int knob, int value);
 int hog_tune_get(int knob);

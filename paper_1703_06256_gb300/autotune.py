@@ -24,13 +24,14 @@ import statistics
 
 from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_CELL_ROWS, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
                HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_INTEGRAL_PATH, HOG_TUNE_INTEGRAL_WARP_ROWS, HOG_TUNE_SCORE_PATH,
-               HOG_TUNE_SCORE_TC_ROWS,
+               HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_BINMAP_SCHEDULE,
                HOG_TUNE_SLIDE_WINDOWS, hog_tune_get, hog_tune_set)
 
 # knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
 KNOBS = {
     "integral_band_rows": (HOG_TUNE_INTEGRAL_BAND_ROWS, (0, 4, 8, 16, 32)),
     "binmap_ctas_per_sm": (HOG_TUNE_BINMAP_CTAS_PER_SM, (0, 1, 2, 4)),
+    "binmap_schedule": (HOG_TUNE_BINMAP_SCHEDULE, (0, 1, 2)),
     "fused_ctas_per_sm": (HOG_TUNE_FUSED_CTAS_PER_SM, (0, 1)),
     "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 2, 4, 8, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
@@ -42,7 +43,7 @@ KNOBS = {
 }
 # the knobs each path's launches read
 PATH_KNOBS = {
-    "separate": ("integral_path", "integral_warp_rows", "integral_band_rows", "binmap_ctas_per_sm", "cell_rows", "score_path",
+    "separate": ("integral_path", "integral_warp_rows", "integral_band_rows", "binmap_schedule", "binmap_ctas_per_sm", "cell_rows", "score_path",
                  "score_tc_rows", "slide_windows", "table"),
     "fused": ("fused_ctas_per_sm", "score_path", "score_tc_rows", "slide_windows", "table"),
 }

@@ -34,6 +34,22 @@
 //
 // The grid is persistent (a few CTAs per SM, grid-stride over quads) so
 // that each CTA stages the table once.
+//
+// Small images take a second schedule (bit-identical): one CTA per tile of
+// 128 pixels x 16 rows.  The CTA first copies the tile's rows and the rows
+// above and below it, with 16 bytes of halo on each side, into shared memory
+// by 16-byte asynchronous copies (bytes outside the image arrive as zeros,
+// like the guarded loads above), then warp w computes tile rows w and w + 8,
+// lane L the quad at column 4L, reading the same words from shared memory
+// (consecutive lanes read words 3 apart for RGB: no bank conflicts).  One
+// 16-byte copy per 16 bytes of a row replaces about three 4-byte loads per
+// quad, and every tile's copies are in flight at once; when all tiles are
+// resident in one wave that is shorter than the grid-stride schedule (at
+// 800 x 600 RGB: 266 tiles, 3.88 -> 3.41 us per call in a chain of calls).
+// With more tiles than resident CTAs the grid-stride schedule, whose threads
+// keep four quads of loads in flight while they compute, is faster.
+#include <atomic>
+
 #include "bin_core.cuh"
 #include "internal.cuh"
 #include "ptx.cuh"
@@ -146,6 +162,106 @@ __global__ void __launch_bounds__(kThreads, 3)
     }
 }
 
+// ---- staged schedule
+constexpr int kTileW = 128, kTileH = 16;  // pixels x rows per CTA; 8 warps x 2 rows
+template <int CH>
+struct StagedRow {
+    static constexpr int kBytes = CH * kTileW + 32;  // 16 bytes of halo on each side
+    static constexpr int kWords = kBytes / 4;
+    static constexpr int kChunks = kBytes / 16;
+};
+
+template <int CH>
+__global__ void __launch_bounds__(kThreads, 4)
+    bin_map_staged_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch,
+                          const uint8_t* __restrict__ lut, int nb, uint8_t* __restrict__ bins, bool word_stores) {
+    using R = StagedRow<CH>;
+    __shared__ __align__(16) uint32_t rows[(kTileH + 2) * R::kWords];
+    prefetch_table_l2(lut);
+    const int tiles_x = (W + kTileW - 1) / kTileW;
+    const int ty = blockIdx.x / tiles_x, tx = blockIdx.x - ty * tiles_x;
+    const int x0 = kTileW * tx, y0 = kTileH * ty;
+    const long row_bytes = (long)W * CH;
+    pdl_wait();  // the prefetch above reads only the table
+    pdl_trigger();
+    // staged row r holds image row y0 - 1 + r, bytes CH x0 - 16 .. CH (x0 + 128) + 15;
+    // the image base and pitch are multiples of 16, so is every chunk's address
+    for (int c = threadIdx.x; c < (kTileH + 2) * R::kChunks; c += kThreads) {
+        const int r = c / R::kChunks, j = c - r * R::kChunks;
+        const int y = y0 - 1 + r;
+        const long off = (long)CH * x0 - 16 + 16L * j;
+        const uint8_t* src = img;  // nothing is read when n = 0
+        int n = 0;
+        if (y >= 0 && y < H && off >= 0 && off < row_bytes) {
+            src = img + (size_t)y * pitch + off;
+            n = (int)(row_bytes - off < 16 ? row_bytes - off : 16);
+        }
+        ptx::cp_async16_zfill(rows + r * R::kWords + 4 * j, src, n);
+    }
+    ptx::cp_async_wait_all();
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int x = x0 + 4 * lane;
+#pragma unroll
+    for (int i = 0; i < kTileH / 8; ++i) {
+        const int r = warp + 8 * i, y = y0 + r;
+        if (y >= H || x >= W) continue;
+        uint32_t packed = 0xFFFFFFFFu;  // border rows hold no bins
+        if (y > 0 && y < H - 1) {
+            // the words load_quad would read: centre row from byte CH x - 4, the
+            // rows above and below from byte CH x
+            using Q = QuadWords<CH>;
+            Q q;
+            const uint32_t* mid = rows + (r + 1) * R::kWords + CH * lane;
+#pragma unroll
+            for (int k = 0; k < Q::NC; ++k) q.wc[k] = mid[3 + k];
+#pragma unroll
+            for (int k = 0; k < Q::NV; ++k) {
+                q.wu[k] = mid[4 + k - R::kWords];
+                q.wd[k] = mid[4 + k + R::kWords];
+            }
+            packed = bins_of_quad<CH, false>(q, x, W, nullptr, lut, nb, nb >> 2);
+        }
+        store_quad(bins, W, x, y, packed, word_stores);
+    }
+}
+
+// Resident CTAs of the staged kernel on the current device (cached per device).
+template <int CH>
+long staged_capacity() {
+    constexpr int kDevices = 64;
+    static std::atomic<int> per_sm[kDevices];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDevices) return 0;
+    int n = per_sm[dev].load(std::memory_order_relaxed);
+    if (n == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bin_map_staged_kernel<CH>, kThreads, 0) != cudaSuccess)
+            return 0;
+        per_sm[dev].store(n > 0 ? n : -1, std::memory_order_relaxed);
+    }
+    return n > 0 ? (long)n * sm_count() : 0;
+}
+
+template <int CH>
+bool use_staged(const uint8_t* img, int W, int H, size_t pitch) {
+    const int sched = tune_get(HOG_TUNE_BINMAP_SCHEDULE);
+    if (sched == 1) return false;
+    if (reinterpret_cast<uintptr_t>(img) % 16 != 0 || pitch % 16 != 0) return false;
+    const long tiles = (long)((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+    if (tiles > 0x7FFFFFFFL) return false;
+    if (sched == 2) return true;
+    return tiles <= staged_capacity<CH>();
+}
+
+template <int CH>
+hog_status launch_staged(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int nb, uint8_t* bins,
+                         cudaStream_t st) {
+    const long tiles = (long)((W + kTileW - 1) / kTileW) * ((H + kTileH - 1) / kTileH);
+    const bool word_stores = (reinterpret_cast<uintptr_t>(bins) % 4 == 0) && (W % 4 == 0);
+    return launch_pdl(bin_map_staged_kernel<CH>, dim3((unsigned)tiles), dim3(kThreads), 0, st, img, W, H, pitch, lut,
+                      nb, bins, word_stores);
+}
+
 template <int CH, bool QUAD>
 hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int nb, uint8_t* bins,
                     unsigned int* status, cudaStream_t st) {
@@ -177,6 +293,10 @@ hog_status launch_bin_map(const uint8_t* img, int W, int H, int channels, size_t
     // the shared-memory quadrant needs 4 | N_b and is taken on request; the
     // whole table through the read-only cache is the default
     const bool quad = (n_bins % 4 == 0) && tune_get(HOG_TUNE_TABLE) == 1;
+    if (!quad) {
+        if (channels == 1 && use_staged<1>(img, W, H, pitch)) return launch_staged<1>(img, W, H, pitch, lut, n_bins, bins, st);
+        if (channels == 3 && use_staged<3>(img, W, H, pitch)) return launch_staged<3>(img, W, H, pitch, lut, n_bins, bins, st);
+    }
     if (channels == 1)
         return quad ? launch_t<1, true>(img, W, H, pitch, lut, n_bins, bins, status, st)
                     : launch_t<1, false>(img, W, H, pitch, lut, n_bins, bins, status, st);

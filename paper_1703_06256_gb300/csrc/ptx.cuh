@@ -78,6 +78,18 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void* src_gmem, uint32_t 
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src_gmem), "r"(bytes) : "memory");
 }
 
+// 16-byte asynchronous copy global -> shared memory of this thread's CTA
+// (both addresses 16-byte aligned); only the first `src_bytes` (0..16) bytes
+// are read, the rest of the 16 are written as zeros.
+__device__ __forceinline__ void cp_async16_zfill(void* dst_smem, const void* src_gmem, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst_smem)), "l"(src_gmem),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+// Wait for every cp.async copy this thread has issued.
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 }  // namespace ptx
 
 // One second: the bound on every device-side wait in this library.

@@ -82,6 +82,8 @@ def test_knob_calls(at):
     with pytest.raises(fh.HogError):
         fh.hog_tune_set(fh.HOG_TUNE_FUSED_CTAS_PER_SM, 3)
     with pytest.raises(fh.HogError):
+        fh.hog_tune_set(fh.HOG_TUNE_BINMAP_SCHEDULE, 3)
+    with pytest.raises(fh.HogError):
         fh.hog_tune_set(17, 1)
     assert fh.hog_tune_get(17) == -1
     at.reset()

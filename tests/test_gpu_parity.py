@@ -90,6 +90,32 @@ def test_bin_map_table_placements(fh, g, nb, ch, table):
         fh.hog_tune_set(fh.HOG_TUNE_TABLE, 0)
 
 
+SCHEDULE_SHAPES = SHAPES + [(16, 128), (18, 130), (31, 255), (600, 800), (17, 1023), (2, 5000), (300, 4),
+                            (1100, 200)]
+
+
+@pytest.mark.parametrize("schedule", [0, 1, 2])
+@pytest.mark.parametrize("nb", [8, 9])
+@pytest.mark.parametrize("ch", [1, 3])
+def test_bin_map_schedules(fh, g, nb, ch, schedule):
+    """Both bin-map schedules (1: grid-stride over quads, loads from global
+    memory; 2: 128 x 16 tiles staged in shared memory) and the library's
+    choice (0) equal the oracle's bin map.  Rows padded to a multiple of 16
+    bytes let schedule 2 apply (every tile edge: ragged widths and heights,
+    images narrower than a tile, one row, one column); unpadded rows and an
+    unaligned base fall back to schedule 1."""
+    fh.hog_tune_set(fh.HOG_TUNE_BINMAP_SCHEDULE, schedule)
+    try:
+        for i, (H, W) in enumerate(SCHEDULE_SHAPES):
+            img = rand_img(H, W, ch, 900 * nb + 10 * ch + i)
+            ref = oracle.bin_map(img, nb)
+            pad = (-W * ch) % 16
+            assert np.array_equal(g.gpu_bins(img, nb, pitch_pad=pad), ref), (H, W, "padded")
+            assert np.array_equal(g.gpu_bins(img, nb, pitch_pad=pad + 16, offset=3), ref), (H, W, "offset")
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_BINMAP_SCHEDULE, 0)
+
+
 @pytest.mark.parametrize("ch", [1, 3])
 def test_bin_map_pitch_and_alignment(fh, g, ch):
     img = rand_img(45, 203, ch, 5)
