@@ -187,6 +187,26 @@ def test_integral_band_heights(fh, g, path, h):
         fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
 
 
+@pytest.mark.parametrize("ii_dtype", ["i32", "u16"])
+def test_integral_three_launches_large(fh, g, ii_dtype):
+    """Three launches (the library's choice above 640 rows) at 1920x1080 and
+    3840x2160, 8 bins: 2160 rows of tiles with every group whole, and
+    1000x1000 with a partial last group; int32 and uint16 planes, against
+    the oracle."""
+    fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 1)
+    try:
+        for i, (H, W) in enumerate([(1080, 1920), (2160, 3840), (1000, 1000)]):
+            bins = oracle_bins(H, W, 8, 700 + i, p_none=0.2)
+            ref = oracle.integral(bins, 8)
+            if ii_dtype == "i32":
+                assert np.array_equal(g.gpu_integral(bins, 8), ref), (H, W)
+            else:
+                out = g.gpu_integral(bins, 8, fh.HOG_U16)
+                assert np.array_equal(out, (ref & 0xFFFF).astype(np.uint16)), (H, W)
+    finally:
+        fh.hog_tune_set(fh.HOG_TUNE_INTEGRAL_PATH, 0)
+
+
 def test_integral_single_pass_many_tiles(fh, g):
     """The single pass forced onto large maps, where a tile sums the
     aggregates of up to 134 tiles above it and 29 to its left: 1920x1080 and
