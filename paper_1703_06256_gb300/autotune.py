@@ -24,7 +24,7 @@ import statistics
 
 from . import (HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_CELL_ROWS, HOG_TUNE_FUSED_CTAS_PER_SM, HOG_TUNE_TABLE,
                HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_INTEGRAL_PATH, HOG_TUNE_INTEGRAL_WARP_ROWS, HOG_TUNE_SCORE_PATH,
-               HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_BINMAP_SCHEDULE,
+               HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_BINMAP_SCHEDULE, HOG_TUNE_FUSED_TILE_ROWS,
                HOG_TUNE_SLIDE_WINDOWS, hog_tune_get, hog_tune_set)
 
 # knob name -> (hog_tune_knob, candidate values; 0 = the library's own choice)
@@ -33,6 +33,7 @@ KNOBS = {
     "binmap_ctas_per_sm": (HOG_TUNE_BINMAP_CTAS_PER_SM, (0, 1, 2, 4)),
     "binmap_schedule": (HOG_TUNE_BINMAP_SCHEDULE, (0, 1, 2)),
     "fused_ctas_per_sm": (HOG_TUNE_FUSED_CTAS_PER_SM, (0, 1)),
+    "fused_tile_rows": (HOG_TUNE_FUSED_TILE_ROWS, (0, 8, 16)),
     "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 2, 4, 8, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),
@@ -45,7 +46,7 @@ KNOBS = {
 PATH_KNOBS = {
     "separate": ("integral_path", "integral_warp_rows", "integral_band_rows", "binmap_schedule", "binmap_ctas_per_sm", "cell_rows", "score_path",
                  "score_tc_rows", "slide_windows", "table"),
-    "fused": ("fused_ctas_per_sm", "score_path", "score_tc_rows", "slide_windows", "table"),
+    "fused": ("fused_ctas_per_sm", "fused_tile_rows", "score_path", "score_tc_rows", "slide_windows", "table"),
 }
 
 

@@ -116,13 +116,14 @@ __device__ __forceinline__ bool stage_lut(uint8_t* lutq, const uint8_t* __restri
 
 // One tile of cell origins [bx0, bx0 + BX) x [by0, by0 + BY) of one image:
 // steps 1-3 above.  Called by every thread of the CTA.
-template <int CH, int NB, int S, typename OutT, bool QUAD>
+template <int CH, int NB, int S, typename OutT, bool QUAD, int BYT>
 __device__ __forceinline__ void fused_tile(FusedSmem<NB, S>& sm, const uint8_t* lutq, const uint8_t* __restrict__ lut,
                                            const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                                            int r, int ncx, int ncy, OutT* __restrict__ cells, int out_align, int bx0,
                                            int by0) {
     using F = FusedSmem<NB, S>;
-    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    static_assert(BYT <= TileShape<S>::BY, "the shared-memory layout holds tiles of at most TileShape rows");
+    constexpr int BX = TileShape<S>::BX, BY = BYT;
     constexpr int QPR = S / 4;  // quads in one block row
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int bxn = BX + r - 1, byn = BY + r - 1;  // blocks of a tile
@@ -274,7 +275,7 @@ __device__ __forceinline__ FusedSmem<NB, S>* fused_prologue(uint8_t* smem, const
     }
 }
 
-template <int CH, int NB, int S, typename OutT, bool QUAD>
+template <int CH, int NB, int S, typename OutT, bool QUAD, int BYT>
 __global__ void __launch_bounds__(kThreads, 2)
     cells_fused_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                        const uint8_t* __restrict__ lut, int r, int ncx, int ncy, OutT* __restrict__ cells,
@@ -283,11 +284,11 @@ __global__ void __launch_bounds__(kThreads, 2)
     __shared__ __align__(8) uint64_t lut_bar;
     FusedSmem<NB, S>* sm = fused_prologue<QUAD, NB, S>(smem, lut, &lut_bar, status);
     if (sm == nullptr) return;
-    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    constexpr int BX = TileShape<S>::BX, BY = BYT;
     const int tiles_x = (ncx + BX - 1) / BX, tiles_y = (ncy + BY - 1) / BY;
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x)
-        fused_tile<CH, NB, S, OutT, QUAD>(*sm, smem, lut, img, W, H, pitch, aligned, r, ncx, ncy, cells, out_align,
-                                          (t % tiles_x) * BX, (t / tiles_x) * BY);
+        fused_tile<CH, NB, S, OutT, QUAD, BYT>(*sm, smem, lut, img, W, H, pitch, aligned, r, ncx, ncy, cells,
+                                               out_align, (t % tiles_x) * BX, (t / tiles_x) * BY);
 }
 
 // The same over every item of a batch plan: the persistent CTAs walk the
@@ -308,9 +309,9 @@ __global__ void __launch_bounds__(kThreads, 2)
         const uint8_t* img = item.img;
         OutT* cells = static_cast<OutT*>(item.cells);
         const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (item.pitch % 4 == 0);
-        fused_tile<CH, NB, S, OutT, QUAD>(*sm, smem, lut, img, item.W, item.H, item.pitch, aligned, r, it->ncx,
-                                          it->ncy, cells, cells_alignment(cells), (local % tx) * BX,
-                                          (local / tx) * BY);
+        fused_tile<CH, NB, S, OutT, QUAD, BY>(*sm, smem, lut, img, item.W, item.H, item.pitch, aligned, r, it->ncx,
+                                              it->ncy, cells, cells_alignment(cells), (local % tx) * BX,
+                                              (local / tx) * BY);
     }
 }
 
@@ -318,14 +319,14 @@ __global__ void __launch_bounds__(kThreads, 2)
 // through the read-only cache.
 inline bool use_quad_table() { return tune_get(HOG_TUNE_TABLE) == 1; }
 
-template <int CH, int NB, int S, typename OutT, bool QUAD>
+template <int CH, int NB, int S, typename OutT, bool QUAD, int BYT>
 hog_status launch_q(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
                     void* cells, unsigned int* status, cudaStream_t st) {
     const size_t smem = (QUAD ? kQuadBytes : 0) + sizeof(FusedSmem<NB, S>);
-    auto kern = cells_fused_kernel<CH, NB, S, OutT, QUAD>;
-    cudaError_t e = smem_at_least<cells_fused_kernel<CH, NB, S, OutT, QUAD>>(smem);
+    auto kern = cells_fused_kernel<CH, NB, S, OutT, QUAD, BYT>;
+    cudaError_t e = smem_at_least<cells_fused_kernel<CH, NB, S, OutT, QUAD, BYT>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    constexpr int BX = TileShape<S>::BX, BY = BYT;
     const int tiles = ((ncx + BX - 1) / BX) * ((ncy + BY - 1) / BY);
     const int per_sm = tune_get(HOG_TUNE_FUSED_CTAS_PER_SM);
     const int cap = (per_sm > 0 ? per_sm : 2) * sm_count();  // two CTAs of this size fit an SM
@@ -336,12 +337,30 @@ hog_status launch_q(const uint8_t* img, int W, int H, size_t pitch, const uint8_
                       static_cast<OutT*>(cells), out_align, status);
 }
 
+// Tile height in cell rows for one image: the tuned choice, else half the
+// usual height when tiles of the usual height would leave SMs without one.
+// A tile's CTA bins its pixels (and its halo's) one quad per thread in turn,
+// so on a small image twice as many tiles of half the height finish sooner;
+// the halo rows then add r - 1 block rows to 8 instead of to 16.
+template <int S>
+int fused_tile_rows(int ncx, int ncy) {
+    const int tuned = tune_get(HOG_TUNE_FUSED_TILE_ROWS);
+    if (tuned > 0) return tuned;
+    constexpr int BX = TileShape<S>::BX, BY = TileShape<S>::BY;
+    const long tiles = (long)((ncx + BX - 1) / BX) * ((ncy + BY - 1) / BY);
+    return tiles < sm_count() ? BY / 2 : BY;
+}
+
 template <int CH, int NB, int S, typename OutT>
 hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
                     void* cells, unsigned int* status, cudaStream_t st) {
+    static_assert(TileShape<S>::BY == 16, "tile heights 16 and 8");
+    const bool half = fused_tile_rows<S>(ncx, ncy) == 8;
     if (use_quad_table())
-        return launch_q<CH, NB, S, OutT, true>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
-    return launch_q<CH, NB, S, OutT, false>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+        return half ? launch_q<CH, NB, S, OutT, true, 8>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st)
+                    : launch_q<CH, NB, S, OutT, true, 16>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    return half ? launch_q<CH, NB, S, OutT, false, 8>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st)
+                : launch_q<CH, NB, S, OutT, false, 16>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
 }
 
 template <int CH, int NB, int S>

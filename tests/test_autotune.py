@@ -56,8 +56,8 @@ def test_cache_roundtrip(at, tmp_path):
 
     t1 = at.Autotuner(path, device_name="GB300-test")
     e = t1.tune({"W": 800, "H": 600, "path": "fused"}, measure, at.PATH_KNOBS["fused"])
-    assert e["config"] == {"fused_ctas_per_sm": 1, "score_path": 0, "score_tc_rows": 32, "slide_windows": 0,
-                           "table": 0}
+    assert e["config"] == {"fused_ctas_per_sm": 1, "fused_tile_rows": 0, "score_path": 0, "score_tc_rows": 32,
+                           "slide_windows": 0, "table": 0}
     assert e["default_ms"] == 2.0 and e["ms"] == 1.25
     k = len(n)
     t2 = at.Autotuner(path, device_name="GB300-test")
@@ -83,6 +83,8 @@ def test_knob_calls(at):
         fh.hog_tune_set(fh.HOG_TUNE_FUSED_CTAS_PER_SM, 3)
     with pytest.raises(fh.HogError):
         fh.hog_tune_set(fh.HOG_TUNE_BINMAP_SCHEDULE, 3)
+    with pytest.raises(fh.HogError):
+        fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 4)
     with pytest.raises(fh.HogError):
         fh.hog_tune_set(17, 1)
     assert fh.hog_tune_get(17) == -1

@@ -719,15 +719,19 @@ def test_score_bf16_error_against_f32_weights(fh, g):
 
 
 # ---------------------------------------------------------------- fused image -> cells
+@pytest.mark.parametrize("tile_rows", [0, 8, 16])
 @pytest.mark.parametrize("table", [1, 2])
 @pytest.mark.parametrize("ch", [1, 3])
 @pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (8, 8, 8), (16, 8, 4), (8, 16, 4), (8, 16, 8)])
-def test_cells_fused(fh, g, ch, nb, cell, stride, table):
+def test_cells_fused(fh, g, ch, nb, cell, stride, table, tile_rows):
     """hog_cell_hist_fused equals the oracle's Eq. 6 cell map of the oracle's
     bins, bit for bit, on images spanning several tiles with ragged edges,
-    with the table staged in shared memory (1) or read through the cache (2)."""
+    with the table staged in shared memory (1) or read through the cache (2),
+    in tiles of 8 or 16 cell rows (HOG_TUNE_FUSED_TILE_ROWS; 0: the library's
+    choice)."""
     fh.hog_tune_set(fh.HOG_TUNE_TABLE, table)
-    for i, (H, W) in enumerate([(77, 300), (240, 320), (131, 517), (16, 16)]):
+    fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, tile_rows)
+    for i, (H, W) in enumerate([(77, 300), (240, 320), (131, 517), (16, 16), (600, 800)]):
         img = rand_img(H, W, ch, 1000 + 10 * nb + i)
         ref = oracle.cell_hist_ii(oracle.integral(oracle.bin_map(img, nb), nb), nb, cell, stride)
         ncy, ncx = ref.shape[:2]
@@ -739,14 +743,17 @@ def test_cells_fused(fh, g, ch, nb, cell, stride, table):
             got = out.float().cpu().numpy()[: ncx * ncy * nb].reshape(ncy, ncx, nb)
             assert np.array_equal(got, ref), (H, W, cd)
     fh.hog_tune_set(fh.HOG_TUNE_TABLE, 0)
+    fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 0)
 
 
+@pytest.mark.parametrize("tile_rows", [8, 16])
 @pytest.mark.parametrize("cell,stride", [(16, 4), (32, 8)])
-def test_cells_fused_single_bin_extremes(fh, g, cell, stride):
+def test_cells_fused_single_bin_extremes(fh, g, cell, stride, tile_rows):
     """A diagonal ramp puts every interior pixel in one bin, so the tile-local
-    corner sums reach their largest values (r = 4, the largest tiles); the
-    counts must still be exact, written at 2-, 4- and 16-byte aligned
-    addresses."""
+    corner sums reach their largest values (r = 4, tiles of 16 rows the
+    largest); the counts must still be exact, written at 2-, 4- and 16-byte
+    aligned addresses."""
+    fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, tile_rows)
     H, W = 300, 700
     yy, xx = np.mgrid[0:H, 0:W]
     img = ((xx + 2 * yy) % 256).astype(np.uint8)  # (dx, dy) = (2, 4) except at the wrap
@@ -765,6 +772,7 @@ def test_cells_fused_single_bin_extremes(fh, g, cell, stride):
             host = buf.float().cpu().numpy()
             assert np.array_equal(host[sh: sh + n].reshape(ncy, ncx, 8), ref), (cd, sh)
             assert np.all(host[:sh] == -1) and np.all(host[sh + n:] == -1)
+    fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 0)
 
 
 def test_pipeline_fused_config1(fh, g):
