@@ -70,12 +70,16 @@ struct SoftTile {
     static constexpr int BYB = BY + kMaxR - 1;
 };
 
-template <int CH, int S, typename OutT>
+// BYT: cell rows per tile (16, or 8 on small images; the shared memory is
+// laid out for 16).
+template <int CH, int S, typename OutT, int BYT>
 __global__ void __launch_bounds__(kThreads, 2)
     cells_soft_kernel(const uint8_t* __restrict__ img, int W, int H, size_t pitch, bool aligned,
                       const uint16_t* __restrict__ lut, int nb, int q, int r, int ncx, int ncy,
                       OutT* __restrict__ cells) {
     using T = SoftTile<S>;
+    static_assert(BYT <= T::BY, "the shared-memory layout holds tiles of at most 16 rows");
+    constexpr int BY = BYT;
     constexpr int QPR = S / 4;
     extern __shared__ __align__(16) uint32_t smem_u[];
     uint32_t* bh = smem_u;                              // [BYB][BXB][nb] block votes
@@ -83,15 +87,15 @@ __global__ void __launch_bounds__(kThreads, 2)
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     pdl_wait();
     pdl_trigger();
-    const int tiles_x = (ncx + T::BX - 1) / T::BX, tiles_y = (ncy + T::BY - 1) / T::BY;
-    const int bxn = T::BX + r - 1, byn = T::BY + r - 1;
+    const int tiles_x = (ncx + T::BX - 1) / T::BX, tiles_y = (ncy + BY - 1) / BY;
+    const int bxn = T::BX + r - 1, byn = BY + r - 1;
     const long row_bytes = (long)W * CH;
     const int row_tasks = bxn * QPR;
     const int n_tasks = byn * S * row_tasks;
     auto BH = [&](int j, int i) { return bh + ((size_t)j * T::BXB + i) * nb; };
     auto G = [&](int j, int i) { return g + ((size_t)j * (T::BXB + 1) + i) * nb; };
     for (int t = blockIdx.x; t < tiles_x * tiles_y; t += gridDim.x) {
-        const int bx0 = (t % tiles_x) * T::BX, by0 = (t / tiles_x) * T::BY;
+        const int bx0 = (t % tiles_x) * T::BX, by0 = (t / tiles_x) * BY;
         __syncthreads();  // the previous tile's reads are done
         for (int k = tid; k < byn * T::BXB * nb; k += kThreads) bh[k] = 0;
         __syncthreads();
@@ -146,7 +150,7 @@ __global__ void __launch_bounds__(kThreads, 2)
         }
         __syncthreads();
         // 3. cells by Eq. 6 on the corner integral image
-        if (tid < T::BX * T::BY) {
+        if (tid < T::BX * BY) {
             const int ci = tid % T::BX, cj = tid / T::BX;
             const int i = bx0 + ci, j = by0 + cj;
             if (i < ncx && j < ncy) {
@@ -158,20 +162,33 @@ __global__ void __launch_bounds__(kThreads, 2)
     }
 }
 
-template <int CH, int S, typename OutT>
-hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint16_t* lut, int nb, int r, int ncx,
+template <int CH, int S, typename OutT, int BYT>
+hog_status launch_b(const uint8_t* img, int W, int H, size_t pitch, const uint16_t* lut, int nb, int r, int ncx,
                     int ncy, void* cells, cudaStream_t st) {
     using T = SoftTile<S>;
     const size_t smem = sizeof(uint32_t) * ((size_t)T::BYB * T::BXB + (size_t)(T::BYB + 1) * (T::BXB + 1)) * kMaxNb;
-    auto kern = cells_soft_kernel<CH, S, OutT>;
-    cudaError_t e = smem_at_least<cells_soft_kernel<CH, S, OutT>>(smem);
+    auto kern = cells_soft_kernel<CH, S, OutT, BYT>;
+    cudaError_t e = smem_at_least<cells_soft_kernel<CH, S, OutT, BYT>>(smem);
     if (e != cudaSuccess) return cuda_fail(e);
-    const int tiles = ((ncx + T::BX - 1) / T::BX) * ((ncy + T::BY - 1) / T::BY);
+    const int tiles = ((ncx + T::BX - 1) / T::BX) * ((ncy + BYT - 1) / BYT);
     const int cap = 2 * sm_count();
     const int grid = tiles < cap ? tiles : cap;
     const bool aligned = (reinterpret_cast<uintptr_t>(img) % 4 == 0) && (pitch % 4 == 0);
     return launch_pdl(kern, dim3(grid), dim3(kThreads), smem, st, img, W, H, pitch, aligned, lut, nb, HOG_SOFT_Q, r,
                       ncx, ncy, static_cast<OutT*>(cells));
+}
+
+// Tile height: the tuned choice (HOG_TUNE_FUSED_TILE_ROWS), else 8 cell rows
+// where tiles of 16 would leave SMs without a tile (as for the fused cells).
+template <int CH, int S, typename OutT>
+hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint16_t* lut, int nb, int r, int ncx,
+                    int ncy, void* cells, cudaStream_t st) {
+    using T = SoftTile<S>;
+    const int tuned = tune_get(HOG_TUNE_FUSED_TILE_ROWS);
+    const long tiles16 = (long)((ncx + T::BX - 1) / T::BX) * ((ncy + T::BY - 1) / T::BY);
+    const bool half = tuned > 0 ? tuned == 8 : tiles16 < sm_count();
+    return half ? launch_b<CH, S, OutT, 8>(img, W, H, pitch, lut, nb, r, ncx, ncy, cells, st)
+                : launch_b<CH, S, OutT, 16>(img, W, H, pitch, lut, nb, r, ncx, ncy, cells, st);
 }
 
 template <int CH, int S>

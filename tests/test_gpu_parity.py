@@ -646,14 +646,17 @@ def test_soft_lut_exhaustive(fh, g, nb):
     assert np.array_equal(tab[:, :511], ref)
 
 
+@pytest.mark.parametrize("tile_rows", [0, 8, 16])
 @pytest.mark.parametrize("ch", [1, 3])
 @pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (8, 8, 8), (16, 8, 4), (9, 16, 4), (8, 32, 8)])
-def test_cells_soft(fh, g, ch, nb, cell, stride):
+def test_cells_soft(fh, g, ch, nb, cell, stride, tile_rows):
     """Soft-vote cells from the image in one kernel equal the oracle's direct
     sums of per-pixel votes, on images spanning several tiles with ragged
-    edges; the window score over them is within the FP32 bound."""
+    edges, in tiles of 8 or 16 cell rows (HOG_TUNE_FUSED_TILE_ROWS; 0: the
+    library's choice); the window score over them is within the FP32 bound."""
     buf = torch.empty(fh.HOG_SOFT_LUT_BYTES // 2, dtype=torch.int16, device="cuda")
     fh.hog_build_soft_lut(nb, buf)
+    fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, tile_rows)
     for i, (H, W) in enumerate([(77, 300), (240, 330), (131, 517)]):
         img = rand_img(H, W, ch, 3000 + 10 * nb + i)
         ref = oracle.soft_cells(img, nb, cell, stride)
@@ -666,6 +669,7 @@ def test_cells_soft(fh, g, ch, nb, cell, stride):
             assert np.all(host[ncx * ncy * nb:] == -1)
             got = host[: ncx * ncy * nb].astype(np.int64).reshape(ncy, ncx, nb)
             assert np.array_equal(got, ref), (H, W, cd)
+    fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 0)
     if cell == 8 and stride == 4:
         rng = np.random.default_rng(nb)
         w = rng.normal(0, 0.001, 128 * nb).astype(np.float32)
