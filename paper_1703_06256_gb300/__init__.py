@@ -33,6 +33,7 @@ HOG_SOFT_LUT_BYTES = HOG_LUT_SIDE * HOG_LUT_PITCH * 2
 (HOG_TUNE_INTEGRAL_BAND_ROWS, HOG_TUNE_BINMAP_CTAS_PER_SM, HOG_TUNE_FUSED_CTAS_PER_SM,
  HOG_TUNE_SCORE_TC_ROWS, HOG_TUNE_TABLE, HOG_TUNE_CELL_ROWS, HOG_TUNE_SCORE_PATH, HOG_TUNE_SLIDE_WINDOWS,
  HOG_TUNE_INTEGRAL_PATH, HOG_TUNE_INTEGRAL_WARP_ROWS, HOG_TUNE_BINMAP_SCHEDULE, HOG_TUNE_FUSED_TILE_ROWS) = range(12)
+HOG_TUNE_KNOBS = 12
 
 TORCH_DTYPE = {HOG_U8: torch.uint8, HOG_I32: torch.int32, HOG_BF16: torch.bfloat16, HOG_F32: torch.float32,
                HOG_I8: torch.int8, HOG_U16: torch.uint16 if hasattr(torch, "uint16") else torch.int16}

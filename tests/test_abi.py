@@ -158,3 +158,33 @@ def test_batch_plan_on_the_host(fh):
     assert fh.hog_pyramid_bytes(640, 480, 3, 1) == 0
     assert L.hog_pyramid(None, 640, 480, 3, 1920, 3, 4096, None) == ARG
     assert L.hog_pyramid(4096, 640, 480, 3, 100, 3, 4096, None) == ARG  # pitch
+
+
+def header_enum(name):
+    """name -> value of the enumerators of the typedef'd enum `name` in include/*.h."""
+    src = "".join(open(h).read() for h in HEADERS)
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef\s+enum\s*\{(.*?)\}\s*" + name + r"\s*;", src, flags=re.S)
+    assert m, name
+    out = {}
+    for k, v in re.findall(r"(HOG_[A-Z0-9_]+)\s*=\s*(-?\d+)", m.group(1)):
+        out[k] = int(v)
+    return out
+
+
+def test_binding_constants_match_the_header(fh):
+    """The binding's knob numbers and the header's enum are one list: every
+    knob the header declares has the same number in Python, and the autotuner
+    only names knobs below HOG_TUNE_KNOBS, each once."""
+    knobs = header_enum("hog_tune_knob")
+    assert knobs, "no knobs parsed"
+    for k, v in knobs.items():
+        assert getattr(fh, k) == v, k
+    n = knobs["HOG_TUNE_KNOBS"]
+    assert sorted(v for k, v in knobs.items() if k != "HOG_TUNE_KNOBS") == list(range(n))
+    from paper_1703_06256_gb300 import autotune
+
+    ids = [knob for knob, _ in autotune.KNOBS.values()]
+    assert len(ids) == len(set(ids)) and all(0 <= i < n for i in ids)
+    for names in autotune.PATH_KNOBS.values():
+        assert set(names) <= set(autotune.KNOBS)
