@@ -164,10 +164,11 @@ def header_enum(name):
     """name -> value of the enumerators of the typedef'd enum `name` in include/*.h."""
     src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    m = re.search(r"typedef\s+enum\s*\{(.*?)\}\s*" + name + r"\s*;", src, flags=re.S)
-    assert m, name
+    end = re.search(r"\}\s*" + name + r"\s*;", src)
+    assert end, name
+    body = src[src.rindex("typedef enum", 0, end.start()):end.start()]  # the last enum opened before it
     out = {}
-    for k, v in re.findall(r"(HOG_[A-Z0-9_]+)\s*=\s*(-?\d+)", m.group(1)):
+    for k, v in re.findall(r"(HOG_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
         out[k] = int(v)
     return out
 
