@@ -437,10 +437,11 @@ hog_status hog_detect_noalloc(const void* scores, int score_dtype, int nx, int n
  *                                 once, else 1
  *   HOG_TUNE_FUSED_CTAS_PER_SM    fused-cells grid cap, CTAs per SM: 1 or 2
  *   HOG_TUNE_FUSED_TILE_ROWS      cell rows per tile of hog_cell_hist_fused and
- *                                 hog_cell_hist_soft: 16 or 8 (the library's
+ *                                 hog_cell_hist_soft: 16, 8 or 4 (the library's
  *                                 choice: 8 where tiles of 16 rows would leave
- *                                 SMs without a tile, else 16; the batch call
- *                                 keeps 16)
+ *                                 SMs without a tile, else 16;
+ *                                 hog_cell_hist_soft takes 8 for 4; the batch
+ *                                 call keeps 16)
  *   HOG_TUNE_SCORE_TC_ROWS        output rows per tensor-core CTA: 1, 2, 4, 8, 16,
  *                                 32 or 64 for the row-GEMM kernel (8 bins); the
  *                                 banded kernel (16 bins) takes 16 or 32 and its

@@ -33,7 +33,7 @@ KNOBS = {
     "binmap_ctas_per_sm": (HOG_TUNE_BINMAP_CTAS_PER_SM, (0, 1, 2, 4)),
     "binmap_schedule": (HOG_TUNE_BINMAP_SCHEDULE, (0, 1, 2)),
     "fused_ctas_per_sm": (HOG_TUNE_FUSED_CTAS_PER_SM, (0, 1)),
-    "fused_tile_rows": (HOG_TUNE_FUSED_TILE_ROWS, (0, 8, 16)),
+    "fused_tile_rows": (HOG_TUNE_FUSED_TILE_ROWS, (0, 4, 8, 16)),
     "score_tc_rows": (HOG_TUNE_SCORE_TC_ROWS, (0, 2, 4, 8, 16, 32)),
     "table": (HOG_TUNE_TABLE, (0, 1, 2)),
     "cell_rows": (HOG_TUNE_CELL_ROWS, (0, 1, 4, 8, 16)),

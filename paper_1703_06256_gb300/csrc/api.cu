@@ -98,7 +98,7 @@ hog_status hog_tune_set(int knob, int value) {
         case HOG_TUNE_INTEGRAL_PATH: ok = ok || value == 1 || value == 2 || value == 3; break;
         case HOG_TUNE_INTEGRAL_WARP_ROWS: ok = ok || value == 2 || value == 4 || value == 8; break;
         case HOG_TUNE_BINMAP_SCHEDULE: ok = ok || value == 1 || value == 2; break;
-        case HOG_TUNE_FUSED_TILE_ROWS: ok = ok || value == 8 || value == 16; break;
+        case HOG_TUNE_FUSED_TILE_ROWS: ok = ok || value == 4 || value == 8 || value == 16; break;
         default: return HOG_ERR_ARG;
     }
     if (!ok) return HOG_ERR_ARG;

@@ -337,11 +337,13 @@ hog_status launch_q(const uint8_t* img, int W, int H, size_t pitch, const uint8_
                       static_cast<OutT*>(cells), out_align, status);
 }
 
-// Tile height in cell rows for one image: the tuned choice, else half the
-// usual height when tiles of the usual height would leave SMs without one.
-// A tile's CTA bins its pixels (and its halo's) one quad per thread in turn,
-// so on a small image twice as many tiles of half the height finish sooner;
-// the halo rows then add r - 1 block rows to 8 instead of to 16.
+// Tile height in cell rows for one image: the tuned choice (16, 8 or 4), else
+// 8 where tiles of 16 rows would leave SMs without one, else 16.  A tile's
+// CTA bins its pixels (and its halo's) one quad per thread in turn, so on a
+// small image twice as many tiles of half the height finish sooner; the halo
+// then adds r - 1 block rows to 8 instead of to 16.  Rows of 4 were measured
+// too: slightly faster than 8 at 800 x 600 (27.8-28.3 against 28.5 us for the
+// fused step), 2 us slower at 640 x 480, so they are left to the tuner.
 template <int S>
 int fused_tile_rows(int ncx, int ncy) {
     const int tuned = tune_get(HOG_TUNE_FUSED_TILE_ROWS);
@@ -351,16 +353,22 @@ int fused_tile_rows(int ncx, int ncy) {
     return tiles < sm_count() ? BY / 2 : BY;
 }
 
+template <int CH, int NB, int S, typename OutT, bool QUAD>
+hog_status launch_h(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
+                    void* cells, unsigned int* status, cudaStream_t st) {
+    static_assert(TileShape<S>::BY == 16, "tile heights 16, 8 and 4");
+    const int rows = fused_tile_rows<S>(ncx, ncy);
+    if (rows == 4) return launch_q<CH, NB, S, OutT, QUAD, 4>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    if (rows == 8) return launch_q<CH, NB, S, OutT, QUAD, 8>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    return launch_q<CH, NB, S, OutT, QUAD, 16>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+}
+
 template <int CH, int NB, int S, typename OutT>
 hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint8_t* lut, int r, int ncx, int ncy,
                     void* cells, unsigned int* status, cudaStream_t st) {
-    static_assert(TileShape<S>::BY == 16, "tile heights 16 and 8");
-    const bool half = fused_tile_rows<S>(ncx, ncy) == 8;
     if (use_quad_table())
-        return half ? launch_q<CH, NB, S, OutT, true, 8>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st)
-                    : launch_q<CH, NB, S, OutT, true, 16>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
-    return half ? launch_q<CH, NB, S, OutT, false, 8>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st)
-                : launch_q<CH, NB, S, OutT, false, 16>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+        return launch_h<CH, NB, S, OutT, true>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
+    return launch_h<CH, NB, S, OutT, false>(img, W, H, pitch, lut, r, ncx, ncy, cells, status, st);
 }
 
 template <int CH, int NB, int S>

@@ -186,7 +186,7 @@ hog_status launch_t(const uint8_t* img, int W, int H, size_t pitch, const uint16
     using T = SoftTile<S>;
     const int tuned = tune_get(HOG_TUNE_FUSED_TILE_ROWS);
     const long tiles16 = (long)((ncx + T::BX - 1) / T::BX) * ((ncy + T::BY - 1) / T::BY);
-    const bool half = tuned > 0 ? tuned == 8 : tiles16 < sm_count();
+    const bool half = tuned > 0 ? tuned < 16 : tiles16 < sm_count();  // 8 rows also for a tuned 4
     return half ? launch_b<CH, S, OutT, 8>(img, W, H, pitch, lut, nb, r, ncx, ncy, cells, st)
                 : launch_b<CH, S, OutT, 16>(img, W, H, pitch, lut, nb, r, ncx, ncy, cells, st);
 }

@@ -84,7 +84,7 @@ def test_knob_calls(at):
     with pytest.raises(fh.HogError):
         fh.hog_tune_set(fh.HOG_TUNE_BINMAP_SCHEDULE, 3)
     with pytest.raises(fh.HogError):
-        fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 4)
+        fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 12)
     with pytest.raises(fh.HogError):
         fh.hog_tune_set(17, 1)
     assert fh.hog_tune_get(17) == -1

@@ -723,7 +723,7 @@ def test_score_bf16_error_against_f32_weights(fh, g):
 
 
 # ---------------------------------------------------------------- fused image -> cells
-@pytest.mark.parametrize("tile_rows", [0, 8, 16])
+@pytest.mark.parametrize("tile_rows", [0, 4, 8, 16])
 @pytest.mark.parametrize("table", [1, 2])
 @pytest.mark.parametrize("ch", [1, 3])
 @pytest.mark.parametrize("nb,cell,stride", [(8, 8, 4), (8, 8, 8), (16, 8, 4), (8, 16, 4), (8, 16, 8)])
@@ -731,8 +731,8 @@ def test_cells_fused(fh, g, ch, nb, cell, stride, table, tile_rows):
     """hog_cell_hist_fused equals the oracle's Eq. 6 cell map of the oracle's
     bins, bit for bit, on images spanning several tiles with ragged edges,
     with the table staged in shared memory (1) or read through the cache (2),
-    in tiles of 8 or 16 cell rows (HOG_TUNE_FUSED_TILE_ROWS; 0: the library's
-    choice)."""
+    in tiles of 4, 8 or 16 cell rows (HOG_TUNE_FUSED_TILE_ROWS; 0: the
+    library's choice)."""
     fh.hog_tune_set(fh.HOG_TUNE_TABLE, table)
     fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, tile_rows)
     for i, (H, W) in enumerate([(77, 300), (240, 320), (131, 517), (16, 16), (600, 800)]):
@@ -750,7 +750,7 @@ def test_cells_fused(fh, g, ch, nb, cell, stride, table, tile_rows):
     fh.hog_tune_set(fh.HOG_TUNE_FUSED_TILE_ROWS, 0)
 
 
-@pytest.mark.parametrize("tile_rows", [8, 16])
+@pytest.mark.parametrize("tile_rows", [4, 8, 16])
 @pytest.mark.parametrize("cell,stride", [(16, 4), (32, 8)])
 def test_cells_fused_single_bin_extremes(fh, g, cell, stride, tile_rows):
     """A diagonal ramp puts every interior pixel in one bin, so the tile-local
